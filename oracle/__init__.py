@@ -57,6 +57,8 @@ def lib():
             "orc_bspline": (ctypes.c_double, [ctypes.c_int, ctypes.c_double]),
             "orc_parzen": (ctypes.c_double, [ctypes.c_double]),
             "orc_parzen_dleft": (ctypes.c_double, [ctypes.c_double]),
+            "orc_parzen_dright": (ctypes.c_double, [ctypes.c_double]),
+            "orc_parzen_dkappa": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_int]),
             "orc_normalise": (ctypes.c_int, [_F, ctypes.c_int64, ctypes.c_double, _D]),
             "orc_n_ffd_nodes": (ctypes.c_int64, [_PP, ctypes.c_int]),
             "orc_n_sbins": (ctypes.c_int64, [_PP, ctypes.c_int]),
@@ -161,6 +163,15 @@ def parzen(t: float) -> float:
 
 def parzen_dleft(t: float) -> float:
     return lib().orc_parzen_dleft(t)
+
+
+def parzen_dright(t: float) -> float:
+    return lib().orc_parzen_dright(t)
+
+
+def parzen_dkappa(b: float, B: float, L: int) -> float:
+    """dh/dkappa at kappa = b - B inside the cell of B (Eqs. 19, 27)."""
+    return lib().orc_parzen_dkappa(b, B, L)
 
 
 def normalise(img: np.ndarray, L: float) -> np.ndarray:

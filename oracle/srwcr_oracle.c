@@ -21,8 +21,9 @@
  *    interpolation with clamp-to-border; its gradient is the analytic
  *    gradient of the interpolant, zero along an axis where T(x) left
  *    [0, N-1].  Cell [floor(y), floor(y)+1], and [N-2, N-1] at y = N-1.
- *  - Intensity bins a, b run over 0..L (Eq. 3).  The Parzen derivative is the
- *    left derivative of h (a right derivative with respect to B).
+ *  - Intensity bins a, b run over 0..L (Eq. 3).  The Parzen derivative in
+ *    Eqs. (19)/(27) is taken inside the cell [k, k+1] holding B,
+ *    k = min(floor(B), L-1) (see orc_parzen_dkappa).
  *  - A region whose p(r) is 0, or whose variance sigma_r^2 is at most 1e-9
  *    times its mean square intensity, is degenerate: it contributes nothing
  *    to the value or the gradient and is counted.
@@ -70,8 +71,7 @@ double orc_parzen(double t) {
   return 0.0;
 }
 
-/* Left derivative of Eq. (5), dh/dkappa taken from below.  Differentiating
- * h(b - B) from the right in B gives -orc_parzen_dleft(b - B). */
+/* Left derivative of Eq. (5), dh/dkappa taken from below. */
 double orc_parzen_dleft(double t) {
   if (t <= -1.0) return 0.0;
   if (t <= -0.5) return 3.6 * t + 3.7;   /* h = 1.8 t^2 + 3.7 t + 1.9 on (-1,-0.5] */
@@ -79,6 +79,27 @@ double orc_parzen_dleft(double t) {
   if (t <= 0.5) return -3.6 * t - 0.1;   /* h = -1.8 t^2 - 0.1 t + 1 on (0,0.5]   */
   if (t <= 1.0) return 3.6 * t - 3.7;    /* h = 1.8 t^2 - 3.7 t + 1.9 on (0.5,1]  */
   return 0.0;
+}
+
+/* Right derivative of Eq. (5), dh/dkappa taken from above. */
+double orc_parzen_dright(double t) {
+  if (t < -1.0) return 0.0;
+  if (t < -0.5) return 3.6 * t + 3.7;
+  if (t < 0.0) return -3.6 * t + 0.1;
+  if (t < 0.5) return -3.6 * t - 0.1;
+  if (t < 1.0) return 3.6 * t - 3.7;
+  return 0.0;
+}
+
+/* dh/dkappa at kappa = b - B, as it enters Eqs. (19)/(27).  h has kinks at
+ * integer kappa, so the derivative is taken inside the cell [k, k+1] that
+ * holds B, k = min(floor(B), L-1): from above in B (below in kappa) except
+ * at the top B = L, where the cell is [L-1, L] and the derivative is from
+ * below in B.  B outside [0, L] never occurs (warped values of an image in
+ * [0, L] stay in [0, L]). */
+double orc_parzen_dkappa(double b, double B, int L) {
+  if (B >= (double)L) return orc_parzen_dright(b - B);
+  return orc_parzen_dleft(b - B);
 }
 
 /* Sec. II (normalisation to [0, L_eps]): linear min-max map in FP64.
@@ -417,7 +438,7 @@ static double dD_dB(const orc_problem* P, const orc_tables* T, const int64_t xv[
       if (ha == 0.0) continue;
       double mua = T->mu_ra[r * nb + a];
       for (int b = 0; b < nb; ++b) {
-        double dh = orc_parzen_dleft((double)b - Bx);
+        double dh = orc_parzen_dkappa((double)b, Bx, nb - 1);
         if (dh == 0.0) continue;
         double bb = (double)b;
         double coef = (omc * (bb * bb - 2.0 * bb * mu) + 2.0 * bb * mua - bb * bb) / var;

@@ -376,3 +376,21 @@ def test_gradient_chain_rule_from_per_voxel_derivative(oracle_lib):
         field = (G * gradM[:, k]).reshape(prob.image_shape)
         gk = np.einsum("zyx,zc,yb,xa->cba", field, Bz, By, Bx)
         assert np.allclose(gk, g[k], atol=1e-14 * max(1, np.abs(g).max()) + 1e-16)
+
+
+def test_parzen_derivative_convention_is_one_sided_inside_the_cell(oracle_lib):
+    """dh/dkappa as used in Eq. (27): the moments m1(B) = sum_b b h(b-B) and
+    m2(B) = sum_b b^2 h(b-B) must be differentiated inside [0, L] -- from
+    above in B, and from below at the top bin B = L."""
+    L = 15
+    bins = np.arange(L + 1.0)
+    eps = 1e-7
+    for B in [0.0, 0.3, 0.5, 4.0, 7.25, 14.6, 14.999, 15.0]:
+        for p in (1, 2):
+            mom = lambda v: float((bins ** p * parzen_np(bins - v)).sum())
+            if B >= L:
+                num = (mom(B) - mom(B - eps)) / eps
+            else:
+                num = (mom(B + eps) - mom(B)) / eps
+            ana = -sum(b ** p * oracle.parzen_dkappa(b, B, L) for b in bins)
+            assert abs(num - ana) < 1e-5 * max(1.0, abs(ana)), (B, p, num, ana)
