@@ -1,0 +1,329 @@
+"""SRWCR value+gradient throughput on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config c2|c1|c3|c5] [--storage f32|bf16]
+
+A step is one full value+gradient pass (fused warp/statistics kernel,
+FP64 finalisation, adjoint) over the 256x256x96 CT-shaped pair (default),
+inputs resident in HBM.  The L2 is flushed (256 MB write) between steps,
+outside the timed events.  Under torchrun every rank runs its own replica
+(weak scaling, no collective on the data path); the timed region is
+bracketed by a barrier and synchronisation and the max over ranks is used.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (a slab of the volume).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+CONFIG_NAMES = {"c1": "c1_2d_128", "c2": "c2_ct_256x256x96", "c3": "c3_oct_160",
+                "c5": "c5_ct_512x512x300"}
+METRIC = "SRWCR value+grad Gvoxel/s & HBM-roofline % at 256²×96; batched vs plain pairs/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+KERNEL_SOURCES = ["paper_1804_05061_b300/csrc/kernels.cuh",
+                  "paper_1804_05061_b300/csrc/device_math.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names[1:], parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_cpu_baseline(pair, c):
+    """FP64 oracle value+gradient on the host cores: one full evaluation of
+    the same workload (single thread)."""
+    import oracle
+    prob = pair.prob
+    geo = oracle.Geometry.from_problem(prob)
+    A, M = oracle.prepare(pair.fixed, pair.moving, prob.n_bins, "f32")
+    t = time.perf_counter()
+    st = oracle.value(geo, A, M, c)
+    oracle.gradient(geo, A, M, c, st)
+    dt = time.perf_counter() - t
+    return {"value": prob.n_voxels / dt / 1e9, "unit": "Gvoxel/s", "cores": 1,
+            "kind": "oracle", "sample": f"one full value+gradient of {prob.dims} "
+            f"({prob.n_voxels} voxels), {dt:.1f} s"}
+
+
+def slab(pair, nz):
+    """Sub-volume (first nz slices) as a bounded sample of a 3-D workload."""
+    prob = pair.prob
+    if prob.ndim == 2:
+        return pair
+    p2 = synth.problem(3, (prob.dims[0], prob.dims[1], nz), prob.ffd_spacing,
+                       prob.sbin_intervals, prob.n_bins)
+    return synth.PairSpec(pair.name + f"_slab{nz}", p2, np.ascontiguousarray(pair.fixed[:nz]),
+                          np.ascontiguousarray(pair.moving[:nz]))
+
+
+def run_reference(args, pair, c_full):
+    import oracle
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    sample = slab(pair, 8)
+    prob = sample.prob
+    c = synth.coefficients(prob, 2001, 2.0)
+    geo = oracle.Geometry.from_problem(prob)
+    A, M = oracle.prepare(sample.fixed, sample.moving, prob.n_bins, args.storage)
+    for _ in range(args.warmup):
+        st = oracle.value(geo, A, M, c)
+        oracle.gradient(geo, A, M, c, st)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        st = oracle.value(geo, A, M, c)
+        oracle.gradient(geo, A, M, c, st)
+    dt = time.perf_counter() - t
+    v = prob.n_voxels * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gvoxel/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{pair.name} ({pair.prob.dims[0]}x{pair.prob.dims[1]}x"
+                       f"{pair.prob.dims[2]}, {pair.prob.n_bins} bins); reference steps run on "
+                       f"a {prob.dims[0]}x{prob.dims[1]}x{prob.dims[2]} slab",
+                       "storage": args.storage},
+            "cpu_baseline": {"value": v, "unit": "Gvoxel/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{prob.dims} slab of the workload, {args.steps} "
+                             "value+gradient evaluations"},
+            "e2e": {"value": v, "unit": "Gvoxel/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIG_NAMES))
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    pair = synth.make_pair(CONFIG_NAMES[args.config])
+    prob = pair.prob
+    c_np = synth.coefficients(prob, 2001, 2.0)
+    if args.impl == "reference":
+        run_reference(args, pair, c_np)
+        return
+
+    import torch
+    import paper_1804_05061_b300 as eng
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    e = eng.from_problem(prob, pair.fixed, pair.moving, storage=args.storage)
+    stream = e.stream
+    c = torch.from_numpy(c_np).to(dev)
+    g = torch.empty_like(c)
+    D = torch.empty((), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    for _ in range(args.warmup):
+        e.value_and_grad_async(c, D, g)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    e.profile_read(reset=True)
+    e.set_profiling(True)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        e.value_and_grad_async(c, D, g)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    e.set_profiling(False)
+    kms, kcnt, launches = e.profile_read(reset=True)
+    step_ms = sum(s.elapsed_time(t) for s, t in zip(starts, ends))
+    t_dev = step_ms / 1e3
+    if dist is not None:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    value = ws * prob.n_voxels * args.steps / t_dev / 1e9
+
+    # End to end through the host-buffer entry point: H2D c, compute, D2H g and D.
+    c_host = np.ascontiguousarray(c_np.ravel())
+    g_host = np.zeros_like(c_host)
+    for _ in range(2):
+        e.value_and_grad_host(c_host, g_host)
+    te = time.perf_counter()
+    n_e2e = max(3, min(args.steps, 20))
+    for _ in range(n_e2e):
+        e.value_and_grad_host(c_host, g_host)
+    te = time.perf_counter() - te
+    if dist is not None:
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+    e2e = {"value": ws * prob.n_voxels * n_e2e / te / 1e9, "unit": "Gvoxel/s",
+           "h2d_bytes_per_step": int(c_host.nbytes), "d2h_bytes_per_step": int(g_host.nbytes + 8),
+           "steps": n_e2e}
+
+    # Roofline of the dominant kernel (algorithmic bytes / CUDA-event time).
+    esz = 2 if args.storage == "bf16" else 4
+    lv = e.levels[0]
+    names = ["accumulate", "finalize", "adjoint"]
+    avg = {names[i]: (kms[i] / kcnt[i] if kcnt[i] else 0.0) for i in range(3)}
+    bytes_alg = {
+        "accumulate": 2 * esz * lv.n_voxels + 4 * lv.n_params + 16 * lv.n_regions * prob.n_bins,
+        "adjoint": 2 * esz * lv.n_voxels + 4 * lv.n_params * 2
+                   + 4 * lv.n_regions * (prob.n_bins + 2),
+    }
+    dom = max(("accumulate", "adjoint"), key=lambda k: avg[k])
+    peak, peak_kind = hbm_peak()
+    achieved = bytes_alg[dom] / (avg[dom] / 1e3) / 1e9 if avg[dom] > 0 else 0.0
+    traffic = None
+    prof_file = os.path.join(ROOT, "profiles", f"{dom}_{args.config}_{args.storage}_traffic.json")
+    if os.path.exists(prof_file):
+        try:
+            pj = json.load(open(prof_file))
+            if pj.get("kernel_hash") == kernel_hash():
+                traffic = pj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "algorithmic_bytes": bytes_alg[dom],
+                "kernel_ms": {k: round(v, 4) for k, v in avg.items()},
+                "algorithmic_bytes_per_voxel_step": 4 * esz}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_cpu_baseline(pair, c_np)
+
+    line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": f"{pair.name}: {prob.dims[0]}x{prob.dims[1]}x{prob.dims[2]} "
+                       f"CT-shaped pair, FFD spacing {prob.ffd_spacing[0]}, spatial bins "
+                       f"{prob.sbin_intervals[:prob.ndim]} intervals, {prob.n_bins} intensity "
+                       "bins, M as B, finest level",
+                       "storage": args.storage, "n_voxels": prob.n_voxels,
+                       "n_params": prob.n_params, "parallelism": f"replicas x{ws}",
+                       "l2": "flushed between steps (256 MB write, outside the timed events)",
+                       "wall_ms_per_step_incl_flush": wall / args.steps * 1e3},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

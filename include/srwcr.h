@@ -1,0 +1,198 @@
+/*
+ * srwcr.h -- C ABI of libsrwcr, a B300 (sm_103a) implementation of the
+ * spatially region-weighted correlation ratio (SRWCR) and its analytic
+ * gradient with respect to cubic B-spline FFD coefficients (Gong et al.,
+ * arXiv 1804.05061, Sec. II).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Images are float32 arrays, x fastest: index (z*Ny + y)*Nx + x (Nz = 1 in
+ * 2-D).  The fixed image F plays the model image A and the moving image M
+ * the estimated image B of Eq. (2) ("M as B", gradient Eq. 19).
+ *
+ * FFD coefficients c (displacements in voxels of the level) and gradients g
+ * are float32, component-major: c[k][nz][ny][nx] with k = 0 (x), 1 (y),
+ * 2 (z); node j along an axis sits at (j-1)*delta, j = 0 .. floor((N-1)/delta)+3
+ * (Eq. 17 with p_x = floor(x/delta) - 1).
+ *
+ * Every function returns an srwcr_status and never aborts; on failure
+ * srwcr_last_error() returns a thread-local message.  Device pointers must
+ * belong to the device that was current when the context was created.  All
+ * work is queued on the context's stream; the *_async variants return
+ * without synchronising, the others synchronise that stream before
+ * returning.
+ *
+ * Ownership: the caller owns every pointer it passes; the context owns the
+ * device memory it allocates (normalised images, pyramid, accumulators,
+ * tables) and frees it in srwcr_destroy.  Calls on one context must not
+ * overlap (they share its accumulators).
+ */
+#ifndef SRWCR_H
+#define SRWCR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct srwcr_ctx srwcr_ctx;
+
+typedef enum {
+  SRWCR_OK = 0,
+  SRWCR_EINVAL = 1,        /* bad argument, constant image, size out of range */
+  SRWCR_ENOMEM = 2,        /* device or host allocation failed */
+  SRWCR_ECUDA = 3,         /* a CUDA call or kernel launch failed */
+  SRWCR_ENUMERIC = 4,      /* non-finite coefficients or value */
+  SRWCR_ELINESEARCH = 5,   /* L-BFGS line search exhausted its trials */
+  SRWCR_ETIMEOUT = 6,      /* a bounded device wait gave up */
+  SRWCR_ENOTCONVERGED = 7  /* L-BFGS stopped at its iteration limit */
+} srwcr_status;
+
+enum { SRWCR_STORAGE_F32 = 0, SRWCR_STORAGE_BF16 = 1 };
+
+/* Problem configuration (Sec. II-F gives the paper's defaults: delta = 5,
+ * L_eps = 31, i.e. 32 intensity bins). */
+typedef struct {
+  int ndim;               /* 2 or 3 */
+  int dims[3];            /* Nx, Ny, Nz (Nz = 1 when ndim == 2); each 2..65535 */
+  int ffd_spacing[3];     /* integer control spacing delta per axis, >= 1 */
+  int sbin_intervals[3];  /* K per axis: spatial bins are cubic B-splines of
+                             spacing N/K (K+3 bins, Eq. 7); 0 = bins on the
+                             FFD grid (Sec. II-C) */
+  int n_intensity_bins;   /* L_eps + 1, 2..256 (Eq. 3) */
+  int storage;            /* SRWCR_STORAGE_F32 | SRWCR_STORAGE_BF16 */
+  int pyramid_levels;     /* 1..4; level 0 is the full resolution */
+  int tile[3];            /* voxel tile (x, y, z); 0 = chosen by the library */
+} srwcr_config;
+
+/* Geometry of one pyramid level. */
+typedef struct {
+  int dims[3];            /* voxels per axis */
+  int ffd_nodes[3];       /* control nodes per axis (1 for an absent axis) */
+  int sbins[3];           /* spatial bins per axis */
+  int64_t n_voxels;
+  int64_t n_params;       /* ndim * prod(ffd_nodes) = length of c and g */
+  int64_t n_regions;      /* prod(sbins) */
+  int tile[3];            /* voxel tile used by the kernels */
+} srwcr_level_desc;
+
+/* Create a context: validate cfg, upload both images, normalise each to
+ * [0, L_eps] by its own min and max in FP64 (Sec. II, first paragraph),
+ * round to the storage type, build the pyramid (2^d box averages, floor
+ * sizes) and the fixed-image statistics p(r), p_r(a) of Eq. (4), which do
+ * not depend on the transform.
+ *   fixed, moving  Nx*Ny*Nz float32 each; host memory when
+ *                  images_on_device == 0, device memory otherwise; not
+ *                  retained.
+ *   stream         cudaStream_t to queue all work on (NULL = legacy default).
+ * Errors: SRWCR_EINVAL (bad cfg, constant image), SRWCR_ENOMEM, SRWCR_ECUDA. */
+srwcr_status srwcr_create(const srwcr_config* cfg, const float* fixed, const float* moving,
+                          int images_on_device, void* stream, srwcr_ctx** out);
+
+/* Free everything the context owns.  NULL is accepted. */
+void srwcr_destroy(srwcr_ctx* ctx);
+
+/* Thread-local description of the last failure on this thread. */
+const char* srwcr_last_error(void);
+
+/* Geometry of pyramid level `level` (0 = finest). */
+srwcr_status srwcr_level_info(const srwcr_ctx* ctx, int level, srwcr_level_desc* out);
+
+/* SRWCR value D of Eq. (9) (equivalently Eq. 12) at coefficients c_dev
+ * (device, n_params floats).  D_host receives the FP64 value. */
+srwcr_status srwcr_value(srwcr_ctx* ctx, int level, const float* c_dev, double* D_host);
+
+/* D and its gradient dD/dc (Eqs. 15-17 with dD/dM from Eq. 19 / Eq. 27).
+ * g_dev (device, n_params floats) is overwritten. */
+srwcr_status srwcr_value_and_grad(srwcr_ctx* ctx, int level, const float* c_dev, double* D_host,
+                                  float* g_dev);
+
+/* Same, without synchronising: D is written to D_dev (device double).
+ * Safe to capture in a CUDA graph once the context exists. */
+srwcr_status srwcr_value_and_grad_async(srwcr_ctx* ctx, int level, const float* c_dev,
+                                        double* D_dev, float* g_dev);
+
+/* End-to-end form with host buffers: copies c_host (n_params floats) to the
+ * device, evaluates, copies g back to g_host and D to D_host.  Uses
+ * context-owned staging buffers; host buffers may be pageable or pinned. */
+srwcr_status srwcr_value_and_grad_host(srwcr_ctx* ctx, int level, const float* c_host,
+                                       double* D_host, float* g_host);
+
+/* Forward half used by the autograd form: evaluates D (to D_dev) and keeps
+ * the per-region tables of the finalisation (Table I lines 4-18) in the
+ * context for a later srwcr_backward at the same level. */
+srwcr_status srwcr_forward(srwcr_ctx* ctx, int level, const float* c_dev, double* D_dev);
+
+/* Backward half: g_dev = gD * dD/dc using the tables of the most recent
+ * srwcr_forward at this level.  The warp is recomputed, not stored.
+ * gD_dev: device float scalar (NULL means 1). */
+srwcr_status srwcr_backward(srwcr_ctx* ctx, int level, const float* c_dev, const float* gD_dev,
+                            float* g_dev);
+
+/* Per-region statistics of the last evaluation at `level`, copied to host:
+ * out[4*r + 0..3] = p(r), sigma_r^2, CR(A,B|r), contribution p(r)(1-CR_r)
+ * (Eqs. 4, 9, 10); degenerate regions (p(r) = 0 or sigma_r^2 <= 1e-9 times
+ * the mean square of B) report CR = 0 and contribution 0.
+ * n_degenerate (may be NULL) receives their number. */
+srwcr_status srwcr_region_stats(srwcr_ctx* ctx, int level, double* out, int64_t* n_degenerate);
+
+/* Debug: voxel-to-bin indexing exactly as the kernels compute it.  For each
+ * voxel, out_dev[4*i + 0..2] = spatial-bin cell (x, y, z) (the voxel lies in
+ * bins cell..cell+3 per axis, Eq. 7) and out_dev[4*i + 3] = fixed-image
+ * intensity bin floor(A) clamped to [0, L_eps-1] (Eq. 5 support).
+ * out_dev: device int32 array of 4*n_voxels. */
+srwcr_status srwcr_debug_bins(srwcr_ctx* ctx, int level, int32_t* out_dev);
+
+/* Debug: the warped, normalised moving image B(x) = M(T(x)) (Sec. II-F) as
+ * the kernels compute it, to out_dev (device float, n_voxels). */
+srwcr_status srwcr_debug_warp(srwcr_ctx* ctx, int level, const float* c_dev, float* out_dev);
+
+/* Benchmark hooks.  With profiling enabled the library brackets each of its
+ * kernels with CUDA events on the context's stream.  srwcr_profile_read
+ * synchronises the stream and reports, per kernel kind (0 = fused warp and
+ * statistics, 1 = finalisation and value reduction, 2 = adjoint), the summed
+ * device time in ms and the number of launches bracketed; `launches`
+ * receives the number of kernels the context launched since the last reset
+ * (profiled or not).  Arrays ms and counts hold 3 entries; any pointer may
+ * be NULL.  reset != 0 clears the records. */
+srwcr_status srwcr_set_profiling(srwcr_ctx* ctx, int enable);
+srwcr_status srwcr_profile_read(srwcr_ctx* ctx, double* ms, int64_t* counts, int64_t* launches,
+                                int reset);
+
+/* L-BFGS options (Sec. II-F: 5 corrections; 200/200/120 iterations per
+ * level; backtracking with a Wolfe condition; stop when the metric is stable
+ * over the last 20 steps). */
+typedef struct {
+  int m;                  /* history length (5) */
+  int max_iter[4];        /* per level, finest first (e.g. 120, 200, 200) */
+  int stable_window;      /* 20 */
+  double stable_rtol;     /* 1e-5 */
+  int max_ls;             /* line-search trials (20) */
+  double c1, c2;          /* Armijo and curvature constants (1e-4, 0.9) */
+} srwcr_lbfgs_opts;
+
+typedef struct {
+  int levels_run;
+  int iterations[4];      /* per level, finest first */
+  int evaluations[4];
+  double final_value[4];
+  int status[4];          /* srwcr_status per level */
+} srwcr_report;
+
+/* Fill opts with the defaults above. */
+void srwcr_lbfgs_default_opts(srwcr_lbfgs_opts* opts);
+
+/* Multi-resolution L-BFGS registration minimising D (Sec. II-F).
+ * c_dev_inout (device, n_params of level 0) holds the finest-level start
+ * and receives the result; levels run coarse to fine, each coarse result is
+ * refined to the next level by cubic B-spline subdivision (values x2).
+ * n_levels <= the context's pyramid_levels.  report may be NULL. */
+srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n_levels,
+                            const srwcr_lbfgs_opts* opts, srwcr_report* report);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRWCR_H */

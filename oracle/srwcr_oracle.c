@@ -298,7 +298,9 @@ int orc_joint_pdf(const orc_problem* P, const double* A, const double* M, const 
   memset(p, 0, sizeof(double) * (size_t)(R * nb * nb));
   double* ha = (double*)malloc(sizeof(double) * nb);
   double* hb = (double*)malloc(sizeof(double) * nb);
-  if (!ha || !hb) { free(ha); free(hb); return ORC_ENOMEM; }
+  int* ia = (int*)malloc(sizeof(int) * nb);
+  int* ib = (int*)malloc(sizeof(int) * nb);
+  if (!ha || !hb || !ia || !ib) { free(ha); free(hb); free(ia); free(ib); return ORC_ENOMEM; }
   int64_t bins[64];
   double w[64], gM[3];
   for (int64_t z = 0; z < nz; ++z)
@@ -307,22 +309,31 @@ int orc_joint_pdf(const orc_problem* P, const double* A, const double* M, const 
         int64_t xv[3] = {x, y, z}, idx = (z * ny + y) * nx + x;
         double B;
         warp_voxel(P, M, c, xv, &B, gM);
-        for (int a = 0; a < nb; ++a) ha[a] = orc_parzen((double)a - A[idx]);
-        for (int b = 0; b < nb; ++b) hb[b] = orc_parzen((double)b - B);
+        /* Parzen weights of every bin; only the nonzero ones are kept
+         * (Eq. 5 vanishes for |t| >= 1, so at most three per image). */
+        int na = 0, nbb = 0;
+        for (int a = 0; a < nb; ++a) {
+          double h = orc_parzen((double)a - A[idx]);
+          if (h != 0.0) { ia[na] = a; ha[na++] = h; }
+        }
+        for (int b = 0; b < nb; ++b) {
+          double h = orc_parzen((double)b - B);
+          if (h != 0.0) { ib[nbb] = b; hb[nbb++] = h; }
+        }
         int nw = spatial_weights(P, xv, bins, w);
         for (int s = 0; s < nw; ++s) {
           if (w[s] == 0.0) continue;
           double* pr = p + bins[s] * nb * nb;
-          for (int a = 0; a < nb; ++a) {
-            if (ha[a] == 0.0) continue;
-            double wa = w[s] * ha[a];
-            for (int b = 0; b < nb; ++b)
-              if (hb[b] != 0.0) pr[a * nb + b] += wa * hb[b];
+          for (int i = 0; i < na; ++i) {
+            double wa = w[s] * ha[i];
+            for (int j = 0; j < nbb; ++j) pr[ia[i] * nb + ib[j]] += wa * hb[j];
           }
         }
       }
   free(ha);
   free(hb);
+  free(ia);
+  free(ib);
   double Z = 0.0;
   for (int64_t i = 0; i < R * nb * nb; ++i) Z += p[i];
   if (Z_out) *Z_out = Z;
@@ -428,21 +439,28 @@ static double dD_dB(const orc_problem* P, const orc_tables* T, const int64_t xv[
   int64_t bins[64];
   double w[64];
   int nw = spatial_weights(P, xv, bins, w);
+  /* Nonzero h(a - A) and dh/dkappa(b - B) terms (at most three each). */
+  int ia[4], ib[4], na = 0, ndb = 0;
+  double ha[4], dh[4];
+  for (int a = 0; a < nb && na < 4; ++a) {
+    double h = orc_parzen((double)a - Ax);
+    if (h != 0.0) { ia[na] = a; ha[na++] = h; }
+  }
+  for (int b = 0; b < nb && ndb < 4; ++b) {
+    double d = orc_parzen_dkappa((double)b, Bx, nb - 1);
+    if (d != 0.0) { ib[ndb] = b; dh[ndb++] = d; }
+  }
   double acc = 0.0;
   for (int s = 0; s < nw; ++s) {
     int64_t r = bins[s];
     if (w[s] == 0.0 || !T->valid[r]) continue;
     double mu = T->mu_r[r], var = T->var_r[r], omc = 1.0 - T->cr[r];
-    for (int a = 0; a < nb; ++a) {
-      double ha = orc_parzen((double)a - Ax);
-      if (ha == 0.0) continue;
-      double mua = T->mu_ra[r * nb + a];
-      for (int b = 0; b < nb; ++b) {
-        double dh = orc_parzen_dkappa((double)b, Bx, nb - 1);
-        if (dh == 0.0) continue;
-        double bb = (double)b;
+    for (int i = 0; i < na; ++i) {
+      double mua = T->mu_ra[r * nb + ia[i]];
+      for (int j = 0; j < ndb; ++j) {
+        double bb = (double)ib[j];
         double coef = (omc * (bb * bb - 2.0 * bb * mu) + 2.0 * bb * mua - bb * bb) / var;
-        acc += coef * w[s] * ha * dh;
+        acc += coef * w[s] * ha[i] * dh[j];
       }
     }
   }

@@ -1,0 +1,327 @@
+"""B300-native SRWCR (spatially region-weighted correlation ratio) registration.
+
+Thin ctypes binding over ``libsrwcr.so`` (C ABI in ``include/srwcr.h``):
+argument marshalling only.  Every step of the SRWCR value and gradient runs
+in the library's CUDA kernels; PyTorch supplies device memory and streams.
+There is no CPU fallback: if the library cannot be loaded, importing the
+engine raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libsrwcr.so")
+_lib = None
+
+STORAGE = {"f32": 0, "bf16": 1}
+STATUS = {0: "SRWCR_OK", 1: "SRWCR_EINVAL", 2: "SRWCR_ENOMEM", 3: "SRWCR_ECUDA",
+          4: "SRWCR_ENUMERIC", 5: "SRWCR_ELINESEARCH", 6: "SRWCR_ETIMEOUT",
+          7: "SRWCR_ENOTCONVERGED"}
+
+# Every symbol the header exports (checked by the CPU test suite).
+EXPORTS = ("srwcr_create", "srwcr_destroy", "srwcr_last_error", "srwcr_level_info",
+           "srwcr_value", "srwcr_value_and_grad", "srwcr_value_and_grad_async",
+           "srwcr_value_and_grad_host", "srwcr_forward", "srwcr_backward",
+           "srwcr_region_stats", "srwcr_debug_bins", "srwcr_debug_warp",
+           "srwcr_lbfgs_default_opts", "srwcr_register", "srwcr_set_profiling",
+           "srwcr_profile_read")
+
+
+class SrwcrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("dims", ctypes.c_int * 3),
+                ("ffd_spacing", ctypes.c_int * 3), ("sbin_intervals", ctypes.c_int * 3),
+                ("n_intensity_bins", ctypes.c_int), ("storage", ctypes.c_int),
+                ("pyramid_levels", ctypes.c_int), ("tile", ctypes.c_int * 3)]
+
+
+class LevelDesc(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 3), ("ffd_nodes", ctypes.c_int * 3),
+                ("sbins", ctypes.c_int * 3), ("n_voxels", ctypes.c_int64),
+                ("n_params", ctypes.c_int64), ("n_regions", ctypes.c_int64),
+                ("tile", ctypes.c_int * 3)]
+
+
+class LbfgsOpts(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("max_iter", ctypes.c_int * 4),
+                ("stable_window", ctypes.c_int), ("stable_rtol", ctypes.c_double),
+                ("max_ls", ctypes.c_int), ("c1", ctypes.c_double), ("c2", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("levels_run", ctypes.c_int), ("iterations", ctypes.c_int * 4),
+                ("evaluations", ctypes.c_int * 4), ("final_value", ctypes.c_double * 4),
+                ("status", ctypes.c_int * 4)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libsrwcr.so (building it with nvcc if it is absent or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libsrwcr.so not found at {_LIB_PATH}; run "
+                          "`python -m paper_1804_05061_b300.build`")
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+    st = ctypes.c_int
+    sigs = {
+        "srwcr_create": (st, [ctypes.POINTER(Config), vp, vp, ctypes.c_int, vp,
+                              ctypes.POINTER(vp)]),
+        "srwcr_destroy": (None, [vp]),
+        "srwcr_last_error": (ctypes.c_char_p, []),
+        "srwcr_level_info": (st, [vp, ctypes.c_int, ctypes.POINTER(LevelDesc)]),
+        "srwcr_value": (st, [vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double)]),
+        "srwcr_value_and_grad": (st, [vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double), vp]),
+        "srwcr_value_and_grad_async": (st, [vp, ctypes.c_int, vp, vp, vp]),
+        "srwcr_value_and_grad_host": (st, [vp, ctypes.c_int, vp,
+                                           ctypes.POINTER(ctypes.c_double), vp]),
+        "srwcr_forward": (st, [vp, ctypes.c_int, vp, vp]),
+        "srwcr_backward": (st, [vp, ctypes.c_int, vp, vp, vp]),
+        "srwcr_region_stats": (st, [vp, ctypes.c_int, vp, i64p]),
+        "srwcr_debug_bins": (st, [vp, ctypes.c_int, vp]),
+        "srwcr_debug_warp": (st, [vp, ctypes.c_int, vp, vp]),
+        "srwcr_lbfgs_default_opts": (None, [ctypes.POINTER(LbfgsOpts)]),
+        "srwcr_set_profiling": (st, [vp, ctypes.c_int]),
+        "srwcr_profile_read": (st, [vp, vp, vp, i64p, ctypes.c_int]),
+        "srwcr_register": (st, [vp, vp, ctypes.c_int, ctypes.POINTER(LbfgsOpts),
+                                ctypes.POINTER(Report)]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise SrwcrError(status, load().srwcr_last_error().decode(errors="replace"))
+
+
+def _ptr(t) -> int:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class LevelInfo:
+    dims: tuple
+    ffd_nodes: tuple
+    sbins: tuple
+    n_voxels: int
+    n_params: int
+    n_regions: int
+    tile: tuple
+
+
+class SRWCR:
+    """One fixed/moving pair on the current CUDA device.
+
+    fixed, moving: float32 arrays shaped (ny, nx) or (nz, ny, nx), as NumPy
+    (host) arrays or CUDA tensors.  ``sbin_intervals`` K > 0 puts K+3 cubic
+    B-spline spatial bins per axis; 0 puts them on the FFD grid.
+    """
+
+    def __init__(self, fixed, moving, ffd_spacing: Sequence[int],
+                 sbin_intervals: Sequence[int] = (0, 0, 0), n_bins: int = 32,
+                 storage: str = "f32", pyramid_levels: int = 1,
+                 tile: Optional[Sequence[int]] = None, stream=None):
+        import torch
+        self._torch = torch
+        lib = load()
+        shape = tuple(fixed.shape)
+        if tuple(moving.shape) != shape or len(shape) not in (2, 3):
+            raise ValueError("fixed and moving must share a 2-D or 3-D shape")
+        ndim = len(shape)
+        cfg = Config()
+        cfg.ndim = ndim
+        dims = list(reversed(shape)) + [1] * (3 - ndim)
+        for d in range(3):
+            cfg.dims[d] = int(dims[d])
+            cfg.ffd_spacing[d] = int(ffd_spacing[d]) if d < len(ffd_spacing) else 1
+            cfg.sbin_intervals[d] = int(sbin_intervals[d]) if d < len(sbin_intervals) else 0
+            cfg.tile[d] = int(tile[d]) if tile is not None and d < len(tile) else 0
+        cfg.n_intensity_bins = int(n_bins)
+        cfg.storage = STORAGE[storage]
+        cfg.pyramid_levels = int(pyramid_levels)
+        self.cfg = cfg
+        self.ndim = ndim
+        self.storage = storage
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        on_dev = isinstance(fixed, torch.Tensor) and fixed.is_cuda
+        if on_dev:
+            f = fixed.detach().to(torch.float32).contiguous()
+            m = moving.detach().to(torch.float32).contiguous()
+            pf, pm = _ptr(f), _ptr(m)
+        else:
+            f = np.ascontiguousarray(fixed, dtype=np.float32)
+            m = np.ascontiguousarray(moving, dtype=np.float32)
+            pf, pm = f.ctypes.data_as(ctypes.c_void_p), m.ctypes.data_as(ctypes.c_void_p)
+        handle = ctypes.c_void_p()
+        _check(lib.srwcr_create(ctypes.byref(cfg), pf, pm, 1 if on_dev else 0,
+                                ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)))
+        self._h = handle
+        self._gen = [0] * cfg.pyramid_levels
+        self.levels = [self.level_info(l) for l in range(cfg.pyramid_levels)]
+
+    # -- lifetime ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().srwcr_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- geometry ----------------------------------------------------------
+    def level_info(self, level: int = 0) -> LevelInfo:
+        d = LevelDesc()
+        _check(load().srwcr_level_info(self._h, level, ctypes.byref(d)))
+        return LevelInfo(tuple(d.dims), tuple(d.ffd_nodes), tuple(d.sbins), d.n_voxels,
+                         d.n_params, d.n_regions, tuple(d.tile))
+
+    def coef_shape(self, level: int = 0):
+        n = self.levels[level].ffd_nodes
+        return (self.ndim, n[1], n[0]) if self.ndim == 2 else (self.ndim, n[2], n[1], n[0])
+
+    def zeros(self, level: int = 0):
+        return self._torch.zeros(self.coef_shape(level), dtype=self._torch.float32,
+                                 device=self.device)
+
+    def _c(self, c, level):
+        t = self._torch
+        if not (isinstance(c, t.Tensor) and c.is_cuda and c.dtype == t.float32):
+            raise TypeError("c must be a float32 CUDA tensor")
+        if c.numel() != self.levels[level].n_params:
+            raise ValueError(f"c has {c.numel()} entries, level {level} needs "
+                             f"{self.levels[level].n_params}")
+        return c.contiguous()
+
+    # -- evaluation --------------------------------------------------------
+    def value(self, c, level: int = 0) -> float:
+        c = self._c(c, level)
+        D = ctypes.c_double()
+        _check(load().srwcr_value(self._h, level, _ptr(c), ctypes.byref(D)))
+        self._gen[level] += 1
+        return D.value
+
+    def value_and_grad(self, c, level: int = 0, out=None):
+        c = self._c(c, level)
+        g = self._torch.empty_like(c) if out is None else out
+        D = ctypes.c_double()
+        _check(load().srwcr_value_and_grad(self._h, level, _ptr(c), ctypes.byref(D), _ptr(g)))
+        self._gen[level] += 1
+        return D.value, g
+
+    def value_and_grad_async(self, c, D_out, g_out, level: int = 0):
+        """Queue value+gradient on the stream; D_out is a float64 CUDA scalar."""
+        _check(load().srwcr_value_and_grad_async(self._h, level, _ptr(c), _ptr(D_out),
+                                                 _ptr(g_out)))
+        self._gen[level] += 1
+
+    def value_and_grad_host(self, c_host: np.ndarray, g_host: np.ndarray, level: int = 0) -> float:
+        """End-to-end call with host buffers (copies inside the library)."""
+        assert c_host.dtype == np.float32 and g_host.dtype == np.float32
+        D = ctypes.c_double()
+        _check(load().srwcr_value_and_grad_host(
+            self._h, level, c_host.ctypes.data_as(ctypes.c_void_p), ctypes.byref(D),
+            g_host.ctypes.data_as(ctypes.c_void_p)))
+        self._gen[level] += 1
+        return D.value
+
+    def forward(self, c, D_out, level: int = 0) -> int:
+        _check(load().srwcr_forward(self._h, level, _ptr(c), _ptr(D_out)))
+        self._gen[level] += 1
+        return self._gen[level]
+
+    def backward(self, c, gD, g_out, level: int = 0):
+        _check(load().srwcr_backward(self._h, level, _ptr(c),
+                                     _ptr(gD) if gD is not None else None, _ptr(g_out)))
+
+    def generation(self, level: int = 0) -> int:
+        return self._gen[level]
+
+    # -- inspection --------------------------------------------------------
+    def region_stats(self, level: int = 0):
+        R = self.levels[level].n_regions
+        out = np.zeros((R, 4), np.float64)
+        nd = ctypes.c_int64()
+        _check(load().srwcr_region_stats(self._h, level, out.ctypes.data_as(ctypes.c_void_p),
+                                         ctypes.byref(nd)))
+        return out, int(nd.value)
+
+    def debug_bins(self, level: int = 0):
+        n = self.levels[level].n_voxels
+        out = self._torch.empty((n, 4), dtype=self._torch.int32, device=self.device)
+        _check(load().srwcr_debug_bins(self._h, level, _ptr(out)))
+        return out
+
+    def debug_warp(self, c, level: int = 0):
+        c = self._c(c, level)
+        out = self._torch.empty(self.levels[level].n_voxels, dtype=self._torch.float32,
+                                device=self.device)
+        _check(load().srwcr_debug_warp(self._h, level, _ptr(c), _ptr(out)))
+        return out
+
+    # -- benchmark hooks ---------------------------------------------------
+    def set_profiling(self, on: bool = True):
+        _check(load().srwcr_set_profiling(self._h, 1 if on else 0))
+
+    def profile_read(self, reset: bool = True):
+        """(ms[3], counts[3], launches): device ms per kernel kind
+        (accumulate, finalize, adjoint), bracketed launches, kernels launched."""
+        ms = np.zeros(3, np.float64)
+        cnt = np.zeros(3, np.int64)
+        n = ctypes.c_int64()
+        _check(load().srwcr_profile_read(self._h, ms.ctypes.data_as(ctypes.c_void_p),
+                                         cnt.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n),
+                                         1 if reset else 0))
+        return ms, cnt, int(n.value)
+
+    # -- registration ------------------------------------------------------
+    @staticmethod
+    def default_opts() -> LbfgsOpts:
+        o = LbfgsOpts()
+        load().srwcr_lbfgs_default_opts(ctypes.byref(o))
+        return o
+
+    def register(self, c, n_levels: int = 1, opts: Optional[LbfgsOpts] = None,
+                 check: bool = True) -> Report:
+        c = self._c(c, 0)
+        rep = Report()
+        st = load().srwcr_register(self._h, _ptr(c), int(n_levels),
+                                   ctypes.byref(opts) if opts is not None else None,
+                                   ctypes.byref(rep))
+        if check and st not in (0, 7, 5):
+            _check(st)
+        rep.status_code = st
+        return rep
+
+
+def from_problem(prob, fixed, moving, storage: str = "f32", pyramid_levels: int = 1, **kw) -> SRWCR:
+    """Build an engine from a ``synth.Problem``-like description."""
+    return SRWCR(fixed, moving, prob.ffd_spacing[:prob.ndim], prob.sbin_intervals[:prob.ndim],
+                 prob.n_bins, storage=storage, pyramid_levels=pyramid_levels, **kw)

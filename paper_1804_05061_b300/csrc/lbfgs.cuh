@@ -1,0 +1,348 @@
+// L-BFGS registration driver (Sec. II-F): limited-memory BFGS with m
+// corrections (two-loop recursion), backtracking line search with the
+// Armijo and weak-Wolfe conditions, and the "metric stable over the last w
+// steps" stop; coarse-to-fine over the pyramid with cubic B-spline
+// subdivision of the coefficients between levels.
+//
+// Vectors (coefficients, gradients, the m (s, y) pairs) live on the device
+// in FP32; every inner product is accumulated in FP64 on the device with a
+// fixed reduction order, then read by the host, which runs the control flow.
+// Included once, at the end of srwcr.cu.
+#pragma once
+
+namespace {
+
+constexpr int kDotBlocks = 148;
+
+// Partial FP64 dot products with a fixed partition; k_dot_final sums them in
+// a fixed order, so results do not depend on scheduling.
+__global__ void __launch_bounds__(256)
+k_dot_partial(const float* __restrict__ a, const float* __restrict__ b, long long n,
+              double* __restrict__ part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+    s += (double)a[i] * (double)b[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_dot_final(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nparts; ++i) s += part[i];
+    out[0] = s;
+  }
+}
+
+// y = a*x + b*y
+__global__ void k_axpby(float a, const float* __restrict__ x, float b, float* __restrict__ y,
+                        long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+// y = a*x (x and y may alias)
+__global__ void k_scal(float a, const float* __restrict__ x, float* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// z = x + a*y
+__global__ void k_xpay(const float* __restrict__ x, float a, const float* __restrict__ y,
+                       float* __restrict__ z, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    z[i] = x[i] + a * y[i];
+}
+
+// Dyadic refinement of uniform cubic B-spline coefficients (knot doubling):
+// fine node j sits at coarse node position (j+1)/2 (offset indices); odd j
+// take (c[i-1] + 6c[i] + c[i+1])/8 with i = (j+1)/2, even j take
+// (c[i] + c[i+1])/2 with i = j/2; coarse indices are clamped.  Values are
+// doubled: displacements are in voxels of the level.
+__device__ __forceinline__ int stencil(int j, int nc, int idx[3], float w[3]) {
+  auto cl = [nc](int i) { return i < 0 ? 0 : (i >= nc ? nc - 1 : i); };
+  if (j & 1) {
+    const int i = (j + 1) / 2;
+    idx[0] = cl(i - 1); idx[1] = cl(i); idx[2] = cl(i + 1);
+    w[0] = 0.125f; w[1] = 0.75f; w[2] = 0.125f;
+    return 3;
+  }
+  const int i = j / 2;
+  idx[0] = cl(i); idx[1] = cl(i + 1);
+  w[0] = 0.5f; w[1] = 0.5f;
+  return 2;
+}
+
+__global__ void k_subdivide(const float* __restrict__ cc, int ndim, int cx, int cy, int cz,
+                            float* __restrict__ cf, int fx, int fy, int fz) {
+  const long long nfine = (long long)fx * fy * fz, ncoarse = (long long)cx * cy * cz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nfine * ndim;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i / nfine);
+    const long long nidx = i % nfine;
+    const int jx = (int)(nidx % fx), jy = (int)((nidx / fx) % fy), jz = (int)(nidx / ((long long)fx * fy));
+    int ix[3], iy[3], iz[3] = {0, 0, 0};
+    float wx[3], wy[3], wz[3] = {1.f, 0.f, 0.f};
+    const int nx = stencil(jx, cx, ix, wx), ny = stencil(jy, cy, iy, wy);
+    const int nz = ndim == 3 ? stencil(jz, cz, iz, wz) : 1;
+    float s = 0.f;
+    for (int c = 0; c < nz; ++c)
+      for (int b = 0; b < ny; ++b)
+        for (int a = 0; a < nx; ++a)
+          s += wx[a] * wy[b] * wz[c] * cc[k * ncoarse + ((long long)iz[c] * cy + iy[b]) * cx + ix[a]];
+    cf[i] = 2.f * s;
+  }
+}
+
+struct LbfgsWork {
+  long long n = 0;
+  int m = 0;
+  float *x = nullptr, *g = nullptr, *d = nullptr, *xn = nullptr, *gn = nullptr;
+  float* S = nullptr;  // [m][n]
+  float* Y = nullptr;  // [m][n]
+  double* part = nullptr;
+  double* dot = nullptr;   // device scalar
+  double* Ddev = nullptr;  // device scalar
+  double* host = nullptr;  // pinned [2]
+};
+
+void free_work(LbfgsWork& w) {
+  void* p[] = {w.x, w.g, w.d, w.xn, w.gn, w.S, w.Y, w.part, w.dot, w.Ddev};
+  for (void* q : p)
+    if (q) cudaFree(q);
+  if (w.host) cudaFreeHost(w.host);
+  w = LbfgsWork();
+}
+
+srwcr_status alloc_work(LbfgsWork& w, long long n, int m) {
+  w.n = n;
+  w.m = m;
+  CK(cudaMalloc((void**)&w.x, sizeof(float) * n));
+  CK(cudaMalloc((void**)&w.g, sizeof(float) * n));
+  CK(cudaMalloc((void**)&w.d, sizeof(float) * n));
+  CK(cudaMalloc((void**)&w.xn, sizeof(float) * n));
+  CK(cudaMalloc((void**)&w.gn, sizeof(float) * n));
+  CK(cudaMalloc((void**)&w.S, sizeof(float) * n * m));
+  CK(cudaMalloc((void**)&w.Y, sizeof(float) * n * m));
+  CK(cudaMalloc((void**)&w.part, sizeof(double) * kDotBlocks));
+  CK(cudaMalloc((void**)&w.dot, sizeof(double)));
+  CK(cudaMalloc((void**)&w.Ddev, sizeof(double)));
+  CK(cudaMallocHost((void**)&w.host, sizeof(double) * 2));
+  return SRWCR_OK;
+}
+
+srwcr_status dot(srwcr_ctx* ctx, LbfgsWork& w, const float* a, const float* b, double* out) {
+  k_dot_partial<<<kDotBlocks, 256, 0, ctx->stream>>>(a, b, w.n, w.part);
+  CKL();
+  k_dot_final<<<1, 32, 0, ctx->stream>>>(w.part, kDotBlocks, w.dot);
+  CKL();
+  CK(cudaMemcpyAsync(w.host, w.dot, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *out = w.host[0];
+  return SRWCR_OK;
+}
+
+srwcr_status axpby(srwcr_ctx* ctx, LbfgsWork& w, float a, const float* x, float b, float* y) {
+  k_axpby<<<kDotBlocks, 256, 0, ctx->stream>>>(a, x, b, y, w.n);
+  CKL();
+  return SRWCR_OK;
+}
+
+srwcr_status scal(srwcr_ctx* ctx, LbfgsWork& w, float a, const float* x, float* y) {
+  k_scal<<<kDotBlocks, 256, 0, ctx->stream>>>(a, x, y, w.n);
+  CKL();
+  return SRWCR_OK;
+}
+
+srwcr_status eval(srwcr_ctx* ctx, int level, LbfgsWork& w, const float* x, float* g, double* f) {
+  Level& lv = ctx->lev[level];
+  RET_IF(run_value(ctx, lv, x));
+  RET_IF(run_grad(ctx, lv, x, nullptr, g));
+  CK(cudaMemcpyAsync(w.host + 1, lv.D, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *f = w.host[1];
+  return SRWCR_OK;
+}
+
+// One level of L-BFGS starting from w.x; result left in w.x.
+srwcr_status lbfgs_level(srwcr_ctx* ctx, int level, LbfgsWork& w, const srwcr_lbfgs_opts& o,
+                         int max_iter, int* iters, int* evals, double* fout) {
+  double f;
+  RET_IF(eval(ctx, level, w, w.x, w.g, &f));
+  int ne = 1, hist_len = 0, head = 0;  // ring buffer of (s, y); head = next slot
+  double rho[16], alpha_k[16];
+  std::vector<double> fh{f};
+  bool restart = true;
+  srwcr_status status = SRWCR_ENOTCONVERGED;
+  int it = 0;
+  const long long n = w.n;
+  for (it = 1; it <= max_iter; ++it) {
+    double gg;
+    RET_IF(dot(ctx, w, w.g, w.g, &gg));
+    if (!(gg > 0.0)) { status = SRWCR_OK; --it; break; }
+    // Two-loop recursion on d = q.
+    CK(cudaMemcpyAsync(w.d, w.g, sizeof(float) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int t = 0; t < hist_len; ++t) {
+      const int slot = (head - 1 - t + o.m) % o.m;
+      double sq;
+      RET_IF(dot(ctx, w, w.S + slot * n, w.d, &sq));
+      alpha_k[slot] = rho[slot] * sq;
+      RET_IF(axpby(ctx, w, (float)-alpha_k[slot], w.Y + slot * n, 1.f, w.d));
+    }
+    if (hist_len > 0) {
+      const int newest = (head - 1 + o.m) % o.m;
+      double sy, yy;
+      RET_IF(dot(ctx, w, w.S + newest * n, w.Y + newest * n, &sy));
+      RET_IF(dot(ctx, w, w.Y + newest * n, w.Y + newest * n, &yy));
+      RET_IF(scal(ctx, w, (float)(sy / yy), w.d, w.d));
+    }
+    for (int t = hist_len - 1; t >= 0; --t) {
+      const int slot = (head - 1 - t + o.m) % o.m;
+      double yq;
+      RET_IF(dot(ctx, w, w.Y + slot * n, w.d, &yq));
+      const double beta = rho[slot] * yq;
+      RET_IF(axpby(ctx, w, (float)(alpha_k[slot] - beta), w.S + slot * n, 1.f, w.d));
+    }
+    RET_IF(scal(ctx, w, -1.f, w.d, w.d));  // d = -H g
+    double gd;
+    RET_IF(dot(ctx, w, w.g, w.d, &gd));
+    if (!(gd < 0.0)) {
+      hist_len = 0;
+      head = 0;
+      RET_IF(scal(ctx, w, -1.f, w.g, w.d));
+      gd = -gg;
+      restart = true;
+    }
+    double dd;
+    RET_IF(dot(ctx, w, w.d, w.d, &dd));
+    double alpha = restart ? 1.0 / std::sqrt(dd) : 1.0;
+    bool accepted = false;
+    double fn = f;
+    for (int ls = 0; ls < o.max_ls; ++ls) {
+      k_xpay<<<kDotBlocks, 256, 0, ctx->stream>>>(w.x, (float)alpha, w.d, w.xn, n);
+      CKL();
+      RET_IF(eval(ctx, level, w, w.xn, w.gn, &fn));
+      ++ne;
+      if (!std::isfinite(fn) || fn > f + o.c1 * alpha * gd) { alpha *= 0.5; continue; }
+      double gnd;
+      RET_IF(dot(ctx, w, w.gn, w.d, &gnd));
+      if (gnd < o.c2 * gd) { alpha *= 2.0; continue; }
+      accepted = true;
+      break;
+    }
+    if (!accepted) { status = SRWCR_ELINESEARCH; --it; break; }
+    // s = xn - x into slot head, y = gn - g; then x = xn, g = gn.
+    float* s = w.S + head * n;
+    float* y = w.Y + head * n;
+    k_xpay<<<kDotBlocks, 256, 0, ctx->stream>>>(w.xn, -1.f, w.x, s, n);
+    CKL();
+    k_xpay<<<kDotBlocks, 256, 0, ctx->stream>>>(w.gn, -1.f, w.g, y, n);
+    CKL();
+    std::swap(w.x, w.xn);
+    std::swap(w.g, w.gn);
+    f = fn;
+    double sy;
+    RET_IF(dot(ctx, w, s, y, &sy));
+    if (sy > 0.0) {
+      rho[head] = 1.0 / sy;
+      head = (head + 1) % o.m;
+      hist_len = std::min(hist_len + 1, o.m);
+    }
+    restart = false;
+    fh.push_back(f);
+    const int win = o.stable_window;
+    if (win > 0 && (int)fh.size() > win &&
+        std::fabs(fh.back() - fh[fh.size() - 1 - win]) <= o.stable_rtol * std::fabs(fh.back())) {
+      status = SRWCR_OK;
+      break;
+    }
+  }
+  if (it > max_iter) it = max_iter;
+  *iters = it;
+  *evals = ne;
+  *fout = f;
+  return status;
+}
+
+}  // namespace
+
+extern "C" srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n_levels,
+                                       const srwcr_lbfgs_opts* opts, srwcr_report* report) {
+  RET_IF(check_level(ctx, 0));
+  if (!c_dev_inout) return fail(SRWCR_EINVAL, "c_dev_inout is NULL");
+  if (n_levels < 1 || n_levels > ctx->nlev)
+    return fail(SRWCR_EINVAL, "n_levels %d outside [1, %d]", n_levels, ctx->nlev);
+  srwcr_lbfgs_opts o;
+  srwcr_lbfgs_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.m < 1 || o.m > 16 || o.max_ls < 1) return fail(SRWCR_EINVAL, "bad L-BFGS options");
+  if (report) memset(report, 0, sizeof *report);
+  const int nd = ctx->cfg.ndim;
+  srwcr_status final_status = SRWCR_OK;
+  float* prev = nullptr;  // coarse result (device), owned here
+  const Geo* prev_g = nullptr;
+  for (int level = n_levels - 1; level >= 0; --level) {
+    const Geo& g = ctx->lev[level].g;
+    LbfgsWork w;
+    srwcr_status st = alloc_work(w, g.ncoef * nd, o.m);
+    if (st != SRWCR_OK) { free_work(w); if (prev) cudaFree(prev); return st; }
+    if (level == n_levels - 1 && n_levels > 1) {
+      cudaMemsetAsync(w.x, 0, sizeof(float) * w.n, ctx->stream);
+    } else if (level == n_levels - 1) {
+      cudaMemcpyAsync(w.x, c_dev_inout, sizeof(float) * w.n, cudaMemcpyDeviceToDevice, ctx->stream);
+    } else {
+      k_subdivide<<<256, 256, 0, ctx->stream>>>(prev, nd, prev_g->nf[0], prev_g->nf[1],
+                                                prev_g->nf[2], w.x, g.nf[0], g.nf[1], g.nf[2]);
+    }
+    int iters = 0, evals = 0;
+    double f = 0.0;
+    st = lbfgs_level(ctx, level, w, o, o.max_iter[level], &iters, &evals, &f);
+    if (report) {
+      report->iterations[level] = iters;
+      report->evaluations[level] = evals;
+      report->final_value[level] = f;
+      report->status[level] = st;
+      report->levels_run++;
+    }
+    if (st != SRWCR_OK && st != SRWCR_ENOTCONVERGED && st != SRWCR_ELINESEARCH) {
+      std::string keep = g_err;
+      free_work(w);
+      if (prev) cudaFree(prev);
+      g_err = keep;
+      return st;
+    }
+    if (level == 0) final_status = st;
+    if (prev) cudaFree(prev);
+    prev = nullptr;
+    if (level > 0) {
+      if (cudaMalloc((void**)&prev, sizeof(float) * w.n) != cudaSuccess) {
+        free_work(w);
+        return fail(SRWCR_ENOMEM, "cudaMalloc failed");
+      }
+      cudaMemcpyAsync(prev, w.x, sizeof(float) * w.n, cudaMemcpyDeviceToDevice, ctx->stream);
+      prev_g = &g;
+    } else {
+      cudaMemcpyAsync(c_dev_inout, w.x, sizeof(float) * w.n, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    free_work(w);
+    if (e != cudaSuccess) {
+      if (prev) cudaFree(prev);
+      return fail(SRWCR_ECUDA, "registration: %s", cudaGetErrorString(e));
+    }
+  }
+  if (final_status == SRWCR_ELINESEARCH)
+    return fail(SRWCR_ELINESEARCH, "line search exhausted at the finest level");
+  if (final_status == SRWCR_ENOTCONVERGED)
+    return fail(SRWCR_ENOTCONVERGED, "iteration limit reached at the finest level");
+  return SRWCR_OK;
+}

@@ -1,0 +1,714 @@
+// libsrwcr: host runtime and C ABI (see include/srwcr.h).
+//
+// One context = one fixed/moving pair with its pyramid.  Per evaluation the
+// stream sees: memset(accumulators) -> k_accumulate -> k_finalize ->
+// k_reduce_D [-> memset(g) -> k_adjoint].  The fixed-image statistics
+// P[r][a] = sum_x w(r,x) h(a - A(x)) are computed once in srwcr_create.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "srwcr.h"
+#include "kernels.cuh"
+
+using namespace srwcr;
+
+namespace {
+
+thread_local std::string g_err;
+
+srwcr_status fail(srwcr_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+srwcr_status fail(srwcr_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? SRWCR_ENOMEM : SRWCR_ECUDA,         \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,      \
+                  __LINE__);                                                             \
+  } while (0)
+
+#define CKL()                                                                            \
+  do {                                                                                   \
+    cudaError_t e_ = cudaGetLastError();                                                 \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(SRWCR_ECUDA, "kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                   \
+  } while (0)
+
+#define RET_IF(x)                        \
+  do {                                   \
+    srwcr_status s_ = (x);               \
+    if (s_ != SRWCR_OK) return s_;       \
+  } while (0)
+
+constexpr int kBlock = 256;
+constexpr size_t kSmemBudget = 112 * 1024;  // per CTA, two CTAs per SM
+
+struct Level {
+  Geo g{};
+  void* A = nullptr;                  // normalised fixed image (storage type)
+  void* M = nullptr;                  // normalised moving image (storage type)
+  unsigned long long* S = nullptr;    // [R][nbins][2] fixed-point S1, S2 (also P scratch)
+  double* P = nullptr;                // [R][nbins] sum_x w h(a - A)
+  float* U = nullptr;                 // [R]
+  float* V = nullptr;                 // [R]
+  float* X = nullptr;                 // [R][nbins]
+  double* Dr = nullptr;               // [R] share of D
+  double* stats = nullptr;            // [R][4]
+  double* D = nullptr;                // device scalar
+  int* ndeg = nullptr;                // device scalar
+  double Z = 0.0;
+  float s1 = 1.f, s2 = 1.f;           // fixed-point scales of S1, S2
+  size_t smem_acc = 0, smem_adj = 0;
+  bool tables = false;
+};
+
+}  // namespace
+
+struct srwcr_ctx {
+  srwcr_config cfg{};
+  int nlev = 0;
+  Level lev[4];
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  double* D_host = nullptr;   // pinned
+  int* flag_host = nullptr;   // pinned
+  int* flag_dev = nullptr;
+  float* c_stage = nullptr;   // device staging for the host-buffer entry point
+  float* g_stage = nullptr;
+  double* D_stage = nullptr;
+  int64_t stage_len = 0;
+  // Benchmark hooks: kernels launched so far, and (when enabled) CUDA-event
+  // pairs around each kernel on the context's stream.
+  long long launches = 0;
+  bool profiling = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;
+};
+
+namespace {
+
+int ceil_log2(double v) {
+  int e = 0;
+  while (std::ldexp(1.0, e) < v) ++e;
+  return e;
+}
+
+// Cells spanned by a tile along one axis: max over tiles of
+// cell(last voxel) - cell(first voxel) + 4 (bins cell..cell+3 per voxel).
+int max_bins_per_tile(int n, int tile, int num, int den) {
+  int best = 0;
+  for (int s = 0; s < n; s += tile) {
+    const int e = std::min(n - 1, s + tile - 1);
+    const int c0 = (int)((long long)s * den / num), c1 = (int)((long long)e * den / num);
+    best = std::max(best, c1 - c0 + 4);
+  }
+  return best;
+}
+
+size_t acc_smem(const Geo& g, int nch) {
+  return (size_t)g.hb[0] * g.hb[1] * g.hb[2] * g.nbins * nch * sizeof(unsigned long long);
+}
+
+void set_tile(Geo& g, int ndim, int tx, int ty, int tz) {
+  g.tile[0] = tx; g.tile[1] = ty; g.tile[2] = ndim == 3 ? tz : 1;
+  for (int d = 0; d < 3; ++d) g.ntile[d] = (g.n[d] + g.tile[d] - 1) / g.tile[d];
+  for (int d = 0; d < 3; ++d) {
+    if (d < ndim) {
+      g.hb[d] = max_bins_per_tile(g.n[d], g.tile[d], g.sbn[d], g.sbd[d]);
+      g.hf[d] = max_bins_per_tile(g.n[d], g.tile[d], g.fsp[d], 1);
+    } else {
+      g.hb[d] = 1; g.hf[d] = 1;
+    }
+  }
+}
+
+srwcr_status choose_tile(Geo& g, int ndim, const int* req) {
+  if (req[0] > 0) {
+    set_tile(g, ndim, req[0], std::max(1, req[1]), std::max(1, req[2]));
+    if (acc_smem(g, 2) > 220 * 1024)
+      return fail(SRWCR_EINVAL, "requested tile needs %zu bytes of shared memory",
+                  acc_smem(g, 2));
+    return SRWCR_OK;
+  }
+  static const int cand3[][3] = {{32, 8, 8}, {32, 8, 4}, {32, 4, 4}, {32, 4, 2}, {32, 2, 2},
+                                 {16, 2, 2}, {8, 2, 2}, {8, 1, 1}, {4, 1, 1}};
+  static const int cand2[][3] = {{32, 32, 1}, {32, 16, 1}, {32, 8, 1}, {32, 4, 1},
+                                 {16, 4, 1}, {8, 2, 1}, {4, 1, 1}};
+  const int (*cand)[3] = ndim == 3 ? cand3 : cand2;
+  const int nc = ndim == 3 ? 9 : 7;
+  for (int i = 0; i < nc; ++i) {
+    set_tile(g, ndim, cand[i][0], cand[i][1], cand[i][2]);
+    if (acc_smem(g, 2) <= kSmemBudget) return SRWCR_OK;
+  }
+  for (int i = 0; i < nc; ++i) {
+    set_tile(g, ndim, cand[i][0], cand[i][1], cand[i][2]);
+    if (acc_smem(g, 2) <= 220 * 1024) return SRWCR_OK;
+  }
+  return fail(SRWCR_EINVAL, "no voxel tile fits the shared-memory histogram (nbins=%d)",
+              g.nbins);
+}
+
+srwcr_status make_geo(const srwcr_config& cfg, const int dims[3], Geo& g) {
+  memset(&g, 0, sizeof g);
+  const int nd = cfg.ndim;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = d < nd ? dims[d] : 1;
+    if (d < nd && g.n[d] < 2) return fail(SRWCR_EINVAL, "dimension %d has %d < 2 voxels", d, g.n[d]);
+    g.fsp[d] = d < nd ? cfg.ffd_spacing[d] : 1;
+    g.nf[d] = d < nd ? (g.n[d] - 1) / g.fsp[d] + 4 : 1;
+    if (d < nd && cfg.sbin_intervals[d] > 0) {
+      if (cfg.sbin_intervals[d] > g.n[d])
+        return fail(SRWCR_EINVAL, "more spatial-bin intervals than voxels on axis %d", d);
+      g.sbn[d] = g.n[d];
+      g.sbd[d] = cfg.sbin_intervals[d];
+    } else {
+      g.sbn[d] = d < nd ? g.fsp[d] : 1;
+      g.sbd[d] = 1;
+    }
+    if ((long long)(g.n[d] - 1) * g.sbd[d] >= (1LL << 31))
+      return fail(SRWCR_EINVAL, "spatial-bin arithmetic would overflow on axis %d", d);
+    g.nsb[d] = d < nd ? (int)((long long)(g.n[d] - 1) * g.sbd[d] / g.sbn[d]) + 4 : 1;
+  }
+  g.nbins = cfg.n_intensity_bins;
+  g.nvox = (long long)g.n[0] * g.n[1] * g.n[2];
+  g.ncoef = (long long)g.nf[0] * g.nf[1] * g.nf[2];
+  g.R = (long long)g.nsb[0] * g.nsb[1] * g.nsb[2];
+  return choose_tile(g, nd, cfg.tile);
+}
+
+// Fixed-point scales: every per-(r,a) total stays below 2^62.  A bin's
+// support covers at most ~4 spacings per axis, so totals are bounded by that
+// box's voxel count times the largest per-voxel term (1, L, L^2).
+void fixed_scales(const Geo& g, int ndim, double* sP, double* s1, double* s2) {
+  double box = 1.0;
+  for (int d = 0; d < ndim; ++d) {
+    const double span = std::min((double)g.n[d], std::floor(4.0 * g.sbn[d] / g.sbd[d]) + 2.0);
+    box *= span;
+  }
+  box = std::min(box, (double)g.nvox);
+  const double L = g.nbins - 1;
+  *sP = std::ldexp(1.0, 62 - ceil_log2(box));
+  *s1 = std::ldexp(1.0, 62 - ceil_log2(box * L));
+  *s2 = std::ldexp(1.0, 62 - ceil_log2(box * L * L));
+}
+
+template <typename T>
+srwcr_status launch_accumulate(srwcr_ctx* ctx, Level& lv, const float* c, bool stat, float s0,
+                               float s1) {
+  const int nblk = lv.g.ntile[0] * lv.g.ntile[1] * lv.g.ntile[2];
+  const T* A = (const T*)lv.A;
+  const T* M = (const T*)lv.M;
+  const size_t sm = stat ? acc_smem(lv.g, 1) : lv.smem_acc;
+  if (ctx->cfg.ndim == 3) {
+    if (stat) k_accumulate<3, T, true><<<nblk, kBlock, sm, ctx->stream>>>(lv.g, A, M, c, lv.S, s0, s1);
+    else k_accumulate<3, T, false><<<nblk, kBlock, sm, ctx->stream>>>(lv.g, A, M, c, lv.S, s0, s1);
+  } else {
+    if (stat) k_accumulate<2, T, true><<<nblk, kBlock, sm, ctx->stream>>>(lv.g, A, M, c, lv.S, s0, s1);
+    else k_accumulate<2, T, false><<<nblk, kBlock, sm, ctx->stream>>>(lv.g, A, M, c, lv.S, s0, s1);
+  }
+  CKL();
+  return SRWCR_OK;
+}
+
+template <typename T>
+srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g) {
+  const int nblk = lv.g.ntile[0] * lv.g.ntile[1] * lv.g.ntile[2];
+  const float invZ = (float)(1.0 / lv.Z);
+  if (ctx->cfg.ndim == 3)
+    k_adjoint<3, T><<<nblk, kBlock, lv.smem_adj, ctx->stream>>>(
+        lv.g, (const T*)lv.A, (const T*)lv.M, c, lv.U, lv.V, lv.X, gD, invZ, g);
+  else
+    k_adjoint<2, T><<<nblk, kBlock, lv.smem_adj, ctx->stream>>>(
+        lv.g, (const T*)lv.A, (const T*)lv.M, c, lv.U, lv.V, lv.X, gD, invZ, g);
+  CKL();
+  return SRWCR_OK;
+}
+
+template <typename T>
+srwcr_status set_smem_limits() {
+  const int mx = 227 * 1024;
+  CK(cudaFuncSetAttribute(k_accumulate<3, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate<3, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate<2, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate<2, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  return SRWCR_OK;
+}
+
+bool is_bf16(const srwcr_ctx* ctx) { return ctx->cfg.storage == SRWCR_STORAGE_BF16; }
+
+// Kernel kinds reported by srwcr_profile_read.
+enum { kProfAccumulate = 0, kProfFinalize = 1, kProfAdjoint = 2, kProfKinds = 3 };
+
+cudaEvent_t prof_begin(srwcr_ctx* ctx) {
+  if (!ctx->profiling) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  cudaEventRecord(e, ctx->stream);
+  return e;
+}
+
+void prof_end(srwcr_ctx* ctx, int kind, cudaEvent_t begin) {
+  if (!ctx->profiling || !begin) return;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaEventDestroy(begin); return; }
+  cudaEventRecord(e, ctx->stream);
+  ctx->prof.push_back({kind, {begin, e}});
+}
+
+srwcr_status check_level(const srwcr_ctx* ctx, int level) {
+  if (!ctx) return fail(SRWCR_EINVAL, "null context");
+  if (level < 0 || level >= ctx->nlev)
+    return fail(SRWCR_EINVAL, "level %d out of range [0, %d)", level, ctx->nlev);
+  return SRWCR_OK;
+}
+
+// (a) + (b): value into lv.D, tables into lv.U/V/X.
+srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c) {
+  const size_t sbytes = (size_t)lv.g.R * lv.g.nbins * 2 * sizeof(unsigned long long);
+  CK(cudaMemsetAsync(lv.S, 0, sbytes, ctx->stream));
+  cudaEvent_t ev = prof_begin(ctx);
+  srwcr_status st = is_bf16(ctx) ? launch_accumulate<__nv_bfloat16>(ctx, lv, c, false, lv.s1, lv.s2)
+                                 : launch_accumulate<float>(ctx, lv, c, false, lv.s1, lv.s2);
+  if (st != SRWCR_OK) return st;
+  prof_end(ctx, kProfAccumulate, ev);
+  const long long warps = lv.g.R;
+  const int fblk = (int)((warps * 32 + kBlock - 1) / kBlock);
+  ev = prof_begin(ctx);
+  k_finalize<<<fblk, kBlock, 0, ctx->stream>>>(lv.g, lv.P, lv.S, 1.0 / lv.s1, 1.0 / lv.s2,
+                                               1.0 / lv.Z, lv.U, lv.V, lv.X, lv.Dr, lv.stats);
+  CKL();
+  k_reduce_D<<<1, 1024, 0, ctx->stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg);
+  CKL();
+  prof_end(ctx, kProfFinalize, ev);
+  ctx->launches += 3;
+  lv.tables = true;
+  return SRWCR_OK;
+}
+
+srwcr_status run_grad(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g) {
+  CK(cudaMemsetAsync(g, 0, sizeof(float) * lv.g.ncoef * ctx->cfg.ndim, ctx->stream));
+  cudaEvent_t ev = prof_begin(ctx);
+  RET_IF(is_bf16(ctx) ? launch_adjoint<__nv_bfloat16>(ctx, lv, c, gD, g)
+                      : launch_adjoint<float>(ctx, lv, c, gD, g));
+  prof_end(ctx, kProfAdjoint, ev);
+  ctx->launches += 1;
+  return SRWCR_OK;
+}
+
+__global__ void k_check_finite(const float* __restrict__ c, long long n, int* __restrict__ flag) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(c[i])) flag[0] = 1;
+}
+
+srwcr_status check_finite_async(srwcr_ctx* ctx, const float* c, long long n) {
+  CK(cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int), ctx->stream));
+  k_check_finite<<<(int)std::min<long long>(1024, (n + 255) / 256), 256, 0, ctx->stream>>>(c, n, ctx->flag_dev);
+  CKL();
+  CK(cudaMemcpyAsync(ctx->flag_host, ctx->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  return SRWCR_OK;
+}
+
+srwcr_status finish_sync(srwcr_ctx* ctx, Level& lv, double* D_host) {
+  CK(cudaMemcpyAsync(ctx->D_host, lv.D, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->flag_host[0]) return fail(SRWCR_ENUMERIC, "non-finite FFD coefficients");
+  if (!std::isfinite(ctx->D_host[0])) return fail(SRWCR_ENUMERIC, "non-finite SRWCR value");
+  if (D_host) *D_host = ctx->D_host[0];
+  return SRWCR_OK;
+}
+
+void free_level(Level& lv) {
+  void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  lv = Level();
+}
+
+template <typename T>
+srwcr_status normalise_into(srwcr_ctx* ctx, const float* src_dev, long long n, T* out,
+                            float* part, int nparts) {
+  k_minmax_partial<<<nparts, 256, 0, ctx->stream>>>(src_dev, n, part);
+  CKL();
+  const double L = ctx->cfg.n_intensity_bins - 1;
+  k_normalise<T><<<1024, 256, 0, ctx->stream>>>(src_dev, n, part, nparts, L, out);
+  CKL();
+  return SRWCR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* srwcr_last_error(void) { return g_err.c_str(); }
+
+void srwcr_destroy(srwcr_ctx* ctx) {
+  if (!ctx) return;
+  for (int l = 0; l < ctx->nlev; ++l) free_level(ctx->lev[l]);
+  if (ctx->D_host) cudaFreeHost(ctx->D_host);
+  if (ctx->flag_host) cudaFreeHost(ctx->flag_host);
+  if (ctx->flag_dev) cudaFree(ctx->flag_dev);
+  if (ctx->c_stage) cudaFree(ctx->c_stage);
+  if (ctx->g_stage) cudaFree(ctx->g_stage);
+  if (ctx->D_stage) cudaFree(ctx->D_stage);
+  for (auto& p : ctx->prof) {
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  delete ctx;
+}
+
+static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, const float* moving,
+                                int on_device, void* stream, srwcr_ctx* ctx) {
+  ctx->cfg = *cfg;
+  ctx->stream = (cudaStream_t)stream;
+  CK(cudaGetDevice(&ctx->device));
+  CK(cudaMallocHost((void**)&ctx->D_host, sizeof(double)));
+  CK(cudaMallocHost((void**)&ctx->flag_host, sizeof(int)));
+  ctx->flag_host[0] = 0;
+  CK(cudaMalloc((void**)&ctx->flag_dev, sizeof(int)));
+  RET_IF(set_smem_limits<float>());
+  RET_IF(set_smem_limits<__nv_bfloat16>());
+  const size_t esz = is_bf16(ctx) ? 2 : 4;
+
+  // Level geometry: level l halves every axis of level l-1 (floor).
+  int dims[3] = {cfg->dims[0], cfg->dims[1], cfg->ndim == 3 ? cfg->dims[2] : 1};
+  ctx->nlev = cfg->pyramid_levels;
+  for (int l = 0; l < ctx->nlev; ++l) {
+    if (l > 0)
+      for (int d = 0; d < cfg->ndim; ++d) dims[d] /= 2;
+    Level& lv = ctx->lev[l];
+    RET_IF(make_geo(*cfg, dims, lv.g));
+    const Geo& g = lv.g;
+    CK(cudaMalloc(&lv.A, esz * g.nvox));
+    CK(cudaMalloc(&lv.M, esz * g.nvox));
+    CK(cudaMalloc((void**)&lv.S, sizeof(unsigned long long) * g.R * g.nbins * 2));
+    CK(cudaMalloc((void**)&lv.P, sizeof(double) * g.R * g.nbins));
+    CK(cudaMalloc((void**)&lv.U, sizeof(float) * g.R));
+    CK(cudaMalloc((void**)&lv.V, sizeof(float) * g.R));
+    CK(cudaMalloc((void**)&lv.X, sizeof(float) * g.R * g.nbins));
+    CK(cudaMalloc((void**)&lv.Dr, sizeof(double) * g.R));
+    CK(cudaMalloc((void**)&lv.stats, sizeof(double) * g.R * 4));
+    CK(cudaMalloc((void**)&lv.D, sizeof(double)));
+    CK(cudaMalloc((void**)&lv.ndeg, sizeof(int)));
+    lv.smem_acc = acc_smem(g, 2);
+    lv.smem_adj = sizeof(float) * cfg->ndim * g.hf[0] * g.hf[1] * g.hf[2];
+  }
+
+  // Normalise the two images into level 0 (Sec. II: [0, L_eps]).
+  const long long n0 = ctx->lev[0].g.nvox;
+  float* tmp = nullptr;
+  float* part = nullptr;
+  const int nparts = 512;
+  CK(cudaMalloc((void**)&tmp, sizeof(float) * n0));
+  cudaError_t e = cudaMalloc((void**)&part, sizeof(float) * 2 * nparts);
+  if (e != cudaSuccess) { cudaFree(tmp); return fail(SRWCR_ENOMEM, "cudaMalloc failed"); }
+  srwcr_status st = SRWCR_OK;
+  const float* src[2] = {fixed, moving};
+  void* dst[2] = {ctx->lev[0].A, ctx->lev[0].M};
+  for (int im = 0; im < 2 && st == SRWCR_OK; ++im) {
+    e = cudaMemcpyAsync(tmp, src[im], sizeof(float) * n0,
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) { st = fail(SRWCR_ECUDA, "image upload: %s", cudaGetErrorString(e)); break; }
+    // Reject constant images (max == min) before dividing by zero.
+    k_minmax_partial<<<nparts, 256, 0, ctx->stream>>>(tmp, n0, part);
+    float hpart[2 * nparts];
+    e = cudaMemcpyAsync(hpart, part, sizeof hpart, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { st = fail(SRWCR_ECUDA, "min/max: %s", cudaGetErrorString(e)); break; }
+    float mn = INFINITY, mx = -INFINITY;
+    for (int i = 0; i < nparts; ++i) { mn = std::min(mn, hpart[2 * i]); mx = std::max(mx, hpart[2 * i + 1]); }
+    if (!(mx > mn) || !std::isfinite(mn) || !std::isfinite(mx)) {
+      st = fail(SRWCR_EINVAL, "%s image is constant or not finite", im ? "moving" : "fixed");
+      break;
+    }
+    st = is_bf16(ctx) ? normalise_into(ctx, tmp, n0, (__nv_bfloat16*)dst[im], part, nparts)
+                      : normalise_into(ctx, tmp, n0, (float*)dst[im], part, nparts);
+    if (st == SRWCR_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+      st = fail(SRWCR_ECUDA, "normalisation failed");
+  }
+  cudaFree(tmp);
+  cudaFree(part);
+  RET_IF(st);
+
+  // Pyramid.
+  for (int l = 1; l < ctx->nlev; ++l) {
+    const Geo& gi = ctx->lev[l - 1].g;
+    const Geo& go = ctx->lev[l].g;
+    for (int im = 0; im < 2; ++im) {
+      const void* in = im ? ctx->lev[l - 1].M : ctx->lev[l - 1].A;
+      void* out = im ? ctx->lev[l].M : ctx->lev[l].A;
+      if (cfg->ndim == 3) {
+        if (is_bf16(ctx)) k_downsample<3, __nv_bfloat16><<<1024, 256, 0, ctx->stream>>>((const __nv_bfloat16*)in, gi.n[0], gi.n[1], (__nv_bfloat16*)out, go.n[0], go.n[1], go.n[2]);
+        else k_downsample<3, float><<<1024, 256, 0, ctx->stream>>>((const float*)in, gi.n[0], gi.n[1], (float*)out, go.n[0], go.n[1], go.n[2]);
+      } else {
+        if (is_bf16(ctx)) k_downsample<2, __nv_bfloat16><<<1024, 256, 0, ctx->stream>>>((const __nv_bfloat16*)in, gi.n[0], gi.n[1], (__nv_bfloat16*)out, go.n[0], go.n[1], go.n[2]);
+        else k_downsample<2, float><<<1024, 256, 0, ctx->stream>>>((const float*)in, gi.n[0], gi.n[1], (float*)out, go.n[0], go.n[1], go.n[2]);
+      }
+      CKL();
+    }
+  }
+
+  // Static fixed-image statistics P[r][a] and Z = sum P.
+  for (int l = 0; l < ctx->nlev; ++l) {
+    Level& lv = ctx->lev[l];
+    double sP, s1, s2;
+    fixed_scales(lv.g, cfg->ndim, &sP, &s1, &s2);
+    lv.s1 = (float)s1;
+    lv.s2 = (float)s2;
+    CK(cudaMemsetAsync(lv.S, 0, sizeof(unsigned long long) * lv.g.R * lv.g.nbins, ctx->stream));
+    RET_IF(is_bf16(ctx) ? launch_accumulate<__nv_bfloat16>(ctx, lv, nullptr, true, (float)sP, 0.f)
+                        : launch_accumulate<float>(ctx, lv, nullptr, true, (float)sP, 0.f));
+    const long long n = lv.g.R * lv.g.nbins;
+    k_fixed_to_double<<<256, 256, 0, ctx->stream>>>(lv.S, 1.0 / sP, lv.P, n);
+    CKL();
+    double* hP = (double*)malloc(sizeof(double) * n);
+    if (!hP) return fail(SRWCR_ENOMEM, "host allocation failed");
+    e = cudaMemcpyAsync(hP, lv.P, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { free(hP); return fail(SRWCR_ECUDA, "P readback: %s", cudaGetErrorString(e)); }
+    double Z = 0.0;
+    for (long long i = 0; i < n; ++i) Z += hP[i];
+    free(hP);
+    lv.Z = Z;
+    if (!(Z > 0.0)) return fail(SRWCR_EINVAL, "empty fixed-image statistics at level %d", l);
+  }
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_create(const srwcr_config* cfg, const float* fixed, const float* moving,
+                          int images_on_device, void* stream, srwcr_ctx** out) {
+  if (!out) return fail(SRWCR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !fixed || !moving) return fail(SRWCR_EINVAL, "null argument");
+  if (cfg->ndim != 2 && cfg->ndim != 3) return fail(SRWCR_EINVAL, "ndim must be 2 or 3");
+  if (cfg->n_intensity_bins < 2 || cfg->n_intensity_bins > 256)
+    return fail(SRWCR_EINVAL, "n_intensity_bins must be in [2, 256]");
+  if (cfg->storage != SRWCR_STORAGE_F32 && cfg->storage != SRWCR_STORAGE_BF16)
+    return fail(SRWCR_EINVAL, "unknown storage type");
+  if (cfg->pyramid_levels < 1 || cfg->pyramid_levels > 4)
+    return fail(SRWCR_EINVAL, "pyramid_levels must be in [1, 4]");
+  for (int d = 0; d < cfg->ndim; ++d) {
+    if (cfg->dims[d] < 2 || cfg->dims[d] > 65535) return fail(SRWCR_EINVAL, "dims[%d] out of range", d);
+    if (cfg->ffd_spacing[d] < 1 || cfg->ffd_spacing[d] > cfg->dims[d])
+      return fail(SRWCR_EINVAL, "ffd_spacing[%d] out of range", d);
+    if (cfg->sbin_intervals[d] < 0) return fail(SRWCR_EINVAL, "negative sbin_intervals");
+    if ((cfg->dims[d] >> (cfg->pyramid_levels - 1)) < 2)
+      return fail(SRWCR_EINVAL, "too many pyramid levels for dims[%d]", d);
+  }
+  if (cfg->tile[0] < 0 || cfg->tile[1] < 0 || cfg->tile[2] < 0)
+    return fail(SRWCR_EINVAL, "negative tile size");
+  srwcr_ctx* ctx = new (std::nothrow) srwcr_ctx();
+  if (!ctx) return fail(SRWCR_ENOMEM, "host allocation failed");
+  srwcr_status st = create_impl(cfg, fixed, moving, images_on_device, stream, ctx);
+  if (st != SRWCR_OK) {
+    std::string keep = g_err;
+    srwcr_destroy(ctx);
+    g_err = keep;
+    return st;
+  }
+  *out = ctx;
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_level_info(const srwcr_ctx* ctx, int level, srwcr_level_desc* out) {
+  RET_IF(check_level(ctx, level));
+  if (!out) return fail(SRWCR_EINVAL, "out is NULL");
+  const Geo& g = ctx->lev[level].g;
+  for (int d = 0; d < 3; ++d) {
+    out->dims[d] = g.n[d];
+    out->ffd_nodes[d] = g.nf[d];
+    out->sbins[d] = g.nsb[d];
+    out->tile[d] = g.tile[d];
+  }
+  out->n_voxels = g.nvox;
+  out->n_params = g.ncoef * ctx->cfg.ndim;
+  out->n_regions = g.R;
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_value(srwcr_ctx* ctx, int level, const float* c_dev, double* D_host) {
+  RET_IF(check_level(ctx, level));
+  if (!c_dev) return fail(SRWCR_EINVAL, "c_dev is NULL");
+  Level& lv = ctx->lev[level];
+  RET_IF(check_finite_async(ctx, c_dev, lv.g.ncoef * ctx->cfg.ndim));
+  RET_IF(run_value(ctx, lv, c_dev));
+  return finish_sync(ctx, lv, D_host);
+}
+
+srwcr_status srwcr_value_and_grad(srwcr_ctx* ctx, int level, const float* c_dev, double* D_host,
+                                  float* g_dev) {
+  RET_IF(check_level(ctx, level));
+  if (!c_dev || !g_dev) return fail(SRWCR_EINVAL, "null device pointer");
+  Level& lv = ctx->lev[level];
+  RET_IF(check_finite_async(ctx, c_dev, lv.g.ncoef * ctx->cfg.ndim));
+  RET_IF(run_value(ctx, lv, c_dev));
+  RET_IF(run_grad(ctx, lv, c_dev, nullptr, g_dev));
+  return finish_sync(ctx, lv, D_host);
+}
+
+srwcr_status srwcr_value_and_grad_async(srwcr_ctx* ctx, int level, const float* c_dev,
+                                        double* D_dev, float* g_dev) {
+  RET_IF(check_level(ctx, level));
+  if (!c_dev || !g_dev || !D_dev) return fail(SRWCR_EINVAL, "null device pointer");
+  Level& lv = ctx->lev[level];
+  RET_IF(run_value(ctx, lv, c_dev));
+  RET_IF(run_grad(ctx, lv, c_dev, nullptr, g_dev));
+  CK(cudaMemcpyAsync(D_dev, lv.D, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_value_and_grad_host(srwcr_ctx* ctx, int level, const float* c_host,
+                                       double* D_host, float* g_host) {
+  RET_IF(check_level(ctx, level));
+  if (!c_host || !g_host) return fail(SRWCR_EINVAL, "null host pointer");
+  Level& lv = ctx->lev[level];
+  const int64_t np = lv.g.ncoef * ctx->cfg.ndim;
+  if (ctx->stage_len < np) {
+    if (ctx->c_stage) cudaFree(ctx->c_stage);
+    if (ctx->g_stage) cudaFree(ctx->g_stage);
+    ctx->c_stage = ctx->g_stage = nullptr;
+    CK(cudaMalloc((void**)&ctx->c_stage, sizeof(float) * np));
+    CK(cudaMalloc((void**)&ctx->g_stage, sizeof(float) * np));
+    ctx->stage_len = np;
+  }
+  CK(cudaMemcpyAsync(ctx->c_stage, c_host, sizeof(float) * np, cudaMemcpyHostToDevice, ctx->stream));
+  RET_IF(check_finite_async(ctx, ctx->c_stage, np));
+  RET_IF(run_value(ctx, lv, ctx->c_stage));
+  RET_IF(run_grad(ctx, lv, ctx->c_stage, nullptr, ctx->g_stage));
+  CK(cudaMemcpyAsync(g_host, ctx->g_stage, sizeof(float) * np, cudaMemcpyDeviceToHost, ctx->stream));
+  return finish_sync(ctx, lv, D_host);
+}
+
+srwcr_status srwcr_forward(srwcr_ctx* ctx, int level, const float* c_dev, double* D_dev) {
+  RET_IF(check_level(ctx, level));
+  if (!c_dev || !D_dev) return fail(SRWCR_EINVAL, "null device pointer");
+  Level& lv = ctx->lev[level];
+  RET_IF(run_value(ctx, lv, c_dev));
+  CK(cudaMemcpyAsync(D_dev, lv.D, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_backward(srwcr_ctx* ctx, int level, const float* c_dev, const float* gD_dev,
+                            float* g_dev) {
+  RET_IF(check_level(ctx, level));
+  if (!c_dev || !g_dev) return fail(SRWCR_EINVAL, "null device pointer");
+  Level& lv = ctx->lev[level];
+  if (!lv.tables) return fail(SRWCR_EINVAL, "srwcr_backward before srwcr_forward at level %d", level);
+  return run_grad(ctx, lv, c_dev, gD_dev, g_dev);
+}
+
+srwcr_status srwcr_region_stats(srwcr_ctx* ctx, int level, double* out, int64_t* n_degenerate) {
+  RET_IF(check_level(ctx, level));
+  Level& lv = ctx->lev[level];
+  if (!lv.tables) return fail(SRWCR_EINVAL, "no evaluation at level %d yet", level);
+  if (out) CK(cudaMemcpyAsync(out, lv.stats, sizeof(double) * 4 * lv.g.R, cudaMemcpyDeviceToHost, ctx->stream));
+  int nd = 0;
+  CK(cudaMemcpyAsync(ctx->flag_host, lv.ndeg, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  nd = ctx->flag_host[0];
+  ctx->flag_host[0] = 0;
+  if (n_degenerate) *n_degenerate = nd;
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_debug_bins(srwcr_ctx* ctx, int level, int32_t* out_dev) {
+  RET_IF(check_level(ctx, level));
+  if (!out_dev) return fail(SRWCR_EINVAL, "out_dev is NULL");
+  Level& lv = ctx->lev[level];
+  if (ctx->cfg.ndim == 3) {
+    if (is_bf16(ctx)) k_debug_bins<3, __nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(lv.g, (const __nv_bfloat16*)lv.A, out_dev);
+    else k_debug_bins<3, float><<<1024, 256, 0, ctx->stream>>>(lv.g, (const float*)lv.A, out_dev);
+  } else {
+    if (is_bf16(ctx)) k_debug_bins<2, __nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(lv.g, (const __nv_bfloat16*)lv.A, out_dev);
+    else k_debug_bins<2, float><<<1024, 256, 0, ctx->stream>>>(lv.g, (const float*)lv.A, out_dev);
+  }
+  CKL();
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_debug_warp(srwcr_ctx* ctx, int level, const float* c_dev, float* out_dev) {
+  RET_IF(check_level(ctx, level));
+  if (!c_dev || !out_dev) return fail(SRWCR_EINVAL, "null device pointer");
+  Level& lv = ctx->lev[level];
+  if (ctx->cfg.ndim == 3) {
+    if (is_bf16(ctx)) k_debug_warp<3, __nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(lv.g, (const __nv_bfloat16*)lv.M, c_dev, out_dev);
+    else k_debug_warp<3, float><<<1024, 256, 0, ctx->stream>>>(lv.g, (const float*)lv.M, c_dev, out_dev);
+  } else {
+    if (is_bf16(ctx)) k_debug_warp<2, __nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(lv.g, (const __nv_bfloat16*)lv.M, c_dev, out_dev);
+    else k_debug_warp<2, float><<<1024, 256, 0, ctx->stream>>>(lv.g, (const float*)lv.M, c_dev, out_dev);
+  }
+  CKL();
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_set_profiling(srwcr_ctx* ctx, int enable) {
+  if (!ctx) return fail(SRWCR_EINVAL, "null context");
+  ctx->profiling = enable != 0;
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_profile_read(srwcr_ctx* ctx, double* ms, int64_t* counts, int64_t* launches,
+                                int reset) {
+  if (!ctx) return fail(SRWCR_EINVAL, "null context");
+  CK(cudaStreamSynchronize(ctx->stream));
+  double acc[kProfKinds] = {0, 0, 0};
+  int64_t cnt[kProfKinds] = {0, 0, 0};
+  for (auto& p : ctx->prof) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, p.second.first, p.second.second));
+    acc[p.first] += t;
+    cnt[p.first] += 1;
+  }
+  for (int k = 0; k < kProfKinds; ++k) {
+    if (ms) ms[k] = acc[k];
+    if (counts) counts[k] = cnt[k];
+  }
+  if (launches) *launches = ctx->launches;
+  if (reset) {
+    for (auto& p : ctx->prof) {
+      cudaEventDestroy(p.second.first);
+      cudaEventDestroy(p.second.second);
+    }
+    ctx->prof.clear();
+    ctx->launches = 0;
+  }
+  return SRWCR_OK;
+}
+
+void srwcr_lbfgs_default_opts(srwcr_lbfgs_opts* o) {
+  if (!o) return;
+  o->m = 5;
+  o->max_iter[0] = 120; o->max_iter[1] = 200; o->max_iter[2] = 200; o->max_iter[3] = 200;
+  o->stable_window = 20;
+  o->stable_rtol = 1e-5;
+  o->max_ls = 20;
+  o->c1 = 1e-4;
+  o->c2 = 0.9;
+}
+
+}  // extern "C"
+
+#include "lbfgs.cuh"

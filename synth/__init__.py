@@ -348,3 +348,36 @@ def downsample2(img: np.ndarray) -> np.ndarray:
             for dx in (0, 1):
                 acc += v[dz::2, dy::2, dx::2]
     return (acc / 8.0).astype(np.float32)
+
+
+def small_pair(kind: str, dims, ffd_spacing, sigma: float, seed: int):
+    """A fixed/moving pair of any size with one of the workload recipes:
+    'ellipse' (2-D phantom, nonlinear intensity map with bias), 'ct' (3-D
+    thoracic CT with 10% drift), 'oct' (layered speckle volume) or 'pet'
+    (label volume vs. smoothed Poisson uptake).  dims = (nx, ny[, nz])."""
+    rng = np.random.default_rng(seed)
+    if kind == "ellipse":
+        nx, ny = dims
+        n = max(nx, ny)
+        f = _ellipses_2d(n, rng)[:ny, :nx] + rng.normal(0, 0.02, (ny, nx))
+        fw = random_ffd_warp(f.astype(np.float32), ffd_spacing, sigma, rng).astype(np.float64)
+        m = 1.0 - fw * fw + 0.1 * (np.arange(nx)[None, :] / nx)
+        return f.astype(np.float32), m.astype(np.float32)
+    nx, ny, nz = dims
+    if kind == "ct":
+        f = _ct_phantom(nx, ny, nz, rng, n_vessels=8)
+        m = np.clip(1.10 * random_ffd_warp(f.astype(np.float32), ffd_spacing, sigma, rng),
+                    -1000.0, 1500.0)
+    elif kind == "oct":
+        n = max(nx, ny, nz)
+        f = _oct_phantom(n, rng)[:nz, :ny, :nx]
+        m = random_ffd_warp(f.astype(np.float32), ffd_spacing, sigma, rng)
+    elif kind == "pet":
+        n = max(nx, ny, nz)
+        lab = _label_phantom(n, rng)[:nz, :ny, :nx]
+        up = rng.uniform(1.0, 100.0, 5)[lab.astype(int)]
+        up = rng.poisson(ndimage.gaussian_filter(up, 3.0 / 2.3548)).astype(np.float32)
+        f, m = lab, random_ffd_warp(up, ffd_spacing, sigma, rng)
+    else:
+        raise ValueError(kind)
+    return np.ascontiguousarray(f, np.float32), np.ascontiguousarray(m, np.float32)

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP32 path): SRWCR value relative 1e-5; gradient norm relative
+1e-4; gradient elementwise within 1e-3 of the largest entry (isolated voxels
+whose warped intensity sits within FP32 rounding of an integer may take the
+other one-sided Parzen derivative, Eq. 19); voxel-to-bin indices bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+D_RTOL = 1e-5
+GNORM_RTOL = 1e-4
+G_ELEM = 1e-3
+
+
+def engine_for(prob, fixed, moving, storage="f32", **kw):
+    import paper_1804_05061_b300 as eng
+    return eng.from_problem(prob, fixed, moving, storage=storage, **kw)
+
+
+def oracle_eval(prob, fixed, moving, c, storage="f32", grad=True):
+    geo = oracle.Geometry.from_problem(prob)
+    A, M = oracle.prepare(fixed, moving, prob.n_bins, storage)
+    st = oracle.value(geo, A, M, c)
+    g = oracle.gradient(geo, A, M, c, st) if grad else None
+    return st, g, geo, A, M
+
+
+SMALL = [
+    ("ellipse_2d_ragged", "ellipse", synth.problem(2, (100, 77), (7, 7), (3, 2), 16), 1.5),
+    ("ct_3d_ragged", "ct", synth.problem(3, (70, 45, 23), (6, 5, 4), (3, 2, 2), 24), 1.5),
+    ("oct_ffd_grid_bins", "oct", synth.problem(3, (41, 37, 29), (5, 5, 5), (0, 0, 0), 32), 1.0),
+    ("ct_128_bins", "ct", synth.problem(3, (64, 48, 40), (5, 5, 5), (2, 2, 1), 128), 1.5),
+    ("pet_labels", "pet", synth.problem(3, (48, 40, 36), (8, 8, 8), (0, 0, 0), 32), 2.0),
+]
+
+
+@pytest.fixture(scope="module")
+def small_cases():
+    out = {}
+    for i, (name, kind, prob, sig) in enumerate(SMALL):
+        f, m = synth.small_pair(kind, prob.dims[:prob.ndim], prob.ffd_spacing[:prob.ndim], 2.0, 100 + i)
+        c = synth.coefficients(prob, 200 + i, sig)
+        out[name] = (prob, f, m, c)
+    return out
+
+
+@pytest.mark.parametrize("name", [s[0] for s in SMALL])
+def test_value_gradient_and_regions_match_oracle(small_cases, name):
+    prob, f, m, c = small_cases[name]
+    e = engine_for(prob, f, m)
+    D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+    stats, ndeg = e.region_stats()
+    st, go, _, _, _ = oracle_eval(prob, f, m, c)
+    assert abs(D - st.D) <= D_RTOL * abs(st.D), (D, st.D)
+    assert ndeg == st.n_degenerate
+    v = st.valid.astype(bool)
+    assert np.allclose(stats[:, 0], st.pr, rtol=1e-9, atol=1e-15)
+    assert np.allclose(stats[v, 1], st.var_r[v], rtol=1e-5)
+    assert np.allclose(stats[v, 2], st.cr[v], rtol=0, atol=1e-5)
+    g = g.cpu().numpy().astype(np.float64)
+    gn, gon = np.linalg.norm(g), np.linalg.norm(go)
+    assert abs(gn - gon) <= GNORM_RTOL * gon, (gn, gon)
+    assert np.abs(g - go).max() <= G_ELEM * np.abs(go).max()
+
+
+@pytest.mark.parametrize("name", ["ellipse_2d_ragged", "oct_ffd_grid_bins", "ct_128_bins"])
+def test_voxel_to_bin_indexing_is_bit_exact(small_cases, name):
+    prob, f, m, c = small_cases[name]
+    e = engine_for(prob, f, m)
+    bins = e.debug_bins().cpu().numpy()
+    geo = oracle.Geometry.from_problem(prob)
+    A, _ = oracle.prepare(f, m, prob.n_bins)
+    nx, ny, _ = prob.dims
+    nbx, nby, _ = geo.sbins()
+    idx = np.arange(prob.n_voxels)
+    x, y, z = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    L = prob.n_bins - 1
+    first = np.array([oracle.spatial_weights(geo, int(a), int(b), int(cc))[0][0]
+                      for a, b, cc in zip(x, y, z)])
+    assert np.array_equal(bins[:, 0], first % nbx)
+    assert np.array_equal(bins[:, 1], (first // nbx) % nby)
+    assert np.array_equal(bins[:, 2], first // (nbx * nby))
+    assert np.array_equal(bins[:, 3], np.minimum(np.floor(A), L - 1).astype(np.int64))
+
+
+@pytest.mark.parametrize("name", ["ellipse_2d_ragged", "ct_3d_ragged"])
+def test_warp_matches_oracle(small_cases, name):
+    prob, f, m, c = small_cases[name]
+    e = engine_for(prob, f, m)
+    B = e.debug_warp(torch.from_numpy(c).cuda()).cpu().numpy()
+    geo = oracle.Geometry.from_problem(prob)
+    _, M = oracle.prepare(f, m, prob.n_bins)
+    Bo, _ = oracle.warp(geo, M, c)
+    assert np.abs(B - Bo).max() <= 2e-5 * (prob.n_bins - 1)
+
+
+def test_bf16_storage_matches_oracle_on_rounded_inputs(small_cases):
+    prob, f, m, c = small_cases["pet_labels"]
+    e = engine_for(prob, f, m, storage="bf16")
+    D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+    st, go, _, _, _ = oracle_eval(prob, f, m, c, storage="bf16")
+    assert abs(D - st.D) <= D_RTOL * abs(st.D)
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(np.linalg.norm(g) - np.linalg.norm(go)) <= GNORM_RTOL * np.linalg.norm(go)
+
+
+def test_value_is_deterministic(small_cases):
+    prob, f, m, c = small_cases["ct_3d_ragged"]
+    e = engine_for(prob, f, m)
+    ct = torch.from_numpy(c).cuda()
+    vals = [e.value_and_grad(ct)[0] for _ in range(3)]
+    assert vals[0] == vals[1] == vals[2]
+
+
+def test_value_only_equals_value_of_value_and_grad(small_cases):
+    prob, f, m, c = small_cases["oct_ffd_grid_bins"]
+    e = engine_for(prob, f, m)
+    ct = torch.from_numpy(c).cuda()
+    assert e.value(ct) == e.value_and_grad(ct)[0]
+
+
+def test_host_buffer_entry_point_equals_device_entry_point(small_cases):
+    prob, f, m, c = small_cases["ellipse_2d_ragged"]
+    e = engine_for(prob, f, m)
+    D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+    gh = np.zeros(c.size, np.float32)
+    Dh = e.value_and_grad_host(np.ascontiguousarray(c.ravel()), gh)
+    assert Dh == D
+    assert np.allclose(gh, g.cpu().numpy().ravel(), rtol=1e-5, atol=1e-7 * np.abs(gh).max())
+
+
+def test_exact_functional_dependence_gives_zero_on_gpu():
+    prob = synth.problem(3, (40, 36, 20), (5, 5, 5), (3, 3, 2), 16)
+    rng = np.random.default_rng(3)
+    A = rng.integers(0, 16, prob.image_shape).astype(np.float32)
+    A.flat[0], A.flat[1] = 0, 15
+    f = np.array([(5 * a + 2) % 16 for a in range(16)], np.float32)
+    M = f[A.astype(int)]
+    e = engine_for(prob, A, M)
+    D = e.value(e.zeros())
+    _, ndeg = e.region_stats()
+    assert ndeg == 0
+    assert abs(D) < 1e-7
+
+
+def test_errors_are_reported_not_raised_as_crashes(small_cases):
+    import paper_1804_05061_b300 as eng
+    prob, f, m, c = small_cases["ellipse_2d_ragged"]
+    with pytest.raises(eng.SrwcrError) as ei:
+        engine_for(prob, np.ones_like(f), m)
+    assert ei.value.status == 1
+    e = engine_for(prob, f, m)
+    bad = torch.from_numpy(c).cuda()
+    bad.view(-1)[3] = float("nan")
+    with pytest.raises(eng.SrwcrError) as ei:
+        e.value(bad)
+    assert ei.value.status == 4
+    with pytest.raises(eng.SrwcrError):
+        e.level_info(5)
+    with pytest.raises(ValueError):
+        e.value(torch.zeros(7, device="cuda"))
+    # The context stays usable after a rejected call.
+    D = e.value(torch.from_numpy(c).cuda())
+    assert np.isfinite(D)
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads
+# ---------------------------------------------------------------------------
+def test_c1_full_value_and_gradient():
+    pair = synth.make_pair("c1_2d_128")
+    prob = pair.prob
+    c = synth.coefficients(prob, 1001, 3.0)
+    e = engine_for(prob, pair.fixed, pair.moving)
+    D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+    st, go, _, _, _ = oracle_eval(prob, pair.fixed, pair.moving, c)
+    assert abs(D - st.D) <= D_RTOL * st.D
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(np.linalg.norm(g) - np.linalg.norm(go)) <= GNORM_RTOL * np.linalg.norm(go)
+    assert np.abs(g - go).max() <= G_ELEM * np.abs(go).max()
+
+
+@pytest.fixture(scope="module")
+def c2_case():
+    pair = synth.make_pair("c2_ct_256x256x96")
+    c = synth.coefficients(pair.prob, 2001, 2.0)
+    return pair, c
+
+
+def test_c2_full_value_and_gradient(c2_case):
+    pair, c = c2_case
+    prob = pair.prob
+    e = engine_for(prob, pair.fixed, pair.moving)
+    D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+    st, go, _, _, _ = oracle_eval(prob, pair.fixed, pair.moving, c)
+    assert abs(D - st.D) <= D_RTOL * st.D, (D, st.D)
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(np.linalg.norm(g) - np.linalg.norm(go)) <= GNORM_RTOL * np.linalg.norm(go)
+    assert np.abs(g - go).max() <= G_ELEM * np.abs(go).max()
+
+
+def test_c2_bf16_storage(c2_case):
+    pair, c = c2_case
+    prob = pair.prob
+    e = engine_for(prob, pair.fixed, pair.moving, storage="bf16")
+    D = e.value(torch.from_numpy(c).cuda())
+    st, _, _, _, _ = oracle_eval(prob, pair.fixed, pair.moving, c, storage="bf16", grad=False)
+    assert abs(D - st.D) <= D_RTOL * st.D, (D, st.D)
+
+
+def test_c3_full_value_and_sampled_gradient():
+    pair = synth.make_pair("c3_oct_160")
+    prob = pair.prob
+    c = synth.coefficients(prob, 3001, 1.5)
+    e = engine_for(prob, pair.fixed, pair.moving)
+    D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+    st, _, geo, A, M = oracle_eval(prob, pair.fixed, pair.moving, c, grad=False)
+    assert abs(D - st.D) <= D_RTOL * st.D, (D, st.D)
+    rng = np.random.default_rng(3)
+    idx = rng.choice(prob.n_params, 200, replace=False)
+    go = oracle.gradient_at(geo, A, M, c, st, idx)
+    gs = g.cpu().numpy().ravel()[idx].astype(np.float64)
+    assert np.abs(gs - go).max() <= G_ELEM * np.abs(g.cpu().numpy()).max()
