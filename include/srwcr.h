@@ -132,8 +132,9 @@ srwcr_status srwcr_backward(srwcr_ctx* ctx, int level, const float* c_dev, const
 
 /* Per-region statistics of the last evaluation at `level`, copied to host:
  * out[4*r + 0..3] = p(r), sigma_r^2, CR(A,B|r), contribution p(r)(1-CR_r)
- * (Eqs. 4, 9, 10); degenerate regions (p(r) = 0 or sigma_r^2 <= 1e-9 times
- * the mean square of B) report CR = 0 and contribution 0.
+ * (Eqs. 4, 9, 10); degenerate regions (p(r) = 0, or sigma_r^2 <=
+ * 1e-6 * max(1, mean square of B in the region)) report sigma^2 = CR = 0 and
+ * contribute nothing to the value or the gradient.
  * n_degenerate (may be NULL) receives their number. */
 srwcr_status srwcr_region_stats(srwcr_ctx* ctx, int level, double* out, int64_t* n_degenerate);
 

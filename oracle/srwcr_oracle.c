@@ -24,9 +24,12 @@
  *  - Intensity bins a, b run over 0..L (Eq. 3).  The Parzen derivative in
  *    Eqs. (19)/(27) is taken inside the cell [k, k+1] holding B,
  *    k = min(floor(B), L-1) (see orc_parzen_dkappa).
- *  - A region whose p(r) is 0, or whose variance sigma_r^2 is at most 1e-9
- *    times its mean square intensity, is degenerate: it contributes nothing
- *    to the value or the gradient and is counted.
+ *  - A region whose p(r) is 0, or whose variance sigma_r^2 is at most
+ *    1e-6 * max(1, E_r[b^2]) (an intensity standard deviation below 1e-3 bin
+ *    at unit scale), is degenerate: it contributes nothing to the value or
+ *    the gradient and is counted.  Eqs. (9)-(10) divide by sigma_r^2 and the
+ *    paper does not treat sigma_r^2 -> 0; in such regions 1 - CR_r is a 0/0
+ *    limit decided by voxels of negligible spatial weight.
  *
  * Parity: pinned by the -m "not gpu" tests (closed forms, invariants, brute
  * force on tiny inputs, central finite differences).
@@ -383,7 +386,7 @@ int orc_srwcr_from_pdf(const double* p, int64_t R, int nb, double* D9, double* D
     double var = m2 - mu * mu;
     mu_r_out[r] = mu;
     var_r_out[r] = var;
-    if (!(var > 1e-9 * m2)) { ++ndeg; continue; }
+    if (!(var > 1e-6 * fmax(1.0, m2))) { ++ndeg; continue; }
     valid_out[r] = 1;
     /* Eq. (10): conditional mean and variance given fixed bin a; Eq. (9). */
     double within = 0.0;

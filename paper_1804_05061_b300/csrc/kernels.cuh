@@ -174,7 +174,7 @@ __global__ void k_finalize(const Geo g, const double* __restrict__ P,
     mu = T1 / W;
     ms = T2 / W;
     var = ms - mu * mu;
-    valid = var > 1e-9 * ms;
+    valid = var > 1e-6 * fmax(1.0, ms);  // degenerate: sigma_r^2 -> 0 (0/0 in Eq. 9)
   }
   double Q = 0.0;
   for (int a = lane; a < nb; a += 32) {

@@ -61,9 +61,14 @@ def test_value_gradient_and_regions_match_oracle(small_cases, name):
     assert abs(D - st.D) <= D_RTOL * abs(st.D), (D, st.D)
     assert ndeg == st.n_degenerate
     v = st.valid.astype(bool)
-    assert np.allclose(stats[:, 0], st.pr, rtol=1e-9, atol=1e-15)
-    assert np.allclose(stats[v, 1], st.var_r[v], rtol=1e-5)
-    assert np.allclose(stats[v, 2], st.cr[v], rtol=0, atol=1e-5)
+    # p(r): FP32 products w*h summed exactly in fixed point -> ~1e-7 relative.
+    assert np.allclose(stats[:, 0], st.pr, rtol=1e-6, atol=1e-15)
+    # sigma_r^2 = E[b^2] - mu^2 is formed from FP32 per-voxel moments whose
+    # rounding (~1e-7 of E[b^2]) survives the cancellation: compare on the
+    # scale of E_r[b^2]; CR inherits that error divided by sigma_r^2.
+    ms = st.var_r[v] + st.mu_r[v] ** 2
+    assert np.all(np.abs(stats[v, 1] - st.var_r[v]) <= 1e-6 * np.maximum(ms, 1.0))
+    assert np.all(np.abs(stats[v, 2] - st.cr[v]) <= 1e-6 + 4e-6 * np.maximum(ms, 1.0) / st.var_r[v])
     g = g.cpu().numpy().astype(np.float64)
     gn, gon = np.linalg.norm(g), np.linalg.norm(go)
     assert abs(gn - gon) <= GNORM_RTOL * gon, (gn, gon)

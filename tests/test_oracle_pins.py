@@ -86,7 +86,7 @@ def brute_force_D(geo, A, B):
         pa, pb = q.sum(1), q.sum(0)
         mu = (bins * pb).sum()
         var = (bins ** 2 * pb).sum() - mu ** 2
-        if var <= 1e-9 * (bins ** 2 * pb).sum():
+        if var <= 1e-6 * max(1.0, (bins ** 2 * pb).sum()):
             continue
         ok = pa > 0
         mua = (q[ok] * bins[None, :]).sum(1) / pa[ok]
