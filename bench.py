@@ -37,6 +37,7 @@ CONFIG_NAMES = {"c1": "c1_2d_128", "c2": "c2_ct_256x256x96", "c3": "c3_oct_160",
 METRIC = "SRWCR value+grad Gvoxel/s & HBM-roofline % at 256²×96; batched vs plain pairs/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 KERNEL_SOURCES = ["paper_1804_05061_b300/csrc/kernels.cuh",
+                  "paper_1804_05061_b300/csrc/kernels_rows.cuh",
                   "paper_1804_05061_b300/csrc/device_math.cuh"]
 
 

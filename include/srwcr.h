@@ -75,6 +75,9 @@ typedef struct {
   int64_t n_params;       /* ndim * prod(ffd_nodes) = length of c and g */
   int64_t n_regions;      /* prod(sbins) */
   int tile[3];            /* voxel tile used by the kernels */
+  int kernel_path;        /* 1: row-parallel kernels (32-wide tiles, FFD and
+                             spatial-bin spacing >= ~5 voxels along x);
+                             0: general per-voxel kernels */
 } srwcr_level_desc;
 
 /* Create a context: validate cfg, upload both images, normalise each to

@@ -50,7 +50,7 @@ class LevelDesc(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int * 3), ("ffd_nodes", ctypes.c_int * 3),
                 ("sbins", ctypes.c_int * 3), ("n_voxels", ctypes.c_int64),
                 ("n_params", ctypes.c_int64), ("n_regions", ctypes.c_int64),
-                ("tile", ctypes.c_int * 3)]
+                ("tile", ctypes.c_int * 3), ("kernel_path", ctypes.c_int)]
 
 
 class LbfgsOpts(ctypes.Structure):
@@ -131,6 +131,7 @@ class LevelInfo:
     n_params: int
     n_regions: int
     tile: tuple
+    kernel_path: int  # 1 = row-parallel kernels, 0 = general kernels
 
 
 class SRWCR:
@@ -201,7 +202,7 @@ class SRWCR:
         d = LevelDesc()
         _check(load().srwcr_level_info(self._h, level, ctypes.byref(d)))
         return LevelInfo(tuple(d.dims), tuple(d.ffd_nodes), tuple(d.sbins), d.n_voxels,
-                         d.n_params, d.n_regions, tuple(d.tile))
+                         d.n_params, d.n_regions, tuple(d.tile), d.kernel_path)
 
     def coef_shape(self, level: int = 0):
         n = self.levels[level].ffd_nodes

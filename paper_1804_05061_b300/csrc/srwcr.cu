@@ -18,6 +18,7 @@
 
 #include "srwcr.h"
 #include "kernels.cuh"
+#include "kernels_rows.cuh"
 
 using namespace srwcr;
 
@@ -79,6 +80,12 @@ struct Level {
   float s1 = 1.f, s2 = 1.f;           // fixed-point scales of S1, S2
   size_t smem_acc = 0, smem_adj = 0;
   bool tables = false;
+  // Row-parallel fast path (32-wide tiles): static per-row lane permutation
+  // ordering voxels by fixed-image bin, x-bins per row (4 or 8), smem sizes.
+  bool rows = false;
+  int nxb_rows = 0;
+  unsigned char* perm = nullptr;
+  size_t smem_acc_rows = 0, smem_adj_rows = 0;
 };
 
 }  // namespace
@@ -125,6 +132,29 @@ int max_bins_per_tile(int n, int tile, int num, int den) {
 
 size_t acc_smem(const Geo& g, int nch) {
   return (size_t)g.hb[0] * g.hb[1] * g.hb[2] * g.nbins * nch * sizeof(unsigned long long);
+}
+
+size_t rows_acc_smem(const Geo& g, int ndim, int nxb) {
+  const size_t nv = (size_t)nxb * 4;
+  return acc_smem(g, 2) + sizeof(float) * kRowWarps * 32 * nv + sizeof(int) * kRowWarps * 32 +
+         sizeof(float) * kRowWarps * ndim * kMaxRowNodes +
+         sizeof(float) * ndim * g.hf[0] * g.hf[1] * g.hf[2];
+}
+
+size_t rows_adj_smem(const Geo& g, int ndim, int nxb) {
+  const size_t nbt = (size_t)g.hb[0] * g.hb[1] * g.hb[2];
+  const size_t hf = (size_t)g.hf[0] * g.hf[1] * g.hf[2];
+  return sizeof(float) * ndim * hf * 2 + sizeof(float) * nbt * (2 + g.nbins) +
+         sizeof(float) * kRowWarps * 2 * nxb + sizeof(float) * kRowWarps * 32 * nxb * 2 +
+         sizeof(int) * kRowWarps * 32 + sizeof(float) * kRowWarps * ndim * kMaxRowNodes;
+}
+
+// Row kernels need 32-wide tiles, at most 8 spatial x-bins and 10 FFD
+// x-nodes per row (FFD spacing >= 5, spatial-bin spacing >= ~5).
+bool rows_eligible(const Geo& g, int ndim, int* nxb) {
+  if (g.tile[0] != 32 || g.hb[0] > 8 || g.hf[0] > 10) return false;
+  *nxb = g.hb[0] <= 4 ? 4 : 8;
+  return rows_acc_smem(g, ndim, *nxb) <= 220 * 1024 && rows_adj_smem(g, ndim, *nxb) <= 220 * 1024;
 }
 
 void set_tile(Geo& g, int ndim, int tx, int ty, int tz) {
@@ -210,12 +240,43 @@ void fixed_scales(const Geo& g, int ndim, double* sP, double* s1, double* s2) {
   *s2 = std::ldexp(1.0, 62 - ceil_log2(box * L * L));
 }
 
+template <int DIM, typename T>
+void launch_rows_acc(srwcr_ctx* ctx, Level& lv, const float* c, int nblk) {
+  const T* A = (const T*)lv.A;
+  const T* M = (const T*)lv.M;
+  if (lv.nxb_rows == 4)
+    k_accumulate_rows<DIM, T, 4><<<nblk, kBlock, lv.smem_acc_rows, ctx->stream>>>(
+        lv.g, A, M, c, lv.perm, lv.S, lv.s1, lv.s2);
+  else
+    k_accumulate_rows<DIM, T, 8><<<nblk, kBlock, lv.smem_acc_rows, ctx->stream>>>(
+        lv.g, A, M, c, lv.perm, lv.S, lv.s1, lv.s2);
+}
+
+template <int DIM, typename T>
+void launch_rows_adj(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float invZ,
+                     float* g, int nblk) {
+  const T* A = (const T*)lv.A;
+  const T* M = (const T*)lv.M;
+  if (lv.nxb_rows == 4)
+    k_adjoint_rows<DIM, T, 4><<<nblk, kBlock, lv.smem_adj_rows, ctx->stream>>>(
+        lv.g, A, M, c, lv.perm, lv.U, lv.V, lv.X, gD, invZ, g);
+  else
+    k_adjoint_rows<DIM, T, 8><<<nblk, kBlock, lv.smem_adj_rows, ctx->stream>>>(
+        lv.g, A, M, c, lv.perm, lv.U, lv.V, lv.X, gD, invZ, g);
+}
+
 template <typename T>
 srwcr_status launch_accumulate(srwcr_ctx* ctx, Level& lv, const float* c, bool stat, float s0,
                                float s1) {
   const int nblk = lv.g.ntile[0] * lv.g.ntile[1] * lv.g.ntile[2];
   const T* A = (const T*)lv.A;
   const T* M = (const T*)lv.M;
+  if (!stat && lv.rows) {
+    if (ctx->cfg.ndim == 3) launch_rows_acc<3, T>(ctx, lv, c, nblk);
+    else launch_rows_acc<2, T>(ctx, lv, c, nblk);
+    CKL();
+    return SRWCR_OK;
+  }
   const size_t sm = stat ? acc_smem(lv.g, 1) : lv.smem_acc;
   if (ctx->cfg.ndim == 3) {
     if (stat) k_accumulate<3, T, true><<<nblk, kBlock, sm, ctx->stream>>>(lv.g, A, M, c, lv.S, s0, s1);
@@ -232,6 +293,12 @@ template <typename T>
 srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g) {
   const int nblk = lv.g.ntile[0] * lv.g.ntile[1] * lv.g.ntile[2];
   const float invZ = (float)(1.0 / lv.Z);
+  if (lv.rows) {
+    if (ctx->cfg.ndim == 3) launch_rows_adj<3, T>(ctx, lv, c, gD, invZ, g, nblk);
+    else launch_rows_adj<2, T>(ctx, lv, c, gD, invZ, g, nblk);
+    CKL();
+    return SRWCR_OK;
+  }
   if (ctx->cfg.ndim == 3)
     k_adjoint<3, T><<<nblk, kBlock, lv.smem_adj, ctx->stream>>>(
         lv.g, (const T*)lv.A, (const T*)lv.M, c, lv.U, lv.V, lv.X, gD, invZ, g);
@@ -251,6 +318,14 @@ srwcr_status set_smem_limits() {
   CK(cudaFuncSetAttribute(k_accumulate<2, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows<3, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows<3, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows<2, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows<2, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   return SRWCR_OK;
 }
 
@@ -339,7 +414,7 @@ srwcr_status finish_sync(srwcr_ctx* ctx, Level& lv, double* D_host) {
 }
 
 void free_level(Level& lv) {
-  void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg};
+  void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg, lv.perm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   lv = Level();
@@ -413,6 +488,13 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     CK(cudaMalloc((void**)&lv.ndeg, sizeof(int)));
     lv.smem_acc = acc_smem(g, 2);
     lv.smem_adj = sizeof(float) * cfg->ndim * g.hf[0] * g.hf[1] * g.hf[2];
+    lv.rows = rows_eligible(g, cfg->ndim, &lv.nxb_rows);
+    if (lv.rows) {
+      lv.smem_acc_rows = rows_acc_smem(g, cfg->ndim, lv.nxb_rows);
+      lv.smem_adj_rows = rows_adj_smem(g, cfg->ndim, lv.nxb_rows);
+      const long long nrows = (long long)((g.n[0] + 31) / 32) * g.n[1] * g.n[2];
+      CK(cudaMalloc((void**)&lv.perm, 32 * nrows));
+    }
   }
 
   // Normalise the two images into level 0 (Sec. II: [0, L_eps]).
@@ -467,6 +549,15 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
       }
       CKL();
     }
+  }
+
+  // Per-row lane permutations for the row kernels (A is fixed).
+  for (int l = 0; l < ctx->nlev; ++l) {
+    Level& lv = ctx->lev[l];
+    if (!lv.rows) continue;
+    if (is_bf16(ctx)) k_row_perm<__nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(lv.g, (const __nv_bfloat16*)lv.A, lv.perm);
+    else k_row_perm<float><<<1024, 256, 0, ctx->stream>>>(lv.g, (const float*)lv.A, lv.perm);
+    CKL();
   }
 
   // Static fixed-image statistics P[r][a] and Z = sum P.
@@ -544,6 +635,7 @@ srwcr_status srwcr_level_info(const srwcr_ctx* ctx, int level, srwcr_level_desc*
   out->n_voxels = g.nvox;
   out->n_params = g.ncoef * ctx->cfg.ndim;
   out->n_regions = g.R;
+  out->kernel_path = ctx->lev[level].rows ? 1 : 0;
   return SRWCR_OK;
 }
 

@@ -75,6 +75,31 @@ def test_value_gradient_and_regions_match_oracle(small_cases, name):
     assert np.abs(g - go).max() <= G_ELEM * np.abs(go).max()
 
 
+EXPECTED_PATH = {"ellipse_2d_ragged": 1, "ct_3d_ragged": 1, "oct_ffd_grid_bins": 0,
+                 "ct_128_bins": 1, "pet_labels": 1}
+
+
+@pytest.mark.parametrize("name", [s[0] for s in SMALL])
+def test_kernel_path_selection(small_cases, name):
+    prob, f, m, c = small_cases[name]
+    assert engine_for(prob, f, m).levels[0].kernel_path == EXPECTED_PATH[name]
+
+
+@pytest.mark.parametrize("name", ["ellipse_2d_ragged", "ct_3d_ragged", "ct_128_bins"])
+def test_general_kernels_match_oracle(small_cases, name):
+    """The per-voxel kernels (forced by a 16-wide tile) against the oracle."""
+    prob, f, m, c = small_cases[name]
+    tile = (16, 4, 4) if prob.ndim == 3 else (16, 8)
+    e = engine_for(prob, f, m, tile=tile)
+    assert e.levels[0].kernel_path == 0 and e.levels[0].tile[0] == 16
+    D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+    st, go, _, _, _ = oracle_eval(prob, f, m, c)
+    assert abs(D - st.D) <= D_RTOL * abs(st.D), (D, st.D)
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(np.linalg.norm(g) - np.linalg.norm(go)) <= GNORM_RTOL * np.linalg.norm(go)
+    assert np.abs(g - go).max() <= G_ELEM * np.abs(go).max()
+
+
 @pytest.mark.parametrize("name", ["ellipse_2d_ragged", "oct_ffd_grid_bins", "ct_128_bins"])
 def test_voxel_to_bin_indexing_is_bit_exact(small_cases, name):
     prob, f, m, c = small_cases[name]
@@ -203,6 +228,7 @@ def test_c2_full_value_and_gradient(c2_case):
     pair, c = c2_case
     prob = pair.prob
     e = engine_for(prob, pair.fixed, pair.moving)
+    assert e.levels[0].kernel_path == 1
     D, g = e.value_and_grad(torch.from_numpy(c).cuda())
     st, go, _, _, _ = oracle_eval(prob, pair.fixed, pair.moving, c)
     assert abs(D - st.D) <= D_RTOL * st.D, (D, st.D)
