@@ -2,23 +2,29 @@
 //
 // A CTA owns a voxel tile 32 x TY x TZ; each warp walks x-rows of 32 voxels.
 // Along a row y and z are fixed, so the y/z factors of every tensor-product
-// B-spline (FFD nodes, Eq. 17; spatial bins, Eq. 7) are row constants:
+// B-spline (FFD nodes, Eq. 17; spatial bins, Eq. 7) are row constants.  All
+// per-axis geometry (cells, B-spline weights) is computed once per CTA into
+// shared-memory tables for the tile's 32 x-positions, TY y-rows and TZ
+// z-planes, and everything that only depends on z is contracted once per
+// z-plane in the CTA prologue:
 //
-//   * FFD: per row, the warp contracts the staged coefficient tile over the
-//     16 (m, n) y/z nodes once per x-node; each voxel then needs 4 FMAs per
-//     component.
+//   * FFD: CZ[z][k][m][l] = sum_n beta_n(z) c_k[.., m, l]; per row the warp
+//     finishes the y-contraction (4 FMAs per x-node), each voxel then needs
+//     4 FMAs per component.
 //   * Joint statistics (value pass): lanes are ordered by their fixed-image
 //     bin a0 with a static per-row permutation (A does not change between
 //     evaluations), so voxels sharing a0 are adjacent.  A segmented warp
 //     reduction forms, per segment, the FP32 sums over <= 32 voxels of
-//     beta_x(i) h(a - A) {m1, m2}; each sum is then spread over the 16
-//     row-constant y/z weights and added in 64-bit fixed point to the CTA
-//     histogram.  Only short FP32 sums are ever formed, so the
+//     beta_x(i) h(a - A) {m1, m2}; each sum is then spread over the
+//     row-constant y/z weights (one lane per y/z bin) and added in 64-bit
+//     fixed point to the CTA histogram, whose per-bin stride is odd so those
+//     adds hit distinct banks.  Only short FP32 sums are ever formed, so the
 //     E[b^2] - mu^2 cancellation of Eq. (10) keeps full accuracy.
-//   * Adjoint: per row the warp contracts the region tables U, V and X over
-//     the y/z bins; each voxel forms dD/dB (Eq. 19), and the row's
-//     contributions to its control points are combined by a reduce-scatter
-//     butterfly before one shared-memory add per (node, component, y/z node).
+//   * Adjoint: the region tables U, V, X are contracted over z per plane in
+//     the prologue and over y per row; each voxel forms dD/dB (Eq. 19), and
+//     the row's contributions to its control points are combined by a
+//     reduce-scatter butterfly before one shared-memory add per (node,
+//     component, y/z node).
 //
 // Rows in which every warped intensity is exactly 0 (m1 = m2 = 0) add nothing
 // to the statistics, and rows in which the moving-image gradient vanishes at
@@ -29,174 +35,296 @@
 
 namespace srwcr {
 
-constexpr int kRowWarps = 8;            // warps per CTA (256 threads)
-constexpr int kMaxRowNodes = 16;        // FFD x-nodes a row may touch
+constexpr int kAccWarps = 16;           // value pass: 512 threads per CTA
+constexpr int kAdjWarps = 8;            // adjoint: 256 threads per CTA
+constexpr int kMaxRowNodes = 10;        // FFD x-nodes a 32-voxel row may touch
 constexpr int kSentinel = 0x7fffffff;   // key of lanes past the image edge
 
-// Stage the tile's control coefficients (all components) into shared memory.
+// Per-axis geometry of one coordinate: FFD cell (relative to the tile's
+// first node), its 4 weights, spatial-bin cell (relative to the tile's first
+// bin) and its 4 weights.
+struct AxisEntry {
+  int frel;
+  float bf[4];
+  int srel;
+  float bs[4];
+};
+
+__device__ __forceinline__ void axis_entry(const Geo& g, int d, int v, int f0, int c0,
+                                           AxisEntry* e) {
+  float t;
+  e->frel = ffd_cell(g, d, v, &t) - f0;
+  bspline4(t, e->bf);
+  e->srel = sb_cell(g, d, v, &t) - c0;
+  bspline4(t, e->bs);
+}
+
+// Trivial axis (2-D problems have no z).
+__device__ __forceinline__ void axis_unit(AxisEntry* e) {
+  e->frel = 0;
+  e->srel = 0;
+  e->bf[0] = e->bs[0] = 1.f;
+  e->bf[1] = e->bf[2] = e->bf[3] = e->bs[1] = e->bs[2] = e->bs[3] = 0.f;
+}
+
+struct TileOrigin {
+  int o[3];     // first voxel
+  int f[3];     // first FFD node
+  int cb[3];    // first spatial bin (cell)
+};
+
 template <int DIM>
-__device__ __forceinline__ void stage_coef_tile(const Geo& g, const float* __restrict__ c,
-                                                int f0, int f1, int f2, float* ctile) {
-  const int nt = g.hf[0] * g.hf[1] * g.hf[2];
-  for (int t = threadIdx.x; t < DIM * nt; t += blockDim.x) {
-    const int k = t / nt, r = t % nt;
-    const int l0 = r % g.hf[0], l1 = (r / g.hf[0]) % g.hf[1], l2 = r / (g.hf[0] * g.hf[1]);
-    const int n0 = f0 + l0, n1 = f1 + l1, n2 = f2 + l2;
-    float v = 0.f;
-    if (n0 < g.nf[0] && n1 < g.nf[1] && n2 < g.nf[2])
-      v = __ldg(c + k * g.ncoef + ((long long)n2 * g.nf[1] + n1) * g.nf[0] + n0);
-    ctile[t] = v;
+__device__ __forceinline__ TileOrigin tile_setup(const Geo& g) {
+  TileOrigin T;
+  const int b = blockIdx.x;
+  T.o[0] = (b % g.ntile[0]) * g.tile[0];
+  T.o[1] = ((b / g.ntile[0]) % g.ntile[1]) * g.tile[1];
+  T.o[2] = (b / (g.ntile[0] * g.ntile[1])) * g.tile[2];
+  float t;
+  for (int d = 0; d < 3; ++d) {
+    const bool on = d < DIM;
+    T.f[d] = on ? T.o[d] / g.fsp[d] : 0;
+    T.cb[d] = on ? sb_cell(g, d, T.o[d], &t) : 0;
+  }
+  return T;
+}
+
+// Lane-major x tables for the tile's 32 x-positions p (arrays [.][32], so a
+// warp reading entry p per lane touches 32 consecutive words):
+//   frel[p]            FFD cell relative to the tile's first node
+//   bf[l][p]           FFD weights beta_l
+//   bfp[n][p]          the same, placed at the row's x-node n (0 elsewhere)
+//   srel[p], bs[i][p]  spatial-bin cell and weights
+//   bsp[b][p]          spatial weights placed at the row's x-bin b
+struct XTab {
+  int* frel;
+  float* bf;
+  float* bfp;
+  int* srel;
+  float* bs;
+  float* bsp;
+};
+
+__host__ __device__ inline size_t xtab_words(int nxb) { return 32 * (1 + 4 + kMaxRowNodes + 1 + 4 + nxb); }
+
+__device__ __forceinline__ XTab xtab_carve(float* base, int nxb) {
+  XTab t;
+  t.frel = reinterpret_cast<int*>(base);
+  t.bf = base + 32;
+  t.bfp = t.bf + 4 * 32;
+  t.srel = reinterpret_cast<int*>(t.bfp + kMaxRowNodes * 32);
+  t.bs = reinterpret_cast<float*>(t.srel + 32);
+  t.bsp = t.bs + 4 * 32;
+  (void)nxb;
+  return t;
+}
+
+template <int NXB>
+__device__ __forceinline__ void build_xtab(const Geo& g, const TileOrigin& T, XTab xt) {
+  for (int p = threadIdx.x; p < 32; p += blockDim.x) {
+    AxisEntry e;
+    axis_entry(g, 0, min(T.o[0] + p, g.n[0] - 1), T.f[0], T.cb[0], &e);
+    xt.frel[p] = e.frel;
+    xt.srel[p] = e.srel;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      xt.bf[l * 32 + p] = e.bf[l];
+      xt.bs[l * 32 + p] = e.bs[l];
+    }
+    for (int n = 0; n < kMaxRowNodes; ++n) {
+      const int l = n - e.frel;
+      xt.bfp[n * 32 + p] = (l >= 0 && l < 4) ? e.bf[l] : 0.f;
+    }
+    for (int b = 0; b < NXB; ++b) {
+      const int i = b - e.srel;
+      xt.bsp[b * 32 + p] = (i >= 0 && i < 4) ? e.bs[i] : 0.f;
+    }
   }
 }
 
-// Per-row FFD contraction over the y/z nodes: cyz[k][l] for the row's x-nodes.
+// Fill the y-table (tile[1]) and z-table (tile[2]).
 template <int DIM>
-__device__ __forceinline__ void row_ffd_contract(const Geo& g, const float* ctile, int ly, int lz,
-                                                 const float by[4], const float bz[4], int nxn,
-                                                 float* cyz, int lane) {
-  const int nt = g.hf[0] * g.hf[1] * g.hf[2];
+__device__ __forceinline__ void build_axis_tables(const Geo& g, const TileOrigin& T,
+                                                  AxisEntry* yt, AxisEntry* zt) {
+  const int n = g.tile[1] + g.tile[2];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (i < g.tile[1]) {
+      const int y = min(T.o[1] + i, g.n[1] - 1);
+      axis_entry(g, 1, y, T.f[1], T.cb[1], yt + i);
+    } else {
+      const int k = i - g.tile[1];
+      if (DIM == 3) {
+        const int z = min(T.o[2] + k, g.n[2] - 1);
+        axis_entry(g, 2, z, T.f[2], T.cb[2], zt + k);
+      } else {
+        axis_unit(zt + k);
+      }
+    }
+  }
+}
+
+// z-contracted FFD coefficients: CZ[z][k][m][l] for the tile's z-planes,
+// components k, y-nodes m < hf1, x-nodes l < hf0 (read through L1/L2).
+template <int DIM>
+__device__ __forceinline__ void build_cz(const Geo& g, const TileOrigin& T, const float* __restrict__ c,
+                                         const AxisEntry* zt, float* CZ) {
+  const int per_z = DIM * g.hf[1] * g.hf[0];
+  const int n = g.tile[2] * per_z;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int zl = i / per_z, r = i % per_z;
+    const int k = r / (g.hf[1] * g.hf[0]), m = (r / g.hf[0]) % g.hf[1], l = r % g.hf[0];
+    const int n0 = T.f[0] + l, n1 = T.f[1] + m;
+    float s = 0.f;
+    if (n0 < g.nf[0] && n1 < g.nf[1]) {
+      const AxisEntry& e = zt[zl];
+      const int NZ = DIM == 3 ? 4 : 1;
+      for (int q = 0; q < NZ; ++q) {
+        const int n2 = T.f[2] + e.frel + q;
+        if (n2 < g.nf[2])
+          s += e.bf[q] * __ldg(c + k * g.ncoef + ((long long)n2 * g.nf[1] + n1) * g.nf[0] + n0);
+      }
+    }
+    CZ[i] = s;
+  }
+}
+
+// Per-row FFD table: cyz[k][l] = sum_m beta_m(y) CZ[z][k][ly + m][l].
+template <int DIM>
+__device__ __forceinline__ void row_cyz(const Geo& g, const float* CZ, int zl, const AxisEntry& ye,
+                                        int nxn, float* cyz, int lane) {
+  const int per_z = DIM * g.hf[1] * g.hf[0];
   for (int t = lane; t < DIM * nxn; t += 32) {
     const int k = t / nxn, l = t % nxn;
-    float s = 0.f;
-    const int NZ = DIM == 3 ? 4 : 1;
-    for (int n = 0; n < NZ; ++n)
-      for (int m = 0; m < 4; ++m)
-        s += by[m] * bz[n] * ctile[k * nt + ((lz + n) * g.hf[1] + (ly + m)) * g.hf[0] + l];
-    cyz[k * kMaxRowNodes + l] = s;
+    const float* base = CZ + zl * per_z + (k * g.hf[1] + ye.frel) * g.hf[0] + l;
+    cyz[k * kMaxRowNodes + l] = ye.bf[0] * base[0] + ye.bf[1] * base[g.hf[0]] +
+                                ye.bf[2] * base[2 * g.hf[0]] + ye.bf[3] * base[3 * g.hf[0]];
   }
 }
 
-// The lane's voxel: FFD displacement from the row table, warped intensity
-// and (optionally) its gradient.
+// Warp the lane's voxel: displacement from the row table, trilinear sample.
 template <int DIM, typename T>
-__device__ __forceinline__ float row_voxel_warp(const Geo& g, const T* __restrict__ M,
-                                                const float* cyz, int x, int y, int z, int fx0,
-                                                float bx[4], int* fxrel, float gm[3]) {
-  float t;
-  const int fx = ffd_cell(g, 0, x, &t);
-  bspline4(t, bx);
-  const int rel = fx - fx0;
-  *fxrel = rel;
+__device__ __forceinline__ float row_warp(const Geo& g, const T* __restrict__ M, const float* cyz,
+                                          int frel, const float bx[4], int x, int y, int z,
+                                          float gm[3]) {
   float u[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
-    const float* cr = cyz + k * kMaxRowNodes + rel;
+    const float* cr = cyz + k * kMaxRowNodes + frel;
     u[k] = bx[0] * cr[0] + bx[1] * cr[1] + bx[2] * cr[2] + bx[3] * cr[3];
   }
   return sample_moving<DIM, T>(g, M, (float)x + u[0], (float)y + u[1], (float)z + u[2], gm);
 }
 
-// Select beta[i] for a dynamic i in [0, 4); 0 outside.
 __device__ __forceinline__ float pick4(const float b[4], int i) {
   return i == 0 ? b[0] : (i == 1 ? b[1] : (i == 2 ? b[2] : (i == 3 ? b[3] : 0.f)));
 }
 
+// Bytes of the value kernel's shared memory (must match the carve-up below).
+__host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int nxb) {
+  const size_t HB = (size_t)g.hb[0] * g.hb[1] * g.hb[2];
+  const size_t nv = (size_t)nxb * 4;
+  size_t b = HB * 2 * (size_t)g.nbins * 8;                  // hist (u64)
+  b += sizeof(float) * kAccWarps * 32 * nv;                 // segS
+  b += sizeof(int) * kAccWarps * 32;                        // segA
+  b += sizeof(float) * kAccWarps * dim * kMaxRowNodes;      // cyz
+  b += sizeof(float) * xtab_words(nxb);                     // x tables
+  b += sizeof(AxisEntry) * (g.tile[1] + g.tile[2]);         // y, z tables
+  b += sizeof(float) * g.tile[2] * dim * g.hf[1] * g.hf[0]; // CZ
+  return b;
+}
+
 // ---------------------------------------------------------------------------
 // (a) value pass: fused FFD + warp + joint statistics, row-parallel.
-//
-// Dynamic shared memory: hist [hb2][hb1][hb0][nb][2] u64 | segS [warps][32][NXB*4] f32
-//   | segA [warps][32] i32 | cyz [warps][DIM][16] f32 | ctile [DIM][hf] f32
 // ---------------------------------------------------------------------------
 template <int DIM, typename T, int NXB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kAccWarps * 32, 2)
 k_accumulate_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
                   const float* __restrict__ c, const unsigned char* __restrict__ perm,
                   unsigned long long* __restrict__ acc, float s1, float s2) {
   extern __shared__ unsigned long long smem_u64[];
-  constexpr int NV = NXB * 4;  // (x-bin, {h0 m1, h0 m2, h1 m1, h1 m2})
+  constexpr int NV = NXB * 4;                 // (x-bin, slot, moment): v[4b + 2 slot + ch]
+  constexpr int NJK = DIM == 3 ? 16 : 4;      // y/z bins of a row
   const int nb = g.nbins;
   const float L = (float)(nb - 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int hsz = g.hb[0] * g.hb[1] * g.hb[2] * nb * 2;
+  const int P12 = g.hb[1] * g.hb[2];
+  const int HB = g.hb[0] * P12;
+  // Histogram layout hist[a][ch][x-bin][z-bin][y-bin] (u64): the lanes of a
+  // fold pass touch consecutive y/z bins, so their adds hit distinct banks.
   unsigned long long* hist = smem_u64;
-  float* segS = reinterpret_cast<float*>(hist + hsz);
-  int* segA = reinterpret_cast<int*>(segS + kRowWarps * 32 * NV);
-  float* cyz_all = reinterpret_cast<float*>(segA + kRowWarps * 32);
-  float* ctile = cyz_all + kRowWarps * DIM * kMaxRowNodes;
+  float* segS = reinterpret_cast<float*>(hist + (size_t)HB * nb * 2);
+  int* segA = reinterpret_cast<int*>(segS + kAccWarps * 32 * NV);
+  float* cyz_all = reinterpret_cast<float*>(segA + kAccWarps * 32);
+  const XTab xt = xtab_carve(cyz_all + kAccWarps * DIM * kMaxRowNodes, NXB);
+  AxisEntry* yt = reinterpret_cast<AxisEntry*>(reinterpret_cast<float*>(xt.frel) + xtab_words(NXB));
+  AxisEntry* zt = yt + g.tile[1];
+  float* CZ = reinterpret_cast<float*>(zt + g.tile[2]);
   float* cyz = cyz_all + warp * DIM * kMaxRowNodes;
   float* mysegS = segS + warp * 32 * NV;
   int* mysegA = segA + warp * 32;
 
-  int o[3];
-  {
-    const int b = blockIdx.x;
-    o[0] = (b % g.ntile[0]) * g.tile[0];
-    o[1] = ((b / g.ntile[0]) % g.ntile[1]) * g.tile[1];
-    o[2] = (b / (g.ntile[0] * g.ntile[1])) * g.tile[2];
-  }
-  float tdum;
-  const int cb0 = sb_cell(g, 0, o[0], &tdum);
-  const int cb1 = sb_cell(g, 1, o[1], &tdum);
-  const int cb2 = DIM == 3 ? sb_cell(g, 2, o[2], &tdum) : 0;
-  const int f0 = o[0] / g.fsp[0], f1 = o[1] / g.fsp[1], f2 = DIM == 3 ? o[2] / g.fsp[2] : 0;
-  for (int i = threadIdx.x; i < hsz; i += blockDim.x) hist[i] = 0ull;
-  stage_coef_tile<DIM>(g, c, f0, f1, f2, ctile);
+  const TileOrigin TO = tile_setup<DIM>(g);
+  for (int i = threadIdx.x; i < HB * nb * 2; i += blockDim.x) hist[i] = 0ull;
+  build_xtab<NXB>(g, TO, xt);
+  build_axis_tables<DIM>(g, TO, yt, zt);
+  __syncthreads();
+  build_cz<DIM>(g, TO, c, zt, CZ);
   __syncthreads();
 
   const int nxb = (g.n[0] + 31) >> 5;
-  const int xlast = min(o[0] + 31, g.n[0] - 1);
-  const int nxn = xlast / g.fsp[0] - f0 + 4;          // FFD x-nodes of this row
+  const int xlast = min(TO.o[0] + 31, g.n[0] - 1);
+  const int nxn = xlast / g.fsp[0] - TO.f[0] + 4;   // FFD x-nodes of the row
   const int nrows = g.tile[1] * g.tile[2];
-  for (int row = warp; row < nrows; row += kRowWarps) {
-    const int y = o[1] + row % g.tile[1];
-    const int z = o[2] + row / g.tile[1];
+  // Fold lane roles: moment ch (upper/lower half-warp), y/z bin jk.
+  const int fch = lane >> 4, fjk = lane & 15;
+  const int fj = fjk & 3, fk = fjk >> 2;
+  const float fscale = fch ? s2 : s1;
+  for (int row = warp; row < nrows; row += kAccWarps) {
+    const int yl = row % g.tile[1], zl = row / g.tile[1];
+    const int y = TO.o[1] + yl, z = TO.o[2] + zl;
     if (y >= g.n[1] || z >= g.n[2]) continue;  // warp-uniform
-    // Row constants: FFD and spatial y/z weights.
-    float by[4], bz[4], sy[4], sz[4], t;
-    const int fy = ffd_cell(g, 1, y, &t); bspline4(t, by);
-    const int scy = sb_cell(g, 1, y, &t); bspline4(t, sy);
-    int fz = 0, scz = 0;
-    if (DIM == 3) {
-      fz = ffd_cell(g, 2, z, &t); bspline4(t, bz);
-      scz = sb_cell(g, 2, z, &t); bspline4(t, sz);
-    } else {
-      bz[0] = sz[0] = 1.f; bz[1] = bz[2] = bz[3] = sz[1] = sz[2] = sz[3] = 0.f;
-    }
-    row_ffd_contract<DIM>(g, ctile, fy - f1, fz - f2, by, bz, nxn, cyz, lane);
+    const AxisEntry ye = yt[yl], ze = zt[zl];
+    row_cyz<DIM>(g, CZ, zl, ye, nxn, cyz, lane);
     __syncwarp();
 
-    const long long rowid = ((long long)z * g.n[1] + y) * nxb + (o[0] >> 5);
-    const int x = o[0] + perm[rowid * 32 + lane];
+    const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
+    const int p = perm[rowid * 32 + lane];
+    const int x = TO.o[0] + p;
     const bool act = x < g.n[0];
     float m1 = 0.f, m2 = 0.f, h0 = 0.f, h1 = 0.f;
     int key = kSentinel;
-    float bsx[4] = {0.f, 0.f, 0.f, 0.f};
-    int srel = 0;
     if (act) {
       const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
       float fa;
-      const int a0 = bin_split(fminf(fmaxf(ldval(A + idx), 0.f), L), nb, &fa);
-      key = a0;
+      key = bin_split(fminf(fmaxf(ldval(A + idx), 0.f), L), nb, &fa);
       h1 = parzen_upper(fa);
       h0 = 1.f - h1;
-      float bx[4], gm[3];
-      int fxrel;
-      float B = row_voxel_warp<DIM, T>(g, M, cyz, x, y, z, f0, bx, &fxrel, gm);
+      const float bx[4] = {xt.bf[p], xt.bf[32 + p], xt.bf[64 + p], xt.bf[96 + p]};
+      float gm[3];
+      float B = row_warp<DIM, T>(g, M, cyz, xt.frel[p], bx, x, y, z, gm);
       B = fminf(fmaxf(B, 0.f), L);
       float fb;
       const int kb = bin_split(B, nb, &fb);
       const float w1 = parzen_upper(fb), kf = (float)kb;
-      m1 = kf + w1;
-      m2 = kf * kf + (2.f * kf + 1.f) * w1;
-      const int scx = sb_cell(g, 0, x, &t);
-      bspline4(t, bsx);
-      srel = scx - cb0;
+      m1 = kf + w1;                              // sum_b b   h(b - B)
+      m2 = kf * kf + (2.f * kf + 1.f) * w1;      // sum_b b^2 h(b - B)
     }
     const bool live = act && (m1 != 0.f || m2 != 0.f);
-    __syncwarp();
-    if (!__any_sync(0xffffffffu, live)) continue;  // B == 0 everywhere: nothing to add
+    if (!__any_sync(0xffffffffu, live)) continue;  // B == 0 on the whole row
 
     // Per-lane contributions over the row's NXB spatial x-bins.
     float v[NV];
+    const float e0 = live ? h0 * m1 : 0.f, e1 = live ? h0 * m2 : 0.f;
+    const float e2 = live ? h1 * m1 : 0.f, e3 = live ? h1 * m2 : 0.f;
 #pragma unroll
     for (int b = 0; b < NXB; ++b) {
-      const float w = live ? pick4(bsx, b - srel) : 0.f;
-      v[4 * b + 0] = w * h0 * m1;
-      v[4 * b + 1] = w * h0 * m2;
-      v[4 * b + 2] = w * h1 * m1;
-      v[4 * b + 3] = w * h1 * m2;
+      const float w = xt.bsp[b * 32 + p];
+      v[4 * b + 0] = w * e0;
+      v[4 * b + 1] = w * e1;
+      v[4 * b + 2] = w * e2;
+      v[4 * b + 3] = w * e3;
     }
-    // Segments of equal a0 (lanes are sorted by a0).
+    // Segments of equal a0 (lanes are sorted by a0): reduce toward each head.
     const int prev = __shfl_up_sync(0xffffffffu, key, 1);
     const bool head = lane == 0 || key != prev;
     const unsigned heads = __ballot_sync(0xffffffffu, head);
@@ -211,7 +339,7 @@ k_accumulate_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
         if (ok) v[q] += ov;
       }
     }
-    const int nseg = __popc(heads);
+    int nseg = __popc(heads);
     if (head) {
       const int sidx = __popc(heads & ((1u << lane) - 1u));
       mysegA[sidx] = key;
@@ -219,39 +347,51 @@ k_accumulate_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
       for (int q = 0; q < NV; ++q) mysegS[sidx * NV + q] = v[q];
     }
     __syncwarp();
-    // Fold each (segment, x-bin, moment) sum over the 16 y/z bins.
-    const int lb1 = scy - cb1, lb2 = scz - cb2;
-    const int NJK = DIM == 3 ? 16 : 4;
-    for (int it = lane; it < nseg * NV; it += 32) {
-      const int s = it / NV, q = it % NV;
+    if (mysegA[nseg - 1] == kSentinel) --nseg;   // lanes past the image edge
+    // Fold.  Intensity bin e of the row: a_s (slot 0 of segment s, plus slot 1
+    // of segment s-1 when a_{s-1} + 1 = a_s) and a_s + 1 (slot 1 of s, when
+    // a_{s+1} != a_s + 1).  Each lane adds one moment to one y/z bin.
+    const float wjk = (fjk < NJK) ? ye.bs[fj] * ze.bs[fk] : 0.f;
+    const int yz_off = (ze.srel + fk) * g.hb[1] + (ye.srel + fj);
+    for (int s = 0; s < nseg; ++s) {
       const int a = mysegA[s];
-      const float val = mysegS[s * NV + q];
-      const int b = q >> 2, slot = (q >> 1) & 1, ch = q & 1;
-      if (a == kSentinel || val == 0.f || b >= g.hb[0]) continue;
-      const float vs = val * (ch ? s2 : s1);
-      const int abin = a + slot;
-      for (int jk = 0; jk < NJK; ++jk) {
-        const int j = jk & 3, k = jk >> 2;
-        const float w = sy[j] * sz[k];
-        if (w == 0.f) continue;
-        const int hb = ((lb2 + k) * g.hb[1] + (lb1 + j)) * g.hb[0] + b;
-        atomicAdd(hist + ((size_t)hb * nb + abin) * 2 + ch, __float2ull_rn(vs * w));
+      const bool merge_prev = s > 0 && mysegA[s - 1] + 1 == a;
+      const bool own_upper = s + 1 == nseg || mysegA[s + 1] != a + 1;
+      for (int half = 0; half < 2; ++half) {
+        if (half == 1 && !own_upper) continue;   // warp-uniform
+        const int abin = a + half;
+        const unsigned long long* dummy = nullptr;
+        (void)dummy;
+#pragma unroll
+        for (int b = 0; b < NXB; ++b) {
+          if (b >= g.hb[0]) break;
+          float val;
+          if (half == 0) {
+            val = mysegS[s * NV + 4 * b + fch];
+            if (merge_prev) val += mysegS[(s - 1) * NV + 4 * b + 2 + fch];
+          } else {
+            val = mysegS[s * NV + 4 * b + 2 + fch];
+          }
+          if (val != 0.f && wjk != 0.f)
+            atomicAdd(hist + ((size_t)(abin * 2 + fch) * g.hb[0] + b) * P12 + yz_off,
+                      __float2ull_rn(val * fscale * wjk));
+        }
       }
     }
     __syncwarp();
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < hsz; i += blockDim.x) {
+  for (int i = threadIdx.x; i < HB * nb * 2; i += blockDim.x) {
     const unsigned long long val = hist[i];
     if (!val) continue;
-    const int ch = i & 1;
-    const int a = (i >> 1) % nb;
-    const int hbin = (i >> 1) / nb;
-    const int l0 = hbin % g.hb[0];
-    const int l1 = (hbin / g.hb[0]) % g.hb[1];
-    const int l2 = hbin / (g.hb[0] * g.hb[1]);
-    if (cb0 + l0 >= g.nsb[0] || cb1 + l1 >= g.nsb[1] || cb2 + l2 >= g.nsb[2]) continue;
-    const long long r = ((long long)(cb2 + l2) * g.nsb[1] + (cb1 + l1)) * g.nsb[0] + (cb0 + l0);
+    const int l1 = i % g.hb[1];
+    const int l2 = (i / g.hb[1]) % g.hb[2];
+    const int l0 = (i / P12) % g.hb[0];
+    const int ach = i / HB;
+    const int a = ach >> 1, ch = ach & 1;
+    const int r0 = TO.cb[0] + l0, r1 = TO.cb[1] + l1, r2 = TO.cb[2] + l2;
+    if (r0 >= g.nsb[0] || r1 >= g.nsb[1] || r2 >= g.nsb[2]) continue;
+    const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
     atomicAdd(acc + ((size_t)r * nb + a) * 2 + ch, val);
   }
 }
@@ -273,15 +413,26 @@ __device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
   return v[0];
 }
 
+// Bytes of the adjoint's shared memory (must match the carve-up below).
+__host__ __device__ inline size_t adj_rows_smem_bytes(const Geo& g, int dim, int nxb) {
+  const size_t hf = (size_t)g.hf[0] * g.hf[1] * g.hf[2];
+  const size_t p01 = (size_t)g.hb[0] * g.hb[1];
+  size_t b = sizeof(float) * dim * hf;                               // gt
+  b += sizeof(float) * g.tile[2] * p01 * (2 + g.nbins);              // UZ, VZ, XZ
+  b += sizeof(float) * kAdjWarps * (2 * nxb + 32 * nxb * 2);         // rowt, xy
+  b += sizeof(int) * kAdjWarps * 32;                                 // segA
+  b += sizeof(float) * kAdjWarps * dim * kMaxRowNodes;               // cyz
+  b += sizeof(float) * xtab_words(nxb);                              // x tables
+  b += sizeof(AxisEntry) * (g.tile[1] + g.tile[2]);                  // y, z tables
+  b += sizeof(float) * g.tile[2] * dim * g.hf[1] * g.hf[0];          // CZ
+  return b;
+}
+
 // ---------------------------------------------------------------------------
 // (c) adjoint, row-parallel.
-//
-// Dynamic shared memory: gt [DIM][hf2][hf1][hf0] f32 | U, V [hb] f32 | X [hb][nb] f32
-//   | rowt [warps][2*NXB] f32 | xy [warps][32][NXB][2] f32 | segA [warps][32] i32
-//   | cyz [warps][DIM][16] f32 | ctile [DIM][hf] f32
 // ---------------------------------------------------------------------------
 template <int DIM, typename T, int NXB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kAdjWarps * 32)
 k_adjoint_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
                const float* __restrict__ c, const unsigned char* __restrict__ perm,
                const float* __restrict__ U, const float* __restrict__ V,
@@ -292,131 +443,132 @@ k_adjoint_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
   const float L = (float)(nb - 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nodes_tile = g.hf[0] * g.hf[1] * g.hf[2];
-  const int nbt = g.hb[0] * g.hb[1] * g.hb[2];
+  const int p01 = g.hb[0] * g.hb[1];
+  constexpr int NJK = DIM == 3 ? 16 : 4;
   float* gt = smem_f32;
-  float* Ut = gt + DIM * nodes_tile;
-  float* Vt = Ut + nbt;
-  float* Xt = Vt + nbt;
-  float* rowt_all = Xt + (size_t)nbt * nb;
-  float* xy_all = rowt_all + kRowWarps * 2 * NXB;
-  int* segA_all = reinterpret_cast<int*>(xy_all + kRowWarps * 32 * NXB * 2);
-  float* cyz_all = reinterpret_cast<float*>(segA_all + kRowWarps * 32);
-  float* ctile = cyz_all + kRowWarps * DIM * kMaxRowNodes;
+  float* UZ = gt + DIM * nodes_tile;                 // [TZ][hb1][hb0]
+  float* VZ = UZ + g.tile[2] * p01;
+  float* XZ = VZ + g.tile[2] * p01;                  // [TZ][hb1][hb0][nb]
+  float* rowt_all = XZ + (size_t)g.tile[2] * p01 * nb;
+  float* xy_all = rowt_all + kAdjWarps * 2 * NXB;
+  int* segA_all = reinterpret_cast<int*>(xy_all + kAdjWarps * 32 * NXB * 2);
+  float* cyz_all = reinterpret_cast<float*>(segA_all + kAdjWarps * 32);
+  const XTab xt = xtab_carve(cyz_all + kAdjWarps * DIM * kMaxRowNodes, NXB);
+  AxisEntry* yt = reinterpret_cast<AxisEntry*>(reinterpret_cast<float*>(xt.frel) + xtab_words(NXB));
+  AxisEntry* zt = yt + g.tile[1];
+  float* CZ = reinterpret_cast<float*>(zt + g.tile[2]);
   float* rowt = rowt_all + warp * 2 * NXB;
   float* xy = xy_all + warp * 32 * NXB * 2;
   int* mysegA = segA_all + warp * 32;
   float* cyz = cyz_all + warp * DIM * kMaxRowNodes;
 
-  int o[3];
-  {
-    const int b = blockIdx.x;
-    o[0] = (b % g.ntile[0]) * g.tile[0];
-    o[1] = ((b / g.ntile[0]) % g.ntile[1]) * g.tile[1];
-    o[2] = (b / (g.ntile[0] * g.ntile[1])) * g.tile[2];
-  }
-  float tdum;
-  const int cb0 = sb_cell(g, 0, o[0], &tdum);
-  const int cb1 = sb_cell(g, 1, o[1], &tdum);
-  const int cb2 = DIM == 3 ? sb_cell(g, 2, o[2], &tdum) : 0;
-  const int f0 = o[0] / g.fsp[0], f1 = o[1] / g.fsp[1], f2 = DIM == 3 ? o[2] / g.fsp[2] : 0;
+  const TileOrigin TO = tile_setup<DIM>(g);
   for (int i = threadIdx.x; i < DIM * nodes_tile; i += blockDim.x) gt[i] = 0.f;
-  // Region tables of the tile's spatial bins.
-  for (int i = threadIdx.x; i < nbt; i += blockDim.x) {
-    const int l0 = i % g.hb[0], l1 = (i / g.hb[0]) % g.hb[1], l2 = i / (g.hb[0] * g.hb[1]);
-    const int r0 = cb0 + l0, r1 = cb1 + l1, r2 = cb2 + l2;
-    const bool in = r0 < g.nsb[0] && r1 < g.nsb[1] && r2 < g.nsb[2];
-    const long long r = in ? ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0 : 0;
-    Ut[i] = in ? __ldg(U + r) : 0.f;
-    Vt[i] = in ? __ldg(V + r) : 0.f;
+  build_xtab<NXB>(g, TO, xt);
+  build_axis_tables<DIM>(g, TO, yt, zt);
+  __syncthreads();
+  build_cz<DIM>(g, TO, c, zt, CZ);
+  // Region tables contracted over z for each of the tile's z-planes.
+  {
+    const int nuv = 2 * g.tile[2] * p01;
+    const int n = nuv + g.tile[2] * p01 * nb;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      int zl, hb01, col;  // col: 0 = U, 1 = V, 2 + a = X[a]
+      if (i < nuv) {
+        col = i / (g.tile[2] * p01);
+        const int r = i % (g.tile[2] * p01);
+        zl = r / p01;
+        hb01 = r % p01;
+      } else {
+        const int r = i - nuv;
+        zl = r / (p01 * nb);
+        hb01 = (r / nb) % p01;
+        col = 2 + r % nb;
+      }
+      const int r0 = TO.cb[0] + hb01 % g.hb[0], r1 = TO.cb[1] + hb01 / g.hb[0];
+      float s = 0.f;
+      if (r0 < g.nsb[0] && r1 < g.nsb[1]) {
+        const AxisEntry& e = zt[zl];
+        const int NZ = DIM == 3 ? 4 : 1;
+        for (int q = 0; q < NZ; ++q) {
+          const int r2 = TO.cb[2] + e.srel + q;
+          if (r2 >= g.nsb[2]) continue;
+          const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
+          const float tv = col == 0 ? __ldg(U + r)
+                                    : (col == 1 ? __ldg(V + r) : __ldg(X + r * nb + (col - 2)));
+          s += e.bs[q] * tv;
+        }
+      }
+      if (col == 0) UZ[zl * p01 + hb01] = s;
+      else if (col == 1) VZ[zl * p01 + hb01] = s;
+      else XZ[((size_t)zl * p01 + hb01) * nb + (col - 2)] = s;
+    }
   }
-  for (int i = threadIdx.x; i < nbt * nb; i += blockDim.x) {
-    const int hbin = i / nb, a = i % nb;
-    const int l0 = hbin % g.hb[0], l1 = (hbin / g.hb[0]) % g.hb[1], l2 = hbin / (g.hb[0] * g.hb[1]);
-    const int r0 = cb0 + l0, r1 = cb1 + l1, r2 = cb2 + l2;
-    const bool in = r0 < g.nsb[0] && r1 < g.nsb[1] && r2 < g.nsb[2];
-    Xt[i] = in ? __ldg(X + (((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0) * nb + a) : 0.f;
-  }
-  stage_coef_tile<DIM>(g, c, f0, f1, f2, ctile);
   __syncthreads();
   const float scale = (gscale ? __ldg(gscale) : 1.f) * invZ;
 
   const int nxb = (g.n[0] + 31) >> 5;
-  const int xlast = min(o[0] + 31, g.n[0] - 1);
-  const int nxn = xlast / g.fsp[0] - f0 + 4;
+  const int xlast = min(TO.o[0] + 31, g.n[0] - 1);
+  const int nxn = xlast / g.fsp[0] - TO.f[0] + 4;
   const int nrows = g.tile[1] * g.tile[2];
-  const int NJK = DIM == 3 ? 16 : 4;
-  for (int row = warp; row < nrows; row += kRowWarps) {
-    const int y = o[1] + row % g.tile[1];
-    const int z = o[2] + row / g.tile[1];
+  for (int row = warp; row < nrows; row += kAdjWarps) {
+    const int yl = row % g.tile[1], zl = row / g.tile[1];
+    const int y = TO.o[1] + yl, z = TO.o[2] + zl;
     if (y >= g.n[1] || z >= g.n[2]) continue;
-    float by[4], bz[4], sy[4], sz[4], t;
-    const int fy = ffd_cell(g, 1, y, &t); bspline4(t, by);
-    const int scy = sb_cell(g, 1, y, &t); bspline4(t, sy);
-    int fz = 0, scz = 0;
-    if (DIM == 3) {
-      fz = ffd_cell(g, 2, z, &t); bspline4(t, bz);
-      scz = sb_cell(g, 2, z, &t); bspline4(t, sz);
-    } else {
-      bz[0] = sz[0] = 1.f; bz[1] = bz[2] = bz[3] = sz[1] = sz[2] = sz[3] = 0.f;
-    }
-    row_ffd_contract<DIM>(g, ctile, fy - f1, fz - f2, by, bz, nxn, cyz, lane);
+    const AxisEntry ye = yt[yl], ze = zt[zl];
+    row_cyz<DIM>(g, CZ, zl, ye, nxn, cyz, lane);
     __syncwarp();
 
-    const long long rowid = ((long long)z * g.n[1] + y) * nxb + (o[0] >> 5);
-    const int x = o[0] + perm[rowid * 32 + lane];
+    const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
+    const int p = perm[rowid * 32 + lane];
+    const int x = TO.o[0] + p;
     const bool act = x < g.n[0];
-    float gm[3] = {0.f, 0.f, 0.f}, bx[4] = {0.f, 0.f, 0.f, 0.f}, bsx[4] = {0.f, 0.f, 0.f, 0.f};
+    float gm[3] = {0.f, 0.f, 0.f};
     float dm1 = 0.f, dm2 = 0.f, h0 = 0.f, h1 = 0.f;
-    int key = kSentinel, fxrel = 0, srel = 0;
+    int key = kSentinel;
     if (act) {
       const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
       float fa;
       key = bin_split(fminf(fmaxf(ldval(A + idx), 0.f), L), nb, &fa);
       h1 = parzen_upper(fa);
       h0 = 1.f - h1;
-      float B = row_voxel_warp<DIM, T>(g, M, cyz, x, y, z, f0, bx, &fxrel, gm);
+      const float bx[4] = {xt.bf[p], xt.bf[32 + p], xt.bf[64 + p], xt.bf[96 + p]};
+      float B = row_warp<DIM, T>(g, M, cyz, xt.frel[p], bx, x, y, z, gm);
       B = fminf(fmaxf(B, 0.f), L);
       float fb;
       const int kb = bin_split(B, nb, &fb);
       dm1 = parzen_upper_deriv(fb);
       dm2 = (2.f * (float)kb + 1.f) * dm1;
-      const int scx = sb_cell(g, 0, x, &t);
-      bspline4(t, bsx);
-      srel = scx - cb0;
     }
     const bool live = act && (gm[0] != 0.f || gm[1] != 0.f || (DIM == 3 && gm[2] != 0.f));
-    __syncwarp();
     if (!__any_sync(0xffffffffu, live)) continue;  // grad M == 0 on the whole row
 
-    // Row tables: U, V contracted over the y/z bins for the row's x-bins.
-    const int lb1 = scy - cb1, lb2 = scz - cb2;
+    // Row tables: U, V over the y bins (z done per plane) for the row's x-bins.
+    const float* UZr = UZ + zl * p01;
+    const float* VZr = VZ + zl * p01;
     for (int tt = lane; tt < 2 * NXB; tt += 32) {
       const int b = tt % NXB;
-      const float* tab = tt < NXB ? Ut : Vt;
+      const float* tab = tt < NXB ? UZr : VZr;
       float s = 0.f;
-      for (int jk = 0; jk < (b < g.hb[0] ? NJK : 0); ++jk) {
-        const int j = jk & 3, k = jk >> 2;
-        s += sy[j] * sz[k] * tab[((lb2 + k) * g.hb[1] + (lb1 + j)) * g.hb[0] + b];
-      }
+      if (b < g.hb[0])
+        for (int jj = 0; jj < 4; ++jj) s += ye.bs[jj] * tab[(ye.srel + jj) * g.hb[0] + b];
       rowt[tt] = s;
     }
-    // Segments of equal a0; X contracted over y/z for each segment's two bins.
+    // Segments of equal a0; X over the y bins for each segment's two bins.
     const int prev = __shfl_up_sync(0xffffffffu, key, 1);
     const bool head = lane == 0 || key != prev;
     const unsigned heads = __ballot_sync(0xffffffffu, head);
     const int nseg = __popc(heads);
     if (head) mysegA[__popc(heads & ((1u << lane) - 1u))] = key;
     __syncwarp();
+    const float* XZr = XZ + (size_t)zl * p01 * nb;
     for (int it = lane; it < nseg * NXB * 2; it += 32) {
       const int s = it / (NXB * 2), rem = it % (NXB * 2), b = rem >> 1, slot = rem & 1;
       const int a = mysegA[s];
       float acc_x = 0.f;
       if (a != kSentinel && b < g.hb[0]) {
-        const int abin = a + slot;
-        for (int jk = 0; jk < NJK; ++jk) {
-          const int j = jk & 3, k = jk >> 2;
-          acc_x += sy[j] * sz[k] * Xt[(size_t)(((lb2 + k) * g.hb[1] + (lb1 + j)) * g.hb[0] + b) * nb + abin];
-        }
+        for (int jj = 0; jj < 4; ++jj)
+          acc_x += ye.bs[jj] * XZr[(size_t)((ye.srel + jj) * g.hb[0] + b) * nb + a + slot];
       }
       xy[(s * NXB + b) * 2 + slot] = acc_x;
     }
@@ -426,34 +578,36 @@ k_adjoint_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
       const int sidx = __popc(heads & ((2u << lane) - 1u)) - 1;
       float su = 0.f, sv = 0.f, sxr = 0.f;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int b = srel + i;
-        su += bsx[i] * rowt[b];
-        sv += bsx[i] * rowt[NXB + b];
-        sxr += bsx[i] * (h0 * xy[(sidx * NXB + b) * 2] + h1 * xy[(sidx * NXB + b) * 2 + 1]);
+      for (int b = 0; b < NXB; ++b) {
+        const float w = xt.bsp[b * 32 + p];
+        su += w * rowt[b];
+        sv += w * rowt[NXB + b];
+        sxr += w * (h0 * xy[(sidx * NXB + b) * 2] + h1 * xy[(sidx * NXB + b) * 2 + 1]);
       }
       G = scale * (dm2 * su + 2.f * dm1 * (sv - sxr));
     }
-    // Contributions to the row's control points (nxn x-nodes, DIM components).
-    // Value q = 10 k + p: component k, row x-node p (fxrel + l < nxn <= 10).
+    // Value q = 10 k + n: component k, row x-node n (xe.frel + l < nxn <= 10).
     float vals[32];
+    float bn[kMaxRowNodes];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float gk = (live && k < DIM) ? G * gm[k] : 0.f;
+    for (int nn = 0; nn < kMaxRowNodes; ++nn) bn[nn] = xt.bfp[nn * 32 + p];
 #pragma unroll
-      for (int p = 0; p < 10; ++p) vals[k * 10 + p] = gk * pick4(bx, p - fxrel);
+    for (int kk = 0; kk < 3; ++kk) {
+      const float gk = (live && kk < DIM) ? G * gm[kk] : 0.f;
+#pragma unroll
+      for (int nn = 0; nn < 10; ++nn) vals[kk * 10 + nn] = gk * bn[nn];
     }
     vals[30] = vals[31] = 0.f;
     const float tot = warp_reduce_scatter32(vals, lane);
-    // Lane q holds component q/10, x-node q%10: spread over the 16 y/z nodes.
+    // Lane q holds component q/10, x-node q%10: spread over the y/z nodes.
     const int kq = lane / 10, lq = lane % 10;
     if (lane < DIM * 10 && lq < nxn && tot != 0.f) {
-      const int lyf = fy - f1, lzf = fz - f2;
       for (int mn = 0; mn < NJK; ++mn) {
         const int m = mn & 3, n = mn >> 2;
-        const float w = by[m] * bz[n];
+        const float w = ye.bf[m] * ze.bf[n];
         if (w == 0.f) continue;
-        atomicAdd(gt + kq * nodes_tile + ((lzf + n) * g.hf[1] + (lyf + m)) * g.hf[0] + lq, tot * w);
+        atomicAdd(gt + kq * nodes_tile + ((ze.frel + n) * g.hf[1] + (ye.frel + m)) * g.hf[0] + lq,
+                  tot * w);
       }
     }
     __syncwarp();
@@ -463,8 +617,8 @@ k_adjoint_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
     const float val = gt[i];
     if (val == 0.f) continue;
     const int k = i / nodes_tile, nl = i % nodes_tile;
-    const int n0 = f0 + nl % g.hf[0], n1 = f1 + (nl / g.hf[0]) % g.hf[1],
-              n2 = f2 + nl / (g.hf[0] * g.hf[1]);
+    const int n0 = TO.f[0] + nl % g.hf[0], n1 = TO.f[1] + (nl / g.hf[0]) % g.hf[1],
+              n2 = TO.f[2] + nl / (g.hf[0] * g.hf[1]);
     if (n0 >= g.nf[0] || n1 >= g.nf[1] || n2 >= g.nf[2]) continue;
     atomicAdd(grad + k * g.ncoef + ((long long)n2 * g.nf[1] + n1) * g.nf[0] + n0, val);
   }

@@ -134,27 +134,13 @@ size_t acc_smem(const Geo& g, int nch) {
   return (size_t)g.hb[0] * g.hb[1] * g.hb[2] * g.nbins * nch * sizeof(unsigned long long);
 }
 
-size_t rows_acc_smem(const Geo& g, int ndim, int nxb) {
-  const size_t nv = (size_t)nxb * 4;
-  return acc_smem(g, 2) + sizeof(float) * kRowWarps * 32 * nv + sizeof(int) * kRowWarps * 32 +
-         sizeof(float) * kRowWarps * ndim * kMaxRowNodes +
-         sizeof(float) * ndim * g.hf[0] * g.hf[1] * g.hf[2];
-}
-
-size_t rows_adj_smem(const Geo& g, int ndim, int nxb) {
-  const size_t nbt = (size_t)g.hb[0] * g.hb[1] * g.hb[2];
-  const size_t hf = (size_t)g.hf[0] * g.hf[1] * g.hf[2];
-  return sizeof(float) * ndim * hf * 2 + sizeof(float) * nbt * (2 + g.nbins) +
-         sizeof(float) * kRowWarps * 2 * nxb + sizeof(float) * kRowWarps * 32 * nxb * 2 +
-         sizeof(int) * kRowWarps * 32 + sizeof(float) * kRowWarps * ndim * kMaxRowNodes;
-}
-
 // Row kernels need 32-wide tiles, at most 8 spatial x-bins and 10 FFD
 // x-nodes per row (FFD spacing >= 5, spatial-bin spacing >= ~5).
 bool rows_eligible(const Geo& g, int ndim, int* nxb) {
   if (g.tile[0] != 32 || g.hb[0] > 8 || g.hf[0] > 10) return false;
   *nxb = g.hb[0] <= 4 ? 4 : 8;
-  return rows_acc_smem(g, ndim, *nxb) <= 220 * 1024 && rows_adj_smem(g, ndim, *nxb) <= 220 * 1024;
+  return acc_rows_smem_bytes(g, ndim, *nxb) <= 220 * 1024 &&
+         adj_rows_smem_bytes(g, ndim, *nxb) <= 220 * 1024;
 }
 
 void set_tile(Geo& g, int ndim, int tx, int ty, int tz) {
@@ -178,12 +164,12 @@ srwcr_status choose_tile(Geo& g, int ndim, const int* req) {
                   acc_smem(g, 2));
     return SRWCR_OK;
   }
-  static const int cand3[][3] = {{32, 8, 8}, {32, 8, 4}, {32, 4, 4}, {32, 4, 2}, {32, 2, 2},
-                                 {16, 2, 2}, {8, 2, 2}, {8, 1, 1}, {4, 1, 1}};
-  static const int cand2[][3] = {{32, 32, 1}, {32, 16, 1}, {32, 8, 1}, {32, 4, 1},
+  static const int cand3[][3] = {{32, 16, 8}, {32, 8, 8}, {32, 8, 4}, {32, 4, 4}, {32, 4, 2},
+                                 {32, 2, 2}, {16, 2, 2}, {8, 2, 2}, {8, 1, 1}, {4, 1, 1}};
+  static const int cand2[][3] = {{32, 64, 1}, {32, 32, 1}, {32, 16, 1}, {32, 8, 1}, {32, 4, 1},
                                  {16, 4, 1}, {8, 2, 1}, {4, 1, 1}};
   const int (*cand)[3] = ndim == 3 ? cand3 : cand2;
-  const int nc = ndim == 3 ? 9 : 7;
+  const int nc = ndim == 3 ? 10 : 8;
   for (int i = 0; i < nc; ++i) {
     set_tile(g, ndim, cand[i][0], cand[i][1], cand[i][2]);
     if (acc_smem(g, 2) <= kSmemBudget) return SRWCR_OK;
@@ -245,10 +231,10 @@ void launch_rows_acc(srwcr_ctx* ctx, Level& lv, const float* c, int nblk) {
   const T* A = (const T*)lv.A;
   const T* M = (const T*)lv.M;
   if (lv.nxb_rows == 4)
-    k_accumulate_rows<DIM, T, 4><<<nblk, kBlock, lv.smem_acc_rows, ctx->stream>>>(
+    k_accumulate_rows<DIM, T, 4><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(
         lv.g, A, M, c, lv.perm, lv.S, lv.s1, lv.s2);
   else
-    k_accumulate_rows<DIM, T, 8><<<nblk, kBlock, lv.smem_acc_rows, ctx->stream>>>(
+    k_accumulate_rows<DIM, T, 8><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(
         lv.g, A, M, c, lv.perm, lv.S, lv.s1, lv.s2);
 }
 
@@ -258,10 +244,10 @@ void launch_rows_adj(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD,
   const T* A = (const T*)lv.A;
   const T* M = (const T*)lv.M;
   if (lv.nxb_rows == 4)
-    k_adjoint_rows<DIM, T, 4><<<nblk, kBlock, lv.smem_adj_rows, ctx->stream>>>(
+    k_adjoint_rows<DIM, T, 4><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(
         lv.g, A, M, c, lv.perm, lv.U, lv.V, lv.X, gD, invZ, g);
   else
-    k_adjoint_rows<DIM, T, 8><<<nblk, kBlock, lv.smem_adj_rows, ctx->stream>>>(
+    k_adjoint_rows<DIM, T, 8><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(
         lv.g, A, M, c, lv.perm, lv.U, lv.V, lv.X, gD, invZ, g);
 }
 
@@ -490,8 +476,8 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     lv.smem_adj = sizeof(float) * cfg->ndim * g.hf[0] * g.hf[1] * g.hf[2];
     lv.rows = rows_eligible(g, cfg->ndim, &lv.nxb_rows);
     if (lv.rows) {
-      lv.smem_acc_rows = rows_acc_smem(g, cfg->ndim, lv.nxb_rows);
-      lv.smem_adj_rows = rows_adj_smem(g, cfg->ndim, lv.nxb_rows);
+      lv.smem_acc_rows = acc_rows_smem_bytes(g, cfg->ndim, lv.nxb_rows);
+      lv.smem_adj_rows = adj_rows_smem_bytes(g, cfg->ndim, lv.nxb_rows);
       const long long nrows = (long long)((g.n[0] + 31) / 32) * g.n[1] * g.n[2];
       CK(cudaMalloc((void**)&lv.perm, 32 * nrows));
     }
