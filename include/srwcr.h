@@ -164,6 +164,34 @@ srwcr_status srwcr_set_profiling(srwcr_ctx* ctx, int enable);
 srwcr_status srwcr_profile_read(srwcr_ctx* ctx, double* ms, int64_t* counts, int64_t* launches,
                                 int reset);
 
+/* Allocation-free SRWCR value, for callers that may not allocate device
+ * memory: code inside a CUDA-graph capture or an allocator callback, plugins
+ * whose host application owns every cudaMalloc, real-time loops that must
+ * not touch the allocator.  The paper has no counterpart; it is a deployment
+ * variant of srwcr_value (general per-voxel kernels) that needs no context.
+ *   cfg            problem as for srwcr_create (storage and pyramid_levels
+ *                  are ignored: level 0, float32 images)
+ *   fixed_dev, moving_dev  device float32 images ALREADY normalised to
+ *                  [0, L_eps] (L_eps = n_intensity_bins - 1), e.g.
+ *                  L*(v - min)/(max - min) in FP64 rounded to float32
+ *   c_dev          device coefficients (layout as for srwcr_value)
+ *   D_dev          device double receiving D of Eq. (9)
+ *   stream         cudaStream_t (NULL = legacy default)
+ * Work is queued on `stream`; the call does not synchronise.  Scratch is a
+ * file-scope device array of 16 MiB that every device that loads the library
+ * holds until exit; problems needing more (about 28 bytes per spatial bin
+ * and intensity bin) are rejected with SRWCR_EINVAL.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it, so make that first call before any stream capture.  Every call
+ * shares the array and re-zeroes the parts it accumulates into: calls that
+ * overlap on the GPU (other streams, other host threads) race.  The
+ * normalising factor Z is the voxel count (weights sum to one per voxel),
+ * so D can differ from srwcr_value's in the last digits.  No cudaMalloc,
+ * cudaFree or other allocation happens. */
+srwcr_status srwcr_value_noalloc(const srwcr_config* cfg, const float* fixed_dev,
+                                 const float* moving_dev, const float* c_dev, double* D_dev,
+                                 void* stream);
+
 /* L-BFGS options (Sec. II-F: 5 corrections; 200/200/120 iterations per
  * level; backtracking with a Wolfe condition; stop when the metric is stable
  * over the last 20 steps). */

@@ -30,7 +30,7 @@ EXPORTS = ("srwcr_create", "srwcr_destroy", "srwcr_last_error", "srwcr_level_inf
            "srwcr_value_and_grad_host", "srwcr_forward", "srwcr_backward",
            "srwcr_region_stats", "srwcr_debug_bins", "srwcr_debug_warp",
            "srwcr_lbfgs_default_opts", "srwcr_register", "srwcr_set_profiling",
-           "srwcr_profile_read")
+           "srwcr_profile_read", "srwcr_value_noalloc")
 
 
 class SrwcrError(RuntimeError):
@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "srwcr_profile_read": (st, [vp, vp, vp, i64p, ctypes.c_int]),
         "srwcr_register": (st, [vp, vp, ctypes.c_int, ctypes.POINTER(LbfgsOpts),
                                 ctypes.POINTER(Report)]),
+        "srwcr_value_noalloc": (st, [ctypes.POINTER(Config), vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -788,5 +789,129 @@ void srwcr_lbfgs_default_opts(srwcr_lbfgs_opts* o) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free value entry point (srwcr_value_noalloc).
+//
+// For callers that cannot allocate device memory: code running inside a
+// CUDA-graph capture or a stream-ordered allocator's callback, plugins of a
+// host application that owns every cudaMalloc, or real-time loops that must
+// not touch the allocator.  All scratch (fixed-point accumulators, region
+// statistics and tables) lives in one file-scope device array of
+// kNoAllocScratchBytes, which every device that loads this library keeps
+// until the process exits.  Host code only sees that array's name as a
+// host-side stand-in, never as a device address, so the device address is
+// obtained once per device with cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" srwcr_status srwcr_value_noalloc(const srwcr_config* cfg, const float* fixed_dev,
+                                            const float* moving_dev, const float* c_dev,
+                                            double* D_dev, void* stream) {
+  if (!cfg || !fixed_dev || !moving_dev || !c_dev || !D_dev)
+    return fail(SRWCR_EINVAL, "null argument");
+  if (cfg->ndim != 2 && cfg->ndim != 3) return fail(SRWCR_EINVAL, "ndim must be 2 or 3");
+  if (cfg->n_intensity_bins < 2 || cfg->n_intensity_bins > 256)
+    return fail(SRWCR_EINVAL, "n_intensity_bins must be in [2, 256]");
+  for (int d = 0; d < cfg->ndim; ++d) {
+    if (cfg->dims[d] < 2 || cfg->dims[d] > 65535) return fail(SRWCR_EINVAL, "dims[%d] out of range", d);
+    if (cfg->ffd_spacing[d] < 1 || cfg->ffd_spacing[d] > cfg->dims[d])
+      return fail(SRWCR_EINVAL, "ffd_spacing[%d] out of range", d);
+    if (cfg->sbin_intervals[d] < 0) return fail(SRWCR_EINVAL, "negative sbin_intervals");
+  }
+  if (cfg->tile[0] < 0 || cfg->tile[1] < 0 || cfg->tile[2] < 0)
+    return fail(SRWCR_EINVAL, "negative tile size");
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // Device address of the scratch array, looked up once per device.
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(SRWCR_EINVAL, "device %d beyond the %d devices this entry point serves", dev,
+                kNoAllocMaxDevices);
+  unsigned char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return fail(SRWCR_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = p;
+    }
+    scratch = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  }
+
+  Geo g;
+  const int dims[3] = {cfg->dims[0], cfg->dims[1], cfg->ndim == 3 ? cfg->dims[2] : 1};
+  RET_IF(make_geo(*cfg, dims, g));
+  const size_t R = (size_t)g.R, nb = (size_t)g.nbins;
+  const size_t offS = 0;
+  const size_t offPf = align256(offS + sizeof(unsigned long long) * R * nb * 2);
+  const size_t offP = align256(offPf + sizeof(unsigned long long) * R * nb);
+  const size_t offX = align256(offP + sizeof(double) * R * nb);
+  const size_t offU = align256(offX + sizeof(float) * R * nb);
+  const size_t offV = align256(offU + sizeof(float) * R);
+  const size_t offDr = align256(offV + sizeof(float) * R);
+  const size_t offSt = align256(offDr + sizeof(double) * R);
+  const size_t offNd = align256(offSt + sizeof(double) * R * 4);
+  const size_t need = offNd + sizeof(int);
+  if (need > kNoAllocScratchBytes)
+    return fail(SRWCR_EINVAL,
+                "problem needs %zu bytes of scratch (%zu spatial bins x %zu intensity bins); "
+                "the allocation-free entry point holds %zu bytes",
+                need, R, nb, kNoAllocScratchBytes);
+  unsigned long long* S = reinterpret_cast<unsigned long long*>(scratch + offS);
+  unsigned long long* Pfix = reinterpret_cast<unsigned long long*>(scratch + offPf);
+  double* P = reinterpret_cast<double*>(scratch + offP);
+  float* X = reinterpret_cast<float*>(scratch + offX);
+  float* U = reinterpret_cast<float*>(scratch + offU);
+  float* V = reinterpret_cast<float*>(scratch + offV);
+  double* Dr = reinterpret_cast<double*>(scratch + offDr);
+  double* stats = reinterpret_cast<double*>(scratch + offSt);
+  int* ndeg = reinterpret_cast<int*>(scratch + offNd);
+
+  RET_IF(set_smem_limits<float>());
+  double sP, s1, s2;
+  fixed_scales(g, cfg->ndim, &sP, &s1, &s2);
+  // Everything the kernels accumulate into starts at zero on every call.
+  CK(cudaMemsetAsync(S, 0, sizeof(unsigned long long) * R * nb * 2, st));
+  CK(cudaMemsetAsync(Pfix, 0, sizeof(unsigned long long) * R * nb, st));
+  const int nblk = g.ntile[0] * g.ntile[1] * g.ntile[2];
+  if (cfg->ndim == 3) {
+    k_accumulate<3, float, true><<<nblk, kBlock, acc_smem(g, 1), st>>>(
+        g, fixed_dev, moving_dev, nullptr, Pfix, (float)sP, 0.f);
+    k_accumulate<3, float, false><<<nblk, kBlock, acc_smem(g, 2), st>>>(
+        g, fixed_dev, moving_dev, c_dev, S, (float)s1, (float)s2);
+  } else {
+    k_accumulate<2, float, true><<<nblk, kBlock, acc_smem(g, 1), st>>>(
+        g, fixed_dev, moving_dev, nullptr, Pfix, (float)sP, 0.f);
+    k_accumulate<2, float, false><<<nblk, kBlock, acc_smem(g, 2), st>>>(
+        g, fixed_dev, moving_dev, c_dev, S, (float)s1, (float)s2);
+  }
+  CKL();
+  k_fixed_to_double<<<256, 256, 0, st>>>(Pfix, 1.0 / sP, P, (long long)(R * nb));
+  CKL();
+  // Z = N: the spatial weights and Parzen weights each sum to one per voxel.
+  const double invZ = 1.0 / (double)g.nvox;
+  const int fblk = (int)((R * 32 + kBlock - 1) / kBlock);
+  k_finalize<<<fblk, kBlock, 0, st>>>(g, P, S, 1.0 / s1, 1.0 / s2, invZ, U, V, X, Dr, stats);
+  CKL();
+  k_reduce_D<<<1, 1024, 0, st>>>(Dr, stats, g.R, D_dev, ndeg);
+  CKL();
+  return SRWCR_OK;
+}
 
 #include "lbfgs.cuh"
