@@ -12,8 +12,9 @@ this repository adopts:
   * Armijo constant c1 = 1e-4, weak-Wolfe curvature constant c2 = 0.9;
     the step halves when Armijo fails, doubles when only the curvature test
     fails; at most ``max_ls`` trials;
-  * stop when |D_k - D_{k-w}| <= rtol * |D_k| for the window w (20), when the
-    gradient vanishes, or after ``max_iter`` iterations.
+  * stop when |D_k - D_{k-w}| <= rtol * |D_k| for the window w (20; w <= 0
+    turns this test off), when the gradient vanishes, or after ``max_iter``
+    iterations.
 """
 from __future__ import annotations
 
@@ -116,7 +117,7 @@ def minimise(fg: Callable[[np.ndarray], Tuple[float, np.ndarray]], x0: np.ndarra
         fhist.append(f)
         hist.append((it, f, float(np.linalg.norm(g)), alpha, n_evals))
         w = opts.stable_window
-        if len(fhist) > w and abs(fhist[-1] - fhist[-1 - w]) <= opts.stable_rtol * abs(fhist[-1]):
+        if w > 0 and len(fhist) > w and abs(fhist[-1] - fhist[-1 - w]) <= opts.stable_rtol * abs(fhist[-1]):
             status = "stable"
             break
     return LbfgsResult(x, f, it, n_evals, status, hist)

@@ -1,0 +1,157 @@
+"""GPU tests of the L-BFGS driver (Sec. II-F) and the autograd form.
+
+* L-BFGS: one iteration from c = 0 is a steepest-descent step of unit length
+  with the same Armijo/Wolfe line search as the oracle's loop, so the
+  coefficients after it agree with the FP64 oracle's; over 50 iterations on the
+  2-D workload both decrease D monotonically and end at close values.
+* autograd: forward equals srwcr_value, backward equals gD * dD/dc from
+  srwcr_value_and_grad (warp recomputed), a stale backward re-runs its own
+  forward, and on the 160^3 OCT workload the gradient matches central
+  differences of the GPU value (step 1e-3 voxel, 200 coefficients) and the
+  oracle gradient at those coefficients.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import lbfgs
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def engine(prob, f, m, **kw):
+    import paper_1804_05061_b300 as eng
+    return eng.from_problem(prob, f, m, **kw)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    pair = synth.make_pair("c1_2d_128")
+    geo = oracle.Geometry.from_problem(pair.prob)
+    A, M = oracle.prepare(pair.fixed, pair.moving, pair.prob.n_bins)
+    return pair, geo, A, M
+
+
+def gpu_register(e, n_iter, window=20):
+    o = e.default_opts()
+    o.max_iter[0] = n_iter
+    o.stable_window = window
+    c = e.zeros()
+    rep = e.register(c, 1, o)
+    return c, rep
+
+
+def test_first_lbfgs_iteration_matches_oracle(c1):
+    pair, geo, A, M = c1
+    prob = pair.prob
+    e = engine(prob, pair.fixed, pair.moving)
+    c, rep = gpu_register(e, 1)
+    assert rep.iterations[0] == 1
+
+    def fg(x):
+        D, g, _ = oracle.value_and_grad(geo, A, M, x.reshape(prob.coef_shape))
+        return D, g.ravel()
+
+    res = lbfgs.minimise(fg, np.zeros(prob.n_params), lbfgs.LbfgsOptions(max_iter=1))
+    cg = c.cpu().numpy().ravel().astype(np.float64)
+    assert np.abs(cg - res.x).max() <= 1e-4 * max(np.abs(res.x).max(), 1e-12)
+    assert abs(rep.final_value[0] - res.f) <= 1e-5 * res.f
+
+
+def test_fifty_lbfgs_iterations_decrease_and_agree_with_oracle(c1):
+    pair, geo, A, M = c1
+    prob = pair.prob
+    e = engine(prob, pair.fixed, pair.moving)
+    c, rep = gpu_register(e, 50, window=0)
+    D0 = e.value(e.zeros())
+    Dg = e.value(c)
+    assert abs(rep.final_value[0] - Dg) <= 1e-12 * Dg + 1e-15
+
+    def fg(x):
+        D, g, _ = oracle.value_and_grad(geo, A, M, x.reshape(prob.coef_shape))
+        return D, g.ravel()
+
+    res = lbfgs.minimise(fg, np.zeros(prob.n_params),
+                         lbfgs.LbfgsOptions(max_iter=50, stable_window=0))
+    fs = [h[1] for h in res.history]
+    assert all(f1 <= f0 for f0, f1 in zip(fs, fs[1:]))
+    assert Dg < 0.9 * D0 and res.f < 0.9 * D0
+    # Same method, different arithmetic (FP32 vectors vs FP64): the runs end
+    # at nearby values.
+    assert abs(Dg - res.f) <= 2e-2 * res.f, (Dg, res.f)
+
+
+def test_pyramid_registration_runs_coarse_to_fine():
+    prob = synth.problem(3, (64, 64, 32), (8, 8, 8), (4, 4, 2), 32)
+    f, m = synth.small_pair("ct", prob.dims, prob.ffd_spacing, 2.0, 5)
+    e = engine(prob, f, m, pyramid_levels=2)
+    o = e.default_opts()
+    o.max_iter[0], o.max_iter[1] = 10, 10
+    c = e.zeros()
+    D0 = e.value(c)
+    rep = e.register(c, 2, o)
+    assert rep.levels_run == 2 and rep.iterations[1] > 0 and rep.iterations[0] > 0
+    assert e.value(c) < D0
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+def test_autograd_forward_backward_match_entry_points():
+    from paper_1804_05061_b300.autograd import srwcr
+    prob = synth.problem(3, (48, 40, 24), (6, 6, 6), (2, 2, 2), 32)
+    f, m = synth.small_pair("ct", prob.dims, prob.ffd_spacing, 2.0, 31)
+    e = engine(prob, f, m)
+    c = torch.from_numpy(synth.coefficients(prob, 32, 1.5)).cuda().requires_grad_(True)
+    D = srwcr(c, e)
+    (2.5 * D).backward()
+    Dv, g = e.value_and_grad(c.detach())
+    assert float(D) == Dv
+    assert torch.allclose(c.grad, 2.5 * g, rtol=1e-5, atol=1e-7 * float(g.abs().max()))
+
+
+def test_autograd_stale_backward_recomputes_its_forward():
+    from paper_1804_05061_b300.autograd import srwcr
+    prob = synth.problem(2, (100, 77), (7, 7), (3, 2), 16)
+    f, m = synth.small_pair("ellipse", prob.dims[:2], prob.ffd_spacing[:2], 2.0, 33)
+    e = engine(prob, f, m)
+    c1 = torch.from_numpy(synth.coefficients(prob, 34, 1.5)).cuda().requires_grad_(True)
+    c2 = torch.from_numpy(synth.coefficients(prob, 35, 1.5)).cuda()
+    D1 = srwcr(c1, e)
+    e.value(c2)                      # overwrites the level's tables
+    D1.backward()
+    _, g1 = e.value_and_grad(c1.detach())
+    assert torch.allclose(c1.grad, g1, rtol=1e-5, atol=1e-7 * float(g1.abs().max()))
+
+
+def test_autograd_gradient_matches_finite_differences_and_oracle_on_oct():
+    from paper_1804_05061_b300.autograd import srwcr
+    pair = synth.make_pair("c3_oct_160")
+    prob = pair.prob
+    e = engine(prob, pair.fixed, pair.moving)
+    c0 = synth.coefficients(prob, 3001, 1.5)
+    c = torch.from_numpy(c0).cuda().requires_grad_(True)
+    srwcr(c, e).backward()
+    g = c.grad.detach().cpu().numpy().ravel().astype(np.float64)
+    rng = np.random.default_rng(3)
+    idx = rng.choice(prob.n_params, 200, replace=False)
+    h = 1e-3
+    fd = np.empty(idx.size)
+    base = torch.from_numpy(c0).cuda().view(-1)
+    for n, i in enumerate(idx):
+        cp = base.clone(); cp[i] += h
+        cm = base.clone(); cm[i] -= h
+        fd[n] = (e.value(cp.view(c.shape)) - e.value(cm.view(c.shape))) / (2 * h)
+    gs = g[idx]
+    scale = np.abs(g).max()
+    # Central differences of the FP32 value are accurate to O(h^2) plus FP32
+    # noise of D / h; compare on the scale of the largest gradient entry.
+    assert np.abs(fd - gs).max() <= 2e-2 * scale, np.abs(fd - gs).max() / scale
+    assert np.corrcoef(fd, gs)[0, 1] > 0.999
+    geo = oracle.Geometry.from_problem(prob)
+    A, M = oracle.prepare(pair.fixed, pair.moving, prob.n_bins)
+    st = oracle.value(geo, A, M, c0)
+    go = oracle.gradient_at(geo, A, M, c0, st, idx)
+    assert np.abs(gs - go).max() <= 1e-3 * scale
