@@ -220,12 +220,23 @@ __device__ __forceinline__ float pick4(const float b[4], int i) {
 }
 
 // Bytes of the value kernel's shared memory (must match the carve-up below).
+// Words per y/z bin of the split histogram: 2 * nabin * hb0 rounded up to
+// 8 (mod 32), so the 4 y/z groups of a fold pass fall on disjoint banks.
+// The intensity axis holds only the fixed-image bins the tile uses (a static
+// per-tile mask), in compact order.
+__host__ __device__ inline int hist_yz_stride(const Geo& g) {
+  const int w = 2 * g.nabin * g.hb[0];
+  return ((w + 23) / 32) * 32 + 8;
+}
+
 __host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int nxb) {
-  const size_t HB = (size_t)g.hb[0] * g.hb[1] * g.hb[2];
+  const size_t nyz = (size_t)g.hb[1] * g.hb[2];
   const size_t nv = (size_t)nxb * 4;
-  size_t b = HB * 2 * (size_t)g.nbins * 8;                  // hist (u64)
+  size_t b = 3 * nyz * hist_yz_stride(g) * sizeof(unsigned);  // hist words (3 per entry)
   b += sizeof(float) * kAccWarps * 32 * nv;                 // segS
   b += sizeof(int) * kAccWarps * 32;                        // segA
+  b += sizeof(int) * kAccWarps * 64 * 2;                    // bin list
+  b += sizeof(int) * ((size_t)g.nbins + g.nabin);           // bin <-> compact index
   b += sizeof(float) * kAccWarps * dim * kMaxRowNodes;      // cyz
   b += sizeof(float) * xtab_words(nxb);                     // x tables
   b += sizeof(AxisEntry) * (g.tile[1] + g.tile[2]);         // y, z tables
@@ -240,21 +251,30 @@ template <int DIM, typename T, int NXB>
 __global__ void __launch_bounds__(kAccWarps * 32, 2)
 k_accumulate_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
                   const float* __restrict__ c, const unsigned char* __restrict__ perm,
-                  unsigned long long* __restrict__ acc, float s1, float s2) {
+                  const unsigned* __restrict__ binmask, unsigned long long* __restrict__ acc,
+                  float s1, float s2) {
   extern __shared__ unsigned long long smem_u64[];
   constexpr int NV = NXB * 4;                 // (x-bin, slot, moment): v[4b + 2 slot + ch]
-  constexpr int NJK = DIM == 3 ? 16 : 4;      // y/z bins of a row
+  constexpr int NK = DIM == 3 ? 4 : 1;        // z bins of a row
   const int nb = g.nbins;
   const float L = (float)(nb - 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int P12 = g.hb[1] * g.hb[2];
-  const int HB = g.hb[0] * P12;
-  // Histogram layout hist[a][ch][x-bin][z-bin][y-bin] (u64): the lanes of a
-  // fold pass touch consecutive y/z bins, so their adds hit distinct banks.
-  unsigned long long* hist = smem_u64;
-  float* segS = reinterpret_cast<float*>(hist + (size_t)HB * nb * 2);
+  // Split fixed-point histogram: three 32-bit words per [y/z bin][bin]
+  // [moment][x-bin] holding bits 0-19, 20-39 and 40-63 of each update (an
+  // FP32 update has 24 significant bits, so it touches at most two of them).
+  // Every entry receives at most one update per row (<= 256 per CTA) of value
+  // < 2^56, so no word overflows; the flush recombines the three exactly.
+  const int S = hist_yz_stride(g);
+  const int NYZ = g.hb[1] * g.hb[2];
+  unsigned* hlo = reinterpret_cast<unsigned*>(smem_u64);
+  unsigned* hmid = hlo + (size_t)NYZ * S;
+  unsigned* hhi = hmid + (size_t)NYZ * S;
+  float* segS = reinterpret_cast<float*>(hhi + (size_t)NYZ * S);
   int* segA = reinterpret_cast<int*>(segS + kAccWarps * 32 * NV);
-  float* cyz_all = reinterpret_cast<float*>(segA + kAccWarps * 32);
+  int* binl = segA + kAccWarps * 32;          // [warp][64][2]: a, (s | slot<<8 | merge<<9)
+  int* a2c = binl + kAccWarps * 64 * 2;       // fixed-image bin -> compact index (-1: unused)
+  int* c2a = a2c + nb;                        // compact index -> bin
+  float* cyz_all = reinterpret_cast<float*>(c2a + g.nabin);
   const XTab xt = xtab_carve(cyz_all + kAccWarps * DIM * kMaxRowNodes, NXB);
   AxisEntry* yt = reinterpret_cast<AxisEntry*>(reinterpret_cast<float*>(xt.frel) + xtab_words(NXB));
   AxisEntry* zt = yt + g.tile[1];
@@ -262,9 +282,23 @@ k_accumulate_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
   float* cyz = cyz_all + warp * DIM * kMaxRowNodes;
   float* mysegS = segS + warp * 32 * NV;
   int* mysegA = segA + warp * 32;
+  int* mybins = binl + warp * 64 * 2;
 
   const TileOrigin TO = tile_setup<DIM>(g);
-  for (int i = threadIdx.x; i < HB * nb * 2; i += blockDim.x) hist[i] = 0ull;
+  for (int i = threadIdx.x; i < 3 * NYZ * S; i += blockDim.x) hlo[i] = 0u;
+  {
+    const int words = (nb + 31) >> 5;
+    const unsigned* tmask = binmask + (size_t)blockIdx.x * words;
+    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+      const int w = a >> 5;
+      const unsigned mw = __ldg(tmask + w);
+      int before = __popc(mw & ((1u << (a & 31)) - 1u));
+      for (int k = 0; k < w; ++k) before += __popc(__ldg(tmask + k));
+      const bool used = (mw >> (a & 31)) & 1u;
+      a2c[a] = used ? before : -1;
+      if (used) c2a[before] = a;
+    }
+  }
   build_xtab<NXB>(g, TO, xt);
   build_axis_tables<DIM>(g, TO, yt, zt);
   __syncthreads();
@@ -275,10 +309,8 @@ k_accumulate_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
   const int xlast = min(TO.o[0] + 31, g.n[0] - 1);
   const int nxn = xlast / g.fsp[0] - TO.f[0] + 4;   // FFD x-nodes of the row
   const int nrows = g.tile[1] * g.tile[2];
-  // Fold lane roles: moment ch (upper/lower half-warp), y/z bin jk.
-  const int fch = lane >> 4, fjk = lane & 15;
-  const int fj = fjk & 3, fk = fjk >> 2;
-  const float fscale = fch ? s2 : s1;
+  // Fold lane roles: item t of a pass (8 per pass), y offset fg (j of the bin).
+  const int ft = lane & 7, fg = lane >> 3;
   for (int row = warp; row < nrows; row += kAccWarps) {
     const int yl = row % g.tile[1], zl = row / g.tile[1];
     const int y = TO.o[1] + yl, z = TO.o[2] + zl;
@@ -339,57 +371,88 @@ k_accumulate_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
         if (ok) v[q] += ov;
       }
     }
-    int nseg = __popc(heads);
-    if (head) {
-      const int sidx = __popc(heads & ((1u << lane) - 1u));
+    // Bin list.  Segment s (key a) adds bin a (slot 0, plus slot 1 of s-1 when
+    // that segment's key is a-1) and, unless segment s+1 has key a+1, bin a+1
+    // (slot 1 alone).
+    const int sidx = __popc(heads & ((1u << lane) - 1u));
+    const int next_head = above ? __ffs(above) - 1 : -1;
+    const int next_key = __shfl_sync(0xffffffffu, key, next_head < 0 ? lane : next_head);
+    const bool real = head && key != kSentinel;
+    const bool upper = real && (next_head < 0 || next_key != key + 1);
+    const unsigned below = heads & ((1u << lane) - 1u);
+    const int prev_head = below ? 31 - __clz(below) : lane;
+    const int prev_key = __shfl_sync(0xffffffffu, key, prev_head);
+    const bool merge = real && below && prev_key + 1 == key;
+    const unsigned emit0 = __ballot_sync(0xffffffffu, real);
+    const unsigned emit1 = __ballot_sync(0xffffffffu, upper);
+    const unsigned lt = (1u << lane) - 1u;
+    const int pos = __popc(emit0 & lt) + __popc(emit1 & lt);
+    const int nbin = __popc(emit0) + __popc(emit1);
+    if (real) {
       mysegA[sidx] = key;
 #pragma unroll
       for (int q = 0; q < NV; ++q) mysegS[sidx * NV + q] = v[q];
+      mybins[2 * pos] = key;
+      mybins[2 * pos + 1] = sidx | (merge ? (1 << 9) : 0);
+      if (upper) {
+        mybins[2 * pos + 2] = key + 1;
+        mybins[2 * pos + 3] = sidx | (1 << 8);
+      }
     }
     __syncwarp();
-    if (mysegA[nseg - 1] == kSentinel) --nseg;   // lanes past the image edge
-    // Fold.  Intensity bin e of the row: a_s (slot 0 of segment s, plus slot 1
-    // of segment s-1 when a_{s-1} + 1 = a_s) and a_s + 1 (slot 1 of s, when
-    // a_{s+1} != a_s + 1).  Each lane adds one moment to one y/z bin.
-    const float wjk = (fjk < NJK) ? ye.bs[fj] * ze.bs[fk] : 0.f;
-    const int yz_off = (ze.srel + fk) * g.hb[1] + (ye.srel + fj);
-    for (int s = 0; s < nseg; ++s) {
-      const int a = mysegA[s];
-      const bool merge_prev = s > 0 && mysegA[s - 1] + 1 == a;
-      const bool own_upper = s + 1 == nseg || mysegA[s + 1] != a + 1;
-      for (int half = 0; half < 2; ++half) {
-        if (half == 1 && !own_upper) continue;   // warp-uniform
-        const int abin = a + half;
-        const unsigned long long* dummy = nullptr;
-        (void)dummy;
+    // Fold: 8 (bin, moment, x-bin) items per pass, each lane adds its item to
+    // the 4 z bins of y bin fg (3-D; one z bin in 2-D).
+    float wk[NK];
+    int yzb[NK];
 #pragma unroll
-        for (int b = 0; b < NXB; ++b) {
-          if (b >= g.hb[0]) break;
-          float val;
-          if (half == 0) {
-            val = mysegS[s * NV + 4 * b + fch];
-            if (merge_prev) val += mysegS[(s - 1) * NV + 4 * b + 2 + fch];
-          } else {
-            val = mysegS[s * NV + 4 * b + 2 + fch];
-          }
-          if (val != 0.f && wjk != 0.f)
-            atomicAdd(hist + ((size_t)(abin * 2 + fch) * g.hb[0] + b) * P12 + yz_off,
-                      __float2ull_rn(val * fscale * wjk));
-        }
+    for (int m = 0; m < NK; ++m) {
+      wk[m] = ye.bs[fg] * ze.bs[m];
+      yzb[m] = ((ze.srel + m) * g.hb[1] + (ye.srel + fg)) * S;
+    }
+    const int per_bin = 2 * NXB;
+    for (int f = ft; f < nbin * per_bin; f += 8) {
+      const int e = f / per_bin, r = f % per_bin;
+      const int ch = r / NXB, b = r % NXB;
+      if (b >= g.hb[0]) continue;
+      const int a = mybins[2 * e];
+      const int info = mybins[2 * e + 1];
+      const int sg = info & 0xff, slot = (info >> 8) & 1;
+      float val = mysegS[sg * NV + 4 * b + 2 * slot + ch];
+      if (info & (1 << 9)) val += mysegS[(sg - 1) * NV + 4 * b + 2 + ch];
+      if (val == 0.f) continue;
+      const float vs = val * (ch ? s2 : s1);
+      const int col = (a2c[a] * 2 + ch) * g.hb[0] + b;
+#pragma unroll
+      for (int m = 0; m < NK; ++m) {
+        const float u = vs * wk[m];
+        if (u == 0.f) continue;
+        // Exact split of u into 20-bit fields (power-of-two scalings, floors
+        // and fused subtractions of FP32 values are exact here).
+        const float hf = floorf(u * 0x1p-40f);
+        const float r1 = fmaf(hf, -0x1p40f, u);
+        const float mf = floorf(r1 * 0x1p-20f);
+        const unsigned lo = __float2uint_rn(fmaf(mf, -0x1p20f, r1));
+        const unsigned mid = (unsigned)mf, hi = (unsigned)hf;
+        const int at = yzb[m] + col;
+        if (lo) atomicAdd(hlo + at, lo);
+        if (mid) atomicAdd(hmid + at, mid);
+        if (hi) atomicAdd(hhi + at, hi);
       }
     }
     __syncwarp();
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < HB * nb * 2; i += blockDim.x) {
-    const unsigned long long val = hist[i];
+  const int wcols = 2 * g.nabin * g.hb[0];
+  for (int i = threadIdx.x; i < NYZ * S; i += blockDim.x) {
+    const int yz = i / S, col = i % S;
+    if (col >= wcols) continue;
+    const unsigned long long val =
+        ((unsigned long long)hhi[i] << 40) + ((unsigned long long)hmid[i] << 20) + hlo[i];
     if (!val) continue;
-    const int l1 = i % g.hb[1];
-    const int l2 = (i / g.hb[1]) % g.hb[2];
-    const int l0 = (i / P12) % g.hb[0];
-    const int ach = i / HB;
-    const int a = ach >> 1, ch = ach & 1;
-    const int r0 = TO.cb[0] + l0, r1 = TO.cb[1] + l1, r2 = TO.cb[2] + l2;
+    const int b = col % g.hb[0], ach = col / g.hb[0];
+    const int a = c2a[ach >> 1], ch = ach & 1;
+    const int l1 = yz % g.hb[1], l2 = yz / g.hb[1];
+    const int r0 = TO.cb[0] + b, r1 = TO.cb[1] + l1, r2 = TO.cb[2] + l2;
     if (r0 >= g.nsb[0] || r1 >= g.nsb[1] || r2 >= g.nsb[2]) continue;
     const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
     atomicAdd(acc + ((size_t)r * nb + a) * 2 + ch, val);
@@ -435,9 +498,9 @@ template <int DIM, typename T, int NXB>
 __global__ void __launch_bounds__(kAdjWarps * 32)
 k_adjoint_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
                const float* __restrict__ c, const unsigned char* __restrict__ perm,
-               const float* __restrict__ U, const float* __restrict__ V,
-               const float* __restrict__ X, const float* __restrict__ gscale, float invZ,
-               float* __restrict__ grad) {
+               const unsigned* __restrict__ binmask, const float* __restrict__ U,
+               const float* __restrict__ V, const float* __restrict__ X,
+               const float* __restrict__ gscale, float invZ, float* __restrict__ grad) {
   extern __shared__ float smem_f32[];
   const int nb = g.nbins;
   const float L = (float)(nb - 1);
@@ -468,28 +531,35 @@ k_adjoint_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
   build_axis_tables<DIM>(g, TO, yt, zt);
   __syncthreads();
   build_cz<DIM>(g, TO, c, zt, CZ);
-  // Region tables contracted over z for each of the tile's z-planes.
+  // Region tables contracted over z for each of the tile's z-planes.  X is
+  // only needed for the fixed-image bins present in the tile (a0 and a0+1 of
+  // its voxels, a static mask); other entries are never read.
+  const unsigned* tmask = binmask + (size_t)blockIdx.x * ((nb + 31) >> 5);
   {
-    const int nuv = 2 * g.tile[2] * p01;
-    const int n = nuv + g.tile[2] * p01 * nb;
+    const int nzp = g.tile[2] * p01;
+    const int n = nzp * (2 + nb);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       int zl, hb01, col;  // col: 0 = U, 1 = V, 2 + a = X[a]
-      if (i < nuv) {
-        col = i / (g.tile[2] * p01);
-        const int r = i % (g.tile[2] * p01);
+      if (i < 2 * nzp) {
+        col = i / nzp;
+        const int r = i - col * nzp;
         zl = r / p01;
-        hb01 = r % p01;
+        hb01 = r - zl * p01;
       } else {
-        const int r = i - nuv;
-        zl = r / (p01 * nb);
-        hb01 = (r / nb) % p01;
-        col = 2 + r % nb;
+        const int r = i - 2 * nzp;
+        const int zh = r / nb;
+        col = 2 + (r - zh * nb);
+        zl = zh / p01;
+        hb01 = zh - zl * p01;
+        const int a = col - 2;
+        if (!((__ldg(tmask + (a >> 5)) >> (a & 31)) & 1u)) continue;
       }
       const int r0 = TO.cb[0] + hb01 % g.hb[0], r1 = TO.cb[1] + hb01 / g.hb[0];
       float s = 0.f;
       if (r0 < g.nsb[0] && r1 < g.nsb[1]) {
         const AxisEntry& e = zt[zl];
         const int NZ = DIM == 3 ? 4 : 1;
+#pragma unroll
         for (int q = 0; q < NZ; ++q) {
           const int r2 = TO.cb[2] + e.srel + q;
           if (r2 >= g.nsb[2]) continue;
@@ -621,6 +691,23 @@ k_adjoint_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
               n2 = TO.f[2] + nl / (g.hf[0] * g.hf[1]);
     if (n0 >= g.nf[0] || n1 >= g.nf[1] || n2 >= g.nf[2]) continue;
     atomicAdd(grad + k * g.ncoef + ((long long)n2 * g.nf[1] + n1) * g.nf[0] + n0, val);
+  }
+}
+
+// Static per-tile mask of the fixed-image bins its voxels touch (a0, a0+1).
+template <int DIM, typename T>
+__global__ void k_tile_binmask(const Geo g, const T* __restrict__ A, unsigned* __restrict__ mask) {
+  const float L = (float)(g.nbins - 1);
+  const int words = (g.nbins + 31) >> 5;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.nvox;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.n[0]), y = (int)((i / g.n[0]) % g.n[1]),
+              z = (int)(i / ((long long)g.n[0] * g.n[1]));
+    const int t = (x / g.tile[0]) + g.ntile[0] * ((y / g.tile[1]) + g.ntile[1] * (z / g.tile[2]));
+    float fa;
+    const int a0 = bin_split(fminf(fmaxf(ldval(A + i), 0.f), L), g.nbins, &fa);
+    atomicOr(mask + (size_t)t * words + (a0 >> 5), 1u << (a0 & 31));
+    atomicOr(mask + (size_t)t * words + ((a0 + 1) >> 5), 1u << ((a0 + 1) & 31));
   }
 }
 

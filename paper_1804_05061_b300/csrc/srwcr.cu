@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
@@ -65,7 +66,8 @@ constexpr int kBlock = 256;
 constexpr size_t kSmemBudget = 112 * 1024;  // per CTA, two CTAs per SM
 
 struct Level {
-  Geo g{};
+  Geo g{};                            // geometry of the kernels that run per evaluation
+  Geo gv{};                           // general-path geometry (create-time statistics)
   void* A = nullptr;                  // normalised fixed image (storage type)
   void* M = nullptr;                  // normalised moving image (storage type)
   unsigned long long* S = nullptr;    // [R][nbins][2] fixed-point S1, S2 (also P scratch)
@@ -86,6 +88,7 @@ struct Level {
   bool rows = false;
   int nxb_rows = 0;
   unsigned char* perm = nullptr;
+  unsigned* binmask = nullptr;        // per tile: fixed-image bins present
   size_t smem_acc_rows = 0, smem_adj_rows = 0;
 };
 
@@ -137,11 +140,8 @@ size_t acc_smem(const Geo& g, int nch) {
 
 // Row kernels need 32-wide tiles, at most 8 spatial x-bins and 10 FFD
 // x-nodes per row (FFD spacing >= 5, spatial-bin spacing >= ~5).
-bool rows_eligible(const Geo& g, int ndim, int* nxb) {
-  if (g.tile[0] != 32 || g.hb[0] > 8 || g.hf[0] > 10) return false;
-  *nxb = g.hb[0] <= 4 ? 4 : 8;
-  return acc_rows_smem_bytes(g, ndim, *nxb) <= 220 * 1024 &&
-         adj_rows_smem_bytes(g, ndim, *nxb) <= 220 * 1024;
+bool rows_geometry_ok(const Geo& g) {
+  return g.tile[0] == 32 && g.hb[0] <= 8 && g.hf[0] <= 10 && g.tile[1] * g.tile[2] <= 256;
 }
 
 void set_tile(Geo& g, int ndim, int tx, int ty, int tz) {
@@ -165,12 +165,12 @@ srwcr_status choose_tile(Geo& g, int ndim, const int* req) {
                   acc_smem(g, 2));
     return SRWCR_OK;
   }
-  static const int cand3[][3] = {{32, 16, 8}, {32, 8, 8}, {32, 8, 4}, {32, 4, 4}, {32, 4, 2},
+  static const int cand3[][3] = {{32, 32, 8}, {32, 16, 8}, {32, 8, 8}, {32, 8, 4}, {32, 4, 4}, {32, 4, 2},
                                  {32, 2, 2}, {16, 2, 2}, {8, 2, 2}, {8, 1, 1}, {4, 1, 1}};
   static const int cand2[][3] = {{32, 64, 1}, {32, 32, 1}, {32, 16, 1}, {32, 8, 1}, {32, 4, 1},
                                  {16, 4, 1}, {8, 2, 1}, {4, 1, 1}};
   const int (*cand)[3] = ndim == 3 ? cand3 : cand2;
-  const int nc = ndim == 3 ? 10 : 8;
+  const int nc = ndim == 3 ? 11 : 8;
   for (int i = 0; i < nc; ++i) {
     set_tile(g, ndim, cand[i][0], cand[i][1], cand[i][2]);
     if (acc_smem(g, 2) <= kSmemBudget) return SRWCR_OK;
@@ -208,6 +208,7 @@ srwcr_status make_geo(const srwcr_config& cfg, const int dims[3], Geo& g) {
   g.nvox = (long long)g.n[0] * g.n[1] * g.n[2];
   g.ncoef = (long long)g.nf[0] * g.nf[1] * g.nf[2];
   g.R = (long long)g.nsb[0] * g.nsb[1] * g.nsb[2];
+  g.nabin = g.nbins;
   return choose_tile(g, nd, cfg.tile);
 }
 
@@ -225,6 +226,12 @@ void fixed_scales(const Geo& g, int ndim, double* sP, double* s1, double* s2) {
   *sP = std::ldexp(1.0, 62 - ceil_log2(box));
   *s1 = std::ldexp(1.0, 62 - ceil_log2(box * L));
   *s2 = std::ldexp(1.0, 62 - ceil_log2(box * L * L));
+  // The row kernels add sums over at most two 32-voxel row segments (terms
+  // <= L, L^2) into three 32-bit words (bits 0-19, 20-39, 40-63), at most
+  // 256 updates per word per CTA: one update stays below 2^56, so no word
+  // overflows.
+  *s1 = std::min(*s1, std::ldexp(1.0, 56 - ceil_log2(64.0 * L)));
+  *s2 = std::min(*s2, std::ldexp(1.0, 56 - ceil_log2(64.0 * L * L)));
 }
 
 template <int DIM, typename T>
@@ -233,10 +240,10 @@ void launch_rows_acc(srwcr_ctx* ctx, Level& lv, const float* c, int nblk) {
   const T* M = (const T*)lv.M;
   if (lv.nxb_rows == 4)
     k_accumulate_rows<DIM, T, 4><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(
-        lv.g, A, M, c, lv.perm, lv.S, lv.s1, lv.s2);
+        lv.g, A, M, c, lv.perm, lv.binmask, lv.S, lv.s1, lv.s2);
   else
     k_accumulate_rows<DIM, T, 8><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(
-        lv.g, A, M, c, lv.perm, lv.S, lv.s1, lv.s2);
+        lv.g, A, M, c, lv.perm, lv.binmask, lv.S, lv.s1, lv.s2);
 }
 
 template <int DIM, typename T>
@@ -246,16 +253,17 @@ void launch_rows_adj(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD,
   const T* M = (const T*)lv.M;
   if (lv.nxb_rows == 4)
     k_adjoint_rows<DIM, T, 4><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(
-        lv.g, A, M, c, lv.perm, lv.U, lv.V, lv.X, gD, invZ, g);
+        lv.g, A, M, c, lv.perm, lv.binmask, lv.U, lv.V, lv.X, gD, invZ, g);
   else
     k_adjoint_rows<DIM, T, 8><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(
-        lv.g, A, M, c, lv.perm, lv.U, lv.V, lv.X, gD, invZ, g);
+        lv.g, A, M, c, lv.perm, lv.binmask, lv.U, lv.V, lv.X, gD, invZ, g);
 }
 
 template <typename T>
 srwcr_status launch_accumulate(srwcr_ctx* ctx, Level& lv, const float* c, bool stat, float s0,
                                float s1) {
-  const int nblk = lv.g.ntile[0] * lv.g.ntile[1] * lv.g.ntile[2];
+  const Geo& gg = stat ? lv.gv : lv.g;
+  const int nblk = gg.ntile[0] * gg.ntile[1] * gg.ntile[2];
   const T* A = (const T*)lv.A;
   const T* M = (const T*)lv.M;
   if (!stat && lv.rows) {
@@ -264,13 +272,13 @@ srwcr_status launch_accumulate(srwcr_ctx* ctx, Level& lv, const float* c, bool s
     CKL();
     return SRWCR_OK;
   }
-  const size_t sm = stat ? acc_smem(lv.g, 1) : lv.smem_acc;
+  const size_t sm = stat ? acc_smem(gg, 1) : lv.smem_acc;
   if (ctx->cfg.ndim == 3) {
-    if (stat) k_accumulate<3, T, true><<<nblk, kBlock, sm, ctx->stream>>>(lv.g, A, M, c, lv.S, s0, s1);
-    else k_accumulate<3, T, false><<<nblk, kBlock, sm, ctx->stream>>>(lv.g, A, M, c, lv.S, s0, s1);
+    if (stat) k_accumulate<3, T, true><<<nblk, kBlock, sm, ctx->stream>>>(gg, A, M, c, lv.S, s0, s1);
+    else k_accumulate<3, T, false><<<nblk, kBlock, sm, ctx->stream>>>(gg, A, M, c, lv.S, s0, s1);
   } else {
-    if (stat) k_accumulate<2, T, true><<<nblk, kBlock, sm, ctx->stream>>>(lv.g, A, M, c, lv.S, s0, s1);
-    else k_accumulate<2, T, false><<<nblk, kBlock, sm, ctx->stream>>>(lv.g, A, M, c, lv.S, s0, s1);
+    if (stat) k_accumulate<2, T, true><<<nblk, kBlock, sm, ctx->stream>>>(gg, A, M, c, lv.S, s0, s1);
+    else k_accumulate<2, T, false><<<nblk, kBlock, sm, ctx->stream>>>(gg, A, M, c, lv.S, s0, s1);
   }
   CKL();
   return SRWCR_OK;
@@ -401,7 +409,8 @@ srwcr_status finish_sync(srwcr_ctx* ctx, Level& lv, double* D_host) {
 }
 
 void free_level(Level& lv) {
-  void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg, lv.perm};
+  void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg, lv.perm,
+                  lv.binmask};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   lv = Level();
@@ -415,6 +424,87 @@ srwcr_status normalise_into(srwcr_ctx* ctx, const float* src_dev, long long n, T
   const double L = ctx->cfg.n_intensity_bins - 1;
   k_normalise<T><<<1024, 256, 0, ctx->stream>>>(src_dev, n, part, nparts, L, out);
   CKL();
+  return SRWCR_OK;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+void launch_tile_binmask(srwcr_ctx* ctx, const Geo& g, const void* A, unsigned* mask) {
+  if (ctx->cfg.ndim == 3) k_tile_binmask<3, T><<<1024, 256, 0, ctx->stream>>>(g, (const T*)A, mask);
+  else k_tile_binmask<2, T><<<1024, 256, 0, ctx->stream>>>(g, (const T*)A, mask);
+}
+
+// Pick the largest 32-wide tile whose row kernels fit in shared memory.  The
+// value kernel's histogram holds only the fixed-image bins a tile uses, so
+// each candidate's per-tile masks are built on the device and the largest
+// per-tile count sizes the histogram.  Levels without such a tile keep the
+// general path.
+srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv) {
+  const srwcr_config& cfg = ctx->cfg;
+  const int nd = cfg.ndim;
+  static const int cand3[][3] = {{32, 32, 8}, {32, 16, 8}, {32, 8, 8}, {32, 8, 4}, {32, 4, 4},
+                                 {32, 4, 2}, {32, 2, 2}, {32, 1, 1}};
+  static const int cand2[][3] = {{32, 64, 1}, {32, 32, 1}, {32, 16, 1}, {32, 8, 1}, {32, 4, 1},
+                                 {32, 1, 1}};
+  std::vector<std::array<int, 3>> cands;
+  if (cfg.tile[0] > 0) {
+    if (cfg.tile[0] == 32) cands.push_back({32, std::max(1, cfg.tile[1]), std::max(1, cfg.tile[2])});
+  } else if (nd == 3) {
+    for (auto& t : cand3) cands.push_back({t[0], t[1], t[2]});
+  } else {
+    for (auto& t : cand2) cands.push_back({t[0], t[1], t[2]});
+  }
+  const int words = (lv.g.nbins + 31) / 32;
+  std::vector<unsigned> hmask;
+  for (const auto& t : cands) {
+    Geo g = lv.gv;
+    set_tile(g, nd, t[0], t[1], t[2]);
+    if (!rows_geometry_ok(g)) continue;
+    const size_t ntiles = (size_t)g.ntile[0] * g.ntile[1] * g.ntile[2];
+    unsigned* mask = nullptr;
+    CK(cudaMalloc((void**)&mask, sizeof(unsigned) * ntiles * words));
+    CK(cudaMemsetAsync(mask, 0, sizeof(unsigned) * ntiles * words, ctx->stream));
+    if (is_bf16(ctx)) launch_tile_binmask<__nv_bfloat16>(ctx, g, lv.A, mask);
+    else launch_tile_binmask<float>(ctx, g, lv.A, mask);
+    cudaError_t e = cudaGetLastError();
+    hmask.assign(ntiles * words, 0u);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hmask.data(), mask, sizeof(unsigned) * ntiles * words,
+                          cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      cudaFree(mask);
+      return fail(SRWCR_ECUDA, "tile bin masks: %s", cudaGetErrorString(e));
+    }
+    int nab = 1;
+    for (size_t tt = 0; tt < ntiles; ++tt) {
+      int cnt = 0;
+      for (int w = 0; w < words; ++w) cnt += __builtin_popcount(hmask[tt * words + w]);
+      nab = std::max(nab, cnt);
+    }
+    g.nabin = nab;
+    const int nxb = g.hb[0] <= 4 ? 4 : 8;
+    const size_t sa = acc_rows_smem_bytes(g, nd, nxb), sj = adj_rows_smem_bytes(g, nd, nxb);
+    if (sa > 220 * 1024 || sj > 220 * 1024) {
+      cudaFree(mask);
+      continue;
+    }
+    lv.g = g;
+    lv.rows = true;
+    lv.nxb_rows = nxb;
+    lv.binmask = mask;
+    lv.smem_acc_rows = sa;
+    lv.smem_adj_rows = sj;
+    const long long nrows = (long long)((g.n[0] + 31) / 32) * g.n[1] * g.n[2];
+    CK(cudaMalloc((void**)&lv.perm, 32 * nrows));
+    if (is_bf16(ctx)) k_row_perm<__nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(g, (const __nv_bfloat16*)lv.A, lv.perm);
+    else k_row_perm<float><<<1024, 256, 0, ctx->stream>>>(g, (const float*)lv.A, lv.perm);
+    CKL();
+    return SRWCR_OK;
+  }
   return SRWCR_OK;
 }
 
@@ -475,13 +565,7 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     CK(cudaMalloc((void**)&lv.ndeg, sizeof(int)));
     lv.smem_acc = acc_smem(g, 2);
     lv.smem_adj = sizeof(float) * cfg->ndim * g.hf[0] * g.hf[1] * g.hf[2];
-    lv.rows = rows_eligible(g, cfg->ndim, &lv.nxb_rows);
-    if (lv.rows) {
-      lv.smem_acc_rows = acc_rows_smem_bytes(g, cfg->ndim, lv.nxb_rows);
-      lv.smem_adj_rows = adj_rows_smem_bytes(g, cfg->ndim, lv.nxb_rows);
-      const long long nrows = (long long)((g.n[0] + 31) / 32) * g.n[1] * g.n[2];
-      CK(cudaMalloc((void**)&lv.perm, 32 * nrows));
-    }
+    lv.gv = g;
   }
 
   // Normalise the two images into level 0 (Sec. II: [0, L_eps]).
@@ -538,14 +622,9 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     }
   }
 
-  // Per-row lane permutations for the row kernels (A is fixed).
-  for (int l = 0; l < ctx->nlev; ++l) {
-    Level& lv = ctx->lev[l];
-    if (!lv.rows) continue;
-    if (is_bf16(ctx)) k_row_perm<__nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(lv.g, (const __nv_bfloat16*)lv.A, lv.perm);
-    else k_row_perm<float><<<1024, 256, 0, ctx->stream>>>(lv.g, (const float*)lv.A, lv.perm);
-    CKL();
-  }
+  // Row-parallel path: tile, per-tile fixed-image bin masks and per-row
+  // lane permutations (A is fixed).
+  for (int l = 0; l < ctx->nlev; ++l) RET_IF(select_rows_path(ctx, ctx->lev[l]));
 
   // Static fixed-image statistics P[r][a] and Z = sum P.
   for (int l = 0; l < ctx->nlev; ++l) {

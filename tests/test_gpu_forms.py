@@ -109,7 +109,8 @@ def test_autograd_forward_backward_match_entry_points():
     (2.5 * D).backward()
     Dv, g = e.value_and_grad(c.detach())
     assert float(D) == Dv
-    assert torch.allclose(c.grad, 2.5 * g, rtol=1e-5, atol=1e-7 * float(g.abs().max()))
+    # The gradient scatter adds FP32 contributions in a run-dependent order.
+    assert torch.allclose(c.grad, 2.5 * g, rtol=1e-5, atol=1e-5 * float(g.abs().max()))
 
 
 def test_autograd_stale_backward_recomputes_its_forward():
@@ -123,7 +124,7 @@ def test_autograd_stale_backward_recomputes_its_forward():
     e.value(c2)                      # overwrites the level's tables
     D1.backward()
     _, g1 = e.value_and_grad(c1.detach())
-    assert torch.allclose(c1.grad, g1, rtol=1e-5, atol=1e-7 * float(g1.abs().max()))
+    assert torch.allclose(c1.grad, g1, rtol=1e-5, atol=1e-5 * float(g1.abs().max()))
 
 
 def test_autograd_gradient_matches_finite_differences_and_oracle_on_oct():
