@@ -164,6 +164,17 @@ srwcr_status srwcr_set_profiling(srwcr_ctx* ctx, int enable);
 srwcr_status srwcr_profile_read(srwcr_ctx* ctx, double* ms, int64_t* counts, int64_t* launches,
                                 int reset);
 
+/* Tile autotuner: times value+gradient at coefficients c_dev (device) for
+ * each 32-wide voxel tile that fits the row-parallel kernels, `reps` runs
+ * each, and keeps the fastest for this level.  The choice is cached per
+ * problem signature (dimensions, spacings, bins, storage) for the life of
+ * the process and, if the environment variable SRWCR_AUTOTUNE_CACHE names a
+ * file, appended to that file and read back by later processes, which then
+ * skip the timing.  tile_out (may be NULL) receives the chosen tile.  Uses
+ * scratch allocations; not for use under stream capture. */
+srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c_dev, int reps,
+                            int* tile_out);
+
 /* Allocation-free SRWCR value, for callers that may not allocate device
  * memory: code inside a CUDA-graph capture or an allocator callback, plugins
  * whose host application owns every cudaMalloc, real-time loops that must
@@ -222,6 +233,78 @@ void srwcr_lbfgs_default_opts(srwcr_lbfgs_opts* opts);
  * n_levels <= the context's pyramid_levels.  report may be NULL. */
 srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n_levels,
                             const srwcr_lbfgs_opts* opts, srwcr_report* report);
+
+/* ------------------------------------------------------------------------
+ * Batched form: many pairs (contexts) of uneven sizes evaluated and
+ * registered together.  The paper treats one pair at a time; this is a
+ * throughput form of the same method.  Each phase of an evaluation (clear,
+ * fused warp + statistics, per-region finalisation, value reduction,
+ * adjoint) is ONE launch over every (pair, tile) work item, so a batched
+ * value+gradient costs a handful of launches whatever the number of pairs,
+ * and can be replayed from a CUDA graph.
+ *
+ * The batch owns packed device buffers: c and g (float32, pair i at
+ * offsets[i] .. offsets[i] + n_params[i], each pair's layout as for
+ * srwcr_value) and D (n_pairs doubles).  It reads each member context's
+ * images and statistics and writes into that context's accumulators and
+ * tables at `level`: while the batch exists its contexts must stay alive,
+ * must not be re-tuned (srwcr_autotune), and must not run work of their own
+ * at that level concurrently with the batch.  After a batched call, a
+ * member's srwcr_backward needs a fresh srwcr_forward. */
+typedef struct srwcr_batch srwcr_batch;
+
+typedef struct {
+  int n_pairs;
+  int launches_per_eval;  /* kernels in one batched value+gradient */
+  int64_t n_params_total; /* floats in the packed c and g buffers */
+  int64_t n_voxels_total;
+  int64_t work_items;     /* (pair, tile) items of one fused-kernel launch */
+  int64_t launches;       /* kernels queued by this batch so far */
+} srwcr_batch_desc;
+
+/* Build a batch over ctxs[0..n_pairs-1] at pyramid level `level`.  All
+ * contexts must be on the current device, share ndim and storage, and run
+ * that level on the row-parallel kernels (srwcr_level_desc.kernel_path = 1).
+ * stream: cudaStream_t for all batch work; NULL = a stream the batch creates
+ * (graph capture needs a stream other than the legacy default).  c and g
+ * start at zero.  Errors: SRWCR_EINVAL, SRWCR_ENOMEM, SRWCR_ECUDA. */
+srwcr_status srwcr_batch_create(srwcr_ctx* const* ctxs, int n_pairs, int level, void* stream,
+                                srwcr_batch** out);
+void srwcr_batch_destroy(srwcr_batch* b);
+srwcr_status srwcr_batch_info(const srwcr_batch* b, srwcr_batch_desc* out);
+
+/* offsets: n_pairs + 1 entries (may be NULL); n_params: n_pairs entries
+ * (may be NULL). */
+srwcr_status srwcr_batch_layout(const srwcr_batch* b, int64_t* offsets, int64_t* n_params);
+
+/* Device pointers of the packed buffers (owned by the batch). */
+srwcr_status srwcr_batch_buffers(srwcr_batch* b, float** c_dev, float** g_dev, double** D_dev);
+
+/* Queue D_i and dD_i/dc_i for every pair at the coefficients in the packed c
+ * buffer (results in D and g) without synchronising.  use_graph != 0 replays
+ * a CUDA graph of the phases, captured on the first such call. */
+srwcr_status srwcr_batch_value_and_grad(srwcr_batch* b, int use_graph);
+
+/* Synchronise the batch stream; D_host (n_pairs doubles, may be NULL)
+ * receives D. */
+srwcr_status srwcr_batch_sync(srwcr_batch* b, double* D_host);
+
+/* Single-level L-BFGS (Sec. II-F, the method of srwcr_register) for every
+ * pair at once, from the coefficients in the packed c buffer, with
+ * opts->max_iter[level] iterations at most.  The optimiser state lives on
+ * the device and each round (one batched evaluation plus one decision
+ * kernel) is the same launch sequence for every pair, replayed from a CUDA
+ * graph when use_graph != 0; pairs that stop drop out of later rounds.  On
+ * return c holds each pair's last accepted point, g its gradient and D its
+ * value.  Per-pair outputs (n_pairs entries each, any may be NULL):
+ * iterations, evaluations, final value, srwcr_status (SRWCR_OK when the value
+ * was stable over the window or the gradient vanished, SRWCR_ENOTCONVERGED
+ * at the iteration limit, SRWCR_ELINESEARCH when the line search failed).
+ * Returns SRWCR_ENUMERIC if some pair's value was not finite at its start,
+ * SRWCR_EINVAL for bad options (stable_window must be below 64). */
+srwcr_status srwcr_batch_register(srwcr_batch* b, const srwcr_lbfgs_opts* opts, int use_graph,
+                                  int* iterations, int* evaluations, double* final_value,
+                                  int* status);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,10 @@ EXPORTS = ("srwcr_create", "srwcr_destroy", "srwcr_last_error", "srwcr_level_inf
            "srwcr_value_and_grad_host", "srwcr_forward", "srwcr_backward",
            "srwcr_region_stats", "srwcr_debug_bins", "srwcr_debug_warp",
            "srwcr_lbfgs_default_opts", "srwcr_register", "srwcr_set_profiling",
-           "srwcr_profile_read", "srwcr_value_noalloc")
+           "srwcr_profile_read", "srwcr_value_noalloc", "srwcr_autotune",
+           "srwcr_batch_create", "srwcr_batch_destroy", "srwcr_batch_info",
+           "srwcr_batch_layout", "srwcr_batch_buffers", "srwcr_batch_value_and_grad",
+           "srwcr_batch_sync", "srwcr_batch_register")
 
 
 class SrwcrError(RuntimeError):
@@ -63,6 +66,12 @@ class Report(ctypes.Structure):
     _fields_ = [("levels_run", ctypes.c_int), ("iterations", ctypes.c_int * 4),
                 ("evaluations", ctypes.c_int * 4), ("final_value", ctypes.c_double * 4),
                 ("status", ctypes.c_int * 4)]
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int), ("launches_per_eval", ctypes.c_int),
+                ("n_params_total", ctypes.c_int64), ("n_voxels_total", ctypes.c_int64),
+                ("work_items", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
 
 def library_path() -> str:
@@ -105,6 +114,17 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "srwcr_register": (st, [vp, vp, ctypes.c_int, ctypes.POINTER(LbfgsOpts),
                                 ctypes.POINTER(Report)]),
         "srwcr_value_noalloc": (st, [ctypes.POINTER(Config), vp, vp, vp, vp, vp]),
+        "srwcr_autotune": (st, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "srwcr_batch_create": (st, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+        "srwcr_batch_destroy": (None, [vp]),
+        "srwcr_batch_info": (st, [vp, ctypes.POINTER(BatchDesc)]),
+        "srwcr_batch_layout": (st, [vp, vp, vp]),
+        "srwcr_batch_buffers": (st, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(vp)]),
+        "srwcr_batch_value_and_grad": (st, [vp, ctypes.c_int]),
+        "srwcr_batch_sync": (st, [vp, vp]),
+        "srwcr_batch_register": (st, [vp, ctypes.POINTER(LbfgsOpts), ctypes.c_int, vp, vp, vp,
+                                      vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -303,6 +323,16 @@ class SRWCR:
                                          1 if reset else 0))
         return ms, cnt, int(n.value)
 
+    def autotune(self, c=None, level: int = 0, reps: int = 3):
+        """Pick the fastest voxel tile for this level (cached per problem)."""
+        if c is None:
+            c = self.zeros(level)
+        c = self._c(c, level)
+        t = (ctypes.c_int * 3)()
+        _check(load().srwcr_autotune(self._h, level, _ptr(c), int(reps), t))
+        self.levels[level] = self.level_info(level)
+        return tuple(t)
+
     # -- registration ------------------------------------------------------
     @staticmethod
     def default_opts() -> LbfgsOpts:
@@ -321,6 +351,122 @@ class SRWCR:
             _check(st)
         rep.status_code = st
         return rep
+
+
+class _DeviceArray:
+    """Zero-copy view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+class Batch:
+    """Many pairs (SRWCR engines) evaluated and registered together.
+
+    Each phase of an evaluation is one launch over every (pair, tile) work
+    item; ``use_graph`` replays the phases from a CUDA graph.  The batch owns
+    packed coefficient and gradient buffers (``coef(i)``, ``grad(i)`` are
+    views of pair i) and runs on a stream of its own that is ordered after
+    the current torch stream on entry and before it on exit.
+    """
+
+    def __init__(self, engines: Sequence["SRWCR"], level: int = 0):
+        import torch
+        self._torch = torch
+        lib = load()
+        self.engines = list(engines)
+        self.level = level
+        self.stream = torch.cuda.Stream(device=self.engines[0].device)
+        arr = (ctypes.c_void_p * len(self.engines))(*[e._h.value for e in self.engines])
+        h = ctypes.c_void_p()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        _check(lib.srwcr_batch_create(arr, len(self.engines), int(level),
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+        n = len(self.engines)
+        off = np.zeros(n + 1, np.int64)
+        npar = np.zeros(n, np.int64)
+        _check(lib.srwcr_batch_layout(h, off.ctypes.data_as(ctypes.c_void_p),
+                                      npar.ctypes.data_as(ctypes.c_void_p)))
+        self.offsets, self.n_params = off, npar
+        pc, pg, pD = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib.srwcr_batch_buffers(h, ctypes.byref(pc), ctypes.byref(pg), ctypes.byref(pD)))
+        dev = self.engines[0].device
+        self.c = torch.as_tensor(_DeviceArray(pc.value, int(off[-1]), "<f4"), device=dev)
+        self.g = torch.as_tensor(_DeviceArray(pg.value, int(off[-1]), "<f4"), device=dev)
+        self.D = torch.as_tensor(_DeviceArray(pD.value, n, "<f8"), device=dev)
+
+    def __len__(self):
+        return len(self.engines)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.stream.synchronize()
+            load().srwcr_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> BatchDesc:
+        d = BatchDesc()
+        _check(load().srwcr_batch_info(self._h, ctypes.byref(d)))
+        return d
+
+    def coef(self, i: int):
+        """View of pair i's coefficients in the packed buffer."""
+        o, n = int(self.offsets[i]), int(self.n_params[i])
+        return self.c[o:o + n].view(self.engines[i].coef_shape(self.level))
+
+    def grad(self, i: int):
+        o, n = int(self.offsets[i]), int(self.n_params[i])
+        return self.g[o:o + n].view(self.engines[i].coef_shape(self.level))
+
+    def _enter(self):
+        self.stream.wait_stream(self._torch.cuda.current_stream())
+
+    def _leave(self):
+        self._torch.cuda.current_stream().wait_stream(self.stream)
+        for e in self.engines:
+            e._gen[self.level] += 1
+
+    def value_and_grad_async(self, use_graph: bool = True):
+        """Queue D_i, dD_i/dc_i for every pair at the packed coefficients."""
+        self._enter()
+        _check(load().srwcr_batch_value_and_grad(self._h, 1 if use_graph else 0))
+        self._leave()
+
+    def value_and_grad(self, use_graph: bool = True) -> np.ndarray:
+        self.value_and_grad_async(use_graph)
+        return self.values()
+
+    def values(self) -> np.ndarray:
+        out = np.zeros(len(self), np.float64)
+        _check(load().srwcr_batch_sync(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def register(self, opts: Optional[LbfgsOpts] = None, use_graph: bool = True,
+                 check: bool = True) -> dict:
+        """Single-level L-BFGS of every pair from the packed coefficients."""
+        n = len(self)
+        it = np.zeros(n, np.int32)
+        ev = np.zeros(n, np.int32)
+        fv = np.zeros(n, np.float64)
+        stt = np.zeros(n, np.int32)
+        self._enter()
+        st = load().srwcr_batch_register(
+            self._h, ctypes.byref(opts) if opts is not None else None, 1 if use_graph else 0,
+            it.ctypes.data_as(ctypes.c_void_p), ev.ctypes.data_as(ctypes.c_void_p),
+            fv.ctypes.data_as(ctypes.c_void_p), stt.ctypes.data_as(ctypes.c_void_p))
+        self._leave()
+        if check:
+            _check(st)
+        return {"iterations": it, "evaluations": ev, "final_value": fv, "status": stt}
 
 
 def from_problem(prob, fixed, moving, storage: str = "f32", pyramid_levels: int = 1, **kw) -> SRWCR:

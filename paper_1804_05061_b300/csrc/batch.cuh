@@ -1,0 +1,712 @@
+// Batched form: many registration pairs of uneven sizes evaluated, and
+// registered, together.  One launch per phase covers every (pair, tile) work
+// item (kernels_batch.cuh); the phases of one evaluation, or of one L-BFGS
+// round, can be captured once in a CUDA graph and replayed.
+//
+// The batched L-BFGS keeps the whole optimiser state on the device: after
+// each batched evaluation one CTA per pair takes the line-search decision
+// (Armijo and weak-Wolfe tests, halve or double the step), accepts the step
+// and updates the (s, y) history, runs the two-loop recursion for the next
+// direction and writes the next trial point, all with FP64 inner products in
+// a fixed order.  A round is therefore the same fixed sequence of launches
+// for every pair and every iteration; pairs that stop drop out through their
+// active flag.  The host only checks, every few rounds, whether any pair is
+// still active.  The method per pair is the one of lbfgs.cuh (Sec. II-F).
+// Included once, at the end of srwcr.cu.
+#pragma once
+
+#include "kernels_batch.cuh"
+
+namespace {
+
+constexpr int kLbHist = 64;  // ring of accepted values for the stability test
+
+struct LbOpts {
+  int m, max_iter, window, max_ls;
+  double rtol, c1, c2;
+};
+
+struct LbState {
+  double f;            // value at x
+  double gd;           // g . d at x
+  double alpha;        // current trial step
+  double rho[16];      // 1 / (s . y) per history slot
+  double fh[kLbHist];  // accepted values (including the start), ring
+  int nfh;
+  int head, hist_len;  // history ring: next slot, entries in use
+  int iter, evals, trials, restart, phase, status;
+};
+
+// FP64 inner product over one pair's vectors by one CTA, in a fixed order;
+// every thread receives the same value.  All threads must call it.
+__device__ double block_dot(const float* __restrict__ a, const float* __restrict__ b,
+                            long long n, double* sh) {
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s += (double)a[i] * (double)b[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __syncthreads();  // earlier readers of sh are done
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int w = 0; w < nw; ++w) t += sh[w];
+  return t;
+}
+
+// Start: trial point = start point, first evaluation pending.
+__global__ void k_lbfgs_init(LbState* __restrict__ st, int* __restrict__ active,
+                             const long long* __restrict__ off, const float* __restrict__ x,
+                             float* __restrict__ xn) {
+  const int p = blockIdx.x;
+  for (long long i = off[p] + threadIdx.x; i < off[p + 1]; i += blockDim.x) xn[i] = x[i];
+  if (threadIdx.x == 0) {
+    LbState s;
+    memset(&s, 0, sizeof s);
+    s.restart = 1;
+    st[p] = s;
+    active[p] = 1;
+  }
+}
+
+struct LbVectors {
+  float *x, *g, *xn, *gn, *d, *S, *Y;
+  const long long* off;  // [n+1] offsets of each pair's vectors
+  double* D;             // [n] values at xn; a finished pair's final value
+};
+
+// One CTA per pair: consume the evaluation at xn, decide, and prepare the
+// next trial point.  Control flow is uniform across the CTA: it depends only
+// on the shared state and on values every thread computes identically.
+__global__ void __launch_bounds__(1024)
+k_lbfgs_step(LbState* __restrict__ st_all, int* __restrict__ active, LbVectors v, LbOpts o) {
+  const int p = blockIdx.x;
+  if (!active[p]) return;
+  __shared__ LbState s;
+  __shared__ double sh[32];
+  __shared__ double ak[16];
+  if (threadIdx.x == 0) s = st_all[p];
+  __syncthreads();
+  const long long n = v.off[p + 1] - v.off[p];
+  float* __restrict__ x = v.x + v.off[p];
+  float* __restrict__ g = v.g + v.off[p];
+  float* __restrict__ xn = v.xn + v.off[p];
+  float* __restrict__ gn = v.gn + v.off[p];
+  float* __restrict__ d = v.d + v.off[p];
+  float* __restrict__ S = v.S + (long long)o.m * v.off[p];
+  float* __restrict__ Y = v.Y + (long long)o.m * v.off[p];
+  const double fn = v.D[p];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int done = 0, status = SRWCR_OK;
+
+  if (s.phase == 0) {
+    // First evaluation: x = xn already.
+    for (long long i = tid; i < n; i += nt) g[i] = gn[i];
+    __syncthreads();
+    if (tid == 0) {
+      s.f = fn;
+      s.evals = 1;
+      s.fh[0] = fn;
+      s.nfh = 1;
+    }
+    if (!isfinite(fn)) { done = 1; status = SRWCR_ENUMERIC; }
+    else if (o.max_iter <= 0) { done = 1; status = SRWCR_ENOTCONVERGED; }
+  } else {
+    if (tid == 0) s.evals += 1;
+    int act = 0;  // 0 accept, 1 shrink, 2 grow
+    if (!isfinite(fn) || fn > s.f + o.c1 * s.alpha * s.gd) {
+      act = 1;
+    } else {
+      const double gnd = block_dot(gn, d, n, sh);
+      if (gnd < o.c2 * s.gd) act = 2;
+    }
+    if (act != 0) {
+      __syncthreads();
+      const double alpha = act == 1 ? 0.5 * s.alpha : 2.0 * s.alpha;
+      const int trials = s.trials + 1;
+      if (trials >= o.max_ls) {
+        done = 1;
+        status = SRWCR_ELINESEARCH;
+      } else {
+        for (long long i = tid; i < n; i += nt) xn[i] = x[i] + (float)alpha * d[i];
+      }
+      __syncthreads();
+      if (tid == 0) { s.alpha = alpha; s.trials = trials; }
+      __syncthreads();
+      if (!done) {
+        if (tid == 0) st_all[p] = s;
+        return;
+      }
+    } else {
+      // Accept: s = xn - x, y = gn - g into the head slot; x = xn, g = gn.
+      float* sv = S + (long long)s.head * n;
+      float* yv = Y + (long long)s.head * n;
+      for (long long i = tid; i < n; i += nt) {
+        sv[i] = xn[i] - x[i];
+        yv[i] = gn[i] - g[i];
+        x[i] = xn[i];
+        g[i] = gn[i];
+      }
+      __syncthreads();
+      const double sy = block_dot(sv, yv, n, sh);
+      __syncthreads();
+      if (tid == 0) {
+        if (sy > 0.0) {
+          s.rho[s.head] = 1.0 / sy;
+          s.head = (s.head + 1) % o.m;
+          s.hist_len = min(s.hist_len + 1, o.m);
+        }
+        s.f = fn;
+        s.restart = 0;
+        s.iter += 1;
+        s.fh[s.nfh % kLbHist] = fn;
+        s.nfh += 1;
+      }
+      __syncthreads();
+      const int w = o.window;
+      if (w > 0 && s.nfh > w &&
+          fabs(s.fh[(s.nfh - 1) % kLbHist] - s.fh[(s.nfh - 1 - w) % kLbHist]) <=
+              o.rtol * fabs(s.fh[(s.nfh - 1) % kLbHist])) {
+        done = 1;
+        status = SRWCR_OK;
+      } else if (s.iter >= o.max_iter) {
+        done = 1;
+        status = SRWCR_ENOTCONVERGED;
+      }
+    }
+  }
+
+  if (!done) {
+    // Next direction d = -H g by the two-loop recursion.
+    const double gg = block_dot(g, g, n, sh);
+    if (!(gg > 0.0)) {
+      done = 1;
+      status = SRWCR_OK;
+    } else {
+      for (long long i = tid; i < n; i += nt) d[i] = g[i];
+      __syncthreads();
+      const int m = o.m, head = s.head, hl = s.hist_len;
+      for (int t = 0; t < hl; ++t) {
+        const int slot = (head - 1 - t + m) % m;
+        const double a = s.rho[slot] * block_dot(S + (long long)slot * n, d, n, sh);
+        if (tid == 0) ak[slot] = a;
+        const float* yv = Y + (long long)slot * n;
+        for (long long i = tid; i < n; i += nt) d[i] = (float)-a * yv[i] + d[i];
+        __syncthreads();
+      }
+      if (hl > 0) {
+        const int nw = (head - 1 + m) % m;
+        const double sy = block_dot(S + (long long)nw * n, Y + (long long)nw * n, n, sh);
+        const double yy = block_dot(Y + (long long)nw * n, Y + (long long)nw * n, n, sh);
+        const float sc = (float)(sy / yy);
+        for (long long i = tid; i < n; i += nt) d[i] = sc * d[i];
+        __syncthreads();
+      }
+      for (int t = hl - 1; t >= 0; --t) {
+        const int slot = (head - 1 - t + m) % m;
+        const double beta = s.rho[slot] * block_dot(Y + (long long)slot * n, d, n, sh);
+        const float coef = (float)(ak[slot] - beta);
+        const float* sv = S + (long long)slot * n;
+        for (long long i = tid; i < n; i += nt) d[i] = coef * sv[i] + d[i];
+        __syncthreads();
+      }
+      for (long long i = tid; i < n; i += nt) d[i] = -d[i];
+      __syncthreads();
+      double gd = block_dot(g, d, n, sh);
+      int restart = s.restart, clear = 0;
+      if (!(gd < 0.0)) {
+        // Not a descent direction: drop the history, steepest descent.
+        for (long long i = tid; i < n; i += nt) d[i] = -g[i];
+        __syncthreads();
+        gd = -gg;
+        restart = 1;
+        clear = 1;
+      }
+      const double dd = block_dot(d, d, n, sh);
+      const double alpha = restart ? 1.0 / sqrt(dd) : 1.0;
+      for (long long i = tid; i < n; i += nt) xn[i] = x[i] + (float)alpha * d[i];
+      __syncthreads();
+      if (tid == 0) {
+        if (clear) { s.hist_len = 0; s.head = 0; }
+        s.restart = restart;
+        s.gd = gd;
+        s.alpha = alpha;
+        s.trials = 0;
+        s.phase = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (done) {
+      s.status = status;
+      active[p] = 0;
+      v.D[p] = s.f;
+    }
+    st_all[p] = s;
+  }
+}
+
+}  // namespace
+
+struct srwcr_batch {
+  int n = 0;
+  int level = 0;
+  int ndim = 0;
+  bool bf16 = false;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<srwcr_ctx*> ctx;
+  std::vector<long long> off;  // caller order, n+1 float offsets into c and g
+  // One row-kernel launch: pairs of one x-bin class (4 or 8 per row), at
+  // most kBatchChunk of them, with their parameter tables for the plain
+  // evaluation and for the optimiser's (which reads xn and writes gn).
+  struct Launch {
+    int nxb, nblk;
+    size_t smem_acc, smem_adj;
+    AccTable acc, acc_lb;
+    AdjTable adj, adj_lb;
+  };
+  std::vector<Launch> launches_rows;
+  std::vector<BatchPair> host_tab;  // table order (by group, then size)
+  long long total_regions = 0;
+  long long total_vox = 0;
+  long long work_items = 0;
+  float* c = nullptr;
+  float* g = nullptr;
+  double* D = nullptr;  // [n] caller order
+  int* ndeg = nullptr;
+  long long* off_dev = nullptr;
+  BatchPair* tab_eval = nullptr;
+  BatchPair* tab_lb = nullptr;
+  // L-BFGS work (allocated on first registration).
+  float *xn = nullptr, *gn = nullptr, *d = nullptr, *S = nullptr, *Y = nullptr;
+  int lb_m = 0;
+  LbState* lbs = nullptr;
+  int* active = nullptr;
+  int* active_host = nullptr;
+  cudaGraphExec_t graph_eval = nullptr;
+  cudaGraphExec_t graph_round = nullptr;
+  LbOpts graph_round_opts{};
+  long long launches = 0;
+};
+
+namespace {
+
+template <int DIM, typename T>
+void launch_batch_rows(srwcr_batch* b, bool lb, const int* active, bool adj) {
+  for (const auto& L : b->launches_rows) {
+    if (adj) {
+      const AdjTable& t = lb ? L.adj_lb : L.adj;
+      if (L.nxb == 4)
+        k_adjoint_rows_batch<DIM, T, 4><<<L.nblk, kAdjWarps * 32, L.smem_adj, b->stream>>>(t, active);
+      else
+        k_adjoint_rows_batch<DIM, T, 8><<<L.nblk, kAdjWarps * 32, L.smem_adj, b->stream>>>(t, active);
+    } else {
+      const AccTable& t = lb ? L.acc_lb : L.acc;
+      if (L.nxb == 4)
+        k_accumulate_rows_batch<DIM, T, 4><<<L.nblk, kAccWarps * 32, L.smem_acc, b->stream>>>(t, active);
+      else
+        k_accumulate_rows_batch<DIM, T, 8><<<L.nblk, kAccWarps * 32, L.smem_acc, b->stream>>>(t, active);
+    }
+  }
+}
+
+void launch_rows_any(srwcr_batch* b, bool lb, const int* active, bool adj) {
+  if (b->ndim == 3) {
+    if (b->bf16) launch_batch_rows<3, __nv_bfloat16>(b, lb, active, adj);
+    else launch_batch_rows<3, float>(b, lb, active, adj);
+  } else {
+    if (b->bf16) launch_batch_rows<2, __nv_bfloat16>(b, lb, active, adj);
+    else launch_batch_rows<2, float>(b, lb, active, adj);
+  }
+}
+
+template <typename T>
+srwcr_status set_smem_limits_batch_t() {
+  // The row path keeps dynamic shared memory at or below 220 KB; the batched
+  // kernels also hold a few hundred bytes of static descriptors.
+  const int mx = 221 * 1024;
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  CK(cudaFuncSetAttribute(k_accumulate_rows_batch<3, T, 4>, a, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows_batch<3, T, 8>, a, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows_batch<2, T, 4>, a, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows_batch<2, T, 8>, a, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_batch<3, T, 4>, a, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_batch<3, T, 8>, a, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_batch<2, T, 4>, a, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_batch<2, T, 8>, a, mx));
+  return SRWCR_OK;
+}
+
+srwcr_status set_smem_limits_batch() {
+  RET_IF(set_smem_limits_batch_t<float>());
+  return set_smem_limits_batch_t<__nv_bfloat16>();
+}
+
+// The phases of one batched value+gradient, queued on the batch stream.
+// lb selects the optimiser's tables (xn -> gn) instead of (c -> g).
+srwcr_status queue_batch_eval(srwcr_batch* b, bool lb, const int* active) {
+  const BatchPair* tab = lb ? b->tab_lb : b->tab_eval;
+  k_zero_batch<<<dim3(64, b->n), 256, 0, b->stream>>>(tab, active);
+  CKL();
+  launch_rows_any(b, lb, active, false);
+  CKL();
+  const long long threads = b->total_regions * 32;
+  k_finalize_batch<<<(unsigned)((threads + 255) / 256), 256, 0, b->stream>>>(tab, b->n, b->total_regions,
+                                                                        active);
+  CKL();
+  k_reduce_D_batch<<<b->n, 1024, 0, b->stream>>>(tab, active);
+  CKL();
+  launch_rows_any(b, lb, active, true);
+  CKL();
+  return SRWCR_OK;
+}
+
+int launches_per_eval(const srwcr_batch* b) { return 3 + 2 * (int)b->launches_rows.size(); }
+
+srwcr_status queue_lbfgs_round(srwcr_batch* b, const LbOpts& o) {
+  RET_IF(queue_batch_eval(b, true, b->active));
+  LbVectors v{b->c, b->g, b->xn, b->gn, b->d, b->S, b->Y, b->off_dev, b->D};
+  k_lbfgs_step<<<b->n, 1024, 0, b->stream>>>(b->lbs, b->active, v, o);
+  CKL();
+  return SRWCR_OK;
+}
+
+// Capture `fn` on the batch stream into an executable graph.
+template <typename Fn>
+srwcr_status capture(srwcr_batch* b, cudaGraphExec_t* out, Fn fn) {
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  srwcr_status st = fn();
+  cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+  if (st != SRWCR_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(SRWCR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(SRWCR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return SRWCR_OK;
+}
+
+void invalidate_member_tables(srwcr_batch* b) {
+  for (srwcr_ctx* c : b->ctx) c->lev[b->level].tables = false;
+}
+
+srwcr_status batch_alloc_lbfgs(srwcr_batch* b, int m) {
+  if (b->lb_m == m) return SRWCR_OK;
+  if (b->graph_round) { cudaGraphExecDestroy(b->graph_round); b->graph_round = nullptr; }
+  void* ptrs[] = {b->xn, b->gn, b->d, b->S, b->Y};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  b->xn = b->gn = b->d = b->S = b->Y = nullptr;
+  b->lb_m = 0;
+  const long long tot = b->off[b->n];
+  CK(cudaMalloc((void**)&b->xn, sizeof(float) * tot));
+  CK(cudaMalloc((void**)&b->gn, sizeof(float) * tot));
+  CK(cudaMalloc((void**)&b->d, sizeof(float) * tot));
+  CK(cudaMalloc((void**)&b->S, sizeof(float) * tot * m));
+  CK(cudaMalloc((void**)&b->Y, sizeof(float) * tot * m));
+  // Padding between pairs must read as zero in every inner product.
+  CK(cudaMemsetAsync(b->xn, 0, sizeof(float) * tot, b->stream));
+  CK(cudaMemsetAsync(b->gn, 0, sizeof(float) * tot, b->stream));
+  CK(cudaMemsetAsync(b->d, 0, sizeof(float) * tot, b->stream));
+  CK(cudaMemsetAsync(b->S, 0, sizeof(float) * tot * m, b->stream));
+  CK(cudaMemsetAsync(b->Y, 0, sizeof(float) * tot * m, b->stream));
+  if (!b->lbs) CK(cudaMalloc((void**)&b->lbs, sizeof(LbState) * b->n));
+  // Evaluation table of the optimiser: reads xn, writes gn.
+  std::vector<BatchPair> tab = b->host_tab;
+  for (auto& bp : tab) {
+    const long long o = (const float*)bp.acc.c - b->c;
+    bp.acc.c = bp.adj.c = b->xn + o;
+    bp.adj.grad = b->gn + o;
+  }
+  if (!b->tab_lb) CK(cudaMalloc((void**)&b->tab_lb, sizeof(BatchPair) * b->n));
+  CK(cudaMemcpy(b->tab_lb, tab.data(), sizeof(BatchPair) * b->n, cudaMemcpyHostToDevice));
+  for (auto& L : b->launches_rows) {
+    for (int k = 0; k < L.acc.n; ++k) {
+      const long long o = L.acc.it[k].a.c - b->c;
+      L.acc_lb.it[k].a.c = b->xn + o;
+      L.adj_lb.it[k].a.c = b->xn + o;
+      L.adj_lb.it[k].a.grad = b->gn + o;
+    }
+  }
+  b->lb_m = m;
+  return SRWCR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void srwcr_batch_destroy(srwcr_batch* b) {
+  if (!b) return;
+  if (b->graph_eval) cudaGraphExecDestroy(b->graph_eval);
+  if (b->graph_round) cudaGraphExecDestroy(b->graph_round);
+  void* ptrs[] = {b->c, b->g, b->D, b->ndeg, b->off_dev, b->tab_eval, b->tab_lb, b->xn, b->gn,
+                  b->d, b->S, b->Y, b->lbs, b->active};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (b->active_host) cudaFreeHost(b->active_host);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, int n, int level,
+                                      void* stream) {
+  b->n = n;
+  b->level = level;
+  b->ctx.assign(ctxs, ctxs + n);
+  CK(cudaGetDevice(&b->device));
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    b->own_stream = true;
+  }
+  b->ndim = ctxs[0]->cfg.ndim;
+  b->bf16 = is_bf16(ctxs[0]);
+  for (int i = 0; i < n; ++i) {
+    const srwcr_ctx* c = ctxs[i];
+    if (!c) return fail(SRWCR_EINVAL, "pair %d: null context", i);
+    if (c->device != b->device) return fail(SRWCR_EINVAL, "pair %d: context on another device", i);
+    if (c->cfg.ndim != b->ndim || is_bf16(c) != b->bf16)
+      return fail(SRWCR_EINVAL, "pair %d: dimension or storage differs from pair 0", i);
+    if (level >= c->nlev) return fail(SRWCR_EINVAL, "pair %d has no level %d", i, level);
+    if (!c->lev[level].rows)
+      return fail(SRWCR_EINVAL, "pair %d: level %d is not on the row-parallel kernels", i, level);
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(SRWCR_EINVAL, "pair %d repeats pair %d", i, j);
+  }
+  // Packed coefficient layout (caller order), 64-float aligned per pair.
+  b->off.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const Geo& g = ctxs[i]->lev[level].g;
+    const long long np = g.ncoef * b->ndim;
+    b->off[i + 1] = b->off[i] + (np + 63) / 64 * 64;
+  }
+  const long long tot = b->off[n];
+  CK(cudaMalloc((void**)&b->c, sizeof(float) * tot));
+  CK(cudaMalloc((void**)&b->g, sizeof(float) * tot));
+  CK(cudaMemsetAsync(b->c, 0, sizeof(float) * tot, b->stream));
+  CK(cudaMemsetAsync(b->g, 0, sizeof(float) * tot, b->stream));
+  CK(cudaMalloc((void**)&b->D, sizeof(double) * n));
+  CK(cudaMalloc((void**)&b->ndeg, sizeof(int) * n));
+  CK(cudaMalloc((void**)&b->active, sizeof(int) * n));
+  CK(cudaMallocHost((void**)&b->active_host, sizeof(int) * n));
+  CK(cudaMalloc((void**)&b->off_dev, sizeof(long long) * (n + 1)));
+  CK(cudaMemcpy(b->off_dev, b->off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));
+
+  // Table order: by launch group (x-bins per row), then by decreasing voxel
+  // count, so the largest pairs' tiles are issued first.
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    const Level& la = ctxs[a]->lev[level];
+    const Level& lc = ctxs[c]->lev[level];
+    if (la.nxb_rows != lc.nxb_rows) return la.nxb_rows < lc.nxb_rows;
+    return la.g.nvox > lc.g.nvox;
+  });
+  b->host_tab.resize(n);
+  long long region = 0;
+  for (int t = 0; t < n; ++t) {
+    const int i = order[t];
+    Level& lv = ctxs[i]->lev[level];
+    BatchPair& bp = b->host_tab[t];
+    memset(&bp, 0, sizeof bp);
+    bp.g = lv.g;
+    bp.id = i;
+    float* ci = b->c + b->off[i];
+    float* gi = b->g + b->off[i];
+    bp.acc = acc_args(lv, ci);
+    bp.adj = adj_args(lv, ci, nullptr, gi);
+    bp.group = lv.nxb_rows;
+    bp.region_begin = region;
+    region += lv.g.R;
+    bp.rs = region_static(lv);
+    bp.inv_s1 = 1.0 / lv.s1;
+    bp.inv_s2 = 1.0 / lv.s2;
+    bp.invZ = 1.0 / lv.Z;
+    bp.U = lv.U;
+    bp.V = lv.V;
+    bp.X = lv.X;
+    bp.Dr = lv.Dr;
+    bp.stats = lv.stats;
+    bp.D = b->D + i;
+    bp.ndeg = b->ndeg + i;
+    bp.acc_len = lv.g.R * lv.g.nbins * 2;
+    bp.grad_len = lv.g.ncoef * b->ndim;
+    b->total_vox += lv.g.nvox;
+  }
+  b->total_regions = region;
+  // Row-kernel launches: runs of pairs of one x-bin class, at most
+  // kBatchChunk per launch, with CTA prefix sums.
+  for (int t = 0; t < n;) {
+    srwcr_batch::Launch L;
+    memset(&L, 0, sizeof L);
+    L.nxb = b->host_tab[t].group;
+    int tile = 0;
+    while (t < n && b->host_tab[t].group == L.nxb && L.acc.n < kBatchChunk) {
+      const BatchPair& bp = b->host_tab[t];
+      const Level& lv = ctxs[order[t]]->lev[level];
+      const int k = L.acc.n++;
+      L.adj.n++;
+      L.acc.it[k].g = bp.g;
+      L.acc.it[k].a = bp.acc;
+      L.acc.it[k].id = bp.id;
+      L.acc.it[k].tile_begin = tile;
+      L.adj.it[k].g = bp.g;
+      L.adj.it[k].a = bp.adj;
+      L.adj.it[k].id = bp.id;
+      L.adj.it[k].tile_begin = tile;
+      tile += bp.g.ntile[0] * bp.g.ntile[1] * bp.g.ntile[2];
+      L.smem_acc = std::max(L.smem_acc, lv.smem_acc_rows);
+      L.smem_adj = std::max(L.smem_adj, lv.smem_adj_rows);
+      ++t;
+    }
+    L.nblk = tile;
+    L.acc_lb = L.acc;
+    L.adj_lb = L.adj;
+    b->work_items += tile;
+    b->launches_rows.push_back(L);
+  }
+  CK(cudaMalloc((void**)&b->tab_eval, sizeof(BatchPair) * n));
+  CK(cudaMemcpy(b->tab_eval, b->host_tab.data(), sizeof(BatchPair) * n, cudaMemcpyHostToDevice));
+  RET_IF(set_smem_limits_batch());
+  CK(cudaStreamSynchronize(b->stream));
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_batch_create(srwcr_ctx* const* ctxs, int n_pairs, int level, void* stream,
+                                srwcr_batch** out) {
+  if (!out) return fail(SRWCR_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctxs || n_pairs < 1 || n_pairs > 65535) return fail(SRWCR_EINVAL, "need 1..65535 contexts");
+  if (level < 0 || level > 3) return fail(SRWCR_EINVAL, "level %d out of range", level);
+  srwcr_batch* b = new (std::nothrow) srwcr_batch();
+  if (!b) return fail(SRWCR_ENOMEM, "host allocation failed");
+  srwcr_status st = batch_create_impl(b, ctxs, n_pairs, level, stream);
+  if (st != SRWCR_OK) {
+    std::string keep = g_err;
+    srwcr_batch_destroy(b);
+    g_err = keep;
+    return st;
+  }
+  *out = b;
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_batch_info(const srwcr_batch* b, srwcr_batch_desc* out) {
+  if (!b || !out) return fail(SRWCR_EINVAL, "null argument");
+  out->n_pairs = b->n;
+  out->launches_per_eval = launches_per_eval(b);
+  out->n_params_total = b->off[b->n];
+  out->n_voxels_total = b->total_vox;
+  out->work_items = b->work_items;
+  out->launches = b->launches;
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_batch_layout(const srwcr_batch* b, int64_t* offsets, int64_t* n_params) {
+  if (!b) return fail(SRWCR_EINVAL, "null batch");
+  for (int i = 0; i <= b->n && offsets; ++i) offsets[i] = b->off[i];
+  for (int i = 0; i < b->n && n_params; ++i)
+    n_params[i] = b->ctx[i]->lev[b->level].g.ncoef * b->ndim;
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_batch_buffers(srwcr_batch* b, float** c_dev, float** g_dev, double** D_dev) {
+  if (!b) return fail(SRWCR_EINVAL, "null batch");
+  if (c_dev) *c_dev = b->c;
+  if (g_dev) *g_dev = b->g;
+  if (D_dev) *D_dev = b->D;
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_batch_value_and_grad(srwcr_batch* b, int use_graph) {
+  if (!b) return fail(SRWCR_EINVAL, "null batch");
+  if (use_graph) {
+    if (!b->graph_eval)
+      RET_IF(capture(b, &b->graph_eval, [&] { return queue_batch_eval(b, false, nullptr); }));
+    CK(cudaGraphLaunch(b->graph_eval, b->stream));
+  } else {
+    RET_IF(queue_batch_eval(b, false, nullptr));
+  }
+  b->launches += launches_per_eval(b);
+  invalidate_member_tables(b);
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_batch_sync(srwcr_batch* b, double* D_host) {
+  if (!b) return fail(SRWCR_EINVAL, "null batch");
+  if (D_host) CK(cudaMemcpyAsync(D_host, b->D, sizeof(double) * b->n, cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_batch_register(srwcr_batch* b, const srwcr_lbfgs_opts* opts, int use_graph,
+                                  int* iterations, int* evaluations, double* final_value,
+                                  int* status) {
+  if (!b) return fail(SRWCR_EINVAL, "null batch");
+  srwcr_lbfgs_opts oo;
+  srwcr_lbfgs_default_opts(&oo);
+  if (opts) oo = *opts;
+  if (oo.m < 1 || oo.m > 16 || oo.max_ls < 1 || oo.stable_window >= kLbHist ||
+      oo.max_iter[b->level] < 0)
+    return fail(SRWCR_EINVAL, "bad L-BFGS options (m in 1..16, max_ls >= 1, window < %d)", kLbHist);
+  LbOpts o{oo.m, oo.max_iter[b->level], oo.stable_window, oo.max_ls, oo.stable_rtol, oo.c1, oo.c2};
+  RET_IF(batch_alloc_lbfgs(b, o.m));
+  k_lbfgs_init<<<b->n, 256, 0, b->stream>>>(b->lbs, b->active, b->off_dev, b->c, b->xn);
+  CKL();
+  b->launches += 1;
+  if (use_graph && b->graph_round &&
+      memcmp(&b->graph_round_opts, &o, sizeof o) != 0) {
+    cudaGraphExecDestroy(b->graph_round);
+    b->graph_round = nullptr;
+  }
+  if (use_graph && !b->graph_round) {
+    RET_IF(capture(b, &b->graph_round, [&] { return queue_lbfgs_round(b, o); }));
+    b->graph_round_opts = o;
+  }
+  // Every round spends one evaluation per active pair; a pair needs at most
+  // 1 + max_iter * max_ls of them.
+  const long long max_rounds = 1 + (long long)o.max_iter * o.max_ls;
+  const int chunk = 4;
+  long long rounds = 0;
+  while (rounds < max_rounds) {
+    for (int k = 0; k < chunk && rounds < max_rounds; ++k, ++rounds) {
+      if (use_graph) CK(cudaGraphLaunch(b->graph_round, b->stream));
+      else RET_IF(queue_lbfgs_round(b, o));
+      b->launches += launches_per_eval(b) + 1;
+    }
+    CK(cudaMemcpyAsync(b->active_host, b->active, sizeof(int) * b->n, cudaMemcpyDeviceToHost,
+                       b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    bool any = false;
+    for (int i = 0; i < b->n; ++i) any = any || b->active_host[i] != 0;
+    if (!any) break;
+  }
+  invalidate_member_tables(b);
+  std::vector<LbState> hs(b->n);
+  CK(cudaMemcpyAsync(hs.data(), b->lbs, sizeof(LbState) * b->n, cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  bool bad = false;
+  for (int i = 0; i < b->n; ++i) {
+    // Pairs still active ran out of rounds, which the bound above excludes;
+    // report them as not converged.
+    const int stt = b->active_host[i] ? SRWCR_ENOTCONVERGED : hs[i].status;
+    if (iterations) iterations[i] = hs[i].iter;
+    if (evaluations) evaluations[i] = hs[i].evals;
+    if (final_value) final_value[i] = hs[i].f;
+    if (status) status[i] = stt;
+    bad = bad || stt == SRWCR_ENUMERIC;
+  }
+  // The batch's coefficient buffer holds each pair's accepted point and the
+  // gradient buffer the gradient there.
+  if (bad) return fail(SRWCR_ENUMERIC, "non-finite SRWCR value in the batch");
+  return SRWCR_OK;
+}
+
+}  // extern "C"

@@ -145,14 +145,13 @@ __global__ void k_fixed_to_double(const unsigned long long* __restrict__ in, dou
 //   1 - CR_r = Q_r/(W_r sigma_r^2),  share of D = Q_r/(Z sigma_r^2)      (Eq. 9)
 // and the gradient tables of Eq. (19) with the b-sum done in closed form:
 //   U_r = CR_r/sigma_r^2,  V_r = (1-CR_r) mu_r/sigma_r^2,  X_ra = mu_r(a)/sigma_r^2.
-__global__ void k_finalize(const Geo g, const double* __restrict__ P,
-                           const unsigned long long* __restrict__ S, double inv_s1,
-                           double inv_s2, double invZ, float* __restrict__ U,
-                           float* __restrict__ V, float* __restrict__ X, double* __restrict__ Dr,
-                           double* __restrict__ stats) {
-  const int lane = threadIdx.x & 31;
-  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  if (r >= g.R) return;
+__device__ __forceinline__ void finalize_region(const Geo& g, long long r, int lane,
+                                                const double* __restrict__ P,
+                                                const unsigned long long* __restrict__ S,
+                                                double inv_s1, double inv_s2, double invZ,
+                                                float* __restrict__ U, float* __restrict__ V,
+                                                float* __restrict__ X, double* __restrict__ Dr,
+                                                double* __restrict__ stats) {
   const int nb = g.nbins;
   const double* Pr = P + r * nb;
   const unsigned long long* Sr = S + r * nb * 2;
@@ -205,10 +204,107 @@ __global__ void k_finalize(const Geo g, const double* __restrict__ P,
   }
 }
 
+// Static per-region data of the fixed image that the finalisation reuses at
+// every evaluation: W_r = sum_a P[r][a] = Z p(r), and the bins with
+// P[r][a] > 0 (the only ones where S1, S2 can be nonzero) with 1/P[r][a], in
+// compressed rows.
+struct RegionStatic {
+  const double* W;      // [R]
+  const int* ptr;       // [R+1] row offsets into bin/inv_p
+  const int* bin;       // [nnz] fixed-image bin a
+  const double* inv_p;  // [nnz] 1 / P[r][a]
+};
+
+// Same quantities as finalize_region, over the static nonzero bins only:
+// the moment sums T1, T2 are formed exactly in 64-bit integers and rounded
+// once, divisions by P become products with the stored reciprocals, and one
+// division by sigma_r^2 per region remains.  X entries of bins outside the
+// list stay at the zero they were initialised to.
+__device__ __forceinline__ void finalize_region_sparse(long long r, int lane, int nb,
+                                                       const RegionStatic& rs,
+                                                       const unsigned long long* __restrict__ S,
+                                                       double inv_s1, double inv_s2, double invZ,
+                                                       float* __restrict__ U, float* __restrict__ V,
+                                                       float* __restrict__ X, double* __restrict__ Dr,
+                                                       double* __restrict__ stats) {
+  const unsigned long long* Sr = S + r * nb * 2;
+  const int beg = rs.ptr[r], end = rs.ptr[r + 1];
+  unsigned long long t1 = 0ull, t2 = 0ull;
+  for (int k = beg + lane; k < end; k += 32) {
+    const int a = rs.bin[k];
+    t1 += Sr[2 * a];
+    t2 += Sr[2 * a + 1];
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    t1 += __shfl_xor_sync(0xffffffffu, t1, off);
+    t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+  }
+  const double W = rs.W[r];
+  bool valid = W > 0.0;
+  double mu = 0.0, var = 0.0, ms = 0.0;
+  if (valid) {
+    mu = (double)t1 * inv_s1 / W;
+    ms = (double)t2 * inv_s2 / W;
+    var = ms - mu * mu;
+    valid = var > 1e-6 * fmax(1.0, ms);  // degenerate: sigma_r^2 -> 0 (0/0 in Eq. 9)
+  }
+  const double iv = valid ? 1.0 / var : 0.0;
+  double Q = 0.0;
+  for (int k = beg + lane; k < end; k += 32) {
+    const int a = rs.bin[k];
+    double x = 0.0;
+    if (valid) {
+      const double s1 = (double)Sr[2 * a] * inv_s1, s2 = (double)Sr[2 * a + 1] * inv_s2;
+      const double m = s1 * rs.inv_p[k];     // mu_r(a) = S1 / P
+      Q += s2 - s1 * m;
+      x = m * iv;
+    }
+    X[r * nb + a] = (float)x;
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) Q += __shfl_xor_sync(0xffffffffu, Q, off);
+  if (lane == 0) {
+    double omc = 0.0, share = 0.0;
+    if (valid) {
+      omc = Q * iv / W;
+      share = Q * invZ * iv;
+    }
+    U[r] = valid ? (float)((1.0 - omc) * iv) : 0.f;
+    V[r] = valid ? (float)(omc * mu * iv) : 0.f;
+    Dr[r] = share;
+    stats[4 * r + 0] = W * invZ;
+    stats[4 * r + 1] = valid ? var : 0.0;
+    stats[4 * r + 2] = valid ? 1.0 - omc : 0.0;
+    stats[4 * r + 3] = share;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_finalize_sparse(long long R, int nb, const RegionStatic rs,
+                  const unsigned long long* __restrict__ S, double inv_s1, double inv_s2,
+                  double invZ, float* __restrict__ U, float* __restrict__ V,
+                  float* __restrict__ X, double* __restrict__ Dr, double* __restrict__ stats) {
+  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (r >= R) return;  // warp-uniform
+  finalize_region_sparse(r, threadIdx.x & 31, nb, rs, S, inv_s1, inv_s2, invZ, U, V, X, Dr,
+                         stats);
+}
+
+__global__ void k_finalize(const Geo g, const double* __restrict__ P,
+                           const unsigned long long* __restrict__ S, double inv_s1,
+                           double inv_s2, double invZ, float* __restrict__ U,
+                           float* __restrict__ V, float* __restrict__ X, double* __restrict__ Dr,
+                           double* __restrict__ stats) {
+  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (r >= g.R) return;  // warp-uniform
+  finalize_region(g, r, threadIdx.x & 31, P, S, inv_s1, inv_s2, invZ, U, V, X, Dr, stats);
+}
+
 // Deterministic sum of the regions' shares (fixed partition, fixed tree).
-__global__ void __launch_bounds__(1024)
-k_reduce_D(const double* __restrict__ Dr, const double* __restrict__ stats, long long R,
-           double* __restrict__ D, int* __restrict__ ndeg) {
+__device__ __forceinline__ void reduce_D_block(const double* __restrict__ Dr,
+                                               const double* __restrict__ stats, long long R,
+                                               double* __restrict__ D, int* __restrict__ ndeg) {
   __shared__ double sh[1024];
   __shared__ int shn[1024];
   double s = 0.0;
@@ -231,6 +327,12 @@ k_reduce_D(const double* __restrict__ Dr, const double* __restrict__ stats, long
     D[0] = sh[0];
     ndeg[0] = shn[0];
   }
+}
+
+__global__ void __launch_bounds__(1024)
+k_reduce_D(const double* __restrict__ Dr, const double* __restrict__ stats, long long R,
+           double* __restrict__ D, int* __restrict__ ndeg) {
+  reduce_D_block(Dr, stats, R, D, ndeg);
 }
 
 // (c) Adjoint.  dD/dB(x) of Eq. (19) with the b-sums in closed form:

@@ -74,9 +74,8 @@ struct TileOrigin {
 };
 
 template <int DIM>
-__device__ __forceinline__ TileOrigin tile_setup(const Geo& g) {
+__device__ __forceinline__ TileOrigin tile_setup(const Geo& g, int b) {
   TileOrigin T;
-  const int b = blockIdx.x;
   T.o[0] = (b % g.ntile[0]) * g.tile[0];
   T.o[1] = ((b / g.ntile[0]) % g.ntile[1]) * g.tile[1];
   T.o[2] = (b / (g.ntile[0] * g.ntile[1])) * g.tile[2];
@@ -219,6 +218,31 @@ __device__ __forceinline__ float pick4(const float b[4], int i) {
   return i == 0 ? b[0] : (i == 1 ? b[1] : (i == 2 ? b[2] : (i == 3 ? b[3] : 0.f)));
 }
 
+// Per-problem arguments of the row kernels (also the batch descriptors).
+struct AccArgs {
+  const void* A;                 // normalised fixed image (storage type)
+  const void* M;                 // normalised moving image (storage type)
+  const float* c;                // FFD coefficients
+  const unsigned char* perm;     // per-row lane permutation
+  const unsigned* binmask;       // per-tile fixed-image bins present
+  unsigned long long* acc;       // [R][nbins][2] fixed-point sums
+  float s1, s2;                  // fixed-point scales of the two moments
+};
+
+struct AdjArgs {
+  const void* A;
+  const void* M;
+  const float* c;
+  const unsigned char* perm;
+  const unsigned* binmask;
+  const float* U;
+  const float* V;
+  const float* X;
+  const float* gscale;           // device scalar or NULL (1)
+  float invZ;
+  float* grad;
+};
+
 // Bytes of the value kernel's shared memory (must match the carve-up below).
 // Words per y/z bin of the split histogram: 2 * nabin * hb0 rounded up to
 // 8 (mod 32), so the 4 y/z groups of a fold pass fall on disjoint banks.
@@ -248,12 +272,15 @@ __host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int
 // (a) value pass: fused FFD + warp + joint statistics, row-parallel.
 // ---------------------------------------------------------------------------
 template <int DIM, typename T, int NXB>
-__global__ void __launch_bounds__(kAccWarps * 32, 2)
-k_accumulate_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
-                  const float* __restrict__ c, const unsigned char* __restrict__ perm,
-                  const unsigned* __restrict__ binmask, unsigned long long* __restrict__ acc,
-                  float s1, float s2) {
-  extern __shared__ unsigned long long smem_u64[];
+__device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args, int tile,
+                                              unsigned long long* smem_u64) {
+  const T* __restrict__ A = static_cast<const T*>(args.A);
+  const T* __restrict__ M = static_cast<const T*>(args.M);
+  const float* __restrict__ c = args.c;
+  const unsigned char* __restrict__ perm = args.perm;
+  const unsigned* __restrict__ binmask = args.binmask;
+  unsigned long long* __restrict__ acc = args.acc;
+  const float s1 = args.s1, s2 = args.s2;
   constexpr int NV = NXB * 4;                 // (x-bin, slot, moment): v[4b + 2 slot + ch]
   constexpr int NK = DIM == 3 ? 4 : 1;        // z bins of a row
   const int nb = g.nbins;
@@ -284,11 +311,11 @@ k_accumulate_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
   int* mysegA = segA + warp * 32;
   int* mybins = binl + warp * 64 * 2;
 
-  const TileOrigin TO = tile_setup<DIM>(g);
+  const TileOrigin TO = tile_setup<DIM>(g, tile);
   for (int i = threadIdx.x; i < 3 * NYZ * S; i += blockDim.x) hlo[i] = 0u;
   {
     const int words = (nb + 31) >> 5;
-    const unsigned* tmask = binmask + (size_t)blockIdx.x * words;
+    const unsigned* tmask = binmask + (size_t)tile * words;
     for (int a = threadIdx.x; a < nb; a += blockDim.x) {
       const int w = a >> 5;
       const unsigned mw = __ldg(tmask + w);
@@ -495,13 +522,19 @@ __host__ __device__ inline size_t adj_rows_smem_bytes(const Geo& g, int dim, int
 // (c) adjoint, row-parallel.
 // ---------------------------------------------------------------------------
 template <int DIM, typename T, int NXB>
-__global__ void __launch_bounds__(kAdjWarps * 32)
-k_adjoint_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
-               const float* __restrict__ c, const unsigned char* __restrict__ perm,
-               const unsigned* __restrict__ binmask, const float* __restrict__ U,
-               const float* __restrict__ V, const float* __restrict__ X,
-               const float* __restrict__ gscale, float invZ, float* __restrict__ grad) {
-  extern __shared__ float smem_f32[];
+__device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args, int tile,
+                                              float* smem_f32) {
+  const T* __restrict__ A = static_cast<const T*>(args.A);
+  const T* __restrict__ M = static_cast<const T*>(args.M);
+  const float* __restrict__ c = args.c;
+  const unsigned char* __restrict__ perm = args.perm;
+  const unsigned* __restrict__ binmask = args.binmask;
+  const float* __restrict__ U = args.U;
+  const float* __restrict__ V = args.V;
+  const float* __restrict__ X = args.X;
+  const float* __restrict__ gscale = args.gscale;
+  const float invZ = args.invZ;
+  float* __restrict__ grad = args.grad;
   const int nb = g.nbins;
   const float L = (float)(nb - 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -525,7 +558,7 @@ k_adjoint_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
   int* mysegA = segA_all + warp * 32;
   float* cyz = cyz_all + warp * DIM * kMaxRowNodes;
 
-  const TileOrigin TO = tile_setup<DIM>(g);
+  const TileOrigin TO = tile_setup<DIM>(g, tile);
   for (int i = threadIdx.x; i < DIM * nodes_tile; i += blockDim.x) gt[i] = 0.f;
   build_xtab<NXB>(g, TO, xt);
   build_axis_tables<DIM>(g, TO, yt, zt);
@@ -534,7 +567,7 @@ k_adjoint_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
   // Region tables contracted over z for each of the tile's z-planes.  X is
   // only needed for the fixed-image bins present in the tile (a0 and a0+1 of
   // its voxels, a static mask); other entries are never read.
-  const unsigned* tmask = binmask + (size_t)blockIdx.x * ((nb + 31) >> 5);
+  const unsigned* tmask = binmask + (size_t)tile * ((nb + 31) >> 5);
   {
     const int nzp = g.tile[2] * p01;
     const int n = nzp * (2 + nb);
@@ -692,6 +725,21 @@ k_adjoint_rows(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
     if (n0 >= g.nf[0] || n1 >= g.nf[1] || n2 >= g.nf[2]) continue;
     atomicAdd(grad + k * g.ncoef + ((long long)n2 * g.nf[1] + n1) * g.nf[0] + n0, val);
   }
+}
+
+// One problem: one CTA per tile.
+template <int DIM, typename T, int NXB>
+__global__ void __launch_bounds__(kAccWarps * 32, 2)
+k_accumulate_rows(const Geo g, const AccArgs args) {
+  extern __shared__ unsigned long long smem_acc[];
+  acc_rows_body<DIM, T, NXB>(g, args, blockIdx.x, smem_acc);
+}
+
+template <int DIM, typename T, int NXB>
+__global__ void __launch_bounds__(kAdjWarps * 32)
+k_adjoint_rows(const Geo g, const AdjArgs args) {
+  extern __shared__ float smem_adj[];
+  adj_rows_body<DIM, T, NXB>(g, args, blockIdx.x, smem_adj);
 }
 
 // Static per-tile mask of the fixed-image bins its voxels touch (a0, a0+1).

@@ -72,6 +72,10 @@ struct Level {
   void* M = nullptr;                  // normalised moving image (storage type)
   unsigned long long* S = nullptr;    // [R][nbins][2] fixed-point S1, S2 (also P scratch)
   double* P = nullptr;                // [R][nbins] sum_x w h(a - A)
+  double* Wr = nullptr;               // [R] sum_a P[r][a]
+  int* nz_ptr = nullptr;              // [R+1] bins with P > 0, compressed rows
+  int* nz_bin = nullptr;              // [nnz]
+  double* nz_inv_p = nullptr;         // [nnz] 1 / P
   float* U = nullptr;                 // [R]
   float* V = nullptr;                 // [R]
   float* X = nullptr;                 // [R][nbins]
@@ -234,29 +238,37 @@ void fixed_scales(const Geo& g, int ndim, double* sP, double* s1, double* s2) {
   *s2 = std::min(*s2, std::ldexp(1.0, 56 - ceil_log2(64.0 * L * L)));
 }
 
-template <int DIM, typename T>
-void launch_rows_acc(srwcr_ctx* ctx, Level& lv, const float* c, int nblk) {
-  const T* A = (const T*)lv.A;
-  const T* M = (const T*)lv.M;
-  if (lv.nxb_rows == 4)
-    k_accumulate_rows<DIM, T, 4><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(
-        lv.g, A, M, c, lv.perm, lv.binmask, lv.S, lv.s1, lv.s2);
-  else
-    k_accumulate_rows<DIM, T, 8><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(
-        lv.g, A, M, c, lv.perm, lv.binmask, lv.S, lv.s1, lv.s2);
+AccArgs acc_args(const Level& lv, const float* c) {
+  AccArgs a;
+  a.A = lv.A; a.M = lv.M; a.c = c; a.perm = lv.perm; a.binmask = lv.binmask;
+  a.acc = lv.S; a.s1 = lv.s1; a.s2 = lv.s2;
+  return a;
+}
+
+AdjArgs adj_args(const Level& lv, const float* c, const float* gD, float* g) {
+  AdjArgs a;
+  a.A = lv.A; a.M = lv.M; a.c = c; a.perm = lv.perm; a.binmask = lv.binmask;
+  a.U = lv.U; a.V = lv.V; a.X = lv.X; a.gscale = gD; a.invZ = (float)(1.0 / lv.Z); a.grad = g;
+  return a;
 }
 
 template <int DIM, typename T>
-void launch_rows_adj(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float invZ,
-                     float* g, int nblk) {
-  const T* A = (const T*)lv.A;
-  const T* M = (const T*)lv.M;
+void launch_rows_acc(srwcr_ctx* ctx, Level& lv, const float* c, int nblk) {
+  const AccArgs a = acc_args(lv, c);
   if (lv.nxb_rows == 4)
-    k_adjoint_rows<DIM, T, 4><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(
-        lv.g, A, M, c, lv.perm, lv.binmask, lv.U, lv.V, lv.X, gD, invZ, g);
+    k_accumulate_rows<DIM, T, 4><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
   else
-    k_adjoint_rows<DIM, T, 8><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(
-        lv.g, A, M, c, lv.perm, lv.binmask, lv.U, lv.V, lv.X, gD, invZ, g);
+    k_accumulate_rows<DIM, T, 8><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
+}
+
+template <int DIM, typename T>
+void launch_rows_adj(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g,
+                     int nblk) {
+  const AdjArgs a = adj_args(lv, c, gD, g);
+  if (lv.nxb_rows == 4)
+    k_adjoint_rows<DIM, T, 4><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a);
+  else
+    k_adjoint_rows<DIM, T, 8><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a);
 }
 
 template <typename T>
@@ -289,8 +301,8 @@ srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const flo
   const int nblk = lv.g.ntile[0] * lv.g.ntile[1] * lv.g.ntile[2];
   const float invZ = (float)(1.0 / lv.Z);
   if (lv.rows) {
-    if (ctx->cfg.ndim == 3) launch_rows_adj<3, T>(ctx, lv, c, gD, invZ, g, nblk);
-    else launch_rows_adj<2, T>(ctx, lv, c, gD, invZ, g, nblk);
+    if (ctx->cfg.ndim == 3) launch_rows_adj<3, T>(ctx, lv, c, gD, g, nblk);
+    else launch_rows_adj<2, T>(ctx, lv, c, gD, g, nblk);
     CKL();
     return SRWCR_OK;
   }
@@ -352,6 +364,15 @@ srwcr_status check_level(const srwcr_ctx* ctx, int level) {
   return SRWCR_OK;
 }
 
+RegionStatic region_static(const Level& lv) {
+  RegionStatic rs;
+  rs.W = lv.Wr;
+  rs.ptr = lv.nz_ptr;
+  rs.bin = lv.nz_bin;
+  rs.inv_p = lv.nz_inv_p;
+  return rs;
+}
+
 // (a) + (b): value into lv.D, tables into lv.U/V/X.
 srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c) {
   const size_t sbytes = (size_t)lv.g.R * lv.g.nbins * 2 * sizeof(unsigned long long);
@@ -364,8 +385,9 @@ srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c) {
   const long long warps = lv.g.R;
   const int fblk = (int)((warps * 32 + kBlock - 1) / kBlock);
   ev = prof_begin(ctx);
-  k_finalize<<<fblk, kBlock, 0, ctx->stream>>>(lv.g, lv.P, lv.S, 1.0 / lv.s1, 1.0 / lv.s2,
-                                               1.0 / lv.Z, lv.U, lv.V, lv.X, lv.Dr, lv.stats);
+  k_finalize_sparse<<<fblk, kBlock, 0, ctx->stream>>>(lv.g.R, lv.g.nbins, region_static(lv), lv.S,
+                                                      1.0 / lv.s1, 1.0 / lv.s2, 1.0 / lv.Z, lv.U,
+                                                      lv.V, lv.X, lv.Dr, lv.stats);
   CKL();
   k_reduce_D<<<1, 1024, 0, ctx->stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg);
   CKL();
@@ -410,7 +432,7 @@ srwcr_status finish_sync(srwcr_ctx* ctx, Level& lv, double* D_host) {
 
 void free_level(Level& lv) {
   void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg, lv.perm,
-                  lv.binmask};
+                  lv.binmask, lv.Wr, lv.nz_ptr, lv.nz_bin, lv.nz_inv_p};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   lv = Level();
@@ -442,7 +464,7 @@ void launch_tile_binmask(srwcr_ctx* ctx, const Geo& g, const void* A, unsigned* 
 // each candidate's per-tile masks are built on the device and the largest
 // per-tile count sizes the histogram.  Levels without such a tile keep the
 // general path.
-srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv) {
+srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv, const int* force_tile = nullptr) {
   const srwcr_config& cfg = ctx->cfg;
   const int nd = cfg.ndim;
   static const int cand3[][3] = {{32, 32, 8}, {32, 16, 8}, {32, 8, 8}, {32, 8, 4}, {32, 4, 4},
@@ -450,7 +472,9 @@ srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv) {
   static const int cand2[][3] = {{32, 64, 1}, {32, 32, 1}, {32, 16, 1}, {32, 8, 1}, {32, 4, 1},
                                  {32, 1, 1}};
   std::vector<std::array<int, 3>> cands;
-  if (cfg.tile[0] > 0) {
+  if (force_tile) {
+    cands.push_back({force_tile[0], force_tile[1], force_tile[2]});
+  } else if (cfg.tile[0] > 0) {
     if (cfg.tile[0] == 32) cands.push_back({32, std::max(1, cfg.tile[1]), std::max(1, cfg.tile[2])});
   } else if (nd == 3) {
     for (auto& t : cand3) cands.push_back({t[0], t[1], t[2]});
@@ -646,7 +670,37 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     if (e != cudaSuccess) { free(hP); return fail(SRWCR_ECUDA, "P readback: %s", cudaGetErrorString(e)); }
     double Z = 0.0;
     for (long long i = 0; i < n; ++i) Z += hP[i];
+    // Static per-region data of the finalisation (bins with P > 0).
+    const int nb = lv.g.nbins;
+    std::vector<double> Wr(lv.g.R), inv_p;
+    std::vector<int> ptr(lv.g.R + 1, 0), bin;
+    for (long long r = 0; r < lv.g.R; ++r) {
+      double w = 0.0;
+      for (int a = 0; a < nb; ++a) {
+        const double p = hP[r * nb + a];
+        w += p;
+        if (p > 0.0) {
+          bin.push_back(a);
+          inv_p.push_back(1.0 / p);
+        }
+      }
+      Wr[r] = w;
+      ptr[r + 1] = (int)bin.size();
+    }
     free(hP);
+    const size_t nnz = std::max<size_t>(bin.size(), 1);
+    CK(cudaMalloc((void**)&lv.Wr, sizeof(double) * lv.g.R));
+    CK(cudaMalloc((void**)&lv.nz_ptr, sizeof(int) * (lv.g.R + 1)));
+    CK(cudaMalloc((void**)&lv.nz_bin, sizeof(int) * nnz));
+    CK(cudaMalloc((void**)&lv.nz_inv_p, sizeof(double) * nnz));
+    CK(cudaMemcpy(lv.Wr, Wr.data(), sizeof(double) * lv.g.R, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(lv.nz_ptr, ptr.data(), sizeof(int) * (lv.g.R + 1), cudaMemcpyHostToDevice));
+    if (!bin.empty()) {
+      CK(cudaMemcpy(lv.nz_bin, bin.data(), sizeof(int) * bin.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(lv.nz_inv_p, inv_p.data(), sizeof(double) * bin.size(), cudaMemcpyHostToDevice));
+    }
+    // X entries of bins with P = 0 are never written by the finalisation.
+    CK(cudaMemsetAsync(lv.X, 0, sizeof(float) * lv.g.R * nb, ctx->stream));
     lv.Z = Z;
     if (!(Z > 0.0)) return fail(SRWCR_EINVAL, "empty fixed-image statistics at level %d", l);
   }
@@ -993,4 +1047,140 @@ extern "C" srwcr_status srwcr_value_noalloc(const srwcr_config* cfg, const float
   return SRWCR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Tile autotuner.  Times value+gradient for each 32-wide tile that fits the
+// row kernels and keeps the fastest; the choice is cached per problem
+// signature in memory and, when SRWCR_AUTOTUNE_CACHE names a file, in that
+// file (one "signature tile_x tile_y tile_z" line per problem).
+// ---------------------------------------------------------------------------
+namespace {
+
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, std::array<int, 3>>> g_tune_cache;
+
+std::string tune_key(const srwcr_ctx* ctx, const Geo& g) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "d%d_n%dx%dx%d_f%dx%dx%d_s%d/%d,%d/%d,%d/%d_b%d_t%d", ctx->cfg.ndim, g.n[0],
+           g.n[1], g.n[2], g.fsp[0], g.fsp[1], g.fsp[2], g.sbn[0], g.sbd[0], g.sbn[1], g.sbd[1],
+           g.sbn[2], g.sbd[2], g.nbins, ctx->cfg.storage);
+  return buf;
+}
+
+bool tune_lookup(const std::string& key, std::array<int, 3>* t) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (auto& e : g_tune_cache)
+    if (e.first == key) { *t = e.second; return true; }
+  const char* path = getenv("SRWCR_AUTOTUNE_CACHE");
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char k[256];
+  int a, b, c;
+  bool found = false;
+  while (fscanf(f, "%255s %d %d %d", k, &a, &b, &c) == 4)
+    if (key == k) { *t = {a, b, c}; found = true; }
+  fclose(f);
+  if (found) g_tune_cache.push_back({key, *t});
+  return found;
+}
+
+void tune_store(const std::string& key, const std::array<int, 3>& t) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache.push_back({key, t});
+  const char* path = getenv("SRWCR_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d %d\n", key.c_str(), t[0], t[1], t[2]);
+  fclose(f);
+}
+
+void release_rows(Level& lv) {
+  if (lv.perm) cudaFree(lv.perm);
+  if (lv.binmask) cudaFree(lv.binmask);
+  lv.perm = nullptr;
+  lv.binmask = nullptr;
+  lv.rows = false;
+  lv.g = lv.gv;
+}
+
+}  // namespace
+
+extern "C" srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c_dev, int reps,
+                                       int* tile_out) {
+  RET_IF(check_level(ctx, level));
+  if (!c_dev) return fail(SRWCR_EINVAL, "c_dev is NULL");
+  if (reps < 1) reps = 3;
+  Level& lv = ctx->lev[level];
+  const std::string key = tune_key(ctx, lv.gv);
+  std::array<int, 3> best{0, 0, 0};
+  if (tune_lookup(key, &best)) {
+    release_rows(lv);
+    RET_IF(select_rows_path(ctx, lv, best.data()));
+    if (!lv.rows) RET_IF(select_rows_path(ctx, lv));
+  } else {
+    static const int cand3[][3] = {{32, 32, 8}, {32, 32, 4}, {32, 16, 8}, {32, 16, 4},
+                                   {32, 8, 8}, {32, 8, 4}, {32, 32, 2}, {32, 16, 2}};
+    static const int cand2[][3] = {{32, 64, 1}, {32, 32, 1}, {32, 16, 1}, {32, 8, 1}};
+    const int nc = ctx->cfg.ndim == 3 ? 8 : 4;
+    const int (*cand)[3] = ctx->cfg.ndim == 3 ? cand3 : cand2;
+    float* g = nullptr;
+    double* D = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const size_t np = (size_t)lv.gv.ncoef * ctx->cfg.ndim;
+    CK(cudaMalloc((void**)&g, sizeof(float) * np));
+    cudaError_t ce = cudaMalloc((void**)&D, sizeof(double));
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    float best_ms = INFINITY;
+    srwcr_status st = ce == cudaSuccess ? SRWCR_OK : fail(SRWCR_ECUDA, "autotune set-up failed");
+    const bool prof = ctx->profiling;
+    ctx->profiling = false;
+    for (int i = 0; i < nc && st == SRWCR_OK; ++i) {
+      release_rows(lv);
+      st = select_rows_path(ctx, lv, cand[i]);
+      if (st != SRWCR_OK || !lv.rows) continue;
+      for (int w = 0; w < 2 && st == SRWCR_OK; ++w) {
+        st = run_value(ctx, lv, c_dev);
+        if (st == SRWCR_OK) st = run_grad(ctx, lv, c_dev, nullptr, g);
+      }
+      cudaEventRecord(e0, ctx->stream);
+      for (int r = 0; r < reps && st == SRWCR_OK; ++r) {
+        st = run_value(ctx, lv, c_dev);
+        if (st == SRWCR_OK) st = run_grad(ctx, lv, c_dev, nullptr, g);
+      }
+      cudaEventRecord(e1, ctx->stream);
+      if (st != SRWCR_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(SRWCR_ECUDA, "autotune timing failed"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = {cand[i][0], cand[i][1], cand[i][2]};
+      }
+    }
+    ctx->profiling = prof;
+    cudaFree(g);
+    cudaFree(D);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    RET_IF(st);
+    release_rows(lv);
+    if (best[0]) {
+      RET_IF(select_rows_path(ctx, lv, best.data()));
+      tune_store(key, best);
+    } else {
+      RET_IF(select_rows_path(ctx, lv));
+    }
+  }
+  lv.tables = false;
+  if (tile_out) {
+    tile_out[0] = lv.g.tile[0];
+    tile_out[1] = lv.g.tile[1];
+    tile_out[2] = lv.g.tile[2];
+  }
+  return SRWCR_OK;
+}
+
 #include "lbfgs.cuh"
+#include "batch.cuh"

@@ -1,0 +1,148 @@
+"""GPU tests of the batched form (many pairs per launch, CUDA-graph replay,
+device-resident batched L-BFGS).
+
+* Values: the batched kernels run the same per-tile code on each pair's own
+  geometry, and the value is summed in fixed point, so every pair's D equals
+  the single-pair entry point's bit for bit, eager or replayed from a graph;
+  gradients agree to FP32 scatter order.  Each pair is also checked against
+  the FP64 oracle on the same (BF16-rounded where stored so) inputs with the
+  FP32-path tolerances.
+* L-BFGS: one batched iteration equals the oracle's first iteration (a unit
+  steepest-descent step with the Armijo/Wolfe search); several iterations
+  end near the single-pair driver's values; graph replay and eager launches
+  agree; the reported final values are the values at the returned points.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import lbfgs
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+D_RTOL = 1e-5
+GNORM_RTOL = 1e-4
+
+
+def make_engines(specs, storage):
+    import paper_1804_05061_b300 as eng
+    return [eng.from_problem(s.prob, s.fixed, s.moving, storage=storage) for s in specs]
+
+
+@pytest.fixture(scope="module")
+def specs():
+    # Uneven cubes, some narrower than one 32-voxel row tile.
+    return synth.batch_specs(5, seed=77, edges=(24, 40, 56))
+
+
+def coefs(specs, seed, sigma):
+    return [synth.coefficients(s.prob, seed + i, sigma) for i, s in enumerate(specs)]
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_batched_value_and_gradient_equal_single_pair_and_oracle(specs, storage):
+    import paper_1804_05061_b300 as eng
+    es = make_engines(specs, storage)
+    assert all(e.levels[0].kernel_path == 1 for e in es)
+    b = eng.Batch(es)
+    info = b.info()
+    assert info.n_pairs == len(specs) and info.launches_per_eval <= 5
+    cs = coefs(specs, 500, 2.0)
+    for i, c in enumerate(cs):
+        b.coef(i).copy_(torch.from_numpy(c))
+    D_eager = b.value_and_grad(use_graph=False)
+    g_eager = [b.grad(i).clone() for i in range(len(es))]
+    D_graph = b.value_and_grad(use_graph=True)
+    D_graph2 = b.value_and_grad(use_graph=True)
+    assert np.array_equal(D_eager, D_graph) and np.array_equal(D_eager, D_graph2)
+    for i, (s, e) in enumerate(zip(specs, es)):
+        D, g = e.value_and_grad(torch.from_numpy(cs[i]).cuda())
+        assert D_eager[i] == D
+        assert torch.allclose(g_eager[i], g, rtol=1e-5, atol=1e-5 * float(g.abs().max()))
+        assert torch.allclose(b.grad(i), g, rtol=1e-5, atol=1e-5 * float(g.abs().max()))
+        geo = oracle.Geometry.from_problem(s.prob)
+        A, M = oracle.prepare(s.fixed, s.moving, s.prob.n_bins, storage)
+        st = oracle.value(geo, A, M, cs[i])
+        go = oracle.gradient(geo, A, M, cs[i], st)
+        assert abs(D - st.D) <= D_RTOL * abs(st.D), (i, D, st.D)
+        gn, gon = float(np.linalg.norm(g.cpu().numpy().astype(np.float64))), np.linalg.norm(go)
+        assert abs(gn - gon) <= GNORM_RTOL * gon, (i, gn, gon)
+
+
+def test_batch_rejects_mixed_storage_and_general_path_levels(specs):
+    import paper_1804_05061_b300 as eng
+    es = make_engines(specs[:1], "f32") + make_engines(specs[1:2], "bf16")
+    with pytest.raises(eng.SrwcrError, match="EINVAL"):
+        eng.Batch(es)
+    prob = synth.problem(3, (41, 37, 29), (5, 5, 5), (0, 0, 0), 32)
+    f, m = synth.small_pair("oct", prob.dims, prob.ffd_spacing, 1.0, 9)
+    general = eng.from_problem(prob, f, m)
+    assert general.levels[0].kernel_path == 0
+    with pytest.raises(eng.SrwcrError, match="row-parallel"):
+        eng.Batch([general])
+
+
+def test_batched_lbfgs_first_iteration_matches_oracle(specs):
+    import paper_1804_05061_b300 as eng
+    sub = specs[:3]
+    es = make_engines(sub, "f32")
+    b = eng.Batch(es)
+    o = eng.SRWCR.default_opts()
+    o.max_iter[0] = 1
+    rep = b.register(o)
+    assert np.all(rep["iterations"] == 1)
+    for i, s in enumerate(sub):
+        geo = oracle.Geometry.from_problem(s.prob)
+        A, M = oracle.prepare(s.fixed, s.moving, s.prob.n_bins)
+
+        def fg(x, geo=geo, A=A, M=M, shape=s.prob.coef_shape):
+            D, g, _ = oracle.value_and_grad(geo, A, M, x.reshape(shape))
+            return D, g.ravel()
+
+        res = lbfgs.minimise(fg, np.zeros(s.prob.n_params), lbfgs.LbfgsOptions(max_iter=1))
+        cg = b.coef(i).cpu().numpy().ravel().astype(np.float64)
+        assert np.abs(cg - res.x).max() <= 1e-4 * max(np.abs(res.x).max(), 1e-12)
+        assert abs(rep["final_value"][i] - res.f) <= D_RTOL * res.f
+        assert rep["evaluations"][i] == res.n_evals
+
+
+def test_batched_lbfgs_agrees_with_single_pair_driver_and_graph_with_eager(specs):
+    import paper_1804_05061_b300 as eng
+    es = make_engines(specs, "bf16")
+    o = eng.SRWCR.default_opts()
+    o.max_iter[0] = 8
+    o.stable_window = 0
+    b = eng.Batch(es)
+    rep_g = b.register(o, use_graph=True)
+    xs_g = [b.coef(i).clone() for i in range(len(es))]
+    D_after = b.values()
+    for i in range(len(es)):
+        b.coef(i).zero_()
+    rep_e = b.register(o, use_graph=False)
+    singles = []
+    for i, e in enumerate(es):
+        c = e.zeros()
+        D0 = e.value(c)
+        r = e.register(c, 1, o)
+        singles.append(r.final_value[0])
+        f_g, f_e = rep_g["final_value"][i], rep_e["final_value"][i]
+        assert f_g < D0 and f_e < D0
+        # Same method and arithmetic up to FP64 dot order and FP32 gradient
+        # scatter order: the runs end at nearby values.
+        assert abs(f_g - f_e) <= 1e-3 * f_e, (i, f_g, f_e)
+        assert abs(f_g - r.final_value[0]) <= 1e-2 * r.final_value[0], (i, f_g, r.final_value[0])
+        # The reported value is the value at the returned point.
+        assert e.value(xs_g[i]) == f_g
+        assert D_after[i] == f_g
+        assert rep_g["status"][i] in (0, 5, 7)
+
+
+def test_batched_lbfgs_rejects_bad_options(specs):
+    import paper_1804_05061_b300 as eng
+    b = eng.Batch(make_engines(specs[:2], "f32"))
+    o = eng.SRWCR.default_opts()
+    o.stable_window = 64
+    with pytest.raises(eng.SrwcrError, match="EINVAL"):
+        b.register(o)

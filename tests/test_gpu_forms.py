@@ -156,3 +156,29 @@ def test_autograd_gradient_matches_finite_differences_and_oracle_on_oct():
     st = oracle.value(geo, A, M, c0)
     go = oracle.gradient_at(geo, A, M, c0, st, idx)
     assert np.abs(gs - go).max() <= 1e-3 * scale
+
+
+# ---------------------------------------------------------------------------
+# tile autotuner
+# ---------------------------------------------------------------------------
+def test_autotune_keeps_row_path_value_and_gradient(tmp_path, monkeypatch):
+    cache = tmp_path / "tiles.txt"
+    monkeypatch.setenv("SRWCR_AUTOTUNE_CACHE", str(cache))
+    prob = synth.problem(3, (70, 45, 23), (6, 5, 4), (3, 2, 2), 24)
+    f, m = synth.small_pair("ct", prob.dims, prob.ffd_spacing, 2.0, 61)
+    e = engine(prob, f, m)
+    c = torch.from_numpy(synth.coefficients(prob, 62, 1.5)).cuda()
+    D0, g0 = e.value_and_grad(c)
+    tile = e.autotune(c, reps=2)
+    assert tile[0] == 32 and e.levels[0].kernel_path == 1 and tuple(e.levels[0].tile) == tile
+    D1, g1 = e.value_and_grad(c)
+    # Rows stay 32 voxels wide and the statistics are summed in fixed point,
+    # so the value does not depend on the tile's y/z extent.
+    assert D1 == D0
+    assert torch.allclose(g1, g0, rtol=1e-5, atol=1e-5 * float(g0.abs().max()))
+    lines = cache.read_text().split("\n")
+    assert any(l.endswith(" %d %d %d" % tile) for l in lines)
+    # A second engine of the same problem takes the cached choice.
+    e2 = engine(prob, f, m)
+    assert e2.autotune(c, reps=2) == tile
+    assert e2.value(c) == D0
