@@ -215,11 +215,13 @@ def bench_batch(args, eng, torch, dist, ws):
             dist.barrier()
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.profiler.start()
         s0.record(stream)
         for _ in range(steps):
             fn()
         s1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         t = s0.elapsed_time(s1) / 1e3
         if dist is not None:
             tt = torch.tensor([t], dtype=torch.float64, device=cs[0].device)
@@ -330,6 +332,7 @@ def main():
     e = eng.from_problem(prob, pair.fixed, pair.moving, storage=args.storage)
     stream = e.stream
     c = torch.from_numpy(c_np).to(dev)
+    tile = e.autotune(c, reps=3)
     g = torch.empty_like(c)
     D = torch.empty((), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -347,6 +350,7 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    torch.cuda.profiler.start()     # no-op unless a profiler waits for it
     t0 = time.perf_counter()
     for k in range(args.steps):
         flush.zero_()
@@ -354,6 +358,7 @@ def main():
         e.value_and_grad_async(c, D, g)
         ends[k].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     if dist is not None:
         dist.barrier()
     wall = time.perf_counter() - t0
@@ -431,7 +436,9 @@ def main():
                        f"CT-shaped pair, FFD spacing {prob.ffd_spacing[0]}, spatial bins "
                        f"{prob.sbin_intervals[:prob.ndim]} intervals, {prob.n_bins} intensity "
                        "bins, M as B, finest level",
-                       "storage": args.storage, "n_voxels": prob.n_voxels,
+                       "storage": args.storage, "tile": list(tile),
+                       "kernel_path": "row-parallel" if e.levels[0].kernel_path else "general",
+                       "n_voxels": prob.n_voxels,
                        "n_params": prob.n_params, "parallelism": f"replicas x{ws}",
                        "l2": "flushed between steps (256 MB write, outside the timed events)",
                        "wall_ms_per_step_incl_flush": wall / args.steps * 1e3},

@@ -258,16 +258,24 @@ struct srwcr_batch {
   bool own_stream = false;
   std::vector<srwcr_ctx*> ctx;
   std::vector<long long> off;  // caller order, n+1 float offsets into c and g
-  // One row-kernel launch: pairs of one x-bin class (4 or 8 per row), at
-  // most kBatchChunk of them, with their parameter tables for the plain
-  // evaluation and for the optimiser's (which reads xn and writes gn).
-  struct Launch {
+  // Row-kernel launches.  Pairs are grouped by x-bins per row (4 or 8, a
+  // template parameter) and by how many CTAs of their shared-memory size fit
+  // on an SM (a launch's dynamic shared memory is the largest of its pairs',
+  // so mixing sizes would lower the occupancy of the smaller ones); at most
+  // kBatchChunk pairs per launch.  Each launch keeps its parameter table for
+  // the plain evaluation and for the optimiser's (reads xn, writes gn).
+  struct AccLaunch {
     int nxb, nblk;
-    size_t smem_acc, smem_adj;
-    AccTable acc, acc_lb;
-    AdjTable adj, adj_lb;
+    size_t smem;
+    AccTable t, t_lb;
   };
-  std::vector<Launch> launches_rows;
+  struct AdjLaunch {
+    int nxb, nblk;
+    size_t smem;
+    AdjTable t, t_lb;
+  };
+  std::vector<AccLaunch> acc_launches;
+  std::vector<AdjLaunch> adj_launches;
   std::vector<BatchPair> host_tab;  // table order (by group, then size)
   long long total_regions = 0;
   long long total_vox = 0;
@@ -295,19 +303,21 @@ namespace {
 
 template <int DIM, typename T>
 void launch_batch_rows(srwcr_batch* b, bool lb, const int* active, bool adj) {
-  for (const auto& L : b->launches_rows) {
-    if (adj) {
-      const AdjTable& t = lb ? L.adj_lb : L.adj;
+  if (adj) {
+    for (const auto& L : b->adj_launches) {
+      const AdjTable& t = lb ? L.t_lb : L.t;
       if (L.nxb == 4)
-        k_adjoint_rows_batch<DIM, T, 4><<<L.nblk, kAdjWarps * 32, L.smem_adj, b->stream>>>(t, active);
+        k_adjoint_rows_batch<DIM, T, 4><<<L.nblk, kAdjWarps * 32, L.smem, b->stream>>>(t, active);
       else
-        k_adjoint_rows_batch<DIM, T, 8><<<L.nblk, kAdjWarps * 32, L.smem_adj, b->stream>>>(t, active);
-    } else {
-      const AccTable& t = lb ? L.acc_lb : L.acc;
+        k_adjoint_rows_batch<DIM, T, 8><<<L.nblk, kAdjWarps * 32, L.smem, b->stream>>>(t, active);
+    }
+  } else {
+    for (const auto& L : b->acc_launches) {
+      const AccTable& t = lb ? L.t_lb : L.t;
       if (L.nxb == 4)
-        k_accumulate_rows_batch<DIM, T, 4><<<L.nblk, kAccWarps * 32, L.smem_acc, b->stream>>>(t, active);
+        k_accumulate_rows_batch<DIM, T, 4><<<L.nblk, kAccWarps * 32, L.smem, b->stream>>>(t, active);
       else
-        k_accumulate_rows_batch<DIM, T, 8><<<L.nblk, kAccWarps * 32, L.smem_acc, b->stream>>>(t, active);
+        k_accumulate_rows_batch<DIM, T, 8><<<L.nblk, kAccWarps * 32, L.smem, b->stream>>>(t, active);
     }
   }
 }
@@ -363,7 +373,13 @@ srwcr_status queue_batch_eval(srwcr_batch* b, bool lb, const int* active) {
   return SRWCR_OK;
 }
 
-int launches_per_eval(const srwcr_batch* b) { return 3 + 2 * (int)b->launches_rows.size(); }
+int launches_per_eval(const srwcr_batch* b) {
+  return 3 + (int)b->acc_launches.size() + (int)b->adj_launches.size();
+}
+
+// CTAs of a given dynamic shared-memory size that fit on one SM (228 KB of
+// shared memory, 1 KB reserved per CTA).
+int ctas_per_sm(size_t smem) { return (int)std::min<size_t>(4, (228 * 1024) / (smem + 1024)); }
 
 srwcr_status queue_lbfgs_round(srwcr_batch* b, const LbOpts& o) {
   RET_IF(queue_batch_eval(b, true, b->active));
@@ -425,14 +441,14 @@ srwcr_status batch_alloc_lbfgs(srwcr_batch* b, int m) {
   }
   if (!b->tab_lb) CK(cudaMalloc((void**)&b->tab_lb, sizeof(BatchPair) * b->n));
   CK(cudaMemcpy(b->tab_lb, tab.data(), sizeof(BatchPair) * b->n, cudaMemcpyHostToDevice));
-  for (auto& L : b->launches_rows) {
-    for (int k = 0; k < L.acc.n; ++k) {
-      const long long o = L.acc.it[k].a.c - b->c;
-      L.acc_lb.it[k].a.c = b->xn + o;
-      L.adj_lb.it[k].a.c = b->xn + o;
-      L.adj_lb.it[k].a.grad = b->gn + o;
+  for (auto& L : b->acc_launches)
+    for (int k = 0; k < L.t.n; ++k) L.t_lb.it[k].a.c = b->xn + (L.t.it[k].a.c - b->c);
+  for (auto& L : b->adj_launches)
+    for (int k = 0; k < L.t.n; ++k) {
+      const long long o = L.t.it[k].a.c - b->c;
+      L.t_lb.it[k].a.c = b->xn + o;
+      L.t_lb.it[k].a.grad = b->gn + o;
     }
-  }
   b->lb_m = m;
   return SRWCR_OK;
 }
@@ -541,36 +557,66 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
     b->total_vox += lv.g.nvox;
   }
   b->total_regions = region;
-  // Row-kernel launches: runs of pairs of one x-bin class, at most
-  // kBatchChunk per launch, with CTA prefix sums.
-  for (int t = 0; t < n;) {
-    srwcr_batch::Launch L;
-    memset(&L, 0, sizeof L);
-    L.nxb = b->host_tab[t].group;
-    int tile = 0;
-    while (t < n && b->host_tab[t].group == L.nxb && L.acc.n < kBatchChunk) {
-      const BatchPair& bp = b->host_tab[t];
+  // Row-kernel launches: pairs bucketed by (x-bins per row, CTAs per SM),
+  // in table order (largest first), at most kBatchChunk per launch.
+  {
+    std::vector<std::pair<std::pair<int, int>, std::vector<int>>> acc_b, adj_b;
+    auto bucket = [](std::vector<std::pair<std::pair<int, int>, std::vector<int>>>& bs,
+                     std::pair<int, int> key, int t) {
+      for (auto& e : bs)
+        if (e.first == key) { e.second.push_back(t); return; }
+      bs.push_back({key, {t}});
+    };
+    for (int t = 0; t < n; ++t) {
       const Level& lv = ctxs[order[t]]->lev[level];
-      const int k = L.acc.n++;
-      L.adj.n++;
-      L.acc.it[k].g = bp.g;
-      L.acc.it[k].a = bp.acc;
-      L.acc.it[k].id = bp.id;
-      L.acc.it[k].tile_begin = tile;
-      L.adj.it[k].g = bp.g;
-      L.adj.it[k].a = bp.adj;
-      L.adj.it[k].id = bp.id;
-      L.adj.it[k].tile_begin = tile;
-      tile += bp.g.ntile[0] * bp.g.ntile[1] * bp.g.ntile[2];
-      L.smem_acc = std::max(L.smem_acc, lv.smem_acc_rows);
-      L.smem_adj = std::max(L.smem_adj, lv.smem_adj_rows);
-      ++t;
+      bucket(acc_b, {lv.nxb_rows, ctas_per_sm(lv.smem_acc_rows)}, t);
+      bucket(adj_b, {lv.nxb_rows, ctas_per_sm(lv.smem_adj_rows)}, t);
     }
-    L.nblk = tile;
-    L.acc_lb = L.acc;
-    L.adj_lb = L.adj;
-    b->work_items += tile;
-    b->launches_rows.push_back(L);
+    for (const auto& e : acc_b) {
+      for (size_t s0 = 0; s0 < e.second.size(); s0 += kBatchChunk) {
+        srwcr_batch::AccLaunch L;
+        memset(&L, 0, sizeof L);
+        L.nxb = e.first.first;
+        int tile = 0;
+        for (size_t k = s0; k < std::min(e.second.size(), s0 + kBatchChunk); ++k) {
+          const int t = e.second[k];
+          const BatchPair& bp = b->host_tab[t];
+          AccItem& it = L.t.it[L.t.n++];
+          it.g = bp.g;
+          it.a = bp.acc;
+          it.id = bp.id;
+          it.tile_begin = tile;
+          tile += bp.g.ntile[0] * bp.g.ntile[1] * bp.g.ntile[2];
+          L.smem = std::max(L.smem, ctxs[order[t]]->lev[level].smem_acc_rows);
+        }
+        L.nblk = tile;
+        L.t_lb = L.t;
+        b->work_items += tile;
+        b->acc_launches.push_back(L);
+      }
+    }
+    for (const auto& e : adj_b) {
+      for (size_t s0 = 0; s0 < e.second.size(); s0 += kBatchChunk) {
+        srwcr_batch::AdjLaunch L;
+        memset(&L, 0, sizeof L);
+        L.nxb = e.first.first;
+        int tile = 0;
+        for (size_t k = s0; k < std::min(e.second.size(), s0 + kBatchChunk); ++k) {
+          const int t = e.second[k];
+          const BatchPair& bp = b->host_tab[t];
+          AdjItem& it = L.t.it[L.t.n++];
+          it.g = bp.g;
+          it.a = bp.adj;
+          it.id = bp.id;
+          it.tile_begin = tile;
+          tile += bp.g.ntile[0] * bp.g.ntile[1] * bp.g.ntile[2];
+          L.smem = std::max(L.smem, ctxs[order[t]]->lev[level].smem_adj_rows);
+        }
+        L.nblk = tile;
+        L.t_lb = L.t;
+        b->adj_launches.push_back(L);
+      }
+    }
   }
   CK(cudaMalloc((void**)&b->tab_eval, sizeof(BatchPair) * n));
   CK(cudaMemcpy(b->tab_eval, b->host_tab.data(), sizeof(BatchPair) * n, cudaMemcpyHostToDevice));

@@ -271,6 +271,26 @@ __host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int
 // ---------------------------------------------------------------------------
 // (a) value pass: fused FFD + warp + joint statistics, row-parallel.
 // ---------------------------------------------------------------------------
+// Rows with at most this many segments take the transpose route of the
+// value kernel's segment sums (8 x-bins per row); others the shuffle route.
+constexpr int kTransposeMaxSeg = 12;
+
+// Position of value q of row (lane or segment) l in a warp's segment buffer
+// of NV floats per row.  With 8 x-bins per row (NV = 32, the only case that
+// takes the transpose route) 16-byte chunks are XOR-swizzled by the row
+// index, so the row stores and the column reads are free of bank conflicts;
+// with 4 the layout is plain.
+template <int NV>
+__device__ __forceinline__ int seg_chunk(int l, int k) {
+  static_assert(NV == 16 || NV == 32, "4 or 8 x-bins per row");
+  return NV == 32 ? (k ^ (l & 7)) : k;
+}
+
+template <int NV>
+__device__ __forceinline__ int seg_at(int l, int q) {
+  return l * NV + (seg_chunk<NV>(l, q >> 2) << 2) + (q & 3);
+}
+
 template <int DIM, typename T, int NXB>
 __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args, int tile,
                                               unsigned long long* smem_u64) {
@@ -308,7 +328,6 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   float* CZ = reinterpret_cast<float*>(zt + g.tile[2]);
   float* cyz = cyz_all + warp * DIM * kMaxRowNodes;
   float* mysegS = segS + warp * 32 * NV;
-  int* mysegA = segA + warp * 32;
   int* mybins = binl + warp * 64 * 2;
 
   const TileOrigin TO = tile_setup<DIM>(g, tile);
@@ -383,25 +402,62 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
       v[4 * b + 2] = w * e2;
       v[4 * b + 3] = w * e3;
     }
-    // Segments of equal a0 (lanes are sorted by a0): reduce toward each head.
+    // Segments of equal a0 (lanes are sorted by a0).  Their sums land in row
+    // s of the warp's segment buffer, by one of two warp-uniform routes:
+    //  * transpose (8 x-bins per row, few segments): lane l stores its NV
+    //    values as row l, then lane q < NV adds column q down the rows in
+    //    lane order and writes segment s's total into row s (already read);
+    //  * segmented shuffle reduction toward each head, which then stores its
+    //    segment's NV totals (cost independent of the number of segments).
     const int prev = __shfl_up_sync(0xffffffffu, key, 1);
     const bool head = lane == 0 || key != prev;
     const unsigned heads = __ballot_sync(0xffffffffu, head);
     const unsigned above = lane == 31 ? 0u : (heads & (0xffffffffu << (lane + 1)));
-    const int seg_end = above ? __ffs(above) - 1 : 32;
+    const int sidx = __popc(heads & ((1u << lane) - 1u));
+    if (NXB == 8 && __popc(heads) <= kTransposeMaxSeg) {
+      float4* rowp = reinterpret_cast<float4*>(mysegS + lane * NV);
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const bool ok = lane + off < seg_end;
+      for (int k = 0; k < NV / 4; ++k)
+        rowp[seg_chunk<NV>(lane, k)] =
+            make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      __syncwarp();
+      const unsigned ends = (heads >> 1) | 0x80000000u;  // last lane of each segment
+      if (lane < NV) {
+        float sum = 0.f;
+        int sw = 0;
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const float ov = __shfl_down_sync(0xffffffffu, v[q], off);
-        if (ok) v[q] += ov;
+        for (int l = 0; l < 32; ++l) {
+          sum += mysegS[seg_at<NV>(l, lane)];
+          if ((ends >> l) & 1u) {
+            mysegS[seg_at<NV>(sw, lane)] = sum;
+            sum = 0.f;
+            ++sw;
+          }
+        }
+      }
+    } else {
+      const int seg_end = above ? __ffs(above) - 1 : 32;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const bool ok = lane + off < seg_end;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          const float ov = __shfl_down_sync(0xffffffffu, v[q], off);
+          if (ok) v[q] += ov;
+        }
+      }
+      if (head && key != kSentinel) {
+        float4* rowp = reinterpret_cast<float4*>(mysegS + sidx * NV);
+#pragma unroll
+        for (int k = 0; k < NV / 4; ++k)
+          rowp[seg_chunk<NV>(sidx, k)] =
+              make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
       }
     }
+    __syncwarp();
     // Bin list.  Segment s (key a) adds bin a (slot 0, plus slot 1 of s-1 when
     // that segment's key is a-1) and, unless segment s+1 has key a+1, bin a+1
     // (slot 1 alone).
-    const int sidx = __popc(heads & ((1u << lane) - 1u));
     const int next_head = above ? __ffs(above) - 1 : -1;
     const int next_key = __shfl_sync(0xffffffffu, key, next_head < 0 ? lane : next_head);
     const bool real = head && key != kSentinel;
@@ -416,9 +472,6 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
     const int pos = __popc(emit0 & lt) + __popc(emit1 & lt);
     const int nbin = __popc(emit0) + __popc(emit1);
     if (real) {
-      mysegA[sidx] = key;
-#pragma unroll
-      for (int q = 0; q < NV; ++q) mysegS[sidx * NV + q] = v[q];
       mybins[2 * pos] = key;
       mybins[2 * pos + 1] = sidx | (merge ? (1 << 9) : 0);
       if (upper) {
@@ -444,8 +497,8 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
       const int a = mybins[2 * e];
       const int info = mybins[2 * e + 1];
       const int sg = info & 0xff, slot = (info >> 8) & 1;
-      float val = mysegS[sg * NV + 4 * b + 2 * slot + ch];
-      if (info & (1 << 9)) val += mysegS[(sg - 1) * NV + 4 * b + 2 + ch];
+      float val = mysegS[seg_at<NV>(sg, 4 * b + 2 * slot + ch)];
+      if (info & (1 << 9)) val += mysegS[seg_at<NV>(sg - 1, 4 * b + 2 + ch)];
       if (val == 0.f) continue;
       const float vs = val * (ch ? s2 : s1);
       const int col = (a2c[a] * 2 + ch) * g.hb[0] + b;
