@@ -64,6 +64,10 @@ typedef struct {
   int storage;            /* SRWCR_STORAGE_F32 | SRWCR_STORAGE_BF16 */
   int pyramid_levels;     /* 1..4; level 0 is the full resolution */
   int tile[3];            /* voxel tile (x, y, z); 0 = chosen by the library */
+  int bins_per_pass;      /* row-parallel value kernel: at most this many of a
+                             tile's fixed-image bins per pass over its rows
+                             (a tile using more takes several passes); 0 = as
+                             many as fit in shared memory */
 } srwcr_config;
 
 /* Geometry of one pyramid level. */

@@ -46,7 +46,8 @@ class Config(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("dims", ctypes.c_int * 3),
                 ("ffd_spacing", ctypes.c_int * 3), ("sbin_intervals", ctypes.c_int * 3),
                 ("n_intensity_bins", ctypes.c_int), ("storage", ctypes.c_int),
-                ("pyramid_levels", ctypes.c_int), ("tile", ctypes.c_int * 3)]
+                ("pyramid_levels", ctypes.c_int), ("tile", ctypes.c_int * 3),
+                ("bins_per_pass", ctypes.c_int)]
 
 
 class LevelDesc(ctypes.Structure):
@@ -166,7 +167,7 @@ class SRWCR:
     def __init__(self, fixed, moving, ffd_spacing: Sequence[int],
                  sbin_intervals: Sequence[int] = (0, 0, 0), n_bins: int = 32,
                  storage: str = "f32", pyramid_levels: int = 1,
-                 tile: Optional[Sequence[int]] = None, stream=None):
+                 tile: Optional[Sequence[int]] = None, stream=None, bins_per_pass: int = 0):
         import torch
         self._torch = torch
         lib = load()
@@ -185,6 +186,7 @@ class SRWCR:
         cfg.n_intensity_bins = int(n_bins)
         cfg.storage = STORAGE[storage]
         cfg.pyramid_levels = int(pyramid_levels)
+        cfg.bins_per_pass = int(bins_per_pass)
         self.cfg = cfg
         self.ndim = ndim
         self.storage = storage

@@ -34,6 +34,7 @@ struct Geo {
   long long ncoef;  // nodes per component = nf[0]*nf[1]*nf[2]
   long long R;      // spatial bins = nsb[0]*nsb[1]*nsb[2]
   int nabin;        // row kernels: most fixed-image bins any one tile uses
+  int cbin;         // row kernels: compacted bins per pass of the value kernel
 };
 
 __device__ __forceinline__ float ldval(const float* p) { return __ldg(p); }

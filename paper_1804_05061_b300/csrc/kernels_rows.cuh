@@ -37,7 +37,7 @@ namespace srwcr {
 
 constexpr int kAccWarps = 16;           // value pass: 512 threads per CTA
 constexpr int kAdjWarps = 8;            // adjoint: 256 threads per CTA
-constexpr int kMaxRowNodes = 10;        // FFD x-nodes a 32-voxel row may touch
+constexpr int kMaxRowNodes = 11;        // FFD x-nodes a 32-voxel row may touch
 constexpr int kSentinel = 0x7fffffff;   // key of lanes past the image edge
 
 // Per-axis geometry of one coordinate: FFD cell (relative to the tile's
@@ -249,7 +249,7 @@ struct AdjArgs {
 // The intensity axis holds only the fixed-image bins the tile uses (a static
 // per-tile mask), in compact order.
 __host__ __device__ inline int hist_yz_stride(const Geo& g) {
-  const int w = 2 * g.nabin * g.hb[0];
+  const int w = 2 * g.cbin * g.hb[0];
   return ((w + 23) / 32) * 32 + 8;
 }
 
@@ -311,6 +311,9 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   // FP32 update has 24 significant bits, so it touches at most two of them).
   // Every entry receives at most one update per row (<= 256 per CTA) of value
   // < 2^56, so no word overflows; the flush recombines the three exactly.
+  // The bin axis holds g.cbin of the tile's compacted bins; a tile that uses
+  // more takes several passes over its rows, each folding one chunk of bins
+  // and skipping rows with no voxel in that chunk.
   const int S = hist_yz_stride(g);
   const int NYZ = g.hb[1] * g.hb[2];
   unsigned* hlo = reinterpret_cast<unsigned*>(smem_u64);
@@ -331,10 +334,12 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   int* mybins = binl + warp * 64 * 2;
 
   const TileOrigin TO = tile_setup<DIM>(g, tile);
-  for (int i = threadIdx.x; i < 3 * NYZ * S; i += blockDim.x) hlo[i] = 0u;
+  const int cb = g.cbin;
+  int cnt = 0;                                // compacted bins of this tile
   {
     const int words = (nb + 31) >> 5;
     const unsigned* tmask = binmask + (size_t)tile * words;
+    for (int k = 0; k < words; ++k) cnt += __popc(__ldg(tmask + k));
     for (int a = threadIdx.x; a < nb; a += blockDim.x) {
       const int w = a >> 5;
       const unsigned mw = __ldg(tmask + w);
@@ -357,185 +362,202 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   const int nrows = g.tile[1] * g.tile[2];
   // Fold lane roles: item t of a pass (8 per pass), y offset fg (j of the bin).
   const int ft = lane & 7, fg = lane >> 3;
-  for (int row = warp; row < nrows; row += kAccWarps) {
-    const int yl = row % g.tile[1], zl = row / g.tile[1];
-    const int y = TO.o[1] + yl, z = TO.o[2] + zl;
-    if (y >= g.n[1] || z >= g.n[2]) continue;  // warp-uniform
-    const AxisEntry ye = yt[yl], ze = zt[zl];
-    row_cyz<DIM>(g, CZ, zl, ye, nxn, cyz, lane);
-    __syncwarp();
+  for (int c0 = 0; c0 < cnt; c0 += cb) {
+    const bool multi = cnt > cb;                // CTA-uniform
+    for (int i = threadIdx.x; i < 3 * NYZ * S; i += blockDim.x) hlo[i] = 0u;
+    __syncthreads();
+    for (int row = warp; row < nrows; row += kAccWarps) {
+      const int yl = row % g.tile[1], zl = row / g.tile[1];
+      const int y = TO.o[1] + yl, z = TO.o[2] + zl;
+      if (y >= g.n[1] || z >= g.n[2]) continue;  // warp-uniform
 
-    const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
-    const int p = perm[rowid * 32 + lane];
-    const int x = TO.o[0] + p;
-    const bool act = x < g.n[0];
-    float m1 = 0.f, m2 = 0.f, h0 = 0.f, h1 = 0.f;
-    int key = kSentinel;
-    if (act) {
+      const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
+      const int p = perm[rowid * 32 + lane];
+      const int x = TO.o[0] + p;
+      const bool act = x < g.n[0];
       const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
-      float fa;
-      key = bin_split(fminf(fmaxf(ldval(A + idx), 0.f), L), nb, &fa);
-      h1 = parzen_upper(fa);
-      h0 = 1.f - h1;
-      const float bx[4] = {xt.bf[p], xt.bf[32 + p], xt.bf[64 + p], xt.bf[96 + p]};
-      float gm[3];
-      float B = row_warp<DIM, T>(g, M, cyz, xt.frel[p], bx, x, y, z, gm);
-      B = fminf(fmaxf(B, 0.f), L);
-      float fb;
-      const int kb = bin_split(B, nb, &fb);
-      const float w1 = parzen_upper(fb), kf = (float)kb;
-      m1 = kf + w1;                              // sum_b b   h(b - B)
-      m2 = kf * kf + (2.f * kf + 1.f) * w1;      // sum_b b^2 h(b - B)
-    }
-    const bool live = act && (m1 != 0.f || m2 != 0.f);
-    if (!__any_sync(0xffffffffu, live)) continue;  // B == 0 on the whole row
-
-    // Per-lane contributions over the row's NXB spatial x-bins.
-    float v[NV];
-    const float e0 = live ? h0 * m1 : 0.f, e1 = live ? h0 * m2 : 0.f;
-    const float e2 = live ? h1 * m1 : 0.f, e3 = live ? h1 * m2 : 0.f;
-#pragma unroll
-    for (int b = 0; b < NXB; ++b) {
-      const float w = xt.bsp[b * 32 + p];
-      v[4 * b + 0] = w * e0;
-      v[4 * b + 1] = w * e1;
-      v[4 * b + 2] = w * e2;
-      v[4 * b + 3] = w * e3;
-    }
-    // Segments of equal a0 (lanes are sorted by a0).  Their sums land in row
-    // s of the warp's segment buffer, by one of two warp-uniform routes:
-    //  * transpose (8 x-bins per row, few segments): lane l stores its NV
-    //    values as row l, then lane q < NV adds column q down the rows in
-    //    lane order and writes segment s's total into row s (already read);
-    //  * segmented shuffle reduction toward each head, which then stores its
-    //    segment's NV totals (cost independent of the number of segments).
-    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-    const bool head = lane == 0 || key != prev;
-    const unsigned heads = __ballot_sync(0xffffffffu, head);
-    const unsigned above = lane == 31 ? 0u : (heads & (0xffffffffu << (lane + 1)));
-    const int sidx = __popc(heads & ((1u << lane) - 1u));
-    if (NXB == 8 && __popc(heads) <= kTransposeMaxSeg) {
-      float4* rowp = reinterpret_cast<float4*>(mysegS + lane * NV);
-#pragma unroll
-      for (int k = 0; k < NV / 4; ++k)
-        rowp[seg_chunk<NV>(lane, k)] =
-            make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      float fa = 0.f;
+      int key = kSentinel;
+      if (act) key = bin_split(fminf(fmaxf(ldval(A + idx), 0.f), L), nb, &fa);
+      if (multi) {
+        // Rows with no voxel whose bins fall in this chunk wait for their pass.
+        const bool in = act && ((unsigned)(a2c[key] - c0) < (unsigned)cb ||
+                                (unsigned)(a2c[key + 1] - c0) < (unsigned)cb);
+        if (!__any_sync(0xffffffffu, in)) continue;
+      }
+      const AxisEntry ye = yt[yl], ze = zt[zl];
+      row_cyz<DIM>(g, CZ, zl, ye, nxn, cyz, lane);
       __syncwarp();
-      const unsigned ends = (heads >> 1) | 0x80000000u;  // last lane of each segment
-      if (lane < NV) {
-        float sum = 0.f;
-        int sw = 0;
-#pragma unroll
-        for (int l = 0; l < 32; ++l) {
-          sum += mysegS[seg_at<NV>(l, lane)];
-          if ((ends >> l) & 1u) {
-            mysegS[seg_at<NV>(sw, lane)] = sum;
-            sum = 0.f;
-            ++sw;
+      float m1 = 0.f, m2 = 0.f, h0 = 0.f, h1 = 0.f;
+      if (act) {
+        h1 = parzen_upper(fa);
+        h0 = 1.f - h1;
+        const float bx[4] = {xt.bf[p], xt.bf[32 + p], xt.bf[64 + p], xt.bf[96 + p]};
+        float gm[3];
+        float B = row_warp<DIM, T>(g, M, cyz, xt.frel[p], bx, x, y, z, gm);
+        B = fminf(fmaxf(B, 0.f), L);
+        float fb;
+        const int kb = bin_split(B, nb, &fb);
+        const float w1 = parzen_upper(fb), kf = (float)kb;
+        m1 = kf + w1;                              // sum_b b   h(b - B)
+        m2 = kf * kf + (2.f * kf + 1.f) * w1;      // sum_b b^2 h(b - B)
+      }
+      const bool live = act && (m1 != 0.f || m2 != 0.f);
+      if (!__any_sync(0xffffffffu, live)) continue;  // B == 0 on the whole row
+
+      // Per-lane contributions over the row's NXB spatial x-bins.
+      float v[NV];
+      const float e0 = live ? h0 * m1 : 0.f, e1 = live ? h0 * m2 : 0.f;
+      const float e2 = live ? h1 * m1 : 0.f, e3 = live ? h1 * m2 : 0.f;
+  #pragma unroll
+      for (int b = 0; b < NXB; ++b) {
+        const float w = xt.bsp[b * 32 + p];
+        v[4 * b + 0] = w * e0;
+        v[4 * b + 1] = w * e1;
+        v[4 * b + 2] = w * e2;
+        v[4 * b + 3] = w * e3;
+      }
+      // Segments of equal a0 (lanes are sorted by a0).  Their sums land in row
+      // s of the warp's segment buffer, by one of two warp-uniform routes:
+      //  * transpose (8 x-bins per row, few segments): lane l stores its NV
+      //    values as row l, then lane q < NV adds column q down the rows in
+      //    lane order and writes segment s's total into row s (already read);
+      //  * segmented shuffle reduction toward each head, which then stores its
+      //    segment's NV totals (cost independent of the number of segments).
+      const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+      const bool head = lane == 0 || key != prev;
+      const unsigned heads = __ballot_sync(0xffffffffu, head);
+      const unsigned above = lane == 31 ? 0u : (heads & (0xffffffffu << (lane + 1)));
+      const int sidx = __popc(heads & ((1u << lane) - 1u));
+      if (NXB == 8 && __popc(heads) <= kTransposeMaxSeg) {
+        float4* rowp = reinterpret_cast<float4*>(mysegS + lane * NV);
+  #pragma unroll
+        for (int k = 0; k < NV / 4; ++k)
+          rowp[seg_chunk<NV>(lane, k)] =
+              make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        __syncwarp();
+        const unsigned ends = (heads >> 1) | 0x80000000u;  // last lane of each segment
+        if (lane < NV) {
+          float sum = 0.f;
+          int sw = 0;
+  #pragma unroll
+          for (int l = 0; l < 32; ++l) {
+            sum += mysegS[seg_at<NV>(l, lane)];
+            if ((ends >> l) & 1u) {
+              mysegS[seg_at<NV>(sw, lane)] = sum;
+              sum = 0.f;
+              ++sw;
+            }
           }
         }
-      }
-    } else {
-      const int seg_end = above ? __ffs(above) - 1 : 32;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const bool ok = lane + off < seg_end;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-          const float ov = __shfl_down_sync(0xffffffffu, v[q], off);
-          if (ok) v[q] += ov;
+      } else {
+        const int seg_end = above ? __ffs(above) - 1 : 32;
+  #pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const bool ok = lane + off < seg_end;
+  #pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            const float ov = __shfl_down_sync(0xffffffffu, v[q], off);
+            if (ok) v[q] += ov;
+          }
+        }
+        if (head && key != kSentinel) {
+          float4* rowp = reinterpret_cast<float4*>(mysegS + sidx * NV);
+  #pragma unroll
+          for (int k = 0; k < NV / 4; ++k)
+            rowp[seg_chunk<NV>(sidx, k)] =
+                make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
         }
       }
-      if (head && key != kSentinel) {
-        float4* rowp = reinterpret_cast<float4*>(mysegS + sidx * NV);
-#pragma unroll
-        for (int k = 0; k < NV / 4; ++k)
-          rowp[seg_chunk<NV>(sidx, k)] =
-              make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+      __syncwarp();
+      // Bin list.  Segment s (key a) adds bin a (slot 0, plus slot 1 of s-1 when
+      // that segment's key is a-1) and, unless segment s+1 has key a+1, bin a+1
+      // (slot 1 alone).
+      const int next_head = above ? __ffs(above) - 1 : -1;
+      const int next_key = __shfl_sync(0xffffffffu, key, next_head < 0 ? lane : next_head);
+      const bool real = head && key != kSentinel;
+      const bool upper = real && (next_head < 0 || next_key != key + 1);
+      const unsigned below = heads & ((1u << lane) - 1u);
+      const int prev_head = below ? 31 - __clz(below) : lane;
+      const int prev_key = __shfl_sync(0xffffffffu, key, prev_head);
+      const bool merge = real && below && prev_key + 1 == key;
+      // Only bins of the current chunk are listed.
+      const bool in0 = real && (unsigned)(a2c[key] - c0) < (unsigned)cb;
+      const bool in1 = upper && (unsigned)(a2c[key + 1] - c0) < (unsigned)cb;
+      const unsigned emit0 = __ballot_sync(0xffffffffu, in0);
+      const unsigned emit1 = __ballot_sync(0xffffffffu, in1);
+      const unsigned lt = (1u << lane) - 1u;
+      const int pos = __popc(emit0 & lt) + __popc(emit1 & lt);
+      const int nbin = __popc(emit0) + __popc(emit1);
+      if (in0) {
+        mybins[2 * pos] = key;
+        mybins[2 * pos + 1] = sidx | (merge ? (1 << 9) : 0);
       }
-    }
-    __syncwarp();
-    // Bin list.  Segment s (key a) adds bin a (slot 0, plus slot 1 of s-1 when
-    // that segment's key is a-1) and, unless segment s+1 has key a+1, bin a+1
-    // (slot 1 alone).
-    const int next_head = above ? __ffs(above) - 1 : -1;
-    const int next_key = __shfl_sync(0xffffffffu, key, next_head < 0 ? lane : next_head);
-    const bool real = head && key != kSentinel;
-    const bool upper = real && (next_head < 0 || next_key != key + 1);
-    const unsigned below = heads & ((1u << lane) - 1u);
-    const int prev_head = below ? 31 - __clz(below) : lane;
-    const int prev_key = __shfl_sync(0xffffffffu, key, prev_head);
-    const bool merge = real && below && prev_key + 1 == key;
-    const unsigned emit0 = __ballot_sync(0xffffffffu, real);
-    const unsigned emit1 = __ballot_sync(0xffffffffu, upper);
-    const unsigned lt = (1u << lane) - 1u;
-    const int pos = __popc(emit0 & lt) + __popc(emit1 & lt);
-    const int nbin = __popc(emit0) + __popc(emit1);
-    if (real) {
-      mybins[2 * pos] = key;
-      mybins[2 * pos + 1] = sidx | (merge ? (1 << 9) : 0);
-      if (upper) {
-        mybins[2 * pos + 2] = key + 1;
-        mybins[2 * pos + 3] = sidx | (1 << 8);
+      if (in1) {
+        const int q = pos + (in0 ? 1 : 0);
+        mybins[2 * q] = key + 1;
+        mybins[2 * q + 1] = sidx | (1 << 8);
       }
-    }
-    __syncwarp();
-    // Fold: 8 (bin, moment, x-bin) items per pass, each lane adds its item to
-    // the 4 z bins of y bin fg (3-D; one z bin in 2-D).
-    float wk[NK];
-    int yzb[NK];
-#pragma unroll
-    for (int m = 0; m < NK; ++m) {
-      wk[m] = ye.bs[fg] * ze.bs[m];
-      yzb[m] = ((ze.srel + m) * g.hb[1] + (ye.srel + fg)) * S;
-    }
-    const int per_bin = 2 * NXB;
-    for (int f = ft; f < nbin * per_bin; f += 8) {
-      const int e = f / per_bin, r = f % per_bin;
-      const int ch = r / NXB, b = r % NXB;
-      if (b >= g.hb[0]) continue;
-      const int a = mybins[2 * e];
-      const int info = mybins[2 * e + 1];
-      const int sg = info & 0xff, slot = (info >> 8) & 1;
-      float val = mysegS[seg_at<NV>(sg, 4 * b + 2 * slot + ch)];
-      if (info & (1 << 9)) val += mysegS[seg_at<NV>(sg - 1, 4 * b + 2 + ch)];
-      if (val == 0.f) continue;
-      const float vs = val * (ch ? s2 : s1);
-      const int col = (a2c[a] * 2 + ch) * g.hb[0] + b;
-#pragma unroll
+      __syncwarp();
+      // Fold: 8 (bin, moment, x-bin) items per pass, each lane adds its item to
+      // the 4 z bins of y bin fg (3-D; one z bin in 2-D).
+      float wk[NK];
+      int yzb[NK];
+  #pragma unroll
       for (int m = 0; m < NK; ++m) {
-        const float u = vs * wk[m];
-        if (u == 0.f) continue;
-        // Exact split of u into 20-bit fields (power-of-two scalings, floors
-        // and fused subtractions of FP32 values are exact here).
-        const float hf = floorf(u * 0x1p-40f);
-        const float r1 = fmaf(hf, -0x1p40f, u);
-        const float mf = floorf(r1 * 0x1p-20f);
-        const unsigned lo = __float2uint_rn(fmaf(mf, -0x1p20f, r1));
-        const unsigned mid = (unsigned)mf, hi = (unsigned)hf;
-        const int at = yzb[m] + col;
-        if (lo) atomicAdd(hlo + at, lo);
-        if (mid) atomicAdd(hmid + at, mid);
-        if (hi) atomicAdd(hhi + at, hi);
+        wk[m] = ye.bs[fg] * ze.bs[m];
+        yzb[m] = ((ze.srel + m) * g.hb[1] + (ye.srel + fg)) * S;
       }
+      const int per_bin = 2 * NXB;
+      for (int f = ft; f < nbin * per_bin; f += 8) {
+        const int e = f / per_bin, r = f % per_bin;
+        const int ch = r / NXB, b = r % NXB;
+        if (b >= g.hb[0]) continue;
+        const int a = mybins[2 * e];
+        const int info = mybins[2 * e + 1];
+        const int sg = info & 0xff, slot = (info >> 8) & 1;
+        float val = mysegS[seg_at<NV>(sg, 4 * b + 2 * slot + ch)];
+        if (info & (1 << 9)) val += mysegS[seg_at<NV>(sg - 1, 4 * b + 2 + ch)];
+        if (val == 0.f) continue;
+        const float vs = val * (ch ? s2 : s1);
+        const int col = ((a2c[a] - c0) * 2 + ch) * g.hb[0] + b;
+  #pragma unroll
+        for (int m = 0; m < NK; ++m) {
+          const float u = vs * wk[m];
+          if (u == 0.f) continue;
+          // Exact split of u into 20-bit fields (power-of-two scalings, floors
+          // and fused subtractions of FP32 values are exact here).
+          const float hf = floorf(u * 0x1p-40f);
+          const float r1 = fmaf(hf, -0x1p40f, u);
+          const float mf = floorf(r1 * 0x1p-20f);
+          const unsigned lo = __float2uint_rn(fmaf(mf, -0x1p20f, r1));
+          const unsigned mid = (unsigned)mf, hi = (unsigned)hf;
+          const int at = yzb[m] + col;
+          if (lo) atomicAdd(hlo + at, lo);
+          if (mid) atomicAdd(hmid + at, mid);
+          if (hi) atomicAdd(hhi + at, hi);
+        }
+      }
+      __syncwarp();
     }
-    __syncwarp();
-  }
-  __syncthreads();
-  const int wcols = 2 * g.nabin * g.hb[0];
-  for (int i = threadIdx.x; i < NYZ * S; i += blockDim.x) {
-    const int yz = i / S, col = i % S;
-    if (col >= wcols) continue;
-    const unsigned long long val =
-        ((unsigned long long)hhi[i] << 40) + ((unsigned long long)hmid[i] << 20) + hlo[i];
-    if (!val) continue;
-    const int b = col % g.hb[0], ach = col / g.hb[0];
-    const int a = c2a[ach >> 1], ch = ach & 1;
-    const int l1 = yz % g.hb[1], l2 = yz / g.hb[1];
-    const int r0 = TO.cb[0] + b, r1 = TO.cb[1] + l1, r2 = TO.cb[2] + l2;
-    if (r0 >= g.nsb[0] || r1 >= g.nsb[1] || r2 >= g.nsb[2]) continue;
-    const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
-    atomicAdd(acc + ((size_t)r * nb + a) * 2 + ch, val);
+    __syncthreads();
+    const int wcols = 2 * cb * g.hb[0];
+    for (int i = threadIdx.x; i < NYZ * S; i += blockDim.x) {
+      const int yz = i / S, col = i % S;
+      if (col >= wcols) continue;
+      const unsigned long long val =
+          ((unsigned long long)hhi[i] << 40) + ((unsigned long long)hmid[i] << 20) + hlo[i];
+      if (!val) continue;
+      const int b = col % g.hb[0], ach = col / g.hb[0];
+      if (c0 + (ach >> 1) >= cnt) continue;
+      const int a = c2a[c0 + (ach >> 1)], ch = ach & 1;
+      const int l1 = yz % g.hb[1], l2 = yz / g.hb[1];
+      const int r0 = TO.cb[0] + b, r1 = TO.cb[1] + l1, r2 = TO.cb[2] + l2;
+      if (r0 >= g.nsb[0] || r1 >= g.nsb[1] || r2 >= g.nsb[2]) continue;
+      const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
+      atomicAdd(acc + ((size_t)r * nb + a) * 2 + ch, val);
+    }
+    __syncthreads();                            // the next pass clears the histogram
   }
 }
 
@@ -742,28 +764,43 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
       }
       G = scale * (dm2 * su + 2.f * dm1 * (sv - sxr));
     }
-    // Value q = 10 k + n: component k, row x-node n (xe.frel + l < nxn <= 10).
+    // Value q = 11 k + n: component k, row x-node n (n < nxn <= 11), for
+    // q < 32; in 3-D the 33rd (k = 2, n = 10) is summed on its own.
+    constexpr int NN = kMaxRowNodes;
     float vals[32];
-    float bn[kMaxRowNodes];
+    float bn[NN];
 #pragma unroll
-    for (int nn = 0; nn < kMaxRowNodes; ++nn) bn[nn] = xt.bfp[nn * 32 + p];
+    for (int nn = 0; nn < NN; ++nn) bn[nn] = xt.bfp[nn * 32 + p];
+    float gk[3];
 #pragma unroll
-    for (int kk = 0; kk < 3; ++kk) {
-      const float gk = (live && kk < DIM) ? G * gm[kk] : 0.f;
+    for (int kk = 0; kk < 3; ++kk) gk[kk] = (live && kk < DIM) ? G * gm[kk] : 0.f;
 #pragma unroll
-      for (int nn = 0; nn < 10; ++nn) vals[kk * 10 + nn] = gk * bn[nn];
-    }
-    vals[30] = vals[31] = 0.f;
+    for (int q = 0; q < 32; ++q) vals[q] = (q / NN < DIM) ? gk[q / NN] * bn[q % NN] : 0.f;
     const float tot = warp_reduce_scatter32(vals, lane);
-    // Lane q holds component q/10, x-node q%10: spread over the y/z nodes.
-    const int kq = lane / 10, lq = lane % 10;
-    if (lane < DIM * 10 && lq < nxn && tot != 0.f) {
+    // Lane q holds component q/11, x-node q%11: spread over the y/z nodes.
+    const int kq = lane / NN, lq = lane % NN;
+    if (lane < DIM * NN && lq < nxn && tot != 0.f) {
       for (int mn = 0; mn < NJK; ++mn) {
         const int m = mn & 3, n = mn >> 2;
         const float w = ye.bf[m] * ze.bf[n];
         if (w == 0.f) continue;
         atomicAdd(gt + kq * nodes_tile + ((ze.frel + n) * g.hf[1] + (ye.frel + m)) * g.hf[0] + lq,
                   tot * w);
+      }
+    }
+    if (DIM == 3 && nxn > 32 - 2 * NN) {     // rows touching 11 x-nodes (warp-uniform)
+      float e = gk[2] * bn[32 - 2 * NN];
+#pragma unroll
+      for (int off = 16; off; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+      if (lane == 0 && e != 0.f) {
+        for (int mn = 0; mn < NJK; ++mn) {
+          const int m = mn & 3, n = mn >> 2;
+          const float w = ye.bf[m] * ze.bf[n];
+          if (w == 0.f) continue;
+          atomicAdd(gt + 2 * nodes_tile + ((ze.frel + n) * g.hf[1] + (ye.frel + m)) * g.hf[0] +
+                        (32 - 2 * NN),
+                    e * w);
+        }
       }
     }
     __syncwarp();

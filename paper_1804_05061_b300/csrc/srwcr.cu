@@ -63,6 +63,7 @@ srwcr_status fail(srwcr_status st, const char* fmt, ...) {
   } while (0)
 
 constexpr int kBlock = 256;
+constexpr int kMinBinsPerPass = 8;  // value kernel: fewest compacted bins per pass
 constexpr size_t kSmemBudget = 112 * 1024;  // per CTA, two CTAs per SM
 
 struct Level {
@@ -142,10 +143,10 @@ size_t acc_smem(const Geo& g, int nch) {
   return (size_t)g.hb[0] * g.hb[1] * g.hb[2] * g.nbins * nch * sizeof(unsigned long long);
 }
 
-// Row kernels need 32-wide tiles, at most 8 spatial x-bins and 10 FFD
+// Row kernels need 32-wide tiles, at most 8 spatial x-bins and 11 FFD
 // x-nodes per row (FFD spacing >= 5, spatial-bin spacing >= ~5).
 bool rows_geometry_ok(const Geo& g) {
-  return g.tile[0] == 32 && g.hb[0] <= 8 && g.hf[0] <= 10 && g.tile[1] * g.tile[2] <= 256;
+  return g.tile[0] == 32 && g.hb[0] <= 8 && g.hf[0] <= kMaxRowNodes && g.tile[1] * g.tile[2] <= 256;
 }
 
 void set_tile(Geo& g, int ndim, int tx, int ty, int tz) {
@@ -213,6 +214,7 @@ srwcr_status make_geo(const srwcr_config& cfg, const int dims[3], Geo& g) {
   g.ncoef = (long long)g.nf[0] * g.nf[1] * g.nf[2];
   g.R = (long long)g.nsb[0] * g.nsb[1] * g.nsb[2];
   g.nabin = g.nbins;
+  g.cbin = g.nbins;
   return choose_tile(g, nd, cfg.tile);
 }
 
@@ -511,6 +513,10 @@ srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv, const int* force_tile =
     }
     g.nabin = nab;
     const int nxb = g.hb[0] <= 4 ? 4 : 8;
+    // Compacted bins per pass of the value kernel: all of them when they fit,
+    // else the most that fit (a tile using more takes several passes).
+    g.cbin = cfg.bins_per_pass > 0 ? std::min(nab, cfg.bins_per_pass) : nab;
+    while (g.cbin > kMinBinsPerPass && acc_rows_smem_bytes(g, nd, nxb) > 220 * 1024) --g.cbin;
     const size_t sa = acc_rows_smem_bytes(g, nd, nxb), sj = adj_rows_smem_bytes(g, nd, nxb);
     if (sa > 220 * 1024 || sj > 220 * 1024) {
       cudaFree(mask);
@@ -729,6 +735,7 @@ srwcr_status srwcr_create(const srwcr_config* cfg, const float* fixed, const flo
   }
   if (cfg->tile[0] < 0 || cfg->tile[1] < 0 || cfg->tile[2] < 0)
     return fail(SRWCR_EINVAL, "negative tile size");
+  if (cfg->bins_per_pass < 0) return fail(SRWCR_EINVAL, "negative bins_per_pass");
   srwcr_ctx* ctx = new (std::nothrow) srwcr_ctx();
   if (!ctx) return fail(SRWCR_ENOMEM, "host allocation failed");
   srwcr_status st = create_impl(cfg, fixed, moving, images_on_device, stream, ctx);
@@ -966,6 +973,7 @@ extern "C" srwcr_status srwcr_value_noalloc(const srwcr_config* cfg, const float
   }
   if (cfg->tile[0] < 0 || cfg->tile[1] < 0 || cfg->tile[2] < 0)
     return fail(SRWCR_EINVAL, "negative tile size");
+  if (cfg->bins_per_pass < 0) return fail(SRWCR_EINVAL, "negative bins_per_pass");
   cudaStream_t st = (cudaStream_t)stream;
 
   // Device address of the scratch array, looked up once per device.
@@ -1060,9 +1068,9 @@ std::vector<std::pair<std::string, std::array<int, 3>>> g_tune_cache;
 
 std::string tune_key(const srwcr_ctx* ctx, const Geo& g) {
   char buf[256];
-  snprintf(buf, sizeof buf, "d%d_n%dx%dx%d_f%dx%dx%d_s%d/%d,%d/%d,%d/%d_b%d_t%d", ctx->cfg.ndim, g.n[0],
-           g.n[1], g.n[2], g.fsp[0], g.fsp[1], g.fsp[2], g.sbn[0], g.sbd[0], g.sbn[1], g.sbd[1],
-           g.sbn[2], g.sbd[2], g.nbins, ctx->cfg.storage);
+  snprintf(buf, sizeof buf, "d%d_n%dx%dx%d_f%dx%dx%d_s%d/%d,%d/%d,%d/%d_b%d_t%d_p%d", ctx->cfg.ndim,
+           g.n[0], g.n[1], g.n[2], g.fsp[0], g.fsp[1], g.fsp[2], g.sbn[0], g.sbd[0], g.sbn[1],
+           g.sbd[1], g.sbn[2], g.sbd[2], g.nbins, ctx->cfg.storage, ctx->cfg.bins_per_pass);
   return buf;
 }
 

@@ -1,0 +1,87 @@
+"""GPU parity at the full workload sizes whose FP64 oracle results take
+minutes to compute: they are read from ``tests/golden/full_size_oracle.json``,
+written by ``tests/golden/make_full_size.py`` from ``synth`` and ``oracle``
+alone.
+
+* 512x512x300 CT pair (FFD spacing 5, 16x16x8 spatial-bin intervals, 128
+  bins), FP32 and BF16 storage: D within 1e-5 relative, gradient norm within
+  1e-4 relative, 64 seeded gradient entries within 1e-3 of the largest
+  gradient magnitude, same number of degenerate regions.
+* 32 PET/CT-shaped pairs (BF16), evaluated as one batch: the same bounds for
+  every pair, and each pair's D equal to the single-pair entry point's.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+GOLDEN = os.path.join(HERE, "golden", "full_size_oracle.json")
+D_RTOL, GNORM_RTOL, G_ELEM = 1e-5, 1e-4, 1e-3
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(GOLDEN) as f:
+        data = json.load(f)
+    h = hashlib.sha256()
+    for name in ("synth/__init__.py", "oracle/__init__.py", "oracle/srwcr_oracle.c"):
+        with open(os.path.join(ROOT, name), "rb") as fh:
+            h.update(fh.read())
+    assert data["source_hash"] == h.hexdigest()[:16], \
+        "stale golden file: rerun tests/golden/make_full_size.py"
+    return data["cases"]
+
+
+def check(ref, D, g, ndeg=None):
+    g = g.detach().cpu().numpy().ravel().astype(np.float64)
+    assert abs(D - ref["D"]) <= D_RTOL * abs(ref["D"]), (D, ref["D"])
+    gn = float(np.linalg.norm(g))
+    assert abs(gn - ref["gnorm"]) <= GNORM_RTOL * ref["gnorm"], (gn, ref["gnorm"])
+    err = np.abs(g[np.array(ref["idx"])] - np.array(ref["g_idx"])).max()
+    assert err <= G_ELEM * ref["gmax"], err / ref["gmax"]
+    if ndeg is not None:
+        assert ndeg == ref["n_degenerate"]
+
+
+@pytest.fixture(scope="module")
+def c5_pair():
+    return synth.make_pair("c5_ct_512x512x300")
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_c5_full_value_gradient_and_sampled_entries(golden, c5_pair, storage):
+    import paper_1804_05061_b300 as eng
+    ref = golden[f"c5_{storage}"]
+    prob = c5_pair.prob
+    e = eng.from_problem(prob, c5_pair.fixed, c5_pair.moving, storage=storage)
+    c = torch.from_numpy(synth.coefficients(prob, ref["coef_seed"], ref["coef_sigma"])).cuda()
+    D, g = e.value_and_grad(c)
+    _, ndeg = e.region_stats()
+    check(ref, D, g, ndeg)
+
+
+def test_c4_batch_of_32_pairs_per_pair_against_oracle(golden):
+    import paper_1804_05061_b300 as eng
+    specs = synth.batch_specs(32)
+    es = [eng.from_problem(s.prob, s.fixed, s.moving, storage="bf16") for s in specs]
+    b = eng.Batch(es)
+    cs = []
+    for i, s in enumerate(specs):
+        ref = golden[f"c4_pair{i:02d}"]
+        assert list(s.prob.dims) == ref["dims"]
+        cs.append(torch.from_numpy(synth.coefficients(s.prob, ref["coef_seed"],
+                                                      ref["coef_sigma"])).cuda())
+        b.coef(i).copy_(cs[-1])
+    Db = b.value_and_grad(use_graph=True)
+    for i in range(len(specs)):
+        check(golden[f"c4_pair{i:02d}"], Db[i], b.grad(i))
+        assert es[i].value(cs[i]) == Db[i]

@@ -75,6 +75,27 @@ def test_value_gradient_and_regions_match_oracle(small_cases, name):
     assert np.abs(g - go).max() <= G_ELEM * np.abs(go).max()
 
 
+@pytest.mark.parametrize("name", ["ct_128_bins", "ellipse_2d_ragged", "pet_labels"])
+def test_value_in_several_bin_passes_equals_one_pass(small_cases, name):
+    # A tile whose fixed-image bins exceed bins_per_pass takes several passes
+    # over its rows; every (region, bin) entry still receives the same FP32
+    # row sums, added in fixed point, so D is bit-identical.
+    prob, f, m, c = small_cases[name]
+    e1 = engine_for(prob, f, m)
+    e8 = engine_for(prob, f, m, bins_per_pass=8)
+    assert e1.levels[0].kernel_path == 1 and e8.levels[0].kernel_path == 1
+    ct = torch.from_numpy(c).cuda()
+    D1, g1 = e1.value_and_grad(ct)
+    D8, g8 = e8.value_and_grad(ct)
+    assert D8 == D1
+    assert torch.allclose(g8, g1, rtol=1e-5, atol=1e-5 * float(g1.abs().max()))
+    s1, _ = e1.region_stats()
+    s8, _ = e8.region_stats()
+    assert np.array_equal(s1, s8)
+    st, _, _, _, _ = oracle_eval(prob, f, m, c, grad=False)
+    assert abs(D8 - st.D) <= D_RTOL * abs(st.D)
+
+
 EXPECTED_PATH = {"ellipse_2d_ragged": 1, "ct_3d_ragged": 1, "oct_ffd_grid_bins": 0,
                  "ct_128_bins": 1, "pet_labels": 1}
 
