@@ -536,8 +536,8 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
     bp.id = i;
     float* ci = b->c + b->off[i];
     float* gi = b->g + b->off[i];
-    bp.acc = acc_args(lv, ci);
-    bp.adj = adj_args(lv, ci, nullptr, gi);
+    bp.acc = acc_args(lv, ci, true);
+    bp.adj = adj_args(lv, ci, nullptr, gi, true);
     bp.group = lv.nxb_rows;
     bp.region_begin = region;
     region += lv.g.R;

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256)
 k_accumulate(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
              const float* __restrict__ c, unsigned long long* __restrict__ acc, float s0,
              float s1) {
-  extern __shared__ unsigned long long hist[];
+  extern __shared__ __align__(16) unsigned long long hist[];
   constexpr int NCH = STATIC ? 1 : 2;
   const int nb = g.nbins;
   const float L = (float)(nb - 1);
@@ -346,7 +346,7 @@ k_adjoint(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
           const float* __restrict__ c, const float* __restrict__ U, const float* __restrict__ V,
           const float* __restrict__ X, const float* __restrict__ gscale, float invZ,
           float* __restrict__ grad) {
-  extern __shared__ float gt[];
+  extern __shared__ __align__(16) float gt[];
   const int nb = g.nbins;
   const float L = (float)(nb - 1);
   int o[3];

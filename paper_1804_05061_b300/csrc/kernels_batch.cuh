@@ -88,7 +88,7 @@ struct AdjTable {
 template <int DIM, typename T, int NXB>
 __global__ void __launch_bounds__(kAccWarps * 32, 2)
 k_accumulate_rows_batch(const __grid_constant__ AccTable tab, const int* __restrict__ active) {
-  extern __shared__ unsigned long long smem_acc[];
+  extern __shared__ __align__(16) unsigned long long smem_acc[];
   const int p = batch_find(0, tab.n - 1, blockIdx.x,
                            [&](int i) { return (long long)tab.it[i].tile_begin; });
   const AccItem& it = tab.it[p];
@@ -101,7 +101,7 @@ k_accumulate_rows_batch(const __grid_constant__ AccTable tab, const int* __restr
 template <int DIM, typename T, int NXB>
 __global__ void __launch_bounds__(kAdjWarps * 32)
 k_adjoint_rows_batch(const __grid_constant__ AdjTable tab, const int* __restrict__ active) {
-  extern __shared__ float smem_adj[];
+  extern __shared__ __align__(16) float smem_adj[];
   const int p = batch_find(0, tab.n - 1, blockIdx.x,
                            [&](int i) { return (long long)tab.it[i].tile_begin; });
   const AdjItem& it = tab.it[p];

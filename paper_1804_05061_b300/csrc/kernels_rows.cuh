@@ -226,6 +226,7 @@ struct AccArgs {
   const unsigned char* perm;     // per-row lane permutation
   const unsigned* binmask;       // per-tile fixed-image bins present
   unsigned long long* acc;       // [R][nbins][2] fixed-point sums
+  float4* bg;                    // per voxel (B, dM/dy) for the adjoint, or NULL
   float s1, s2;                  // fixed-point scales of the two moments
 };
 
@@ -239,6 +240,7 @@ struct AdjArgs {
   const float* V;
   const float* X;
   const float* gscale;           // device scalar or NULL (1)
+  const float4* bg;              // (B, dM/dy) stored by the value pass, or NULL: recompute
   float invZ;
   float* grad;
 };
@@ -396,6 +398,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
         float gm[3];
         float B = row_warp<DIM, T>(g, M, cyz, xt.frel[p], bx, x, y, z, gm);
         B = fminf(fmaxf(B, 0.f), L);
+        if (args.bg) args.bg[idx] = make_float4(B, gm[0], gm[1], gm[2]);
         float fb;
         const int kb = bin_split(B, nb, &fb);
         const float w1 = parzen_upper(fb), kf = (float)kb;
@@ -633,12 +636,13 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
   int* mysegA = segA_all + warp * 32;
   float* cyz = cyz_all + warp * DIM * kMaxRowNodes;
 
+  const float4* __restrict__ bg = args.bg;  // CTA-uniform: stored warp or recompute
   const TileOrigin TO = tile_setup<DIM>(g, tile);
   for (int i = threadIdx.x; i < DIM * nodes_tile; i += blockDim.x) gt[i] = 0.f;
   build_xtab<NXB>(g, TO, xt);
   build_axis_tables<DIM>(g, TO, yt, zt);
   __syncthreads();
-  build_cz<DIM>(g, TO, c, zt, CZ);
+  if (!bg) build_cz<DIM>(g, TO, c, zt, CZ);
   // Region tables contracted over z for each of the tile's z-planes.  X is
   // only needed for the fixed-image bins present in the tile (a0 and a0+1 of
   // its voxels, a static mask); other entries are never read.
@@ -694,8 +698,10 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
     const int y = TO.o[1] + yl, z = TO.o[2] + zl;
     if (y >= g.n[1] || z >= g.n[2]) continue;
     const AxisEntry ye = yt[yl], ze = zt[zl];
-    row_cyz<DIM>(g, CZ, zl, ye, nxn, cyz, lane);
-    __syncwarp();
+    if (!bg) {
+      row_cyz<DIM>(g, CZ, zl, ye, nxn, cyz, lane);
+      __syncwarp();
+    }
 
     const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
     const int p = perm[rowid * 32 + lane];
@@ -710,9 +716,19 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
       key = bin_split(fminf(fmaxf(ldval(A + idx), 0.f), L), nb, &fa);
       h1 = parzen_upper(fa);
       h0 = 1.f - h1;
-      const float bx[4] = {xt.bf[p], xt.bf[32 + p], xt.bf[64 + p], xt.bf[96 + p]};
-      float B = row_warp<DIM, T>(g, M, cyz, xt.frel[p], bx, x, y, z, gm);
-      B = fminf(fmaxf(B, 0.f), L);
+      float B;
+      if (bg) {
+        // The value pass at the same coefficients stored the warp.
+        const float4 s = __ldg(bg + idx);
+        B = s.x;
+        gm[0] = s.y;
+        gm[1] = s.z;
+        gm[2] = s.w;
+      } else {
+        const float bx[4] = {xt.bf[p], xt.bf[32 + p], xt.bf[64 + p], xt.bf[96 + p]};
+        B = row_warp<DIM, T>(g, M, cyz, xt.frel[p], bx, x, y, z, gm);
+        B = fminf(fmaxf(B, 0.f), L);
+      }
       float fb;
       const int kb = bin_split(B, nb, &fb);
       dm1 = parzen_upper_deriv(fb);
@@ -821,14 +837,14 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
 template <int DIM, typename T, int NXB>
 __global__ void __launch_bounds__(kAccWarps * 32, 2)
 k_accumulate_rows(const Geo g, const AccArgs args) {
-  extern __shared__ unsigned long long smem_acc[];
+  extern __shared__ __align__(16) unsigned long long smem_acc[];
   acc_rows_body<DIM, T, NXB>(g, args, blockIdx.x, smem_acc);
 }
 
 template <int DIM, typename T, int NXB>
 __global__ void __launch_bounds__(kAdjWarps * 32)
 k_adjoint_rows(const Geo g, const AdjArgs args) {
-  extern __shared__ float smem_adj[];
+  extern __shared__ __align__(16) float smem_adj[];
   adj_rows_body<DIM, T, NXB>(g, args, blockIdx.x, smem_adj);
 }
 

@@ -165,8 +165,8 @@ srwcr_status scal(srwcr_ctx* ctx, LbfgsWork& w, float a, const float* x, float* 
 
 srwcr_status eval(srwcr_ctx* ctx, int level, LbfgsWork& w, const float* x, float* g, double* f) {
   Level& lv = ctx->lev[level];
-  RET_IF(run_value(ctx, lv, x));
-  RET_IF(run_grad(ctx, lv, x, nullptr, g));
+  RET_IF(run_value(ctx, lv, x, true));
+  RET_IF(run_grad(ctx, lv, x, nullptr, g, true));
   CK(cudaMemcpyAsync(w.host + 1, lv.D, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   *f = w.host[1];

@@ -94,6 +94,7 @@ struct Level {
   int nxb_rows = 0;
   unsigned char* perm = nullptr;
   unsigned* binmask = nullptr;        // per tile: fixed-image bins present
+  float4* bg = nullptr;               // per voxel (B, dM/dy) of the last kept warp
   size_t smem_acc_rows = 0, smem_adj_rows = 0;
 };
 
@@ -240,23 +241,26 @@ void fixed_scales(const Geo& g, int ndim, double* sP, double* s1, double* s2) {
   *s2 = std::min(*s2, std::ldexp(1.0, 56 - ceil_log2(64.0 * L * L)));
 }
 
-AccArgs acc_args(const Level& lv, const float* c) {
+// keep_warp: the value pass stores (B, dM/dy) per voxel for an adjoint at
+// the same coefficients, which then reads it instead of recomputing the warp.
+AccArgs acc_args(const Level& lv, const float* c, bool keep_warp) {
   AccArgs a;
   a.A = lv.A; a.M = lv.M; a.c = c; a.perm = lv.perm; a.binmask = lv.binmask;
-  a.acc = lv.S; a.s1 = lv.s1; a.s2 = lv.s2;
+  a.acc = lv.S; a.bg = keep_warp ? lv.bg : nullptr; a.s1 = lv.s1; a.s2 = lv.s2;
   return a;
 }
 
-AdjArgs adj_args(const Level& lv, const float* c, const float* gD, float* g) {
+AdjArgs adj_args(const Level& lv, const float* c, const float* gD, float* g, bool kept_warp) {
   AdjArgs a;
   a.A = lv.A; a.M = lv.M; a.c = c; a.perm = lv.perm; a.binmask = lv.binmask;
-  a.U = lv.U; a.V = lv.V; a.X = lv.X; a.gscale = gD; a.invZ = (float)(1.0 / lv.Z); a.grad = g;
+  a.U = lv.U; a.V = lv.V; a.X = lv.X; a.gscale = gD; a.bg = kept_warp ? lv.bg : nullptr;
+  a.invZ = (float)(1.0 / lv.Z); a.grad = g;
   return a;
 }
 
 template <int DIM, typename T>
-void launch_rows_acc(srwcr_ctx* ctx, Level& lv, const float* c, int nblk) {
-  const AccArgs a = acc_args(lv, c);
+void launch_rows_acc(srwcr_ctx* ctx, Level& lv, const float* c, int nblk, bool keep) {
+  const AccArgs a = acc_args(lv, c, keep);
   if (lv.nxb_rows == 4)
     k_accumulate_rows<DIM, T, 4><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
   else
@@ -265,8 +269,8 @@ void launch_rows_acc(srwcr_ctx* ctx, Level& lv, const float* c, int nblk) {
 
 template <int DIM, typename T>
 void launch_rows_adj(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g,
-                     int nblk) {
-  const AdjArgs a = adj_args(lv, c, gD, g);
+                     int nblk, bool kept) {
+  const AdjArgs a = adj_args(lv, c, gD, g, kept);
   if (lv.nxb_rows == 4)
     k_adjoint_rows<DIM, T, 4><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a);
   else
@@ -275,14 +279,14 @@ void launch_rows_adj(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD,
 
 template <typename T>
 srwcr_status launch_accumulate(srwcr_ctx* ctx, Level& lv, const float* c, bool stat, float s0,
-                               float s1) {
+                               float s1, bool keep_warp = false) {
   const Geo& gg = stat ? lv.gv : lv.g;
   const int nblk = gg.ntile[0] * gg.ntile[1] * gg.ntile[2];
   const T* A = (const T*)lv.A;
   const T* M = (const T*)lv.M;
   if (!stat && lv.rows) {
-    if (ctx->cfg.ndim == 3) launch_rows_acc<3, T>(ctx, lv, c, nblk);
-    else launch_rows_acc<2, T>(ctx, lv, c, nblk);
+    if (ctx->cfg.ndim == 3) launch_rows_acc<3, T>(ctx, lv, c, nblk, keep_warp);
+    else launch_rows_acc<2, T>(ctx, lv, c, nblk, keep_warp);
     CKL();
     return SRWCR_OK;
   }
@@ -299,12 +303,13 @@ srwcr_status launch_accumulate(srwcr_ctx* ctx, Level& lv, const float* c, bool s
 }
 
 template <typename T>
-srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g) {
+srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g,
+                            bool kept_warp) {
   const int nblk = lv.g.ntile[0] * lv.g.ntile[1] * lv.g.ntile[2];
   const float invZ = (float)(1.0 / lv.Z);
   if (lv.rows) {
-    if (ctx->cfg.ndim == 3) launch_rows_adj<3, T>(ctx, lv, c, gD, g, nblk);
-    else launch_rows_adj<2, T>(ctx, lv, c, gD, g, nblk);
+    if (ctx->cfg.ndim == 3) launch_rows_adj<3, T>(ctx, lv, c, gD, g, nblk, kept_warp);
+    else launch_rows_adj<2, T>(ctx, lv, c, gD, g, nblk, kept_warp);
     CKL();
     return SRWCR_OK;
   }
@@ -375,13 +380,15 @@ RegionStatic region_static(const Level& lv) {
   return rs;
 }
 
-// (a) + (b): value into lv.D, tables into lv.U/V/X.
-srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c) {
+// (a) + (b): value into lv.D, tables into lv.U/V/X.  keep_warp: also store
+// the per-voxel warp for a following run_grad(..., true) at the same c.
+srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c, bool keep_warp) {
   const size_t sbytes = (size_t)lv.g.R * lv.g.nbins * 2 * sizeof(unsigned long long);
   CK(cudaMemsetAsync(lv.S, 0, sbytes, ctx->stream));
   cudaEvent_t ev = prof_begin(ctx);
-  srwcr_status st = is_bf16(ctx) ? launch_accumulate<__nv_bfloat16>(ctx, lv, c, false, lv.s1, lv.s2)
-                                 : launch_accumulate<float>(ctx, lv, c, false, lv.s1, lv.s2);
+  srwcr_status st =
+      is_bf16(ctx) ? launch_accumulate<__nv_bfloat16>(ctx, lv, c, false, lv.s1, lv.s2, keep_warp)
+                   : launch_accumulate<float>(ctx, lv, c, false, lv.s1, lv.s2, keep_warp);
   if (st != SRWCR_OK) return st;
   prof_end(ctx, kProfAccumulate, ev);
   const long long warps = lv.g.R;
@@ -399,11 +406,14 @@ srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c) {
   return SRWCR_OK;
 }
 
-srwcr_status run_grad(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g) {
+// (c): gradient; kept_warp reads the warp stored by the preceding value pass
+// at the same coefficients instead of recomputing it.
+srwcr_status run_grad(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g,
+                      bool kept_warp) {
   CK(cudaMemsetAsync(g, 0, sizeof(float) * lv.g.ncoef * ctx->cfg.ndim, ctx->stream));
   cudaEvent_t ev = prof_begin(ctx);
-  RET_IF(is_bf16(ctx) ? launch_adjoint<__nv_bfloat16>(ctx, lv, c, gD, g)
-                      : launch_adjoint<float>(ctx, lv, c, gD, g));
+  RET_IF(is_bf16(ctx) ? launch_adjoint<__nv_bfloat16>(ctx, lv, c, gD, g, kept_warp)
+                      : launch_adjoint<float>(ctx, lv, c, gD, g, kept_warp));
   prof_end(ctx, kProfAdjoint, ev);
   ctx->launches += 1;
   return SRWCR_OK;
@@ -434,7 +444,7 @@ srwcr_status finish_sync(srwcr_ctx* ctx, Level& lv, double* D_host) {
 
 void free_level(Level& lv) {
   void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg, lv.perm,
-                  lv.binmask, lv.Wr, lv.nz_ptr, lv.nz_bin, lv.nz_inv_p};
+                  lv.binmask, lv.Wr, lv.nz_ptr, lv.nz_bin, lv.nz_inv_p, lv.bg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   lv = Level();
@@ -653,8 +663,13 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
   }
 
   // Row-parallel path: tile, per-tile fixed-image bin masks and per-row
-  // lane permutations (A is fixed).
-  for (int l = 0; l < ctx->nlev; ++l) RET_IF(select_rows_path(ctx, ctx->lev[l]));
+  // lane permutations (A is fixed); storage for the warp the value pass
+  // keeps for the adjoint (16 bytes per voxel).
+  for (int l = 0; l < ctx->nlev; ++l) {
+    Level& lv = ctx->lev[l];
+    RET_IF(select_rows_path(ctx, lv));
+    if (lv.rows) CK(cudaMalloc((void**)&lv.bg, sizeof(float4) * lv.g.nvox));
+  }
 
   // Static fixed-image statistics P[r][a] and Z = sum P.
   for (int l = 0; l < ctx->nlev; ++l) {
@@ -771,7 +786,7 @@ srwcr_status srwcr_value(srwcr_ctx* ctx, int level, const float* c_dev, double* 
   if (!c_dev) return fail(SRWCR_EINVAL, "c_dev is NULL");
   Level& lv = ctx->lev[level];
   RET_IF(check_finite_async(ctx, c_dev, lv.g.ncoef * ctx->cfg.ndim));
-  RET_IF(run_value(ctx, lv, c_dev));
+  RET_IF(run_value(ctx, lv, c_dev, false));
   return finish_sync(ctx, lv, D_host);
 }
 
@@ -781,8 +796,8 @@ srwcr_status srwcr_value_and_grad(srwcr_ctx* ctx, int level, const float* c_dev,
   if (!c_dev || !g_dev) return fail(SRWCR_EINVAL, "null device pointer");
   Level& lv = ctx->lev[level];
   RET_IF(check_finite_async(ctx, c_dev, lv.g.ncoef * ctx->cfg.ndim));
-  RET_IF(run_value(ctx, lv, c_dev));
-  RET_IF(run_grad(ctx, lv, c_dev, nullptr, g_dev));
+  RET_IF(run_value(ctx, lv, c_dev, true));
+  RET_IF(run_grad(ctx, lv, c_dev, nullptr, g_dev, true));
   return finish_sync(ctx, lv, D_host);
 }
 
@@ -791,8 +806,8 @@ srwcr_status srwcr_value_and_grad_async(srwcr_ctx* ctx, int level, const float* 
   RET_IF(check_level(ctx, level));
   if (!c_dev || !g_dev || !D_dev) return fail(SRWCR_EINVAL, "null device pointer");
   Level& lv = ctx->lev[level];
-  RET_IF(run_value(ctx, lv, c_dev));
-  RET_IF(run_grad(ctx, lv, c_dev, nullptr, g_dev));
+  RET_IF(run_value(ctx, lv, c_dev, true));
+  RET_IF(run_grad(ctx, lv, c_dev, nullptr, g_dev, true));
   CK(cudaMemcpyAsync(D_dev, lv.D, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   return SRWCR_OK;
 }
@@ -813,8 +828,8 @@ srwcr_status srwcr_value_and_grad_host(srwcr_ctx* ctx, int level, const float* c
   }
   CK(cudaMemcpyAsync(ctx->c_stage, c_host, sizeof(float) * np, cudaMemcpyHostToDevice, ctx->stream));
   RET_IF(check_finite_async(ctx, ctx->c_stage, np));
-  RET_IF(run_value(ctx, lv, ctx->c_stage));
-  RET_IF(run_grad(ctx, lv, ctx->c_stage, nullptr, ctx->g_stage));
+  RET_IF(run_value(ctx, lv, ctx->c_stage, true));
+  RET_IF(run_grad(ctx, lv, ctx->c_stage, nullptr, ctx->g_stage, true));
   CK(cudaMemcpyAsync(g_host, ctx->g_stage, sizeof(float) * np, cudaMemcpyDeviceToHost, ctx->stream));
   return finish_sync(ctx, lv, D_host);
 }
@@ -823,7 +838,7 @@ srwcr_status srwcr_forward(srwcr_ctx* ctx, int level, const float* c_dev, double
   RET_IF(check_level(ctx, level));
   if (!c_dev || !D_dev) return fail(SRWCR_EINVAL, "null device pointer");
   Level& lv = ctx->lev[level];
-  RET_IF(run_value(ctx, lv, c_dev));
+  RET_IF(run_value(ctx, lv, c_dev, false));
   CK(cudaMemcpyAsync(D_dev, lv.D, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   return SRWCR_OK;
 }
@@ -834,7 +849,7 @@ srwcr_status srwcr_backward(srwcr_ctx* ctx, int level, const float* c_dev, const
   if (!c_dev || !g_dev) return fail(SRWCR_EINVAL, "null device pointer");
   Level& lv = ctx->lev[level];
   if (!lv.tables) return fail(SRWCR_EINVAL, "srwcr_backward before srwcr_forward at level %d", level);
-  return run_grad(ctx, lv, c_dev, gD_dev, g_dev);
+  return run_grad(ctx, lv, c_dev, gD_dev, g_dev, false);  // warp recomputed
 }
 
 srwcr_status srwcr_region_stats(srwcr_ctx* ctx, int level, double* out, int64_t* n_degenerate) {
@@ -1149,13 +1164,13 @@ extern "C" srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c
       st = select_rows_path(ctx, lv, cand[i]);
       if (st != SRWCR_OK || !lv.rows) continue;
       for (int w = 0; w < 2 && st == SRWCR_OK; ++w) {
-        st = run_value(ctx, lv, c_dev);
-        if (st == SRWCR_OK) st = run_grad(ctx, lv, c_dev, nullptr, g);
+        st = run_value(ctx, lv, c_dev, true);
+        if (st == SRWCR_OK) st = run_grad(ctx, lv, c_dev, nullptr, g, true);
       }
       cudaEventRecord(e0, ctx->stream);
       for (int r = 0; r < reps && st == SRWCR_OK; ++r) {
-        st = run_value(ctx, lv, c_dev);
-        if (st == SRWCR_OK) st = run_grad(ctx, lv, c_dev, nullptr, g);
+        st = run_value(ctx, lv, c_dev, true);
+        if (st == SRWCR_OK) st = run_grad(ctx, lv, c_dev, nullptr, g, true);
       }
       cudaEventRecord(e1, ctx->stream);
       if (st != SRWCR_OK) break;
