@@ -243,7 +243,8 @@ srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n_levels,
  * registered together.  The paper treats one pair at a time; this is a
  * throughput form of the same method.  Each phase of an evaluation (clear,
  * fused warp + statistics, per-region finalisation, value reduction,
- * adjoint) is ONE launch over every (pair, tile) work item, so a batched
+ * per-plane contraction of the gradient tables, adjoint) is ONE launch over
+ * every (pair, tile) work item, so a batched
  * value+gradient costs a handful of launches whatever the number of pairs,
  * and can be replayed from a CUDA graph.
  *

@@ -368,13 +368,16 @@ srwcr_status queue_batch_eval(srwcr_batch* b, bool lb, const int* active) {
   CKL();
   k_reduce_D_batch<<<b->n, 1024, 0, b->stream>>>(tab, active);
   CKL();
+  if (b->ndim == 3) k_zcontract_batch<3><<<dim3(64, b->n), 256, 0, b->stream>>>(tab, active);
+  else k_zcontract_batch<2><<<dim3(64, b->n), 256, 0, b->stream>>>(tab, active);
+  CKL();
   launch_rows_any(b, lb, active, true);
   CKL();
   return SRWCR_OK;
 }
 
 int launches_per_eval(const srwcr_batch* b) {
-  return 3 + (int)b->acc_launches.size() + (int)b->adj_launches.size();
+  return 4 + (int)b->acc_launches.size() + (int)b->adj_launches.size();
 }
 
 // CTAs of a given dynamic shared-memory size that fit on one SM (228 KB of
@@ -548,6 +551,7 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
     bp.U = lv.U;
     bp.V = lv.V;
     bp.X = lv.X;
+    bp.uvxz = lv.uvxz;
     bp.Dr = lv.Dr;
     bp.stats = lv.stats;
     bp.D = b->D + i;

@@ -22,6 +22,7 @@ struct BatchPair {
   RegionStatic rs;               // static per-region data of the fixed image
   double inv_s1, inv_s2, invZ;
   float *U, *V, *X;              // gradient tables written by the finalisation
+  float* uvxz;                   // their per-plane z-contraction (k_zcontract)
   double* Dr;                    // [R] shares of D
   double* stats;                 // [R][4]
   double* D;                     // this pair's value
@@ -122,6 +123,17 @@ k_finalize_batch(const BatchPair* __restrict__ pairs, int n, long long total,
   if (!batch_active(active, bp.id)) return;
   finalize_region_sparse(w - bp.region_begin, threadIdx.x & 31, bp.g.nbins, bp.rs, bp.acc.acc,
                          bp.inv_s1, bp.inv_s2, bp.invZ, bp.U, bp.V, bp.X, bp.Dr, bp.stats);
+}
+
+// Per-plane z-contraction of every active pair's tables; blockIdx.y = slot.
+template <int DIM>
+__global__ void __launch_bounds__(256)
+k_zcontract_batch(const BatchPair* __restrict__ pairs, const int* __restrict__ active) {
+  const BatchPair& bp = pairs[blockIdx.y];
+  if (!batch_active(active, bp.id)) return;
+  const long long n = zcontract_len(bp.g);
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+    bp.uvxz[i] = zcontract_entry<DIM>(bp.g, i, bp.U, bp.V, bp.X);
 }
 
 // One block per table slot: D = sum of the region shares in a fixed order.

@@ -241,6 +241,7 @@ struct AdjArgs {
   const float* X;
   const float* gscale;           // device scalar or NULL (1)
   const float4* bg;              // (B, dM/dy) stored by the value pass, or NULL: recompute
+  const float* uvxz;             // U, V, X contracted over z per image plane (k_zcontract)
   float invZ;
   float* grad;
 };
@@ -607,9 +608,6 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
   const float* __restrict__ c = args.c;
   const unsigned char* __restrict__ perm = args.perm;
   const unsigned* __restrict__ binmask = args.binmask;
-  const float* __restrict__ U = args.U;
-  const float* __restrict__ V = args.V;
-  const float* __restrict__ X = args.X;
   const float* __restrict__ gscale = args.gscale;
   const float invZ = args.invZ;
   float* __restrict__ grad = args.grad;
@@ -643,11 +641,16 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
   build_axis_tables<DIM>(g, TO, yt, zt);
   __syncthreads();
   if (!bg) build_cz<DIM>(g, TO, c, zt, CZ);
-  // Region tables contracted over z for each of the tile's z-planes.  X is
-  // only needed for the fixed-image bins present in the tile (a0 and a0+1 of
-  // its voxels, a static mask); other entries are never read.
+  // Region tables contracted over z for each of the tile's z-planes, read
+  // from the per-plane tables of k_zcontract.  X is only needed for the
+  // fixed-image bins present in the tile (a0 and a0+1 of its voxels, a static
+  // mask); other entries are never read.
   const unsigned* tmask = binmask + (size_t)tile * ((nb + 31) >> 5);
   {
+    const long long nzp_g = (long long)g.n[2] * g.nsb[1] * g.nsb[0];
+    const float* __restrict__ UZg = args.uvxz;
+    const float* __restrict__ VZg = UZg + nzp_g;
+    const float* __restrict__ XZg = UZg + 2 * nzp_g;
     const int nzp = g.tile[2] * p01;
     const int n = nzp * (2 + nb);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -667,19 +670,11 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
         if (!((__ldg(tmask + (a >> 5)) >> (a & 31)) & 1u)) continue;
       }
       const int r0 = TO.cb[0] + hb01 % g.hb[0], r1 = TO.cb[1] + hb01 / g.hb[0];
+      const int z = TO.o[2] + zl;
       float s = 0.f;
-      if (r0 < g.nsb[0] && r1 < g.nsb[1]) {
-        const AxisEntry& e = zt[zl];
-        const int NZ = DIM == 3 ? 4 : 1;
-#pragma unroll
-        for (int q = 0; q < NZ; ++q) {
-          const int r2 = TO.cb[2] + e.srel + q;
-          if (r2 >= g.nsb[2]) continue;
-          const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
-          const float tv = col == 0 ? __ldg(U + r)
-                                    : (col == 1 ? __ldg(V + r) : __ldg(X + r * nb + (col - 2)));
-          s += e.bs[q] * tv;
-        }
+      if (r0 < g.nsb[0] && r1 < g.nsb[1] && z < g.n[2]) {
+        const long long zr = ((long long)z * g.nsb[1] + r1) * g.nsb[0] + r0;
+        s = col == 0 ? __ldg(UZg + zr) : (col == 1 ? __ldg(VZg + zr) : __ldg(XZg + zr * nb + (col - 2)));
       }
       if (col == 0) UZ[zl * p01 + hb01] = s;
       else if (col == 1) VZ[zl * p01 + hb01] = s;
@@ -846,6 +841,59 @@ __global__ void __launch_bounds__(kAdjWarps * 32)
 k_adjoint_rows(const Geo g, const AdjArgs args) {
   extern __shared__ __align__(16) float smem_adj[];
   adj_rows_body<DIM, T, NXB>(g, args, blockIdx.x, smem_adj);
+}
+
+// Region tables contracted over z for every image plane z: entry i of the
+// output is, for i < 2 P (P = nz * nsb1 * nsb0 plane-columns (z, r1, r0)),
+// sum_q beta_q(z) U or V at region (cell(z) + q, r1, r0), and past that
+// sum_q beta_q(z) X[(cell(z) + q, r1, r0)][a] in [z][r1][r0][a] order (Eq. 7
+// weights along z; the same terms and order as a per-tile contraction).
+template <int DIM>
+__device__ __forceinline__ float zcontract_entry(const Geo& g, long long i, const float* __restrict__ U,
+                                                 const float* __restrict__ V,
+                                                 const float* __restrict__ X) {
+  const int nb = g.nbins;
+  const long long P1 = (long long)g.nsb[1] * g.nsb[0];
+  const long long nzp = (long long)g.n[2] * P1;
+  long long zr;
+  int col;
+  if (i < 2 * nzp) {
+    col = (int)(i / nzp);
+    zr = i - col * nzp;
+  } else {
+    const long long r = i - 2 * nzp;
+    zr = r / nb;
+    col = 2 + (int)(r - zr * nb);
+  }
+  const int z = (int)(zr / P1);
+  const long long rr = zr - (long long)z * P1;
+  AxisEntry e;
+  if (DIM == 3) axis_entry(g, 2, z, 0, 0, &e);
+  else axis_unit(&e);
+  const int NZ = DIM == 3 ? 4 : 1;
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < NZ; ++q) {
+    const int r2 = e.srel + q;
+    if (r2 >= g.nsb[2]) continue;
+    const long long r = r2 * P1 + rr;
+    const float tv = col == 0 ? __ldg(U + r) : (col == 1 ? __ldg(V + r) : __ldg(X + r * nb + (col - 2)));
+    s += e.bs[q] * tv;
+  }
+  return s;
+}
+
+__host__ __device__ inline long long zcontract_len(const Geo& g) {
+  return (long long)g.n[2] * g.nsb[1] * g.nsb[0] * (2 + g.nbins);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256)
+k_zcontract(const Geo g, const float* __restrict__ U, const float* __restrict__ V,
+            const float* __restrict__ X, float* __restrict__ out) {
+  const long long n = zcontract_len(g);
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+    out[i] = zcontract_entry<DIM>(g, i, U, V, X);
 }
 
 // Static per-tile mask of the fixed-image bins its voxels touch (a0, a0+1).

@@ -95,6 +95,7 @@ struct Level {
   unsigned char* perm = nullptr;
   unsigned* binmask = nullptr;        // per tile: fixed-image bins present
   float4* bg = nullptr;               // per voxel (B, dM/dy) of the last kept warp
+  float* uvxz = nullptr;              // U, V, X contracted over z per image plane
   size_t smem_acc_rows = 0, smem_adj_rows = 0;
 };
 
@@ -254,6 +255,7 @@ AdjArgs adj_args(const Level& lv, const float* c, const float* gD, float* g, boo
   AdjArgs a;
   a.A = lv.A; a.M = lv.M; a.c = c; a.perm = lv.perm; a.binmask = lv.binmask;
   a.U = lv.U; a.V = lv.V; a.X = lv.X; a.gscale = gD; a.bg = kept_warp ? lv.bg : nullptr;
+  a.uvxz = lv.uvxz;
   a.invZ = (float)(1.0 / lv.Z); a.grad = g;
   return a;
 }
@@ -308,6 +310,13 @@ srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const flo
   const int nblk = lv.g.ntile[0] * lv.g.ntile[1] * lv.g.ntile[2];
   const float invZ = (float)(1.0 / lv.Z);
   if (lv.rows) {
+    // Per-plane z-contraction of the region tables, then the adjoint.
+    const long long nz = zcontract_len(lv.g);
+    const int zb = (int)std::min<long long>(148 * 16, (nz + 255) / 256);
+    if (ctx->cfg.ndim == 3) k_zcontract<3><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.U, lv.V, lv.X, lv.uvxz);
+    else k_zcontract<2><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.U, lv.V, lv.X, lv.uvxz);
+    CKL();
+    ctx->launches += 1;
     if (ctx->cfg.ndim == 3) launch_rows_adj<3, T>(ctx, lv, c, gD, g, nblk, kept_warp);
     else launch_rows_adj<2, T>(ctx, lv, c, gD, g, nblk, kept_warp);
     CKL();
@@ -444,7 +453,7 @@ srwcr_status finish_sync(srwcr_ctx* ctx, Level& lv, double* D_host) {
 
 void free_level(Level& lv) {
   void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg, lv.perm,
-                  lv.binmask, lv.Wr, lv.nz_ptr, lv.nz_bin, lv.nz_inv_p, lv.bg};
+                  lv.binmask, lv.Wr, lv.nz_ptr, lv.nz_bin, lv.nz_inv_p, lv.bg, lv.uvxz};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   lv = Level();
@@ -668,7 +677,10 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
   for (int l = 0; l < ctx->nlev; ++l) {
     Level& lv = ctx->lev[l];
     RET_IF(select_rows_path(ctx, lv));
-    if (lv.rows) CK(cudaMalloc((void**)&lv.bg, sizeof(float4) * lv.g.nvox));
+    if (lv.rows) {
+      CK(cudaMalloc((void**)&lv.bg, sizeof(float4) * lv.g.nvox));
+      CK(cudaMalloc((void**)&lv.uvxz, sizeof(float) * zcontract_len(lv.g)));
+    }
   }
 
   // Static fixed-image statistics P[r][a] and Z = sum P.

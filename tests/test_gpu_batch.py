@@ -48,9 +48,9 @@ def test_batched_value_and_gradient_equal_single_pair_and_oracle(specs, storage)
     assert all(e.levels[0].kernel_path == 1 for e in es)
     b = eng.Batch(es)
     info = b.info()
-    # clear, finalisation, reduction + one launch per (x-bins, occupancy) class
-    # for each of the two row kernels
-    assert info.n_pairs == len(specs) and info.launches_per_eval <= 3 + 2 * 4
+    # clear, finalisation, reduction, plane contraction of the tables + one
+    # launch per (x-bins, occupancy) class for each of the two row kernels
+    assert info.n_pairs == len(specs) and info.launches_per_eval <= 4 + 2 * 4
     cs = coefs(specs, 500, 2.0)
     for i, c in enumerate(cs):
         b.coef(i).copy_(torch.from_numpy(c))
