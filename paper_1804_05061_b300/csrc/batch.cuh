@@ -552,6 +552,8 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
     bp.V = lv.V;
     bp.X = lv.X;
     bp.uvxz = lv.uvxz;
+    bp.ubins = lv.ubins;
+    bp.nu = lv.nu;
     bp.Dr = lv.Dr;
     bp.stats = lv.stats;
     bp.D = b->D + i;

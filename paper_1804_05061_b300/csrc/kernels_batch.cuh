@@ -23,6 +23,8 @@ struct BatchPair {
   double inv_s1, inv_s2, invZ;
   float *U, *V, *X;              // gradient tables written by the finalisation
   float* uvxz;                   // their per-plane z-contraction (k_zcontract)
+  const int* ubins;              // fixed-image bins present in the image
+  int nu;
   double* Dr;                    // [R] shares of D
   double* stats;                 // [R][4]
   double* D;                     // this pair's value
@@ -131,9 +133,9 @@ __global__ void __launch_bounds__(256)
 k_zcontract_batch(const BatchPair* __restrict__ pairs, const int* __restrict__ active) {
   const BatchPair& bp = pairs[blockIdx.y];
   if (!batch_active(active, bp.id)) return;
-  const long long n = zcontract_len(bp.g);
+  const long long n = zcontract_items(bp.g, bp.nu);
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
-    bp.uvxz[i] = zcontract_entry<DIM>(bp.g, i, bp.U, bp.V, bp.X);
+    zcontract_item<DIM>(bp.g, i, bp.ubins, bp.nu, bp.U, bp.V, bp.X, bp.uvxz);
 }
 
 // One block per table slot: D = sum of the region shares in a fixed order.

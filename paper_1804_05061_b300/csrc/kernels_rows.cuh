@@ -843,27 +843,41 @@ k_adjoint_rows(const Geo g, const AdjArgs args) {
   adj_rows_body<DIM, T, NXB>(g, args, blockIdx.x, smem_adj);
 }
 
-// Region tables contracted over z for every image plane z: entry i of the
-// output is, for i < 2 P (P = nz * nsb1 * nsb0 plane-columns (z, r1, r0)),
-// sum_q beta_q(z) U or V at region (cell(z) + q, r1, r0), and past that
-// sum_q beta_q(z) X[(cell(z) + q, r1, r0)][a] in [z][r1][r0][a] order (Eq. 7
-// weights along z; the same terms and order as a per-tile contraction).
+// Region tables contracted over z for every image plane z.  Output layout:
+// [U | V | X], U and V as [z][r1][r0] (P = nz * nsb1 * nsb0 plane-columns),
+// X as [z][r1][r0][a]; each entry is sum_q beta_q(z) T[(cell(z) + q, r1, r0)]
+// (Eq. 7 weights along z; the same terms and order as a per-tile
+// contraction).  Item i enumerates the U and V entries and the X entries of
+// the nu fixed-image bins that occur anywhere in the image (ubins); the
+// adjoint reads no other X entry.
+__host__ __device__ inline long long zcontract_len(const Geo& g) {
+  return (long long)g.n[2] * g.nsb[1] * g.nsb[0] * (2 + g.nbins);
+}
+
+__host__ __device__ inline long long zcontract_items(const Geo& g, int nu) {
+  return (long long)g.n[2] * g.nsb[1] * g.nsb[0] * (2 + nu);
+}
+
 template <int DIM>
-__device__ __forceinline__ float zcontract_entry(const Geo& g, long long i, const float* __restrict__ U,
-                                                 const float* __restrict__ V,
-                                                 const float* __restrict__ X) {
+__device__ __forceinline__ void zcontract_item(const Geo& g, long long i, const int* __restrict__ ubins,
+                                               int nu, const float* __restrict__ U,
+                                               const float* __restrict__ V,
+                                               const float* __restrict__ X, float* __restrict__ out) {
   const int nb = g.nbins;
   const long long P1 = (long long)g.nsb[1] * g.nsb[0];
   const long long nzp = (long long)g.n[2] * P1;
-  long long zr;
+  long long zr, o;
   int col;
   if (i < 2 * nzp) {
     col = (int)(i / nzp);
     zr = i - col * nzp;
+    o = i;
   } else {
     const long long r = i - 2 * nzp;
-    zr = r / nb;
-    col = 2 + (int)(r - zr * nb);
+    zr = r / nu;
+    const int a = __ldg(ubins + (r - zr * nu));
+    col = 2 + a;
+    o = 2 * nzp + zr * nb + a;
   }
   const int z = (int)(zr / P1);
   const long long rr = zr - (long long)z * P1;
@@ -880,20 +894,16 @@ __device__ __forceinline__ float zcontract_entry(const Geo& g, long long i, cons
     const float tv = col == 0 ? __ldg(U + r) : (col == 1 ? __ldg(V + r) : __ldg(X + r * nb + (col - 2)));
     s += e.bs[q] * tv;
   }
-  return s;
-}
-
-__host__ __device__ inline long long zcontract_len(const Geo& g) {
-  return (long long)g.n[2] * g.nsb[1] * g.nsb[0] * (2 + g.nbins);
+  out[o] = s;
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(256)
-k_zcontract(const Geo g, const float* __restrict__ U, const float* __restrict__ V,
-            const float* __restrict__ X, float* __restrict__ out) {
-  const long long n = zcontract_len(g);
+k_zcontract(const Geo g, const int* __restrict__ ubins, int nu, const float* __restrict__ U,
+            const float* __restrict__ V, const float* __restrict__ X, float* __restrict__ out) {
+  const long long n = zcontract_items(g, nu);
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
-    out[i] = zcontract_entry<DIM>(g, i, U, V, X);
+    zcontract_item<DIM>(g, i, ubins, nu, U, V, X, out);
 }
 
 // Static per-tile mask of the fixed-image bins its voxels touch (a0, a0+1).

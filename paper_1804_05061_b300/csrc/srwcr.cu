@@ -96,6 +96,8 @@ struct Level {
   unsigned* binmask = nullptr;        // per tile: fixed-image bins present
   float4* bg = nullptr;               // per voxel (B, dM/dy) of the last kept warp
   float* uvxz = nullptr;              // U, V, X contracted over z per image plane
+  int* ubins = nullptr;               // fixed-image bins present in the image (any tile)
+  int nu = 0;
   size_t smem_acc_rows = 0, smem_adj_rows = 0;
 };
 
@@ -311,10 +313,12 @@ srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const flo
   const float invZ = (float)(1.0 / lv.Z);
   if (lv.rows) {
     // Per-plane z-contraction of the region tables, then the adjoint.
-    const long long nz = zcontract_len(lv.g);
+    const long long nz = zcontract_items(lv.g, lv.nu);
     const int zb = (int)std::min<long long>(148 * 16, (nz + 255) / 256);
-    if (ctx->cfg.ndim == 3) k_zcontract<3><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.U, lv.V, lv.X, lv.uvxz);
-    else k_zcontract<2><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.U, lv.V, lv.X, lv.uvxz);
+    if (ctx->cfg.ndim == 3)
+      k_zcontract<3><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.ubins, lv.nu, lv.U, lv.V, lv.X, lv.uvxz);
+    else
+      k_zcontract<2><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.ubins, lv.nu, lv.U, lv.V, lv.X, lv.uvxz);
     CKL();
     ctx->launches += 1;
     if (ctx->cfg.ndim == 3) launch_rows_adj<3, T>(ctx, lv, c, gD, g, nblk, kept_warp);
@@ -453,7 +457,8 @@ srwcr_status finish_sync(srwcr_ctx* ctx, Level& lv, double* D_host) {
 
 void free_level(Level& lv) {
   void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg, lv.perm,
-                  lv.binmask, lv.Wr, lv.nz_ptr, lv.nz_bin, lv.nz_inv_p, lv.bg, lv.uvxz};
+                  lv.binmask, lv.Wr, lv.nz_ptr, lv.nz_bin, lv.nz_inv_p, lv.bg, lv.uvxz,
+                  lv.ubins};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   lv = Level();
@@ -529,6 +534,19 @@ srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv, const int* force_tile =
       int cnt = 0;
       for (int w = 0; w < words; ++w) cnt += __builtin_popcount(hmask[tt * words + w]);
       nab = std::max(nab, cnt);
+    }
+    if (!lv.ubins) {
+      // Bins present anywhere in the image (the same for every tiling).
+      std::vector<int> ub;
+      for (int a = 0; a < lv.g.nbins; ++a) {
+        bool any = false;
+        for (size_t tt = 0; tt < ntiles && !any; ++tt) any = (hmask[tt * words + (a >> 5)] >> (a & 31)) & 1u;
+        if (any) ub.push_back(a);
+      }
+      if (ub.empty()) ub.push_back(0);
+      CK(cudaMalloc((void**)&lv.ubins, sizeof(int) * ub.size()));
+      CK(cudaMemcpy(lv.ubins, ub.data(), sizeof(int) * ub.size(), cudaMemcpyHostToDevice));
+      lv.nu = (int)ub.size();
     }
     g.nabin = nab;
     const int nxb = g.hb[0] <= 4 ? 4 : 8;
