@@ -297,6 +297,35 @@ def bench_batch(args, eng, torch, dist, ws):
     }
 
 
+def bench_registration(eng, torch, pair):
+    """The 256x256x96 pair registered coarse to fine over a 3-level pyramid
+    (levels 64x64x24, 128x128x48, 256x256x96; default L-BFGS options: at most
+    200/200/120 iterations, stop when D is stable over 20 steps), from zero
+    coefficients.  Wall clock of srwcr_register (host-driven line search)."""
+    prob = pair.prob
+    e = eng.from_problem(prob, pair.fixed, pair.moving, storage="f32", pyramid_levels=3)
+    for lvl in range(3):
+        e.autotune(e.zeros(lvl), level=lvl, reps=2)
+    c = e.zeros()
+    D0 = e.value(c)
+    o = e.default_opts()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    rep = e.register(c, 3, o)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    its = [int(rep.iterations[l]) for l in (2, 1, 0)]
+    evs = [int(rep.evaluations[l]) for l in (2, 1, 0)]
+    names = {0: "SRWCR_OK", 5: "SRWCR_ELINESEARCH", 7: "SRWCR_ENOTCONVERGED"}
+    return {"workload": f"{pair.name}, 3-level pyramid, coarse to fine, from zero coefficients",
+            "levels": [list(e.levels[l].dims) for l in (2, 1, 0)],
+            "iterations": its, "evaluations": evs,
+            "final_value": [float(rep.final_value[l]) for l in (2, 1, 0)],
+            "status": [names.get(int(rep.status[l]), int(rep.status[l])) for l in (2, 1, 0)],
+            "D_start_finest": D0, "D_end_finest": e.value(c), "wall_s": wall,
+            "iterations_per_s": sum(its) / wall}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,6 +338,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form section")
     ap.add_argument("--batch-pairs", type=int, default=32)
     ap.add_argument("--batch-lbfgs-iters", type=int, default=10)
+    ap.add_argument("--no-registration", action="store_true",
+                    help="skip the 3-level pyramid registration run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -419,6 +450,10 @@ def main():
                 "kernel_ms": {k: round(v, 4) for k, v in avg.items()},
                 "algorithmic_bytes_per_voxel_step": 4 * esz}
 
+    reg = None
+    if not args.no_registration and args.config == "c2":
+        reg = bench_registration(eng, torch, pair)
+
     batch = None
     if not args.no_batch:
         del flush
@@ -443,7 +478,7 @@ def main():
                        "l2": "flushed between steps (256 MB write, outside the timed events)",
                        "wall_ms_per_step_incl_flush": wall / args.steps * 1e3},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches, "batched": batch}
+            "gpu_launches": launches, "batched": batch, "registration": reg}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -182,3 +182,20 @@ def test_autotune_keeps_row_path_value_and_gradient(tmp_path, monkeypatch):
     e2 = engine(prob, f, m)
     assert e2.autotune(c, reps=2) == tile
     assert e2.value(c) == D0
+
+
+def test_three_level_pyramid_registration_on_ct_256():
+    pair = synth.make_pair("c2_ct_256x256x96")
+    e = engine(pair.prob, pair.fixed, pair.moving, pyramid_levels=3)
+    assert [e.levels[l].dims for l in range(3)] == [(256, 256, 96), (128, 128, 48), (64, 64, 24)]
+    o = e.default_opts()
+    o.max_iter[0], o.max_iter[1], o.max_iter[2] = 15, 15, 15
+    c = e.zeros()
+    D0 = e.value(c)
+    rep = e.register(c, 3, o)
+    assert rep.levels_run == 3
+    assert all(rep.iterations[l] > 0 for l in range(3))
+    assert all(rep.status[l] in (0, 5, 7) for l in range(3))
+    D1 = e.value(c)
+    assert abs(rep.final_value[0] - D1) <= 1e-12 * D1
+    assert D1 < 0.95 * D0, (D0, D1)
