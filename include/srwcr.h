@@ -217,20 +217,39 @@ typedef struct {
   double stable_rtol;     /* 1e-5 */
   int max_ls;             /* line-search trials (20) */
   double c1, c2;          /* Armijo and curvature constants (1e-4, 0.9) */
+  double penalty_weight;  /* w_p of Eq. (1): the cost is D + w_p * C_p with C_p
+                             the bending energy (srwcr_bending_energy); 0 =
+                             D alone (default).  The paper uses 0.1 for
+                             mono-modal and 30 for multi-modal pairs. */
 } srwcr_lbfgs_opts;
 
 typedef struct {
   int levels_run;
   int iterations[4];      /* per level, finest first */
   int evaluations[4];
-  double final_value[4];
+  double final_value[4];  /* minimised cost (D, or D + w_p C_p) */
   int status[4];          /* srwcr_status per level */
 } srwcr_report;
 
 /* Fill opts with the defaults above. */
 void srwcr_lbfgs_default_opts(srwcr_lbfgs_opts* opts);
 
-/* Multi-resolution L-BFGS registration minimising D (Sec. II-F).
+/* Bending energy of the displacement, the penalty C_p of Eq. (1): the
+ * thin-plate energy (1/|Omega|) * integral over Omega = prod_d [0, N_d - 1]
+ * (voxel units) of sum_k sum_{i,j} (d^2 u_k / dx_i dx_j)^2, over ordered
+ * pairs (i, j), u the FFD displacement at level `level`.  The paper takes
+ * C_p from its ref. [26] without a formula; this is the standard definition,
+ * integrated exactly (u is a tensor-product cubic B-spline).
+ *   c_dev   device coefficients (layout as for srwcr_value)
+ *   E_dev   device double receiving C_p, or NULL
+ *   g_dev   device gradient to which weight * dC_p/dc is ADDED, or NULL
+ * Queued on the context's stream without synchronising.  The first call at a
+ * level allocates that level's work buffers (8 floats per parameter). */
+srwcr_status srwcr_bending_energy(srwcr_ctx* ctx, int level, const float* c_dev, double* E_dev,
+                                  float* g_dev, float weight);
+
+/* Multi-resolution L-BFGS registration minimising D (Sec. II-F), or
+ * D + w_p C_p when opts->penalty_weight > 0.
  * c_dev_inout (device, n_params of level 0) holds the finest-level start
  * and receives the result; levels run coarse to fine, each coarse result is
  * refined to the next level by cubic B-spline subdivision (values x2).
@@ -306,7 +325,8 @@ srwcr_status srwcr_batch_sync(srwcr_batch* b, double* D_host);
  * was stable over the window or the gradient vanished, SRWCR_ENOTCONVERGED
  * at the iteration limit, SRWCR_ELINESEARCH when the line search failed).
  * Returns SRWCR_ENUMERIC if some pair's value was not finite at its start,
- * SRWCR_EINVAL for bad options (stable_window must be below 64). */
+ * SRWCR_EINVAL for bad options (stable_window must be below 64; the
+ * bending-energy penalty is not supported here: penalty_weight must be 0). */
 srwcr_status srwcr_batch_register(srwcr_batch* b, const srwcr_lbfgs_opts* opts, int use_graph,
                                   int* iterations, int* evaluations, double* final_value,
                                   int* status);

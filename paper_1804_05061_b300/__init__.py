@@ -33,7 +33,7 @@ EXPORTS = ("srwcr_create", "srwcr_destroy", "srwcr_last_error", "srwcr_level_inf
            "srwcr_profile_read", "srwcr_value_noalloc", "srwcr_autotune",
            "srwcr_batch_create", "srwcr_batch_destroy", "srwcr_batch_info",
            "srwcr_batch_layout", "srwcr_batch_buffers", "srwcr_batch_value_and_grad",
-           "srwcr_batch_sync", "srwcr_batch_register")
+           "srwcr_batch_sync", "srwcr_batch_register", "srwcr_bending_energy")
 
 
 class SrwcrError(RuntimeError):
@@ -60,7 +60,8 @@ class LevelDesc(ctypes.Structure):
 class LbfgsOpts(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("max_iter", ctypes.c_int * 4),
                 ("stable_window", ctypes.c_int), ("stable_rtol", ctypes.c_double),
-                ("max_ls", ctypes.c_int), ("c1", ctypes.c_double), ("c2", ctypes.c_double)]
+                ("max_ls", ctypes.c_int), ("c1", ctypes.c_double), ("c2", ctypes.c_double),
+                ("penalty_weight", ctypes.c_double)]
 
 
 class Report(ctypes.Structure):
@@ -126,6 +127,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "srwcr_batch_sync": (st, [vp, vp]),
         "srwcr_batch_register": (st, [vp, ctypes.POINTER(LbfgsOpts), ctypes.c_int, vp, vp, vp,
                                       vp]),
+        "srwcr_bending_energy": (st, [vp, ctypes.c_int, vp, vp, vp, ctypes.c_float]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -334,6 +336,16 @@ class SRWCR:
         _check(load().srwcr_autotune(self._h, level, _ptr(c), int(reps), t))
         self.levels[level] = self.level_info(level)
         return tuple(t)
+
+    def bending_energy(self, c, level: int = 0, grad_into=None, weight: float = 1.0) -> float:
+        """C_p of Eq. (1) at c (synchronises); if grad_into is given, adds
+        weight * dC_p/dc to it."""
+        c = self._c(c, level)
+        E = self._torch.zeros((), dtype=self._torch.float64, device=self.device)
+        _check(load().srwcr_bending_energy(self._h, level, _ptr(c), _ptr(E),
+                                           _ptr(grad_into) if grad_into is not None else None,
+                                           float(weight)))
+        return float(E)
 
     # -- registration ------------------------------------------------------
     @staticmethod

@@ -14,7 +14,7 @@ SRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsrwcr.so")
 SOURCES = ["srwcr.cu"]
 DEPS = SOURCES + ["kernels.cuh", "kernels_rows.cuh", "kernels_batch.cuh", "device_math.cuh",
-                  "lbfgs.cuh", "batch.cuh"]
+                  "lbfgs.cuh", "batch.cuh", "bending.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -708,6 +708,8 @@ srwcr_status srwcr_batch_register(srwcr_batch* b, const srwcr_lbfgs_opts* opts, 
   if (oo.m < 1 || oo.m > 16 || oo.max_ls < 1 || oo.stable_window >= kLbHist ||
       oo.max_iter[b->level] < 0)
     return fail(SRWCR_EINVAL, "bad L-BFGS options (m in 1..16, max_ls >= 1, window < %d)", kLbHist);
+  if (oo.penalty_weight != 0.0)
+    return fail(SRWCR_EINVAL, "the batched driver minimises D alone (penalty_weight must be 0)");
   LbOpts o{oo.m, oo.max_iter[b->level], oo.stable_window, oo.max_ls, oo.stable_rtol, oo.c1, oo.c2};
   RET_IF(batch_alloc_lbfgs(b, o.m));
   k_lbfgs_init<<<b->n, 256, 0, b->stream>>>(b->lbs, b->active, b->off_dev, b->c, b->xn);

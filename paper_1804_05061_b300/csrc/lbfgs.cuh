@@ -103,6 +103,11 @@ __global__ void k_subdivide(const float* __restrict__ cc, int ndim, int cx, int 
   }
 }
 
+// bending.cuh: E_dev <- C_p(c), g_dev += weight * dC_p/dc; per-context work.
+srwcr_status bending_energy(srwcr_ctx* ctx, int level, const float* c, double* E_dev, float* g_dev,
+                            float weight);
+srwcr_status ensure_bend(srwcr_ctx* ctx);
+
 struct LbfgsWork {
   long long n = 0;
   int m = 0;
@@ -112,11 +117,13 @@ struct LbfgsWork {
   double* part = nullptr;
   double* dot = nullptr;   // device scalar
   double* Ddev = nullptr;  // device scalar
-  double* host = nullptr;  // pinned [2]
+  double* Edev = nullptr;  // device scalar: bending energy at the evaluated point
+  double* host = nullptr;  // pinned [3]
+  double wp = 0.0;         // penalty weight w_p of Eq. (1)
 };
 
 void free_work(LbfgsWork& w) {
-  void* p[] = {w.x, w.g, w.d, w.xn, w.gn, w.S, w.Y, w.part, w.dot, w.Ddev};
+  void* p[] = {w.x, w.g, w.d, w.xn, w.gn, w.S, w.Y, w.part, w.dot, w.Ddev, w.Edev};
   for (void* q : p)
     if (q) cudaFree(q);
   if (w.host) cudaFreeHost(w.host);
@@ -136,7 +143,8 @@ srwcr_status alloc_work(LbfgsWork& w, long long n, int m) {
   CK(cudaMalloc((void**)&w.part, sizeof(double) * kDotBlocks));
   CK(cudaMalloc((void**)&w.dot, sizeof(double)));
   CK(cudaMalloc((void**)&w.Ddev, sizeof(double)));
-  CK(cudaMallocHost((void**)&w.host, sizeof(double) * 2));
+  CK(cudaMalloc((void**)&w.Edev, sizeof(double)));
+  CK(cudaMallocHost((void**)&w.host, sizeof(double) * 3));
   return SRWCR_OK;
 }
 
@@ -163,13 +171,17 @@ srwcr_status scal(srwcr_ctx* ctx, LbfgsWork& w, float a, const float* x, float* 
   return SRWCR_OK;
 }
 
+// Cost of Eq. (1) at x: f = D + w_p C_p, g = its gradient.
 srwcr_status eval(srwcr_ctx* ctx, int level, LbfgsWork& w, const float* x, float* g, double* f) {
   Level& lv = ctx->lev[level];
   RET_IF(run_value(ctx, lv, x, true));
   RET_IF(run_grad(ctx, lv, x, nullptr, g, true));
+  if (w.wp > 0.0) RET_IF(bending_energy(ctx, level, x, w.Edev, g, (float)w.wp));
   CK(cudaMemcpyAsync(w.host + 1, lv.D, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (w.wp > 0.0)
+    CK(cudaMemcpyAsync(w.host + 2, w.Edev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  *f = w.host[1];
+  *f = w.host[1] + (w.wp > 0.0 ? w.wp * w.host[2] : 0.0);
   return SRWCR_OK;
 }
 
@@ -285,6 +297,8 @@ extern "C" srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n
   srwcr_lbfgs_default_opts(&o);
   if (opts) o = *opts;
   if (o.m < 1 || o.m > 16 || o.max_ls < 1) return fail(SRWCR_EINVAL, "bad L-BFGS options");
+  if (!(o.penalty_weight >= 0.0)) return fail(SRWCR_EINVAL, "penalty_weight must be >= 0");
+  if (o.penalty_weight > 0.0) RET_IF(ensure_bend(ctx));
   if (report) memset(report, 0, sizeof *report);
   const int nd = ctx->cfg.ndim;
   srwcr_status final_status = SRWCR_OK;
@@ -293,6 +307,7 @@ extern "C" srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n
   for (int level = n_levels - 1; level >= 0; --level) {
     const Geo& g = ctx->lev[level].g;
     LbfgsWork w;
+    w.wp = o.penalty_weight;
     srwcr_status st = alloc_work(w, g.ncoef * nd, o.m);
     if (st != SRWCR_OK) { free_work(w); if (prev) cudaFree(prev); return st; }
     if (level == n_levels - 1 && n_levels > 1) {

@@ -103,6 +103,8 @@ struct Level {
 
 }  // namespace
 
+struct srwcr_bend_levels;  // bending-energy work per level (bending.cuh)
+
 struct srwcr_ctx {
   srwcr_config cfg{};
   int nlev = 0;
@@ -121,6 +123,7 @@ struct srwcr_ctx {
   long long launches = 0;
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;
+  srwcr_bend_levels* bend = nullptr;  // created on first use
 };
 
 namespace {
@@ -575,6 +578,8 @@ srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv, const int* force_tile =
   return SRWCR_OK;
 }
 
+void free_bend(srwcr_ctx* ctx);  // bending.cuh
+
 }  // namespace
 
 extern "C" {
@@ -583,6 +588,7 @@ const char* srwcr_last_error(void) { return g_err.c_str(); }
 
 void srwcr_destroy(srwcr_ctx* ctx) {
   if (!ctx) return;
+  free_bend(ctx);
   for (int l = 0; l < ctx->nlev; ++l) free_level(ctx->lev[l]);
   if (ctx->D_host) cudaFreeHost(ctx->D_host);
   if (ctx->flag_host) cudaFreeHost(ctx->flag_host);
@@ -971,6 +977,7 @@ void srwcr_lbfgs_default_opts(srwcr_lbfgs_opts* o) {
   o->max_ls = 20;
   o->c1 = 1e-4;
   o->c2 = 0.9;
+  o->penalty_weight = 0.0;
 }
 
 }  // extern "C"
@@ -1236,4 +1243,5 @@ extern "C" srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c
 }
 
 #include "lbfgs.cuh"
+#include "bending.cuh"
 #include "batch.cuh"
