@@ -26,7 +26,8 @@ from scipy.interpolate import BSpline
 
 __all__ = [
     "Problem", "PairSpec", "CONFIGS", "problem", "make_pair", "coefficients",
-    "n_ffd_nodes", "random_ffd_warp", "batch_specs", "downsample2",
+    "n_ffd_nodes", "random_ffd_warp", "batch_specs", "downsample2", "grid_pair",
+    "displacement_field",
 ]
 
 
@@ -381,3 +382,42 @@ def small_pair(kind: str, dims, ffd_spacing, sigma: float, seed: int):
     else:
         raise ValueError(kind)
     return np.ascontiguousarray(f, np.float32), np.ascontiguousarray(m, np.float32)
+
+
+# ----------------------------------------------------------------------------
+# Synthetic grid experiment (known deformation)
+# ----------------------------------------------------------------------------
+def displacement_field(shape_zyx, spacing_xyz, coef) -> np.ndarray:
+    """Displacement (d, [nz,] ny, nx) of cubic B-spline control coefficients
+    ``coef`` (SciPy design matrices; node j at (j-1)*spacing)."""
+    return np.stack(_displacement(tuple(shape_zyx), spacing_xyz, np.asarray(coef, np.float64)))
+
+
+@dataclasses.dataclass
+class GridPair:
+    original: np.ndarray      # binary grid O
+    warped: np.ndarray        # W(x) = O(x + v(x)) times a smooth bias field
+    true_coef: np.ndarray     # control coefficients of v
+    true_spacing: tuple       # their control spacing (x, y, z)
+
+
+def grid_pair(n: int = 128, seed: int = 0, amplitude: float = 15.0, true_spacing: int = 16,
+              period: int = 16, thickness: int = 2, bias: float = 0.3) -> GridPair:
+    """Binary black-and-white 3-D grid (planes of ``thickness`` voxels every
+    ``period`` along each axis) and a warped copy: control displacements iid
+    uniform in [-amplitude, amplitude] voxels on a grid of spacing
+    ``true_spacing``, trilinear resampling, then a smooth multiplicative bias
+    field 1 + bias * (x/n - 1/2) + bias/2 * (y/n - 1/2)^2."""
+    rng = np.random.default_rng(seed)
+    idx = np.arange(n)
+    line = (idx % period) < thickness
+    O = (line[:, None, None] | line[None, :, None] | line[None, None, :]).astype(np.float64)
+    nodes = n_ffd_nodes(n, true_spacing)
+    coef = rng.uniform(-amplitude, amplitude, size=(3, nodes, nodes, nodes))
+    u = displacement_field((n, n, n), (true_spacing,) * 3, coef)
+    zz, yy, xx = np.meshgrid(idx, idx, idx, indexing="ij")
+    coords = np.stack([zz + u[2], yy + u[1], xx + u[0]])
+    W = ndimage.map_coordinates(O, coords, order=1, mode="nearest")
+    xr, yr = xx / n - 0.5, yy / n - 0.5
+    W = W * (1.0 + bias * xr + 0.5 * bias * yr * yr)
+    return GridPair(O.astype(np.float32), W.astype(np.float32), coef, (true_spacing,) * 3)
