@@ -79,6 +79,9 @@ def lib():
                                             ctypes.c_double, _D]),
             "orc_gradient_at": (ctypes.c_int, [_PP, _D, _D, _D, _D, _D, _D, _D, _U8,
                                                ctypes.c_double, _I64, ctypes.c_int64, _D]),
+            "orc_joint_pdf_mas_a": (ctypes.c_int, [_PP, _D, _D, _D, _D, _D]),
+            "orc_gradient_mas_a": (ctypes.c_int, [_PP, _D, _D, _D, _D, _D, _D, _D, _U8,
+                                                  ctypes.c_double, _D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -336,6 +339,46 @@ def dD_dB_image(geo: Geometry, A, M, c, st: Stats) -> np.ndarray:
     lib().orc_dD_dB_image(ctypes.byref(s), _d(A), _d(M), _d(c), _d(st.mu_r), _d(st.var_r),
                           _d(st.cr), _d(mu_ra), st.valid.ctypes.data_as(_U8), float(st.Z), _d(G))
     return G
+
+
+# ---------------------------------------------------------------------------
+# Moving image as the model image A (Sec. II-E, Eqs. 20, 21)
+# ---------------------------------------------------------------------------
+def joint_pdf_mas_a(geo: Geometry, F: np.ndarray, M: np.ndarray, c: np.ndarray):
+    """Eq. (3) with a from the warped moving image M(T(x)) and b from F."""
+    s = geo.c_struct()
+    R, nb = geo.n_regions(), geo.n_bins
+    p = np.zeros(R * nb * nb)
+    Z = ctypes.c_double(0.0)
+    F = np.ascontiguousarray(F, np.float64).ravel()
+    M = np.ascontiguousarray(M, np.float64).ravel()
+    c = np.ascontiguousarray(c, np.float64)
+    rc = lib().orc_joint_pdf_mas_a(ctypes.byref(s), _d(F), _d(M), _d(c), _d(p), ctypes.byref(Z))
+    if rc != 0:
+        raise RuntimeError(f"orc_joint_pdf_mas_a failed ({rc})")
+    return p.reshape(R, nb, nb), Z.value
+
+
+def value_mas_a(geo: Geometry, F, M, c) -> Stats:
+    """SRWCR (Eq. 9) with the warped moving image as A and F as B."""
+    p, Z = joint_pdf_mas_a(geo, F, M, c)
+    return stats_from_pdf(p, Z)
+
+
+def gradient_mas_a(geo: Geometry, F, M, c, st: Stats) -> np.ndarray:
+    """Eqs. (15)-(17) with Eq. (21): dD/dc when the moving image is A."""
+    s = geo.c_struct()
+    F = np.ascontiguousarray(F, np.float64).ravel()
+    M = np.ascontiguousarray(M, np.float64).ravel()
+    c = np.ascontiguousarray(c, np.float64)
+    g = np.zeros(c.size)
+    mu_ra = np.ascontiguousarray(st.mu_ra, np.float64).ravel()
+    rc = lib().orc_gradient_mas_a(ctypes.byref(s), _d(F), _d(M), _d(c), _d(st.mu_r),
+                                  _d(st.var_r), _d(st.cr), _d(mu_ra),
+                                  st.valid.ctypes.data_as(_U8), float(st.Z), _d(g))
+    if rc != 0:
+        raise RuntimeError(f"orc_gradient_mas_a failed ({rc})")
+    return g.reshape(c.shape)
 
 
 def value_and_grad(geo: Geometry, A, M, c):

@@ -576,3 +576,123 @@ int orc_gradient_at(const orc_problem* P, const double* A, const double* M, cons
   }
   return ORC_OK;
 }
+
+
+/* ---------------------------------------------------------------------- */
+/* Moving image as the model image A (Sec. II-E, Eqs. 20, 21): the warped  */
+/* moving image M(T(x)) is binned by Eq. (5) and the fixed image F is the  */
+/* estimated image B.  Joint PDF p[(r*nb + a)*nb + b], a from M(T(x)), b   */
+/* from F(x); orc_srwcr_from_pdf then gives D and the regional statistics. */
+/* ---------------------------------------------------------------------- */
+int orc_joint_pdf_mas_a(const orc_problem* P, const double* F, const double* M, const double* c,
+                        double* p, double* Z_out) {
+  const int nb = P->nbins;
+  const int64_t R = orc_n_regions(P);
+  int64_t nx = P->n[0], ny = P->n[1], nz = P->n[2];
+  memset(p, 0, sizeof(double) * (size_t)(R * nb * nb));
+  int64_t bins[64];
+  double w[64], gM[3];
+  for (int64_t z = 0; z < nz; ++z)
+    for (int64_t y = 0; y < ny; ++y)
+      for (int64_t x = 0; x < nx; ++x) {
+        int64_t xv[3] = {x, y, z}, idx = (z * ny + y) * nx + x;
+        double Av;
+        warp_voxel(P, M, c, xv, &Av, gM);
+        int ia[4], ib[4], na = 0, nbb = 0;
+        double ha[4], hb[4];
+        for (int a = 0; a < nb && na < 4; ++a) {
+          double h = orc_parzen((double)a - Av);
+          if (h != 0.0) { ia[na] = a; ha[na++] = h; }
+        }
+        for (int b = 0; b < nb && nbb < 4; ++b) {
+          double h = orc_parzen((double)b - F[idx]);
+          if (h != 0.0) { ib[nbb] = b; hb[nbb++] = h; }
+        }
+        int nw = spatial_weights(P, xv, bins, w);
+        for (int s = 0; s < nw; ++s) {
+          if (w[s] == 0.0) continue;
+          double* pr = p + bins[s] * nb * nb;
+          for (int i = 0; i < na; ++i)
+            for (int j = 0; j < nbb; ++j) pr[ia[i] * nb + ib[j]] += w[s] * ha[i] * hb[j];
+        }
+      }
+  double Z = 0.0;
+  for (int64_t i = 0; i < R * nb * nb; ++i) Z += p[i];
+  if (Z_out) *Z_out = Z;
+  if (!(Z > 0.0)) return ORC_EINVAL;
+  for (int64_t i = 0; i < R * nb * nb; ++i) p[i] /= Z;
+  return ORC_OK;
+}
+
+/* Eq. (21): dD/dM(T(x)) at one voxel when M is A:
+ *   (1/Z) sum_r sum_a sum_b (2b - mu_r(a)) mu_r(a) / sigma_r^2
+ *         * w(r, x) h(b - F(x)) dh/dkappa at kappa = a - A(x),
+ * with the in-cell derivative convention of orc_parzen_dkappa (A in the
+ * role of its second argument) and mu_r(a) = 0 for an empty bin. */
+static double dD_dA(const orc_problem* P, const orc_tables* T, const int64_t xv[3], double Ax,
+                    double Fx) {
+  const int nb = P->nbins;
+  int64_t bins[64];
+  double w[64];
+  int nw = spatial_weights(P, xv, bins, w);
+  int ia[4], ib[4], nda = 0, nbb = 0;
+  double da[4], hb[4];
+  for (int a = 0; a < nb && nda < 4; ++a) {
+    double d = orc_parzen_dkappa((double)a, Ax, nb - 1);
+    if (d != 0.0) { ia[nda] = a; da[nda++] = d; }
+  }
+  for (int b = 0; b < nb && nbb < 4; ++b) {
+    double h = orc_parzen((double)b - Fx);
+    if (h != 0.0) { ib[nbb] = b; hb[nbb++] = h; }
+  }
+  double acc = 0.0;
+  for (int s = 0; s < nw; ++s) {
+    int64_t r = bins[s];
+    if (w[s] == 0.0 || !T->valid[r]) continue;
+    double var = T->var_r[r];
+    for (int i = 0; i < nda; ++i) {
+      double mua = T->mu_ra[r * nb + ia[i]];
+      for (int j = 0; j < nbb; ++j)
+        acc += (2.0 * (double)ib[j] - mua) * mua / var * w[s] * hb[j] * da[i];
+    }
+  }
+  return acc / T->Z;
+}
+
+/* Eqs. (15)-(17) with Eq. (21): dD/dc when M is A.  g has the layout of c. */
+int orc_gradient_mas_a(const orc_problem* P, const double* F, const double* M, const double* c,
+                       const double* mu_r, const double* var_r, const double* cr,
+                       const double* mu_ra, const unsigned char* valid, double Z, double* g) {
+  orc_tables T = {mu_r, var_r, cr, mu_ra, valid, Z};
+  int64_t nx = P->n[0], ny = P->n[1], nz = P->n[2];
+  int64_t nfx = ffd_nodes(P, 0), nfy = ffd_nodes(P, 1), nfz = ffd_nodes(P, 2);
+  int64_t ncoef = nfx * nfy * nfz;
+  memset(g, 0, sizeof(double) * (size_t)(P->ndim * ncoef));
+  for (int64_t z = 0; z < nz; ++z)
+    for (int64_t y = 0; y < ny; ++y)
+      for (int64_t x = 0; x < nx; ++x) {
+        int64_t xv[3] = {x, y, z}, idx = (z * ny + y) * nx + x;
+        double Av, gM[3];
+        warp_voxel(P, M, c, xv, &Av, gM);
+        double G = dD_dA(P, &T, xv, Av, F[idx]);
+        if (G == 0.0) continue;
+        int64_t p[3];
+        double wax[3][4];
+        int nax[3];
+        for (int d = 0; d < 3; ++d) {
+          if (d >= P->ndim) { p[d] = 0; nax[d] = 1; wax[d][0] = 1.0; continue; }
+          p[d] = xv[d] / P->ffd_sp[d];
+          double eta = (double)(xv[d] % P->ffd_sp[d]) / (double)P->ffd_sp[d];
+          nax[d] = 4;
+          for (int l = 0; l < 4; ++l) wax[d][l] = orc_bspline(l, eta);
+        }
+        for (int nn = 0; nn < nax[2]; ++nn)
+          for (int m = 0; m < nax[1]; ++m)
+            for (int l = 0; l < nax[0]; ++l) {
+              int64_t node = ((p[2] + nn) * nfy + (p[1] + m)) * nfx + (p[0] + l);
+              double jac = wax[0][l] * wax[1][m] * wax[2][nn]; /* Eq. (17) */
+              for (int k = 0; k < P->ndim; ++k) g[k * ncoef + node] += G * gM[k] * jac;
+            }
+      }
+  return ORC_OK;
+}
