@@ -51,6 +51,13 @@ typedef enum {
 
 enum { SRWCR_STORAGE_F32 = 0, SRWCR_STORAGE_BF16 = 1 };
 
+/* Which image is binned (Sec. II-E).  M as B (default): the fixed image F is
+ * the model image A and the warped moving image the estimated image B
+ * (gradient Eq. 19).  M as A: the warped moving image is A, binned by
+ * Eq. (5), and F is B (gradient Eq. 21); runs on the general per-voxel
+ * kernels. */
+enum { SRWCR_ROLE_M_AS_B = 0, SRWCR_ROLE_M_AS_A = 1 };
+
 /* Problem configuration (Sec. II-F gives the paper's defaults: delta = 5,
  * L_eps = 31, i.e. 32 intensity bins). */
 typedef struct {
@@ -68,6 +75,7 @@ typedef struct {
                              tile's fixed-image bins per pass over its rows
                              (a tile using more takes several passes); 0 = as
                              many as fit in shared memory */
+  int role;               /* SRWCR_ROLE_M_AS_B (0) | SRWCR_ROLE_M_AS_A */
 } srwcr_config;
 
 /* Geometry of one pyramid level. */

@@ -20,6 +20,7 @@ _LIB_PATH = os.path.join(_HERE, "libsrwcr.so")
 _lib = None
 
 STORAGE = {"f32": 0, "bf16": 1}
+ROLE = {"mas_b": 0, "mas_a": 1}   # which image is binned (Sec. II-E)
 STATUS = {0: "SRWCR_OK", 1: "SRWCR_EINVAL", 2: "SRWCR_ENOMEM", 3: "SRWCR_ECUDA",
           4: "SRWCR_ENUMERIC", 5: "SRWCR_ELINESEARCH", 6: "SRWCR_ETIMEOUT",
           7: "SRWCR_ENOTCONVERGED"}
@@ -47,7 +48,7 @@ class Config(ctypes.Structure):
                 ("ffd_spacing", ctypes.c_int * 3), ("sbin_intervals", ctypes.c_int * 3),
                 ("n_intensity_bins", ctypes.c_int), ("storage", ctypes.c_int),
                 ("pyramid_levels", ctypes.c_int), ("tile", ctypes.c_int * 3),
-                ("bins_per_pass", ctypes.c_int)]
+                ("bins_per_pass", ctypes.c_int), ("role", ctypes.c_int)]
 
 
 class LevelDesc(ctypes.Structure):
@@ -169,7 +170,8 @@ class SRWCR:
     def __init__(self, fixed, moving, ffd_spacing: Sequence[int],
                  sbin_intervals: Sequence[int] = (0, 0, 0), n_bins: int = 32,
                  storage: str = "f32", pyramid_levels: int = 1,
-                 tile: Optional[Sequence[int]] = None, stream=None, bins_per_pass: int = 0):
+                 tile: Optional[Sequence[int]] = None, stream=None, bins_per_pass: int = 0,
+                 role: str = "mas_b"):
         import torch
         self._torch = torch
         lib = load()
@@ -189,6 +191,7 @@ class SRWCR:
         cfg.storage = STORAGE[storage]
         cfg.pyramid_levels = int(pyramid_levels)
         cfg.bins_per_pass = int(bins_per_pass)
+        cfg.role = ROLE[role]
         self.cfg = cfg
         self.ndim = ndim
         self.storage = storage

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsrwcr.so")
 SOURCES = ["srwcr.cu"]
-DEPS = SOURCES + ["kernels.cuh", "kernels_rows.cuh", "kernels_batch.cuh", "device_math.cuh",
+DEPS = SOURCES + ["kernels.cuh", "kernels_rows.cuh", "kernels_batch.cuh", "kernels_mas_a.cuh", "device_math.cuh",
                   "lbfgs.cuh", "batch.cuh", "bending.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -20,6 +20,7 @@
 
 #include "srwcr.h"
 #include "kernels.cuh"
+#include "kernels_mas_a.cuh"
 #include "kernels_rows.cuh"
 
 using namespace srwcr;
@@ -79,13 +80,15 @@ struct Level {
   double* nz_inv_p = nullptr;         // [nnz] 1 / P
   float* U = nullptr;                 // [R]
   float* V = nullptr;                 // [R]
-  float* X = nullptr;                 // [R][nbins]
+  float* X = nullptr;                 // [R][nbins] (M as A: mu_r(a) / sigma_r^2)
+  float* Y2 = nullptr;                // M as A: [R][nbins] mu_r(a)^2 / sigma_r^2
   double* Dr = nullptr;               // [R] share of D
   double* stats = nullptr;            // [R][4]
   double* D = nullptr;                // device scalar
   int* ndeg = nullptr;                // device scalar
   double Z = 0.0;
   float s1 = 1.f, s2 = 1.f;           // fixed-point scales of S1, S2
+  float s0 = 1.f;                     // M as A: fixed-point scale of P
   size_t smem_acc = 0, smem_adj = 0;
   bool tables = false;
   // Row-parallel fast path (32-wide tiles): static per-row lane permutation
@@ -169,12 +172,13 @@ void set_tile(Geo& g, int ndim, int tx, int ty, int tz) {
   }
 }
 
-srwcr_status choose_tile(Geo& g, int ndim, const int* req) {
+// nch: histogram channels of the general value kernel (2, or 3 with M as A).
+srwcr_status choose_tile(Geo& g, int ndim, const int* req, int nch) {
   if (req[0] > 0) {
     set_tile(g, ndim, req[0], std::max(1, req[1]), std::max(1, req[2]));
-    if (acc_smem(g, 2) > 220 * 1024)
+    if (acc_smem(g, nch) > 220 * 1024)
       return fail(SRWCR_EINVAL, "requested tile needs %zu bytes of shared memory",
-                  acc_smem(g, 2));
+                  acc_smem(g, nch));
     return SRWCR_OK;
   }
   static const int cand3[][3] = {{32, 32, 8}, {32, 16, 8}, {32, 8, 8}, {32, 8, 4}, {32, 4, 4}, {32, 4, 2},
@@ -185,11 +189,11 @@ srwcr_status choose_tile(Geo& g, int ndim, const int* req) {
   const int nc = ndim == 3 ? 11 : 8;
   for (int i = 0; i < nc; ++i) {
     set_tile(g, ndim, cand[i][0], cand[i][1], cand[i][2]);
-    if (acc_smem(g, 2) <= kSmemBudget) return SRWCR_OK;
+    if (acc_smem(g, nch) <= kSmemBudget) return SRWCR_OK;
   }
   for (int i = 0; i < nc; ++i) {
     set_tile(g, ndim, cand[i][0], cand[i][1], cand[i][2]);
-    if (acc_smem(g, 2) <= 220 * 1024) return SRWCR_OK;
+    if (acc_smem(g, nch) <= 220 * 1024) return SRWCR_OK;
   }
   return fail(SRWCR_EINVAL, "no voxel tile fits the shared-memory histogram (nbins=%d)",
               g.nbins);
@@ -222,7 +226,7 @@ srwcr_status make_geo(const srwcr_config& cfg, const int dims[3], Geo& g) {
   g.R = (long long)g.nsb[0] * g.nsb[1] * g.nsb[2];
   g.nabin = g.nbins;
   g.cbin = g.nbins;
-  return choose_tile(g, nd, cfg.tile);
+  return choose_tile(g, nd, cfg.tile, cfg.role == SRWCR_ROLE_M_AS_A ? 3 : 2);
 }
 
 // Fixed-point scales: every per-(r,a) total stays below 2^62.  A bin's
@@ -297,6 +301,16 @@ srwcr_status launch_accumulate(srwcr_ctx* ctx, Level& lv, const float* c, bool s
     CKL();
     return SRWCR_OK;
   }
+  if (!stat && ctx->cfg.role == SRWCR_ROLE_M_AS_A) {
+    if (ctx->cfg.ndim == 3)
+      k_accumulate_mas_a<3, T><<<nblk, kBlock, lv.smem_acc, ctx->stream>>>(gg, A, M, c, lv.S, lv.s0,
+                                                                            lv.s1, lv.s2);
+    else
+      k_accumulate_mas_a<2, T><<<nblk, kBlock, lv.smem_acc, ctx->stream>>>(gg, A, M, c, lv.S, lv.s0,
+                                                                            lv.s1, lv.s2);
+    CKL();
+    return SRWCR_OK;
+  }
   const size_t sm = stat ? acc_smem(gg, 1) : lv.smem_acc;
   if (ctx->cfg.ndim == 3) {
     if (stat) k_accumulate<3, T, true><<<nblk, kBlock, sm, ctx->stream>>>(gg, A, M, c, lv.S, s0, s1);
@@ -329,6 +343,16 @@ srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const flo
     CKL();
     return SRWCR_OK;
   }
+  if (ctx->cfg.role == SRWCR_ROLE_M_AS_A) {
+    if (ctx->cfg.ndim == 3)
+      k_adjoint_mas_a<3, T><<<nblk, kBlock, lv.smem_adj, ctx->stream>>>(
+          lv.g, (const T*)lv.A, (const T*)lv.M, c, lv.X, lv.Y2, gD, invZ, g);
+    else
+      k_adjoint_mas_a<2, T><<<nblk, kBlock, lv.smem_adj, ctx->stream>>>(
+          lv.g, (const T*)lv.A, (const T*)lv.M, c, lv.X, lv.Y2, gD, invZ, g);
+    CKL();
+    return SRWCR_OK;
+  }
   if (ctx->cfg.ndim == 3)
     k_adjoint<3, T><<<nblk, kBlock, lv.smem_adj, ctx->stream>>>(
         lv.g, (const T*)lv.A, (const T*)lv.M, c, lv.U, lv.V, lv.X, gD, invZ, g);
@@ -348,6 +372,10 @@ srwcr_status set_smem_limits() {
   CK(cudaFuncSetAttribute(k_accumulate<2, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_mas_a<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_mas_a<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_mas_a<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_mas_a<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
@@ -399,7 +427,8 @@ RegionStatic region_static(const Level& lv) {
 // (a) + (b): value into lv.D, tables into lv.U/V/X.  keep_warp: also store
 // the per-voxel warp for a following run_grad(..., true) at the same c.
 srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c, bool keep_warp) {
-  const size_t sbytes = (size_t)lv.g.R * lv.g.nbins * 2 * sizeof(unsigned long long);
+  const bool mas_a = ctx->cfg.role == SRWCR_ROLE_M_AS_A;
+  const size_t sbytes = (size_t)lv.g.R * lv.g.nbins * (mas_a ? 3 : 2) * sizeof(unsigned long long);
   CK(cudaMemsetAsync(lv.S, 0, sbytes, ctx->stream));
   cudaEvent_t ev = prof_begin(ctx);
   srwcr_status st =
@@ -410,9 +439,14 @@ srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c, bool keep_warp
   const long long warps = lv.g.R;
   const int fblk = (int)((warps * 32 + kBlock - 1) / kBlock);
   ev = prof_begin(ctx);
-  k_finalize_sparse<<<fblk, kBlock, 0, ctx->stream>>>(lv.g.R, lv.g.nbins, region_static(lv), lv.S,
-                                                      1.0 / lv.s1, 1.0 / lv.s2, 1.0 / lv.Z, lv.U,
-                                                      lv.V, lv.X, lv.Dr, lv.stats);
+  if (mas_a)
+    k_finalize_mas_a<<<fblk, kBlock, 0, ctx->stream>>>(lv.g, lv.S, 1.0 / lv.s0, 1.0 / lv.s1,
+                                                       1.0 / lv.s2, 1.0 / lv.Z, lv.X, lv.Y2, lv.Dr,
+                                                       lv.stats);
+  else
+    k_finalize_sparse<<<fblk, kBlock, 0, ctx->stream>>>(lv.g.R, lv.g.nbins, region_static(lv), lv.S,
+                                                        1.0 / lv.s1, 1.0 / lv.s2, 1.0 / lv.Z, lv.U,
+                                                        lv.V, lv.X, lv.Dr, lv.stats);
   CKL();
   k_reduce_D<<<1, 1024, 0, ctx->stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg);
   CKL();
@@ -461,7 +495,7 @@ srwcr_status finish_sync(srwcr_ctx* ctx, Level& lv, double* D_host) {
 void free_level(Level& lv) {
   void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg, lv.perm,
                   lv.binmask, lv.Wr, lv.nz_ptr, lv.nz_bin, lv.nz_inv_p, lv.bg, lv.uvxz,
-                  lv.ubins};
+                  lv.ubins, lv.Y2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   lv = Level();
@@ -627,16 +661,18 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     const Geo& g = lv.g;
     CK(cudaMalloc(&lv.A, esz * g.nvox));
     CK(cudaMalloc(&lv.M, esz * g.nvox));
-    CK(cudaMalloc((void**)&lv.S, sizeof(unsigned long long) * g.R * g.nbins * 2));
+    const int nch = cfg->role == SRWCR_ROLE_M_AS_A ? 3 : 2;
+    CK(cudaMalloc((void**)&lv.S, sizeof(unsigned long long) * g.R * g.nbins * nch));
     CK(cudaMalloc((void**)&lv.P, sizeof(double) * g.R * g.nbins));
     CK(cudaMalloc((void**)&lv.U, sizeof(float) * g.R));
     CK(cudaMalloc((void**)&lv.V, sizeof(float) * g.R));
     CK(cudaMalloc((void**)&lv.X, sizeof(float) * g.R * g.nbins));
+    if (nch == 3) CK(cudaMalloc((void**)&lv.Y2, sizeof(float) * g.R * g.nbins));
     CK(cudaMalloc((void**)&lv.Dr, sizeof(double) * g.R));
     CK(cudaMalloc((void**)&lv.stats, sizeof(double) * g.R * 4));
     CK(cudaMalloc((void**)&lv.D, sizeof(double)));
     CK(cudaMalloc((void**)&lv.ndeg, sizeof(int)));
-    lv.smem_acc = acc_smem(g, 2);
+    lv.smem_acc = acc_smem(g, nch);
     lv.smem_adj = sizeof(float) * cfg->ndim * g.hf[0] * g.hf[1] * g.hf[2];
     lv.gv = g;
   }
@@ -700,7 +736,10 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
   // keeps for the adjoint (16 bytes per voxel).
   for (int l = 0; l < ctx->nlev; ++l) {
     Level& lv = ctx->lev[l];
-    RET_IF(select_rows_path(ctx, lv));
+    // The row kernels sort each row's voxels by the static fixed-image bin;
+    // with the moving image as A the binned image moves, so the general
+    // per-voxel kernels run.
+    if (cfg->role == SRWCR_ROLE_M_AS_B) RET_IF(select_rows_path(ctx, lv));
     if (lv.rows) {
       CK(cudaMalloc((void**)&lv.bg, sizeof(float4) * lv.g.nvox));
       CK(cudaMalloc((void**)&lv.uvxz, sizeof(float) * zcontract_len(lv.g)));
@@ -713,6 +752,7 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     double sP, s1, s2;
     fixed_scales(lv.g, cfg->ndim, &sP, &s1, &s2);
     lv.s1 = (float)s1;
+    lv.s0 = (float)sP;
     lv.s2 = (float)s2;
     CK(cudaMemsetAsync(lv.S, 0, sizeof(unsigned long long) * lv.g.R * lv.g.nbins, ctx->stream));
     RET_IF(is_bf16(ctx) ? launch_accumulate<__nv_bfloat16>(ctx, lv, nullptr, true, (float)sP, 0.f)
@@ -787,6 +827,8 @@ srwcr_status srwcr_create(const srwcr_config* cfg, const float* fixed, const flo
   if (cfg->tile[0] < 0 || cfg->tile[1] < 0 || cfg->tile[2] < 0)
     return fail(SRWCR_EINVAL, "negative tile size");
   if (cfg->bins_per_pass < 0) return fail(SRWCR_EINVAL, "negative bins_per_pass");
+  if (cfg->role != SRWCR_ROLE_M_AS_B && cfg->role != SRWCR_ROLE_M_AS_A)
+    return fail(SRWCR_EINVAL, "unknown role");
   srwcr_ctx* ctx = new (std::nothrow) srwcr_ctx();
   if (!ctx) return fail(SRWCR_ENOMEM, "host allocation failed");
   srwcr_status st = create_impl(cfg, fixed, moving, images_on_device, stream, ctx);
@@ -1014,6 +1056,8 @@ extern "C" srwcr_status srwcr_value_noalloc(const srwcr_config* cfg, const float
                                             double* D_dev, void* stream) {
   if (!cfg || !fixed_dev || !moving_dev || !c_dev || !D_dev)
     return fail(SRWCR_EINVAL, "null argument");
+  if (cfg->role != SRWCR_ROLE_M_AS_B)
+    return fail(SRWCR_EINVAL, "the allocation-free value takes the moving image as B only");
   if (cfg->ndim != 2 && cfg->ndim != 3) return fail(SRWCR_EINVAL, "ndim must be 2 or 3");
   if (cfg->n_intensity_bins < 2 || cfg->n_intensity_bins > 256)
     return fail(SRWCR_EINVAL, "n_intensity_bins must be in [2, 256]");
@@ -1026,6 +1070,8 @@ extern "C" srwcr_status srwcr_value_noalloc(const srwcr_config* cfg, const float
   if (cfg->tile[0] < 0 || cfg->tile[1] < 0 || cfg->tile[2] < 0)
     return fail(SRWCR_EINVAL, "negative tile size");
   if (cfg->bins_per_pass < 0) return fail(SRWCR_EINVAL, "negative bins_per_pass");
+  if (cfg->role != SRWCR_ROLE_M_AS_B && cfg->role != SRWCR_ROLE_M_AS_A)
+    return fail(SRWCR_EINVAL, "unknown role");
   cudaStream_t st = (cudaStream_t)stream;
 
   // Device address of the scratch array, looked up once per device.
@@ -1172,6 +1218,11 @@ extern "C" srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c
   if (!c_dev) return fail(SRWCR_EINVAL, "c_dev is NULL");
   if (reps < 1) reps = 3;
   Level& lv = ctx->lev[level];
+  if (ctx->cfg.role == SRWCR_ROLE_M_AS_A) {
+    // Only the row-parallel tiles are tuned; this role runs the general kernels.
+    for (int d = 0; d < 3 && tile_out; ++d) tile_out[d] = lv.g.tile[d];
+    return SRWCR_OK;
+  }
   const std::string key = tune_key(ctx, lv.gv);
   std::array<int, 3> best{0, 0, 0};
   if (tune_lookup(key, &best)) {

@@ -27,7 +27,7 @@ from scipy.interpolate import BSpline
 __all__ = [
     "Problem", "PairSpec", "CONFIGS", "problem", "make_pair", "coefficients",
     "n_ffd_nodes", "random_ffd_warp", "batch_specs", "downsample2", "grid_pair",
-    "displacement_field",
+    "displacement_field", "inverse_displacement",
 ]
 
 
@@ -421,3 +421,20 @@ def grid_pair(n: int = 128, seed: int = 0, amplitude: float = 15.0, true_spacing
     xr, yr = xx / n - 0.5, yy / n - 0.5
     W = W * (1.0 + bias * xr + 0.5 * bias * yr * yr)
     return GridPair(O.astype(np.float32), W.astype(np.float32), coef, (true_spacing,) * 3)
+
+
+def inverse_displacement(v: np.ndarray, iterations: int = 30) -> np.ndarray:
+    """Displacement w of the inverse map of x -> x + v(x) on the voxel grid
+    (x + w(x) + v(x + w(x)) = x), by the fixed-point iteration
+    w <- -v(x + w) with trilinear interpolation of v (converges for smooth,
+    moderate v)."""
+    v = np.asarray(v, np.float64)
+    d = v.shape[0]
+    grids = np.meshgrid(*[np.arange(n) for n in v.shape[1:]], indexing="ij")  # z, y, x order
+    w = -v.copy()
+    for _ in range(iterations):
+        # coordinates in (z, y, x) order; component k of w displaces axis k (x first)
+        coords = np.stack([grids[a] + w[d - 1 - a] for a in range(d)])
+        w = -np.stack([ndimage.map_coordinates(v[k], coords, order=1, mode="nearest")
+                       for k in range(d)])
+    return w
