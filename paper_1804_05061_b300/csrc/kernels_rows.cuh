@@ -257,9 +257,9 @@ __host__ __device__ inline int hist_yz_stride(const Geo& g) {
 }
 
 __host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int nxb) {
-  const size_t nyz = (size_t)g.hb[1] * g.hb[2];
+  const size_t npy = (size_t)g.tile[2] * g.hb[1];          // (z-plane, y-bin) rows
   const size_t nv = (size_t)nxb * 4;
-  size_t b = 3 * nyz * hist_yz_stride(g) * sizeof(unsigned);  // hist words (3 per entry)
+  size_t b = 3 * npy * hist_yz_stride(g) * sizeof(unsigned);  // plane words (3 per entry)
   b += sizeof(float) * kAccWarps * 32 * nv;                 // segS
   b += sizeof(int) * kAccWarps * 32;                        // segA
   b += sizeof(int) * kAccWarps * 64 * 2;                    // bin list
@@ -309,20 +309,24 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   const int nb = g.nbins;
   const float L = (float)(nb - 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // Split fixed-point histogram: three 32-bit words per [y/z bin][bin]
-  // [moment][x-bin] holding bits 0-19, 20-39 and 40-63 of each update (an
-  // FP32 update has 24 significant bits, so it touches at most two of them).
-  // Every entry receives at most one update per row (<= 256 per CTA) of value
-  // < 2^56, so no word overflows; the flush recombines the three exactly.
+  // Per-plane fixed-point accumulators H[z-plane][y bin][bin][moment][x-bin]:
+  // a row's sums are weighted by its y B-spline only (4 updates per item);
+  // the z weights are applied once per plane at the flush.  Each entry is
+  // held as three 32-bit words (bits 0-19, 20-39 and 40-63 of each update;
+  // an FP32 update has 24 significant bits, so it touches at most two) and
+  // receives at most one update per row of its plane (<= 256) of value
+  // < 2^56, so no word overflows.  The flush recombines a plane's words
+  // exactly, combines the planes of one z cell in FP32 in plane order with
+  // their z weights and adds the results to the global accumulators.
   // The bin axis holds g.cbin of the tile's compacted bins; a tile that uses
   // more takes several passes over its rows, each folding one chunk of bins
   // and skipping rows with no voxel in that chunk.
   const int S = hist_yz_stride(g);
-  const int NYZ = g.hb[1] * g.hb[2];
+  const int NPY = g.tile[2] * g.hb[1];
   unsigned* hlo = reinterpret_cast<unsigned*>(smem_u64);
-  unsigned* hmid = hlo + (size_t)NYZ * S;
-  unsigned* hhi = hmid + (size_t)NYZ * S;
-  float* segS = reinterpret_cast<float*>(hhi + (size_t)NYZ * S);
+  unsigned* hmid = hlo + (size_t)NPY * S;
+  unsigned* hhi = hmid + (size_t)NPY * S;
+  float* segS = reinterpret_cast<float*>(hhi + (size_t)NPY * S);
   int* segA = reinterpret_cast<int*>(segS + kAccWarps * 32 * NV);
   int* binl = segA + kAccWarps * 32;          // [warp][64][2]: a, (s | slot<<8 | merge<<9)
   int* a2c = binl + kAccWarps * 64 * 2;       // fixed-image bin -> compact index (-1: unused)
@@ -367,7 +371,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   const int ft = lane & 7, fg = lane >> 3;
   for (int c0 = 0; c0 < cnt; c0 += cb) {
     const bool multi = cnt > cb;                // CTA-uniform
-    for (int i = threadIdx.x; i < 3 * NYZ * S; i += blockDim.x) hlo[i] = 0u;
+    for (int i = threadIdx.x; i < 3 * NPY * S; i += blockDim.x) hlo[i] = 0u;
     __syncthreads();
     for (int row = warp; row < nrows; row += kAccWarps) {
       const int yl = row % g.tile[1], zl = row / g.tile[1];
@@ -388,7 +392,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
                                 (unsigned)(a2c[key + 1] - c0) < (unsigned)cb);
         if (!__any_sync(0xffffffffu, in)) continue;
       }
-      const AxisEntry ye = yt[yl], ze = zt[zl];
+      const AxisEntry ye = yt[yl];
       row_cyz<DIM>(g, CZ, zl, ye, nxn, cyz, lane);
       __syncwarp();
       float m1 = 0.f, m2 = 0.f, h0 = 0.f, h1 = 0.f;
@@ -503,15 +507,10 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
         mybins[2 * q + 1] = sidx | (1 << 8);
       }
       __syncwarp();
-      // Fold: 8 (bin, moment, x-bin) items per pass, each lane adds its item to
-      // the 4 z bins of y bin fg (3-D; one z bin in 2-D).
-      float wk[NK];
-      int yzb[NK];
-  #pragma unroll
-      for (int m = 0; m < NK; ++m) {
-        wk[m] = ye.bs[fg] * ze.bs[m];
-        yzb[m] = ((ze.srel + m) * g.hb[1] + (ye.srel + fg)) * S;
-      }
+      // Fold: 8 (bin, moment, x-bin) items per pass, each lane adds its item
+      // to y bin fg of the row's z-plane.
+      const float wyf = ye.bs[fg];
+      const int prow = (zl * g.hb[1] + ye.srel + fg) * S;
       const int per_bin = 2 * NXB;
       for (int f = ft; f < nbin * per_bin; f += 8) {
         const int e = f / per_bin, r = f % per_bin;
@@ -522,46 +521,62 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
         const int sg = info & 0xff, slot = (info >> 8) & 1;
         float val = mysegS[seg_at<NV>(sg, 4 * b + 2 * slot + ch)];
         if (info & (1 << 9)) val += mysegS[seg_at<NV>(sg - 1, 4 * b + 2 + ch)];
-        if (val == 0.f) continue;
-        const float vs = val * (ch ? s2 : s1);
-        const int col = ((a2c[a] - c0) * 2 + ch) * g.hb[0] + b;
-  #pragma unroll
-        for (int m = 0; m < NK; ++m) {
-          const float u = vs * wk[m];
-          if (u == 0.f) continue;
-          // Exact split of u into 20-bit fields (power-of-two scalings, floors
-          // and fused subtractions of FP32 values are exact here).
-          const float hf = floorf(u * 0x1p-40f);
-          const float r1 = fmaf(hf, -0x1p40f, u);
-          const float mf = floorf(r1 * 0x1p-20f);
-          const unsigned lo = __float2uint_rn(fmaf(mf, -0x1p20f, r1));
-          const unsigned mid = (unsigned)mf, hi = (unsigned)hf;
-          const int at = yzb[m] + col;
-          if (lo) atomicAdd(hlo + at, lo);
-          if (mid) atomicAdd(hmid + at, mid);
-          if (hi) atomicAdd(hhi + at, hi);
-        }
+        const float u = val * (ch ? s2 : s1) * wyf;
+        if (u == 0.f) continue;
+        // Exact split of u into 20-bit fields (power-of-two scalings, floors
+        // and fused subtractions of FP32 values are exact here).
+        const float hf = floorf(u * 0x1p-40f);
+        const float r1 = fmaf(hf, -0x1p40f, u);
+        const float mf = floorf(r1 * 0x1p-20f);
+        const unsigned lo = __float2uint_rn(fmaf(mf, -0x1p20f, r1));
+        const unsigned mid = (unsigned)mf, hi = (unsigned)hf;
+        const int at = prow + ((a2c[a] - c0) * 2 + ch) * g.hb[0] + b;
+        if (lo) atomicAdd(hlo + at, lo);
+        if (mid) atomicAdd(hmid + at, mid);
+        if (hi) atomicAdd(hhi + at, hi);
       }
       __syncwarp();
     }
     __syncthreads();
+    // Flush: one entry per (first plane of a z cell, y bin, column); the
+    // planes of that cell are combined with their z weights, then the NK z
+    // bins are added to the global accumulators.
     const int wcols = 2 * cb * g.hb[0];
-    for (int i = threadIdx.x; i < NYZ * S; i += blockDim.x) {
-      const int yz = i / S, col = i % S;
+    for (int i = threadIdx.x; i < NPY * S; i += blockDim.x) {
+      const int pz = i / S, col = i % S;
       if (col >= wcols) continue;
-      const unsigned long long val =
-          ((unsigned long long)hhi[i] << 40) + ((unsigned long long)hmid[i] << 20) + hlo[i];
-      if (!val) continue;
+      const int zl = pz / g.hb[1], l1 = pz - zl * g.hb[1];
+      const int cz = zt[zl].srel;
+      if (zl > 0 && zt[zl - 1].srel == cz) continue;
       const int b = col % g.hb[0], ach = col / g.hb[0];
       if (c0 + (ach >> 1) >= cnt) continue;
+      float u[NK];
+#pragma unroll
+      for (int m = 0; m < NK; ++m) u[m] = 0.f;
+      bool any = false;
+      for (int pl = zl; pl < g.tile[2] && zt[pl].srel == cz; ++pl) {
+        const int j = (pl * g.hb[1] + l1) * S + col;
+        const unsigned long long h =
+            ((unsigned long long)hhi[j] << 40) + ((unsigned long long)hmid[j] << 20) + hlo[j];
+        if (!h) continue;
+        any = true;
+        const float hv = __ull2float_rn(h);
+#pragma unroll
+        for (int m = 0; m < NK; ++m) u[m] = fmaf(zt[pl].bs[m], hv, u[m]);
+      }
+      if (!any) continue;
       const int a = c2a[c0 + (ach >> 1)], ch = ach & 1;
-      const int l1 = yz % g.hb[1], l2 = yz / g.hb[1];
-      const int r0 = TO.cb[0] + b, r1 = TO.cb[1] + l1, r2 = TO.cb[2] + l2;
-      if (r0 >= g.nsb[0] || r1 >= g.nsb[1] || r2 >= g.nsb[2]) continue;
-      const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
-      atomicAdd(acc + ((size_t)r * nb + a) * 2 + ch, val);
+      const int r0 = TO.cb[0] + b, r1 = TO.cb[1] + l1;
+      if (r0 >= g.nsb[0] || r1 >= g.nsb[1]) continue;
+#pragma unroll
+      for (int m = 0; m < NK; ++m) {
+        const int r2 = TO.cb[2] + cz + m;
+        if (u[m] == 0.f || r2 >= g.nsb[2]) continue;
+        const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
+        atomicAdd(acc + ((size_t)r * nb + a) * 2 + ch, __float2ull_rn(u[m]));
+      }
     }
-    __syncthreads();                            // the next pass clears the histogram
+    __syncthreads();                            // the next pass clears the accumulators
   }
 }
 

@@ -172,16 +172,17 @@ def test_autotune_keeps_row_path_value_and_gradient(tmp_path, monkeypatch):
     tile = e.autotune(c, reps=2)
     assert tile[0] == 32 and e.levels[0].kernel_path == 1 and tuple(e.levels[0].tile) == tile
     D1, g1 = e.value_and_grad(c)
-    # Rows stay 32 voxels wide and the statistics are summed in fixed point,
-    # so the value does not depend on the tile's y/z extent.
-    assert D1 == D0
+    # Rows stay 32 voxels wide and the statistics are summed in fixed point;
+    # only the once-per-plane FP32 combination of the z weights depends on
+    # the tile's z extent.
+    assert abs(D1 - D0) <= 1e-6 * D0
     assert torch.allclose(g1, g0, rtol=1e-5, atol=1e-5 * float(g0.abs().max()))
     lines = cache.read_text().split("\n")
     assert any(l.endswith(" %d %d %d" % tile) for l in lines)
     # A second engine of the same problem takes the cached choice.
     e2 = engine(prob, f, m)
     assert e2.autotune(c, reps=2) == tile
-    assert e2.value(c) == D0
+    assert e2.value(c) == D1                    # same tile: the same value
 
 
 def test_three_level_pyramid_registration_on_ct_256():

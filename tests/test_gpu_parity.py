@@ -78,8 +78,10 @@ def test_value_gradient_and_regions_match_oracle(small_cases, name):
 @pytest.mark.parametrize("name", ["ct_128_bins", "ellipse_2d_ragged", "pet_labels"])
 def test_value_in_several_bin_passes_equals_one_pass(small_cases, name):
     # A tile whose fixed-image bins exceed bins_per_pass takes several passes
-    # over its rows; every (region, bin) entry still receives the same FP32
-    # row sums, added in fixed point, so D is bit-identical.
+    # over its rows; every (region, bin) entry receives the same row sums.
+    # With the same tile the value is bit-identical; a different tile (the
+    # smaller histogram may allow a taller one) changes only the FP32
+    # combination of the z-plane sums.
     prob, f, m, c = small_cases[name]
     e1 = engine_for(prob, f, m)
     e8 = engine_for(prob, f, m, bins_per_pass=8)
@@ -87,11 +89,14 @@ def test_value_in_several_bin_passes_equals_one_pass(small_cases, name):
     ct = torch.from_numpy(c).cuda()
     D1, g1 = e1.value_and_grad(ct)
     D8, g8 = e8.value_and_grad(ct)
-    assert D8 == D1
-    assert torch.allclose(g8, g1, rtol=1e-5, atol=1e-5 * float(g1.abs().max()))
     s1, _ = e1.region_stats()
     s8, _ = e8.region_stats()
-    assert np.array_equal(s1, s8)
+    if e1.levels[0].tile == e8.levels[0].tile:
+        assert D8 == D1 and np.array_equal(s1, s8)
+    assert abs(D8 - D1) <= 1e-6 * D1
+    assert torch.allclose(g8, g1, rtol=1e-5, atol=1e-5 * float(g1.abs().max()))
+    e8b = engine_for(prob, f, m, bins_per_pass=8, tile=e1.levels[0].tile)
+    assert e8b.value(ct) == D1
     st, _, _, _, _ = oracle_eval(prob, f, m, c, grad=False)
     assert abs(D8 - st.D) <= D_RTOL * abs(st.D)
 
