@@ -599,7 +599,7 @@ __device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
 
 // Bytes of the adjoint's shared memory (must match the carve-up below).
 __host__ __device__ inline size_t adj_rows_smem_bytes(const Geo& g, int dim, int nxb) {
-  const size_t hf = (size_t)g.hf[0] * g.hf[1] * g.hf[2];
+  const size_t hf = (size_t)g.hf[0] * g.hf[1] * g.tile[2];         // per-plane nodes
   const size_t p01 = (size_t)g.hb[0] * g.hb[1];
   size_t b = sizeof(float) * dim * hf;                               // gt
   b += sizeof(float) * g.tile[2] * p01 * (2 + g.nbins);              // UZ, VZ, XZ
@@ -629,9 +629,11 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
   const int nb = g.nbins;
   const float L = (float)(nb - 1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nodes_tile = g.hf[0] * g.hf[1] * g.hf[2];
+  // Control-point accumulators per z-plane of the tile: gt[k][zl][m][l] over
+  // the tile's y/x nodes; the z-node weights are applied once per plane at
+  // the flush.
+  const int nodes_tile = g.hf[0] * g.hf[1] * g.tile[2];
   const int p01 = g.hb[0] * g.hb[1];
-  constexpr int NJK = DIM == 3 ? 16 : 4;
   float* gt = smem_f32;
   float* UZ = gt + DIM * nodes_tile;                 // [TZ][hb1][hb0]
   float* VZ = UZ + g.tile[2] * p01;
@@ -707,7 +709,7 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
     const int yl = row % g.tile[1], zl = row / g.tile[1];
     const int y = TO.o[1] + yl, z = TO.o[2] + zl;
     if (y >= g.n[1] || z >= g.n[2]) continue;
-    const AxisEntry ye = yt[yl], ze = zt[zl];
+    const AxisEntry ye = yt[yl];
     if (!bg) {
       row_cyz<DIM>(g, CZ, zl, ye, nxn, cyz, lane);
       __syncwarp();
@@ -805,13 +807,13 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
     const float tot = warp_reduce_scatter32(vals, lane);
     // Lane q holds component q/11, x-node q%11: spread over the y/z nodes.
     const int kq = lane / NN, lq = lane % NN;
+    float* gpl = gt + (zl * g.hf[1] + ye.frel) * g.hf[0];   // this row's plane, first y node
     if (lane < DIM * NN && lq < nxn && tot != 0.f) {
-      for (int mn = 0; mn < NJK; ++mn) {
-        const int m = mn & 3, n = mn >> 2;
-        const float w = ye.bf[m] * ze.bf[n];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float w = ye.bf[m];
         if (w == 0.f) continue;
-        atomicAdd(gt + kq * nodes_tile + ((ze.frel + n) * g.hf[1] + (ye.frel + m)) * g.hf[0] + lq,
-                  tot * w);
+        atomicAdd(gpl + kq * nodes_tile + m * g.hf[0] + lq, tot * w);
       }
     }
     if (DIM == 3 && nxn > 32 - 2 * NN) {     // rows touching 11 x-nodes (warp-uniform)
@@ -819,27 +821,47 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
 #pragma unroll
       for (int off = 16; off; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
       if (lane == 0 && e != 0.f) {
-        for (int mn = 0; mn < NJK; ++mn) {
-          const int m = mn & 3, n = mn >> 2;
-          const float w = ye.bf[m] * ze.bf[n];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const float w = ye.bf[m];
           if (w == 0.f) continue;
-          atomicAdd(gt + 2 * nodes_tile + ((ze.frel + n) * g.hf[1] + (ye.frel + m)) * g.hf[0] +
-                        (32 - 2 * NN),
-                    e * w);
+          atomicAdd(gpl + 2 * nodes_tile + m * g.hf[0] + (32 - 2 * NN), e * w);
         }
       }
     }
     __syncwarp();
   }
   __syncthreads();
+  // Flush: per (component, first plane of an FFD z cell, y node, x node),
+  // combine that cell's planes with their z-node weights and add the NJZ z
+  // nodes to the gradient.
+  constexpr int NJZ = DIM == 3 ? 4 : 1;
+  const int per_plane = g.hf[1] * g.hf[0];
   for (int i = threadIdx.x; i < DIM * nodes_tile; i += blockDim.x) {
-    const float val = gt[i];
-    if (val == 0.f) continue;
-    const int k = i / nodes_tile, nl = i % nodes_tile;
-    const int n0 = TO.f[0] + nl % g.hf[0], n1 = TO.f[1] + (nl / g.hf[0]) % g.hf[1],
-              n2 = TO.f[2] + nl / (g.hf[0] * g.hf[1]);
-    if (n0 >= g.nf[0] || n1 >= g.nf[1] || n2 >= g.nf[2]) continue;
-    atomicAdd(grad + k * g.ncoef + ((long long)n2 * g.nf[1] + n1) * g.nf[0] + n0, val);
+    const int k = i / nodes_tile, rem = i - k * nodes_tile;
+    const int zl = rem / per_plane, myx = rem - zl * per_plane;
+    const int fz = zt[zl].frel;
+    if (zl > 0 && zt[zl - 1].frel == fz) continue;
+    float u[NJZ];
+#pragma unroll
+    for (int n = 0; n < NJZ; ++n) u[n] = 0.f;
+    bool any = false;
+    for (int pl = zl; pl < g.tile[2] && zt[pl].frel == fz; ++pl) {
+      const float v = gt[k * nodes_tile + pl * per_plane + myx];
+      if (v == 0.f) continue;
+      any = true;
+#pragma unroll
+      for (int n = 0; n < NJZ; ++n) u[n] = fmaf(zt[pl].bf[n], v, u[n]);
+    }
+    if (!any) continue;
+    const int n0 = TO.f[0] + myx % g.hf[0], n1 = TO.f[1] + myx / g.hf[0];
+    if (n0 >= g.nf[0] || n1 >= g.nf[1]) continue;
+#pragma unroll
+    for (int n = 0; n < NJZ; ++n) {
+      const int n2 = TO.f[2] + fz + n;
+      if (u[n] == 0.f || n2 >= g.nf[2]) continue;
+      atomicAdd(grad + k * g.ncoef + ((long long)n2 * g.nf[1] + n1) * g.nf[0] + n0, u[n]);
+    }
   }
 }
 

@@ -530,8 +530,8 @@ void launch_tile_binmask(srwcr_ctx* ctx, const Geo& g, const void* A, unsigned* 
 srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv, const int* force_tile = nullptr) {
   const srwcr_config& cfg = ctx->cfg;
   const int nd = cfg.ndim;
-  static const int cand3[][3] = {{32, 32, 8}, {32, 16, 8}, {32, 8, 8}, {32, 8, 4}, {32, 4, 4},
-                                 {32, 4, 2}, {32, 2, 2}, {32, 1, 1}};
+  static const int cand3[][3] = {{32, 32, 4}, {32, 16, 4}, {32, 8, 4}, {32, 8, 2}, {32, 4, 2},
+                                 {32, 2, 2}, {32, 1, 1}};
   static const int cand2[][3] = {{32, 64, 1}, {32, 32, 1}, {32, 16, 1}, {32, 8, 1}, {32, 4, 1},
                                  {32, 1, 1}};
   std::vector<std::array<int, 3>> cands;
@@ -1231,9 +1231,12 @@ extern "C" srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c
     if (!lv.rows) RET_IF(select_rows_path(ctx, lv));
   } else {
     static const int cand3[][3] = {{32, 32, 8}, {32, 32, 4}, {32, 16, 8}, {32, 16, 4},
-                                   {32, 8, 8}, {32, 8, 4}, {32, 32, 2}, {32, 16, 2}};
-    static const int cand2[][3] = {{32, 64, 1}, {32, 32, 1}, {32, 16, 1}, {32, 8, 1}};
-    const int nc = ctx->cfg.ndim == 3 ? 8 : 4;
+                                   {32, 8, 8},  {32, 8, 4},  {32, 32, 2}, {32, 16, 2},
+                                   {32, 64, 4}, {32, 64, 2}, {32, 128, 2}, {32, 64, 1}};
+    static const int cand2[][3] = {{32, 64, 1}, {32, 32, 1}, {32, 16, 1}, {32, 8, 1},
+                                   {32, 128, 1}, {32, 256, 1}};
+    const int nc = ctx->cfg.ndim == 3 ? (int)(sizeof cand3 / sizeof cand3[0])
+                                      : (int)(sizeof cand2 / sizeof cand2[0]);
     const int (*cand)[3] = ctx->cfg.ndim == 3 ? cand3 : cand2;
     float* g = nullptr;
     double* D = nullptr;
