@@ -76,6 +76,10 @@ typedef struct {
                              (a tile using more takes several passes); 0 = as
                              many as fit in shared memory */
   int role;               /* SRWCR_ROLE_M_AS_B (0) | SRWCR_ROLE_M_AS_A */
+  int finalize_lanes;     /* lanes per spatial bin in the per-bin moment
+                             finalisation (Eqs. 9-12): 1, 2, 4, 8, 16 or 32;
+                             0 = chosen per level from the number of
+                             fixed-image bins each spatial bin holds */
 } srwcr_config;
 
 /* Geometry of one pyramid level. */
@@ -90,6 +94,7 @@ typedef struct {
   int kernel_path;        /* 1: row-parallel kernels (32-wide tiles, FFD and
                              spatial-bin spacing >= ~5 voxels along x);
                              0: general per-voxel kernels */
+  int finalize_lanes;     /* lanes per spatial bin in the finalisation */
 } srwcr_level_desc;
 
 /* Create a context: validate cfg, upload both images, normalise each to
@@ -292,6 +297,9 @@ typedef struct {
   int64_t n_voxels_total;
   int64_t work_items;     /* (pair, tile) items of one fused-kernel launch */
   int64_t launches;       /* kernels queued by this batch so far */
+  int finalize_lanes;     /* lanes per spatial bin in the batched
+                             finalisation (the first pair's setting, else
+                             chosen over all pairs) */
 } srwcr_batch_desc;
 
 /* Build a batch over ctxs[0..n_pairs-1] at pyramid level `level`.  All

@@ -48,14 +48,16 @@ class Config(ctypes.Structure):
                 ("ffd_spacing", ctypes.c_int * 3), ("sbin_intervals", ctypes.c_int * 3),
                 ("n_intensity_bins", ctypes.c_int), ("storage", ctypes.c_int),
                 ("pyramid_levels", ctypes.c_int), ("tile", ctypes.c_int * 3),
-                ("bins_per_pass", ctypes.c_int), ("role", ctypes.c_int)]
+                ("bins_per_pass", ctypes.c_int), ("role", ctypes.c_int),
+                ("finalize_lanes", ctypes.c_int)]
 
 
 class LevelDesc(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int * 3), ("ffd_nodes", ctypes.c_int * 3),
                 ("sbins", ctypes.c_int * 3), ("n_voxels", ctypes.c_int64),
                 ("n_params", ctypes.c_int64), ("n_regions", ctypes.c_int64),
-                ("tile", ctypes.c_int * 3), ("kernel_path", ctypes.c_int)]
+                ("tile", ctypes.c_int * 3), ("kernel_path", ctypes.c_int),
+                ("finalize_lanes", ctypes.c_int)]
 
 
 class LbfgsOpts(ctypes.Structure):
@@ -74,7 +76,8 @@ class Report(ctypes.Structure):
 class BatchDesc(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int), ("launches_per_eval", ctypes.c_int),
                 ("n_params_total", ctypes.c_int64), ("n_voxels_total", ctypes.c_int64),
-                ("work_items", ctypes.c_int64), ("launches", ctypes.c_int64)]
+                ("work_items", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("finalize_lanes", ctypes.c_int)]
 
 
 def library_path() -> str:
@@ -157,6 +160,7 @@ class LevelInfo:
     n_regions: int
     tile: tuple
     kernel_path: int  # 1 = row-parallel kernels, 0 = general kernels
+    finalize_lanes: int  # lanes per spatial bin in the finalisation
 
 
 class SRWCR:
@@ -171,7 +175,7 @@ class SRWCR:
                  sbin_intervals: Sequence[int] = (0, 0, 0), n_bins: int = 32,
                  storage: str = "f32", pyramid_levels: int = 1,
                  tile: Optional[Sequence[int]] = None, stream=None, bins_per_pass: int = 0,
-                 role: str = "mas_b"):
+                 role: str = "mas_b", finalize_lanes: int = 0):
         import torch
         self._torch = torch
         lib = load()
@@ -192,6 +196,7 @@ class SRWCR:
         cfg.pyramid_levels = int(pyramid_levels)
         cfg.bins_per_pass = int(bins_per_pass)
         cfg.role = ROLE[role]
+        cfg.finalize_lanes = int(finalize_lanes)
         self.cfg = cfg
         self.ndim = ndim
         self.storage = storage
@@ -230,7 +235,8 @@ class SRWCR:
         d = LevelDesc()
         _check(load().srwcr_level_info(self._h, level, ctypes.byref(d)))
         return LevelInfo(tuple(d.dims), tuple(d.ffd_nodes), tuple(d.sbins), d.n_voxels,
-                         d.n_params, d.n_regions, tuple(d.tile), d.kernel_path)
+                         d.n_params, d.n_regions, tuple(d.tile), d.kernel_path,
+                         d.finalize_lanes)
 
     def coef_shape(self, level: int = 0):
         n = self.levels[level].ffd_nodes

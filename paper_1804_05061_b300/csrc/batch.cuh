@@ -278,6 +278,7 @@ struct srwcr_batch {
   std::vector<AdjLaunch> adj_launches;
   std::vector<BatchPair> host_tab;  // table order (by group, then size)
   long long total_regions = 0;
+  int fin_lanes = 32;               // lanes per region of the finalisation
   long long total_vox = 0;
   long long work_items = 0;
   float* c = nullptr;
@@ -362,9 +363,12 @@ srwcr_status queue_batch_eval(srwcr_batch* b, bool lb, const int* active) {
   CKL();
   launch_rows_any(b, lb, active, false);
   CKL();
-  const long long threads = b->total_regions * 32;
-  k_finalize_batch<<<(unsigned)((threads + 255) / 256), 256, 0, b->stream>>>(tab, b->n, b->total_regions,
-                                                                        active);
+  const long long threads = ((b->total_regions * b->fin_lanes + 31) / 32) * 32;
+  const unsigned fblocks = (unsigned)((threads + 255) / 256);
+#define SRWCR_FIN_CALL(G) \
+  k_finalize_batch<G><<<fblocks, 256, 0, b->stream>>>(tab, b->n, b->total_regions, active)
+  SRWCR_FIN_LANES_SWITCH(b->fin_lanes, SRWCR_FIN_CALL)
+#undef SRWCR_FIN_CALL
   CKL();
   k_reduce_D_batch<<<b->n, 1024, 0, b->stream>>>(tab, active);
   CKL();
@@ -563,6 +567,14 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
     b->total_vox += lv.g.nvox;
   }
   b->total_regions = region;
+  {
+    // One launch finalises every pair: the first pair's explicit setting,
+    // else the cost model over all pairs' region lists.
+    const int req = ctxs[0]->cfg.finalize_lanes;
+    std::vector<const std::vector<int>*> lists;
+    for (int i = 0; i < n; ++i) lists.push_back(&ctxs[i]->lev[level].nz_ptr_host);
+    b->fin_lanes = req > 0 ? req : finalize_lanes_auto(lists, ctxs[0]->device);
+  }
   // Row-kernel launches: pairs bucketed by (x-bins per row, CTAs per SM),
   // in table order (largest first), at most kBatchChunk per launch.
   {
@@ -658,6 +670,7 @@ srwcr_status srwcr_batch_info(const srwcr_batch* b, srwcr_batch_desc* out) {
   out->n_voxels_total = b->total_vox;
   out->work_items = b->work_items;
   out->launches = b->launches;
+  out->finalize_lanes = b->fin_lanes;
   return SRWCR_OK;
 }
 

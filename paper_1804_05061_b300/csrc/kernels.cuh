@@ -205,69 +205,78 @@ __device__ __forceinline__ void finalize_region(const Geo& g, long long r, int l
 }
 
 // Static per-region data of the fixed image that the finalisation reuses at
-// every evaluation: W_r = sum_a P[r][a] = Z p(r), and the bins with
-// P[r][a] > 0 (the only ones where S1, S2 can be nonzero) with 1/P[r][a], in
-// compressed rows.
+// every evaluation: W_r = sum_a P[r][a] = Z p(r) and its reciprocal, and the
+// bins with P[r][a] > 0 (the only ones where S1, S2 can be nonzero) with
+// 1/P[r][a], in compressed rows.
 struct RegionStatic {
   const double* W;      // [R]
+  const double* inv_w;  // [R] 1 / W_r (0 where W_r = 0)
   const int* ptr;       // [R+1] row offsets into bin/inv_p
   const int* bin;       // [nnz] fixed-image bin a
   const double* inv_p;  // [nnz] 1 / P[r][a]
 };
 
-// Same quantities as finalize_region, over the static nonzero bins only:
-// the moment sums T1, T2 are formed exactly in 64-bit integers and rounded
-// once, divisions by P become products with the stored reciprocals, and one
-// division by sigma_r^2 per region remains.  X entries of bins outside the
-// list stay at the zero they were initialised to.
-__device__ __forceinline__ void finalize_region_sparse(long long r, int lane, int nb,
+// Same quantities as finalize_region, over the static nonzero bins only, by
+// a group of G lanes (G divides 32; sub = lane index within the group):
+// the moment sums T1 = sum_a S1[r][a], T2 = sum_a S2[r][a] are formed exactly
+// in 64-bit integers and rounded once, divisions by P and W become products
+// with the stored reciprocals, and one division (1 / sigma_r^2) per region
+// remains.  Q_r = sum_a (S2 - S1^2 / P) is taken as T2 - sum_a S1 mu_r(a).
+// A group with live == false (past the last region, or an inactive batch
+// pair) still takes part in the group shuffles and writes nothing.  X entries
+// of bins outside the list stay at the zero they were initialised to.  FP64
+// issue is the bound of this step, so small G (several regions per warp)
+// pays when the lists are short and regions are many.
+template <int G>
+__device__ __forceinline__ void finalize_region_sparse(long long r, bool live, int sub, int nb,
                                                        const RegionStatic& rs,
                                                        const unsigned long long* __restrict__ S,
                                                        double inv_s1, double inv_s2, double invZ,
                                                        float* __restrict__ U, float* __restrict__ V,
                                                        float* __restrict__ X, double* __restrict__ Dr,
                                                        double* __restrict__ stats) {
-  const unsigned long long* Sr = S + r * nb * 2;
-  const int beg = rs.ptr[r], end = rs.ptr[r + 1];
+  const unsigned long long* Sr = S + (live ? r : 0) * nb * 2;
+  const int beg = live ? rs.ptr[r] : 0, end = live ? rs.ptr[r + 1] : 0;
   unsigned long long t1 = 0ull, t2 = 0ull;
-  for (int k = beg + lane; k < end; k += 32) {
-    const int a = rs.bin[k];
-    t1 += Sr[2 * a];
-    t2 += Sr[2 * a + 1];
+  for (int k = beg + sub; k < end; k += G) {
+    const ulonglong2 s = *reinterpret_cast<const ulonglong2*>(Sr + 2 * rs.bin[k]);
+    t1 += s.x;
+    t2 += s.y;
   }
 #pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    t1 += __shfl_xor_sync(0xffffffffu, t1, off);
-    t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+  for (int off = G / 2; off; off >>= 1) {
+    t1 += __shfl_xor_sync(0xffffffffu, t1, off, G);
+    t2 += __shfl_xor_sync(0xffffffffu, t2, off, G);
   }
-  const double W = rs.W[r];
+  const double W = live ? rs.W[r] : 0.0, iw = live ? rs.inv_w[r] : 0.0;
   bool valid = W > 0.0;
   double mu = 0.0, var = 0.0, ms = 0.0;
   if (valid) {
-    mu = (double)t1 * inv_s1 / W;
-    ms = (double)t2 * inv_s2 / W;
+    mu = (double)t1 * inv_s1 * iw;
+    ms = (double)t2 * inv_s2 * iw;
     var = ms - mu * mu;
     valid = var > 1e-6 * fmax(1.0, ms);  // degenerate: sigma_r^2 -> 0 (0/0 in Eq. 9)
   }
   const double iv = valid ? 1.0 / var : 0.0;
-  double Q = 0.0;
-  for (int k = beg + lane; k < end; k += 32) {
+  double q = 0.0;  // this lane's share of sum_a S1 mu_r(a)
+  for (int k = beg + sub; k < end; k += G) {
     const int a = rs.bin[k];
     double x = 0.0;
     if (valid) {
-      const double s1 = (double)Sr[2 * a] * inv_s1, s2 = (double)Sr[2 * a + 1] * inv_s2;
+      const double s1 = (double)Sr[2 * a] * inv_s1;
       const double m = s1 * rs.inv_p[k];     // mu_r(a) = S1 / P
-      Q += s2 - s1 * m;
+      q = fma(s1, m, q);
       x = m * iv;
     }
     X[r * nb + a] = (float)x;
   }
 #pragma unroll
-  for (int off = 16; off; off >>= 1) Q += __shfl_xor_sync(0xffffffffu, Q, off);
-  if (lane == 0) {
+  for (int off = G / 2; off; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off, G);
+  if (live && sub == 0) {
     double omc = 0.0, share = 0.0;
     if (valid) {
-      omc = Q * iv / W;
+      const double Q = (double)t2 * inv_s2 - q;
+      omc = Q * iv * iw;
       share = Q * invZ * iv;
     }
     U[r] = valid ? (float)((1.0 - omc) * iv) : 0.f;
@@ -280,15 +289,19 @@ __device__ __forceinline__ void finalize_region_sparse(long long r, int lane, in
   }
 }
 
+// Lanes per region of the sparse finalisation.
+constexpr int kFinLanes[6] = {1, 2, 4, 8, 16, 32};
+
+template <int G>
 __global__ void __launch_bounds__(256)
 k_finalize_sparse(long long R, int nb, const RegionStatic rs,
                   const unsigned long long* __restrict__ S, double inv_s1, double inv_s2,
                   double invZ, float* __restrict__ U, float* __restrict__ V,
                   float* __restrict__ X, double* __restrict__ Dr, double* __restrict__ stats) {
-  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  if (r >= R) return;  // warp-uniform
-  finalize_region_sparse(r, threadIdx.x & 31, nb, rs, S, inv_s1, inv_s2, invZ, U, V, X, Dr,
-                         stats);
+  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
+  if ((r - (threadIdx.x & 31) / G) >= R) return;  // the warp's first region: warp-uniform
+  finalize_region_sparse<G>(r, r < R, threadIdx.x & (G - 1), nb, rs, S, inv_s1, inv_s2, invZ, U,
+                            V, X, Dr, stats);
 }
 
 __global__ void k_finalize(const Geo g, const double* __restrict__ P,

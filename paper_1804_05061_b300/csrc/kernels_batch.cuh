@@ -114,17 +114,20 @@ k_adjoint_rows_batch(const __grid_constant__ AdjTable tab, const int* __restrict
   adj_rows_body<DIM, T, NXB>(it.g, it.a, tile, smem_adj);
 }
 
-// One warp per (pair, spatial bin) over all pairs.
+// G lanes per (pair, spatial bin) over all pairs' regions.
+template <int G>
 __global__ void __launch_bounds__(256)
 k_finalize_batch(const BatchPair* __restrict__ pairs, int n, long long total,
                  const int* __restrict__ active) {
-  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  if (w >= total) return;  // warp-uniform
-  const int p = batch_find(0, n - 1, w, [&](int i) { return pairs[i].region_begin; });
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
+  if ((w - (threadIdx.x & 31) / G) >= total) return;  // the warp's first region: warp-uniform
+  bool live = w < total;
+  const int p = live ? batch_find(0, n - 1, w, [&](int i) { return pairs[i].region_begin; }) : 0;
   const BatchPair& bp = pairs[p];
-  if (!batch_active(active, bp.id)) return;
-  finalize_region_sparse(w - bp.region_begin, threadIdx.x & 31, bp.g.nbins, bp.rs, bp.acc.acc,
-                         bp.inv_s1, bp.inv_s2, bp.invZ, bp.U, bp.V, bp.X, bp.Dr, bp.stats);
+  live = live && batch_active(active, bp.id);
+  finalize_region_sparse<G>(w - bp.region_begin, live, threadIdx.x & (G - 1), bp.g.nbins, bp.rs,
+                            bp.acc.acc, bp.inv_s1, bp.inv_s2, bp.invZ, bp.U, bp.V, bp.X, bp.Dr,
+                            bp.stats);
 }
 
 // Per-plane z-contraction of every active pair's tables; blockIdx.y = slot.

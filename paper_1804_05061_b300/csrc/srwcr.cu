@@ -74,7 +74,7 @@ struct Level {
   void* M = nullptr;                  // normalised moving image (storage type)
   unsigned long long* S = nullptr;    // [R][nbins][2] fixed-point S1, S2 (also P scratch)
   double* P = nullptr;                // [R][nbins] sum_x w h(a - A)
-  double* Wr = nullptr;               // [R] sum_a P[r][a]
+  double* Wr = nullptr;               // [2R] sum_a P[r][a], then its reciprocals
   int* nz_ptr = nullptr;              // [R+1] bins with P > 0, compressed rows
   int* nz_bin = nullptr;              // [nnz]
   double* nz_inv_p = nullptr;         // [nnz] 1 / P
@@ -102,6 +102,8 @@ struct Level {
   int* ubins = nullptr;               // fixed-image bins present in the image (any tile)
   int nu = 0;
   size_t smem_acc_rows = 0, smem_adj_rows = 0;
+  std::vector<int> nz_ptr_host;       // host copy of nz_ptr (finalisation cost model)
+  int fin_lanes = 32;                 // lanes per region of the sparse finalisation
 };
 
 }  // namespace
@@ -418,10 +420,76 @@ srwcr_status check_level(const srwcr_ctx* ctx, int level) {
 RegionStatic region_static(const Level& lv) {
   RegionStatic rs;
   rs.W = lv.Wr;
+  rs.inv_w = lv.Wr + lv.g.R;
   rs.ptr = lv.nz_ptr;
   rs.bin = lv.nz_bin;
   rs.inv_p = lv.nz_inv_p;
   return rs;
+}
+
+// FP64 issue model of the sparse finalisation with G lanes per region over
+// the regions whose compressed-row offsets are `ptr`: a warp serves 32/G
+// consecutive regions and issues, per group, a fixed ~32 FP64 operations
+// (moments, one reciprocal, the region's outputs), ~6 per list entry over
+// ceil(nnz / G) rounds of its slowest group, and ~1.5 per shuffle round.
+// Returns the summed warp costs and raises *longest to the largest one.
+double finalize_cost(const std::vector<int>& ptr, int G, double* longest) {
+  const long long R = (long long)ptr.size() - 1;
+  const int per = 32 / G;
+  int lg = 0;
+  while ((1 << lg) < G) ++lg;
+  double sum = 0.0;
+  for (long long w0 = 0; w0 < R; w0 += per) {
+    int rounds = 0;
+    for (long long r = w0; r < std::min(R, w0 + per); ++r)
+      rounds = std::max(rounds, (ptr[r + 1] - ptr[r] + G - 1) / G);
+    const double c = 32.0 + 6.0 * rounds + 1.5 * lg;
+    sum += c;
+    *longest = std::max(*longest, c);
+  }
+  return sum;
+}
+
+// Lanes per region minimising max(sum of warp costs / SM sub-partitions,
+// longest warp) over one or more region lists (one per batch pair).
+int finalize_lanes_auto(const std::vector<const std::vector<int>*>& lists, int device) {
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  int best = 32;
+  double best_t = 0.0;
+  for (int G : kFinLanes) {
+    double sum = 0.0, longest = 0.0;
+    for (const auto* l : lists) sum += finalize_cost(*l, G, &longest);
+    const double t = std::max(sum / (4.0 * sms), longest);
+    if (G == kFinLanes[0] || t < best_t) {
+      best = G;
+      best_t = t;
+    }
+  }
+  return best;
+}
+
+#define SRWCR_FIN_LANES_SWITCH(G, CALL) \
+  switch (G) {                          \
+    case 1: CALL(1); break;             \
+    case 2: CALL(2); break;             \
+    case 4: CALL(4); break;             \
+    case 8: CALL(8); break;             \
+    case 16: CALL(16); break;           \
+    default: CALL(32); break;           \
+  }
+
+void launch_finalize_sparse(srwcr_ctx* ctx, const Level& lv) {
+  const long long threads = ((lv.g.R * lv.fin_lanes + 31) / 32) * 32;
+  const int blocks = (int)((threads + kBlock - 1) / kBlock);
+  const RegionStatic rs = region_static(lv);
+#define SRWCR_FIN_CALL(G)                                                                 \
+  k_finalize_sparse<G><<<blocks, kBlock, 0, ctx->stream>>>(lv.g.R, lv.g.nbins, rs, lv.S,  \
+                                                           1.0 / lv.s1, 1.0 / lv.s2,       \
+                                                           1.0 / lv.Z, lv.U, lv.V, lv.X, \
+                                                           lv.Dr, lv.stats)
+  SRWCR_FIN_LANES_SWITCH(lv.fin_lanes, SRWCR_FIN_CALL)
+#undef SRWCR_FIN_CALL
 }
 
 // (a) + (b): value into lv.D, tables into lv.U/V/X.  keep_warp: also store
@@ -436,17 +504,14 @@ srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c, bool keep_warp
                    : launch_accumulate<float>(ctx, lv, c, false, lv.s1, lv.s2, keep_warp);
   if (st != SRWCR_OK) return st;
   prof_end(ctx, kProfAccumulate, ev);
-  const long long warps = lv.g.R;
-  const int fblk = (int)((warps * 32 + kBlock - 1) / kBlock);
+  const int fblk = (int)((lv.g.R * 32 + kBlock - 1) / kBlock);
   ev = prof_begin(ctx);
   if (mas_a)
     k_finalize_mas_a<<<fblk, kBlock, 0, ctx->stream>>>(lv.g, lv.S, 1.0 / lv.s0, 1.0 / lv.s1,
                                                        1.0 / lv.s2, 1.0 / lv.Z, lv.X, lv.Y2, lv.Dr,
                                                        lv.stats);
   else
-    k_finalize_sparse<<<fblk, kBlock, 0, ctx->stream>>>(lv.g.R, lv.g.nbins, region_static(lv), lv.S,
-                                                        1.0 / lv.s1, 1.0 / lv.s2, 1.0 / lv.Z, lv.U,
-                                                        lv.V, lv.X, lv.Dr, lv.stats);
+    launch_finalize_sparse(ctx, lv);
   CKL();
   k_reduce_D<<<1, 1024, 0, ctx->stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg);
   CKL();
@@ -769,7 +834,7 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     for (long long i = 0; i < n; ++i) Z += hP[i];
     // Static per-region data of the finalisation (bins with P > 0).
     const int nb = lv.g.nbins;
-    std::vector<double> Wr(lv.g.R), inv_p;
+    std::vector<double> Wr(2 * lv.g.R), inv_p;
     std::vector<int> ptr(lv.g.R + 1, 0), bin;
     for (long long r = 0; r < lv.g.R; ++r) {
       double w = 0.0;
@@ -782,20 +847,24 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
         }
       }
       Wr[r] = w;
+      Wr[lv.g.R + r] = w > 0.0 ? 1.0 / w : 0.0;
       ptr[r + 1] = (int)bin.size();
     }
     free(hP);
     const size_t nnz = std::max<size_t>(bin.size(), 1);
-    CK(cudaMalloc((void**)&lv.Wr, sizeof(double) * lv.g.R));
+    CK(cudaMalloc((void**)&lv.Wr, sizeof(double) * 2 * lv.g.R));
     CK(cudaMalloc((void**)&lv.nz_ptr, sizeof(int) * (lv.g.R + 1)));
     CK(cudaMalloc((void**)&lv.nz_bin, sizeof(int) * nnz));
     CK(cudaMalloc((void**)&lv.nz_inv_p, sizeof(double) * nnz));
-    CK(cudaMemcpy(lv.Wr, Wr.data(), sizeof(double) * lv.g.R, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(lv.Wr, Wr.data(), sizeof(double) * 2 * lv.g.R, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(lv.nz_ptr, ptr.data(), sizeof(int) * (lv.g.R + 1), cudaMemcpyHostToDevice));
     if (!bin.empty()) {
       CK(cudaMemcpy(lv.nz_bin, bin.data(), sizeof(int) * bin.size(), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(lv.nz_inv_p, inv_p.data(), sizeof(double) * bin.size(), cudaMemcpyHostToDevice));
     }
+    lv.fin_lanes = cfg->finalize_lanes > 0 ? cfg->finalize_lanes
+                                           : finalize_lanes_auto({&ptr}, ctx->device);
+    lv.nz_ptr_host = std::move(ptr);
     // X entries of bins with P = 0 are never written by the finalisation.
     CK(cudaMemsetAsync(lv.X, 0, sizeof(float) * lv.g.R * nb, ctx->stream));
     lv.Z = Z;
@@ -829,6 +898,10 @@ srwcr_status srwcr_create(const srwcr_config* cfg, const float* fixed, const flo
   if (cfg->bins_per_pass < 0) return fail(SRWCR_EINVAL, "negative bins_per_pass");
   if (cfg->role != SRWCR_ROLE_M_AS_B && cfg->role != SRWCR_ROLE_M_AS_A)
     return fail(SRWCR_EINVAL, "unknown role");
+  if (cfg->finalize_lanes != 0 && cfg->finalize_lanes != 1 && cfg->finalize_lanes != 2 &&
+      cfg->finalize_lanes != 4 && cfg->finalize_lanes != 8 && cfg->finalize_lanes != 16 &&
+      cfg->finalize_lanes != 32)
+    return fail(SRWCR_EINVAL, "finalize_lanes must be 0, 1, 2, 4, 8, 16 or 32");
   srwcr_ctx* ctx = new (std::nothrow) srwcr_ctx();
   if (!ctx) return fail(SRWCR_ENOMEM, "host allocation failed");
   srwcr_status st = create_impl(cfg, fixed, moving, images_on_device, stream, ctx);
@@ -856,6 +929,7 @@ srwcr_status srwcr_level_info(const srwcr_ctx* ctx, int level, srwcr_level_desc*
   out->n_params = g.ncoef * ctx->cfg.ndim;
   out->n_regions = g.R;
   out->kernel_path = ctx->lev[level].rows ? 1 : 0;
+  out->finalize_lanes = ctx->lev[level].fin_lanes;
   return SRWCR_OK;
 }
 

@@ -101,6 +101,39 @@ def test_value_in_several_bin_passes_equals_one_pass(small_cases, name):
     assert abs(D8 - st.D) <= D_RTOL * abs(st.D)
 
 
+@pytest.mark.parametrize("name", ["ct_128_bins", "pet_labels", "ellipse_2d_ragged"])
+def test_every_finalisation_lane_count_matches_oracle(small_cases, name):
+    # G lanes per spatial bin: the bin lists of "ct_128_bins" take several
+    # rounds at small G, those of "pet_labels" fit one.  Moment sums are exact
+    # integers, so only the FP64 sum of S1 mu_r(a) changes order with G.
+    prob, f, m, c = small_cases[name]
+    ct = torch.from_numpy(c).cuda()
+    st, go, _, _, _ = oracle_eval(prob, f, m, c)
+    auto = engine_for(prob, f, m)
+    assert auto.levels[0].finalize_lanes in (1, 2, 4, 8, 16, 32)
+    D0, g0 = auto.value_and_grad(ct)
+    s0, n0 = auto.region_stats()
+    for lanes in (1, 2, 4, 8, 16, 32):
+        e = engine_for(prob, f, m, finalize_lanes=lanes)
+        assert e.levels[0].finalize_lanes == lanes
+        D, g = e.value_and_grad(ct)
+        s, n = e.region_stats()
+        assert n == n0 == st.n_degenerate
+        assert abs(D - D0) <= 1e-12 * abs(D0) and abs(D - st.D) <= D_RTOL * abs(st.D)
+        assert np.allclose(s, s0, rtol=1e-12, atol=1e-12)
+        assert torch.allclose(g, g0, rtol=1e-6, atol=1e-6 * float(g0.abs().max()))
+        gn = np.linalg.norm(g.cpu().numpy().astype(np.float64))
+        assert abs(gn - np.linalg.norm(go)) <= GNORM_RTOL * np.linalg.norm(go)
+
+
+def test_finalisation_lane_count_is_validated(small_cases):
+    import paper_1804_05061_b300 as eng
+    prob, f, m, _ = small_cases["pet_labels"]
+    for bad in (3, 64, -1):
+        with pytest.raises(eng.SrwcrError):
+            engine_for(prob, f, m, finalize_lanes=bad)
+
+
 EXPECTED_PATH = {"ellipse_2d_ragged": 1, "ct_3d_ragged": 1, "oct_ffd_grid_bins": 0,
                  "ct_128_bins": 1, "pet_labels": 1}
 
