@@ -58,6 +58,14 @@ enum { SRWCR_STORAGE_F32 = 0, SRWCR_STORAGE_BF16 = 1 };
  * kernels. */
 enum { SRWCR_ROLE_M_AS_B = 0, SRWCR_ROLE_M_AS_A = 1 };
 
+/* Spatial distribution w(r, x) of Eq. (3).  B-spline (default): the cubic
+ * B-spline bins of Eq. (7), K+3 per axis.  Boxcar: Eq. (6) over a regular
+ * partition into K patches per axis, patch floor(x K / N) holding voxel x with
+ * weight 1 (the RaPTOR-style distribution of Eqs. 13-14, with the Parzen
+ * window of Eq. 5 kept); needs sbin_intervals > 0 and runs on the general
+ * per-voxel kernels. */
+enum { SRWCR_SPATIAL_BSPLINE = 0, SRWCR_SPATIAL_BOXCAR = 1 };
+
 /* Problem configuration (Sec. II-F gives the paper's defaults: delta = 5,
  * L_eps = 31, i.e. 32 intensity bins). */
 typedef struct {
@@ -80,6 +88,7 @@ typedef struct {
                              finalisation (Eqs. 9-12): 1, 2, 4, 8, 16 or 32;
                              0 = chosen per level from the number of
                              fixed-image bins each spatial bin holds */
+  int spatial;            /* SRWCR_SPATIAL_BSPLINE (0) | SRWCR_SPATIAL_BOXCAR */
 } srwcr_config;
 
 /* Geometry of one pyramid level. */

@@ -21,6 +21,7 @@ _lib = None
 
 STORAGE = {"f32": 0, "bf16": 1}
 ROLE = {"mas_b": 0, "mas_a": 1}   # which image is binned (Sec. II-E)
+SPATIAL = {"bspline": 0, "boxcar": 1}  # w(r, x): Eq. (7) or Eq. (6)
 STATUS = {0: "SRWCR_OK", 1: "SRWCR_EINVAL", 2: "SRWCR_ENOMEM", 3: "SRWCR_ECUDA",
           4: "SRWCR_ENUMERIC", 5: "SRWCR_ELINESEARCH", 6: "SRWCR_ETIMEOUT",
           7: "SRWCR_ENOTCONVERGED"}
@@ -49,7 +50,7 @@ class Config(ctypes.Structure):
                 ("n_intensity_bins", ctypes.c_int), ("storage", ctypes.c_int),
                 ("pyramid_levels", ctypes.c_int), ("tile", ctypes.c_int * 3),
                 ("bins_per_pass", ctypes.c_int), ("role", ctypes.c_int),
-                ("finalize_lanes", ctypes.c_int)]
+                ("finalize_lanes", ctypes.c_int), ("spatial", ctypes.c_int)]
 
 
 class LevelDesc(ctypes.Structure):
@@ -175,7 +176,7 @@ class SRWCR:
                  sbin_intervals: Sequence[int] = (0, 0, 0), n_bins: int = 32,
                  storage: str = "f32", pyramid_levels: int = 1,
                  tile: Optional[Sequence[int]] = None, stream=None, bins_per_pass: int = 0,
-                 role: str = "mas_b", finalize_lanes: int = 0):
+                 role: str = "mas_b", finalize_lanes: int = 0, spatial: str = "bspline"):
         import torch
         self._torch = torch
         lib = load()
@@ -197,6 +198,7 @@ class SRWCR:
         cfg.bins_per_pass = int(bins_per_pass)
         cfg.role = ROLE[role]
         cfg.finalize_lanes = int(finalize_lanes)
+        cfg.spatial = SPATIAL[spatial]
         self.cfg = cfg
         self.ndim = ndim
         self.storage = storage

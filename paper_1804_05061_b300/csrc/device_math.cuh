@@ -35,6 +35,7 @@ struct Geo {
   long long R;      // spatial bins = nsb[0]*nsb[1]*nsb[2]
   int nabin;        // row kernels: most fixed-image bins any one tile uses
   int cbin;         // row kernels: compacted bins per pass of the value kernel
+  int boxcar;       // spatial distribution: 0 cubic B-spline (Eq. 7), 1 boxcar (Eq. 6)
 };
 
 __device__ __forceinline__ float ldval(const float* p) { return __ldg(p); }
@@ -164,15 +165,27 @@ __device__ __forceinline__ float sample_moving(const Geo& g, const T* __restrict
   return e0 + t[2] * (e1 - e0);
 }
 
-// Spatial distribution of Eq. (7) at voxel (x, y, z): cells and per-axis
-// B-spline weights; the voxel lies in bins cell+i, i = 0..3, per axis.
+// Spatial distribution at voxel (x, y, z): cells and per-axis weights; the
+// voxel lies in bins cell+i, i = 0..3, per axis.  Eq. (7): cubic B-spline
+// weights.  Eq. (6) (g.boxcar): the patch floor(x K / N) with weight 1 and
+// zero weight for i > 0 (those bins may lie past the last patch: callers
+// skip zero weights before touching a bin).
+__device__ __forceinline__ void axis_weights(const Geo& g, int d, int x, int* sc, float w[4]) {
+  float t;
+  *sc = sb_cell(g, d, x, &t);
+  if (g.boxcar) {
+    w[0] = 1.f; w[1] = w[2] = w[3] = 0.f;
+  } else {
+    bspline4(t, w);
+  }
+}
+
 template <int DIM>
 __device__ __forceinline__ void spatial_weights(const Geo& g, int x, int y, int z, int sc[3],
                                                 float sw[3][4]) {
-  float t;
-  sc[0] = sb_cell(g, 0, x, &t); bspline4(t, sw[0]);
-  sc[1] = sb_cell(g, 1, y, &t); bspline4(t, sw[1]);
-  if (DIM == 3) { sc[2] = sb_cell(g, 2, z, &t); bspline4(t, sw[2]); }
+  axis_weights(g, 0, x, &sc[0], sw[0]);
+  axis_weights(g, 1, y, &sc[1], sw[1]);
+  if (DIM == 3) axis_weights(g, 2, z, &sc[2], sw[2]);
   else { sc[2] = 0; sw[2][0] = 1.f; sw[2][1] = sw[2][2] = sw[2][3] = 0.f; }
 }
 

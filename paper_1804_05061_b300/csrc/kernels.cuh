@@ -403,6 +403,7 @@ k_adjoint(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const float w = wjk * sw[0][i];
+          if (w == 0.f) continue;  // also keeps boxcar reads inside the patch grid
           const long long r = rrow + i;
           const float xr = h0 * __ldg(X + r * nb + a0) + h1 * __ldg(X + r * nb + a0 + 1);
           su += w * __ldg(U + r);

@@ -217,6 +217,7 @@ k_adjoint_mas_a(const Geo g, const T* __restrict__ F, const T* __restrict__ M,
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const float w = wjk * sw[0][i];
+          if (w == 0.f) continue;  // also keeps boxcar reads inside the patch grid
           const long long e = (rrow + i) * nb + a0;
           const float d2 = __ldg(Y2 + e + 1) - __ldg(Y2 + e);
           const float d1 = __ldg(Y1 + e + 1) - __ldg(Y1 + e);

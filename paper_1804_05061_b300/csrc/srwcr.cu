@@ -204,11 +204,15 @@ srwcr_status choose_tile(Geo& g, int ndim, const int* req, int nch) {
 srwcr_status make_geo(const srwcr_config& cfg, const int dims[3], Geo& g) {
   memset(&g, 0, sizeof g);
   const int nd = cfg.ndim;
+  if (cfg.spatial != SRWCR_SPATIAL_BSPLINE && cfg.spatial != SRWCR_SPATIAL_BOXCAR)
+    return fail(SRWCR_EINVAL, "unknown spatial distribution");
   for (int d = 0; d < 3; ++d) {
     g.n[d] = d < nd ? dims[d] : 1;
     if (d < nd && g.n[d] < 2) return fail(SRWCR_EINVAL, "dimension %d has %d < 2 voxels", d, g.n[d]);
     g.fsp[d] = d < nd ? cfg.ffd_spacing[d] : 1;
     g.nf[d] = d < nd ? (g.n[d] - 1) / g.fsp[d] + 4 : 1;
+    if (d < nd && cfg.spatial == SRWCR_SPATIAL_BOXCAR && cfg.sbin_intervals[d] < 1)
+      return fail(SRWCR_EINVAL, "boxcar patches need sbin_intervals > 0 on axis %d", d);
     if (d < nd && cfg.sbin_intervals[d] > 0) {
       if (cfg.sbin_intervals[d] > g.n[d])
         return fail(SRWCR_EINVAL, "more spatial-bin intervals than voxels on axis %d", d);
@@ -221,7 +225,9 @@ srwcr_status make_geo(const srwcr_config& cfg, const int dims[3], Geo& g) {
     if ((long long)(g.n[d] - 1) * g.sbd[d] >= (1LL << 31))
       return fail(SRWCR_EINVAL, "spatial-bin arithmetic would overflow on axis %d", d);
     g.nsb[d] = d < nd ? (int)((long long)(g.n[d] - 1) * g.sbd[d] / g.sbn[d]) + 4 : 1;
+    if (d < nd && cfg.spatial == SRWCR_SPATIAL_BOXCAR) g.nsb[d] = cfg.sbin_intervals[d];
   }
+  g.boxcar = cfg.spatial == SRWCR_SPATIAL_BOXCAR ? 1 : 0;
   g.nbins = cfg.n_intensity_bins;
   g.nvox = (long long)g.n[0] * g.n[1] * g.n[2];
   g.ncoef = (long long)g.nf[0] * g.nf[1] * g.nf[2];
@@ -592,6 +598,12 @@ void launch_tile_binmask(srwcr_ctx* ctx, const Geo& g, const void* A, unsigned* 
 // each candidate's per-tile masks are built on the device and the largest
 // per-tile count sizes the histogram.  Levels without such a tile keep the
 // general path.
+// The row-parallel kernels bin the fixed image with cubic B-spline spatial
+// weights; the other roles and distributions run the general kernels.
+bool rows_allowed(const srwcr_config& cfg) {
+  return cfg.role == SRWCR_ROLE_M_AS_B && cfg.spatial == SRWCR_SPATIAL_BSPLINE;
+}
+
 srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv, const int* force_tile = nullptr) {
   const srwcr_config& cfg = ctx->cfg;
   const int nd = cfg.ndim;
@@ -804,7 +816,7 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     // The row kernels sort each row's voxels by the static fixed-image bin;
     // with the moving image as A the binned image moves, so the general
     // per-voxel kernels run.
-    if (cfg->role == SRWCR_ROLE_M_AS_B) RET_IF(select_rows_path(ctx, lv));
+    if (rows_allowed(*cfg)) RET_IF(select_rows_path(ctx, lv));
     if (lv.rows) {
       CK(cudaMalloc((void**)&lv.bg, sizeof(float4) * lv.g.nvox));
       CK(cudaMalloc((void**)&lv.uvxz, sizeof(float) * zcontract_len(lv.g)));
@@ -902,6 +914,11 @@ srwcr_status srwcr_create(const srwcr_config* cfg, const float* fixed, const flo
       cfg->finalize_lanes != 4 && cfg->finalize_lanes != 8 && cfg->finalize_lanes != 16 &&
       cfg->finalize_lanes != 32)
     return fail(SRWCR_EINVAL, "finalize_lanes must be 0, 1, 2, 4, 8, 16 or 32");
+  if (cfg->spatial != SRWCR_SPATIAL_BSPLINE && cfg->spatial != SRWCR_SPATIAL_BOXCAR)
+    return fail(SRWCR_EINVAL, "unknown spatial distribution");
+  for (int d = 0; d < cfg->ndim && cfg->spatial == SRWCR_SPATIAL_BOXCAR; ++d)
+    if (cfg->sbin_intervals[d] < 1)
+      return fail(SRWCR_EINVAL, "boxcar patches need sbin_intervals > 0 on axis %d", d);
   srwcr_ctx* ctx = new (std::nothrow) srwcr_ctx();
   if (!ctx) return fail(SRWCR_ENOMEM, "host allocation failed");
   srwcr_status st = create_impl(cfg, fixed, moving, images_on_device, stream, ctx);
@@ -1292,8 +1309,8 @@ extern "C" srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c
   if (!c_dev) return fail(SRWCR_EINVAL, "c_dev is NULL");
   if (reps < 1) reps = 3;
   Level& lv = ctx->lev[level];
-  if (ctx->cfg.role == SRWCR_ROLE_M_AS_A) {
-    // Only the row-parallel tiles are tuned; this role runs the general kernels.
+  if (!rows_allowed(ctx->cfg)) {
+    // Only the row-parallel tiles are tuned; this level runs the general kernels.
     for (int d = 0; d < 3 && tile_out; ++d) tile_out[d] = lv.g.tile[d];
     return SRWCR_OK;
   }

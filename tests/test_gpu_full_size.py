@@ -84,4 +84,10 @@ def test_c4_batch_of_32_pairs_per_pair_against_oracle(golden):
     Db = b.value_and_grad(use_graph=True)
     for i in range(len(specs)):
         check(golden[f"c4_pair{i:02d}"], Db[i], b.grad(i))
-        assert es[i].value(cs[i]) == Db[i]
+        # Bit for bit when the pair finalises with the batch's lane count;
+        # otherwise the FP64 sum of S1 mu_r(a) runs in another order.
+        Di = es[i].value(cs[i])
+        if es[i].levels[0].finalize_lanes == b.info().finalize_lanes:
+            assert Di == Db[i]
+        else:
+            assert abs(Di - Db[i]) <= 1e-12 * abs(Db[i])
