@@ -39,7 +39,8 @@ def build(force: bool = False) -> str:
 class _Problem(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int64 * 3),
                 ("ffd_sp", ctypes.c_int64 * 3), ("sb_num", ctypes.c_int64 * 3),
-                ("sb_den", ctypes.c_int64 * 3), ("nbins", ctypes.c_int), ("sb_mode", ctypes.c_int)]
+                ("sb_den", ctypes.c_int64 * 3), ("nbins", ctypes.c_int), ("sb_mode", ctypes.c_int),
+                ("xform", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -82,6 +83,7 @@ def lib():
             "orc_joint_pdf_mas_a": (ctypes.c_int, [_PP, _D, _D, _D, _D, _D]),
             "orc_gradient_mas_a": (ctypes.c_int, [_PP, _D, _D, _D, _D, _D, _D, _D, _U8,
                                                   ctypes.c_double, _D]),
+            "orc_rigid_matrix": (ctypes.c_int, [ctypes.c_int, _D, _D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -106,6 +108,7 @@ class Geometry:
     sbin_den: tuple
     n_bins: int
     boxcar: bool = False
+    rigid: bool = False  # c holds the rigid parameters instead of FFD coefficients
 
     @classmethod
     def from_problem(cls, prob, boxcar_patches: Optional[tuple] = None) -> "Geometry":
@@ -133,6 +136,7 @@ class Geometry:
             s.sb_num[d] = int(self.sbin_num[d]); s.sb_den[d] = int(self.sbin_den[d])
         s.nbins = int(self.n_bins)
         s.sb_mode = 1 if self.boxcar else 0
+        s.xform = 1 if self.rigid else 0
         return s
 
     @property

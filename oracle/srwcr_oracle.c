@@ -51,6 +51,7 @@ typedef struct {
   int64_t sb_den[3];
   int nbins;            /* L + 1 */
   int sb_mode;          /* 0: cubic B-spline distribution, Eq. (7); 1: boxcar patches, Eq. (6) */
+  int xform;            /* 0: FFD, Eq. (17), c = coefficients; 1: rigid, c = parameters */
 } orc_problem;
 
 /* ---------------------------------------------------------------------- */
@@ -184,8 +185,15 @@ int orc_spatial_weights(const orc_problem* P, int64_t x, int64_t y, int64_t z, i
 
 /* FFD, Eqs. (1) and (17): u_k(x) = sum over the 4^d nodes of x of
  * beta_l(eta) beta_m(gamma) beta_n(tau) c_k[node]. */
+static void rigid_displacement(const orc_problem* P, const double* c, const int64_t xv[3],
+                               double u[3]);
+
 static void displacement(const orc_problem* P, const double* c, const int64_t xv[3],
                          double u[3]) {
+  if (P->xform == 1) {
+    rigid_displacement(P, c, xv, u);
+    return;
+  }
   int64_t nfx = ffd_nodes(P, 0), nfy = ffd_nodes(P, 1), nfz = ffd_nodes(P, 2);
   int64_t ncoef = nfx * nfy * nfz;
   int64_t p[3];
@@ -208,6 +216,54 @@ static void displacement(const orc_problem* P, const double* c, const int64_t xv
           s += wax[0][l] * wax[1][m] * wax[2][nn] * c[k * ncoef + node];
         }
     u[k] = s;
+  }
+}
+
+/* Rigid model (the pre-alignment of Sec. III-D, same measure): rotation about
+ * the image centre x_c = (N - 1) / 2 followed by a translation,
+ *   T(x) = R (x - x_c) + x_c + t.
+ * 3-D: c = (t_x, t_y, t_z, alpha, beta, gamma), R = Rz(gamma) Ry(beta) Rx(alpha)
+ * (rotations about the fixed x, then y, then z axis); 2-D: c = (t_x, t_y,
+ * theta), R the plane rotation by theta.  Voxel units, radians.  R is built by
+ * multiplying the elementary rotations. */
+static void mat3_mul(const double a[3][3], const double b[3][3], double out[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += a[i][k] * b[k][j];
+      out[i][j] = s;
+    }
+}
+
+int orc_rigid_matrix(int ndim, const double* c, double R[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) R[i][j] = i == j ? 1.0 : 0.0;
+  if (ndim == 2) {
+    const double th = c[2];
+    R[0][0] = cos(th); R[0][1] = -sin(th);
+    R[1][0] = sin(th); R[1][1] = cos(th);
+    return ORC_OK;
+  }
+  const double a = c[3], b = c[4], g = c[5];
+  const double Rx[3][3] = {{1, 0, 0}, {0, cos(a), -sin(a)}, {0, sin(a), cos(a)}};
+  const double Ry[3][3] = {{cos(b), 0, sin(b)}, {0, 1, 0}, {-sin(b), 0, cos(b)}};
+  const double Rz[3][3] = {{cos(g), -sin(g), 0}, {sin(g), cos(g), 0}, {0, 0, 1}};
+  double t[3][3];
+  mat3_mul(Ry, Rx, t);
+  mat3_mul(Rz, t, R);
+  return ORC_OK;
+}
+
+static void rigid_displacement(const orc_problem* P, const double* c, const int64_t xv[3],
+                               double u[3]) {
+  double R[3][3], q[3];
+  orc_rigid_matrix(P->ndim, c, R);
+  for (int d = 0; d < 3; ++d) q[d] = d < P->ndim ? (double)xv[d] - 0.5 * (double)(P->n[d] - 1) : 0.0;
+  for (int k = 0; k < 3; ++k) {
+    if (k >= P->ndim) { u[k] = 0.0; continue; }
+    double s = 0.0;
+    for (int j = 0; j < P->ndim; ++j) s += R[k][j] * q[j];
+    u[k] = s + 0.5 * (double)(P->n[k] - 1) + c[k] - (double)xv[k];
   }
 }
 
