@@ -280,6 +280,44 @@ srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n_levels,
                             const srwcr_lbfgs_opts* opts, srwcr_report* report);
 
 /* ------------------------------------------------------------------------
+ * Rigid model: the pre-alignment the paper runs with the same measure before
+ * the non-rigid registration (Sec. III-D).  The transform rotates about the
+ * level's centre x_c = (N - 1) / 2 (voxel units) and translates:
+ *   T(x) = R (x - x_c) + x_c + t.
+ * mu (device float32): 3-D (t_x, t_y, t_z, alpha, beta, gamma) with
+ * R = Rz(gamma) Ry(beta) Rx(alpha) (rotations about the fixed x, y, z axes in
+ * that order); 2-D (t_x, t_y, theta).  Translations in voxels of the level,
+ * angles in radians.  The value is Eq. (9) with B(x) = M(T(x)) (the moving
+ * image as B only: SRWCR_EINVAL for SRWCR_ROLE_M_AS_A); the gradient is
+ * Eq. (16) with dT/dmu in place of the FFD basis.  Runs on the general
+ * per-voxel kernels. */
+
+/* D (host) and, when g_dev != NULL, dD/dmu (device, 6 or 3 floats) at mu.
+ * Synchronises.  Errors: SRWCR_EINVAL, SRWCR_ENUMERIC (non-finite mu or
+ * value), SRWCR_ECUDA. */
+srwcr_status srwcr_rigid_value_and_grad(srwcr_ctx* ctx, int level, const float* mu_dev,
+                                        double* D_host, float* g_dev);
+
+/* c_dev (device, n_params of `level`) <- FFD coefficients whose warp equals
+ * the rigid transform mu: the rigid displacement sampled at the control
+ * nodes (node j at (j - 1) delta), which the cubic B-spline reproduces
+ * exactly at every voxel (the displacement is affine).  This hands a rigid
+ * pre-alignment to srwcr_register.  Queued on the context's stream. */
+srwcr_status srwcr_rigid_to_ffd(srwcr_ctx* ctx, int level, const float* mu_dev, float* c_dev);
+
+/* Multi-resolution L-BFGS over the rigid parameters (the options and report
+ * of srwcr_register; penalty_weight is ignored: a rigid displacement has
+ * zero bending energy).  mu_dev_inout holds the start in level-0 voxels and
+ * receives the result.  Levels run coarse to fine; the transform is mapped
+ * exactly between levels (coarse voxel i sits at fine coordinate 2i + 1/2:
+ * translations double, plus (R - I) times the centre offset of odd sizes).
+ * Each level optimises (t, angle * rho), rho the RMS distance of the level's
+ * voxels from its centre, so both kinds of parameter move voxels on the same
+ * scale. */
+srwcr_status srwcr_rigid_register(srwcr_ctx* ctx, float* mu_dev_inout, int n_levels,
+                                  const srwcr_lbfgs_opts* opts, srwcr_report* report);
+
+/* ------------------------------------------------------------------------
  * Batched form: many pairs (contexts) of uneven sizes evaluated and
  * registered together.  The paper treats one pair at a time; this is a
  * throughput form of the same method.  Each phase of an evaluation (clear,

@@ -35,7 +35,8 @@ EXPORTS = ("srwcr_create", "srwcr_destroy", "srwcr_last_error", "srwcr_level_inf
            "srwcr_profile_read", "srwcr_value_noalloc", "srwcr_autotune",
            "srwcr_batch_create", "srwcr_batch_destroy", "srwcr_batch_info",
            "srwcr_batch_layout", "srwcr_batch_buffers", "srwcr_batch_value_and_grad",
-           "srwcr_batch_sync", "srwcr_batch_register", "srwcr_bending_energy")
+           "srwcr_batch_sync", "srwcr_batch_register", "srwcr_bending_energy",
+           "srwcr_rigid_value_and_grad", "srwcr_rigid_to_ffd", "srwcr_rigid_register")
 
 
 class SrwcrError(RuntimeError):
@@ -133,6 +134,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "srwcr_batch_register": (st, [vp, ctypes.POINTER(LbfgsOpts), ctypes.c_int, vp, vp, vp,
                                       vp]),
         "srwcr_bending_energy": (st, [vp, ctypes.c_int, vp, vp, vp, ctypes.c_float]),
+        "srwcr_rigid_value_and_grad": (st, [vp, ctypes.c_int, vp,
+                                            ctypes.POINTER(ctypes.c_double), vp]),
+        "srwcr_rigid_to_ffd": (st, [vp, ctypes.c_int, vp, vp]),
+        "srwcr_rigid_register": (st, [vp, vp, ctypes.c_int, ctypes.POINTER(LbfgsOpts),
+                                      ctypes.POINTER(Report)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -376,6 +382,59 @@ class SRWCR:
             _check(st)
         rep.status_code = st
         return rep
+
+
+# -- rigid model (pre-alignment with the same measure) -------------------------
+def _rigid_methods():
+    def n_rigid(self) -> int:
+        """Rigid parameters: (t_x, t_y, t_z, alpha, beta, gamma) in 3-D,
+        (t_x, t_y, theta) in 2-D; voxels of the level and radians."""
+        return 6 if self.ndim == 3 else 3
+
+    def _mu(self, mu):
+        t = self._torch
+        if not isinstance(mu, t.Tensor):
+            mu = t.as_tensor(np.asarray(mu, np.float32))
+        mu = mu.to(device=self.device, dtype=t.float32).contiguous()
+        if mu.numel() != self.n_rigid():
+            raise ValueError(f"expected {self.n_rigid()} rigid parameters, got {mu.numel()}")
+        return mu
+
+    def rigid_value_and_grad(self, mu, level: int = 0, grad: bool = True):
+        """D and dD/dmu at the rigid transform mu."""
+        mu = _mu(self, mu)
+        g = self._torch.empty_like(mu) if grad else None
+        D = ctypes.c_double()
+        _check(load().srwcr_rigid_value_and_grad(self._h, level, _ptr(mu), ctypes.byref(D),
+                                                 _ptr(g) if grad else None))
+        return (D.value, g) if grad else D.value
+
+    def rigid_to_ffd(self, mu, level: int = 0):
+        """FFD coefficients whose warp equals the rigid transform mu."""
+        mu = _mu(self, mu)
+        c = self.zeros(level)
+        _check(load().srwcr_rigid_to_ffd(self._h, level, _ptr(mu), _ptr(c)))
+        self._torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return c
+
+    def rigid_register(self, mu=None, n_levels: int = 1, opts: Optional[LbfgsOpts] = None,
+                       check: bool = True):
+        """Coarse-to-fine L-BFGS over the rigid parameters; returns (mu, report)."""
+        mu = _mu(self, mu if mu is not None else np.zeros(self.n_rigid(), np.float32)).clone()
+        rep = Report()
+        st = load().srwcr_rigid_register(self._h, _ptr(mu), int(n_levels),
+                                         ctypes.byref(opts) if opts is not None else None,
+                                         ctypes.byref(rep))
+        if check and st not in (0, 7, 5):
+            _check(st)
+        rep.status_code = st
+        return mu, rep
+
+    for f in (n_rigid, rigid_value_and_grad, rigid_to_ffd, rigid_register):
+        setattr(SRWCR, f.__name__, f)
+
+
+_rigid_methods()
 
 
 class _DeviceArray:

@@ -189,4 +189,42 @@ __device__ __forceinline__ void spatial_weights(const Geo& g, int x, int y, int 
   else { sc[2] = 0; sw[2][0] = 1.f; sw[2][1] = sw[2][2] = sw[2][3] = 0.f; }
 }
 
+// Rigid model (the pre-alignment of Sec. III-D with the same measure):
+// T(x) = R (x - x_c) + x_c + t.  The per-evaluation table (built in FP64 by
+// k_rigid_setup from the parameters) holds R row-major [0, 9), t [9, 12),
+// x_c [12, 15) and dR/d(angle) for up to three angles [15, 42).
+constexpr int kRigidTab = 48;
+
+struct Rigid {
+  float R[9];
+  float t[3];
+  float ctr[3];
+};
+
+__device__ __forceinline__ Rigid load_rigid(const float* __restrict__ tab) {
+  Rigid r;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) r.R[i] = __ldg(tab + i);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r.t[i] = __ldg(tab + 9 + i);
+    r.ctr[i] = __ldg(tab + 12 + i);
+  }
+  return r;
+}
+
+// u = T(x) - x for voxel (x, y, z).
+template <int DIM>
+__device__ __forceinline__ void rigid_displacement(const Rigid& r, int x, int y, int z, float u[3]) {
+  const float q0 = (float)x - r.ctr[0], q1 = (float)y - r.ctr[1];
+  const float q2 = DIM == 3 ? (float)z - r.ctr[2] : 0.f;
+  const float xv[3] = {(float)x, (float)y, (float)z};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k >= DIM) { u[k] = 0.f; continue; }
+    const float rq = fmaf(r.R[3 * k], q0, fmaf(r.R[3 * k + 1], q1, r.R[3 * k + 2] * q2));
+    u[k] = (rq + r.ctr[k] + r.t[k]) - xv[k];
+  }
+}
+
 }  // namespace srwcr

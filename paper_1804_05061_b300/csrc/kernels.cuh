@@ -37,12 +37,15 @@ __device__ __forceinline__ void tile_origin(const Geo& g, int b, int o[3]) {
 }
 
 // Histogram layout in shared memory: [hb2][hb1][hb0][nbins][NCH] uint64.
-// Global accumulators: [R][nbins][NCH] uint64 (fixed point).
-template <int DIM, typename T, bool STATIC>
+// Global accumulators: [R][nbins][NCH] uint64 (fixed point).  RIGID: c is
+// the rigid table (kRigidTab floats) and T is the rigid model.
+template <int DIM, typename T, bool STATIC, bool RIGID = false>
 __global__ void __launch_bounds__(256)
 k_accumulate(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
              const float* __restrict__ c, unsigned long long* __restrict__ acc, float s0,
              float s1) {
+  Rigid rg{};
+  if (RIGID) rg = load_rigid(c);
   extern __shared__ __align__(16) unsigned long long hist[];
   constexpr int NCH = STATIC ? 1 : 2;
   const int nb = g.nbins;
@@ -71,9 +74,14 @@ k_accumulate(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
     const float h1 = parzen_upper(fa), h0 = 1.f - h1;
     float m1 = 0.f, m2 = 0.f;
     if (!STATIC) {
-      float u[3], bw[3][4], gm[3];
-      int fc[3];
-      ffd_displacement<DIM>(g, c, x, y, z, u, fc, bw);
+      float u[3], gm[3];
+      if (RIGID) {
+        rigid_displacement<DIM>(rg, x, y, z, u);
+      } else {
+        float bw[3][4];
+        int fc[3];
+        ffd_displacement<DIM>(g, c, x, y, z, u, fc, bw);
+      }
       float B = sample_moving<DIM, T>(g, M, (float)x + u[0], (float)y + u[1],
                                       (float)z + u[2], gm);
       B = fminf(fmaxf(B, 0.f), L);
@@ -353,6 +361,43 @@ k_reduce_D(const double* __restrict__ Dr, const double* __restrict__ stats, long
 // with m1' = d/dB sum_b b h(b-B), m2' = d/dB sum_b b^2 h(b-B); then
 //   g[k][node] += G(x) dM/dy_k(T(x)) beta(node; x)                     (Eqs. 16, 17)
 // accumulated in a CTA-private tile [DIM][hf2][hf1][hf0] of control points.
+// dD/dB at voxel (x, y, z) (Eq. 19 with the b-sums in closed form, Eq. 27):
+// scale * [m2'(B) sum_r w_r U_r + 2 m1'(B) sum_r w_r (V_r - sum_a h X_{r,a})]
+// over the voxel's spatial bins, with U = CR/sigma^2, V = (1-CR) mu/sigma^2,
+// X_a = mu(a)/sigma^2; a0, h0, h1: the fixed image's Parzen bins.
+template <int DIM>
+__device__ __forceinline__ float voxel_dDdB(const Geo& g, int x, int y, int z, int a0, float h0,
+                                            float h1, float B, const float* __restrict__ U,
+                                            const float* __restrict__ V,
+                                            const float* __restrict__ X, float scale) {
+  const int nb = g.nbins;
+  B = fminf(fmaxf(B, 0.f), (float)(nb - 1));
+  float fb;
+  const int kb = bin_split(B, nb, &fb);
+  const float dm1 = parzen_upper_deriv(fb);
+  const float dm2 = (2.f * (float)kb + 1.f) * dm1;
+  int sc[3];
+  float sw[3][4];
+  spatial_weights<DIM>(g, x, y, z, sc, sw);
+  float su = 0.f, sv = 0.f;
+  const int NZ = DIM == 3 ? 4 : 1;
+  for (int k = 0; k < NZ; ++k)
+    for (int j = 0; j < 4; ++j) {
+      const float wjk = sw[1][j] * sw[2][k];
+      const long long rrow = ((long long)(sc[2] + k) * g.nsb[1] + (sc[1] + j)) * g.nsb[0] + sc[0];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float w = wjk * sw[0][i];
+        if (w == 0.f) continue;  // also keeps boxcar reads inside the patch grid
+        const long long r = rrow + i;
+        const float xr = h0 * __ldg(X + r * nb + a0) + h1 * __ldg(X + r * nb + a0 + 1);
+        su += w * __ldg(U + r);
+        sv += w * (__ldg(V + r) - xr);
+      }
+    }
+  return scale * (dm2 * su + 2.f * dm1 * sv);
+}
+
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256)
 k_adjoint(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
@@ -386,32 +431,9 @@ k_adjoint(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
     int fc[3];
     ffd_displacement<DIM>(g, c, x, y, z, u, fc, bw);
     float B = sample_moving<DIM, T>(g, M, (float)x + u[0], (float)y + u[1], (float)z + u[2], gm);
-    B = fminf(fmaxf(B, 0.f), L);
-    float fb;
-    const int kb = bin_split(B, nb, &fb);
-    const float dm1 = parzen_upper_deriv(fb);
-    const float dm2 = (2.f * (float)kb + 1.f) * dm1;
-    int sc[3];
-    float sw[3][4];
-    spatial_weights<DIM>(g, x, y, z, sc, sw);
-    float su = 0.f, sv = 0.f;
-    const int NZ = DIM == 3 ? 4 : 1;
-    for (int k = 0; k < NZ; ++k)
-      for (int j = 0; j < 4; ++j) {
-        const float wjk = sw[1][j] * sw[2][k];
-        const long long rrow = ((long long)(sc[2] + k) * g.nsb[1] + (sc[1] + j)) * g.nsb[0] + sc[0];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float w = wjk * sw[0][i];
-          if (w == 0.f) continue;  // also keeps boxcar reads inside the patch grid
-          const long long r = rrow + i;
-          const float xr = h0 * __ldg(X + r * nb + a0) + h1 * __ldg(X + r * nb + a0 + 1);
-          su += w * __ldg(U + r);
-          sv += w * (__ldg(V + r) - xr);
-        }
-      }
-    const float G = scale * (dm2 * su + 2.f * dm1 * sv);
+    const float G = voxel_dDdB<DIM>(g, x, y, z, a0, h0, h1, B, U, V, X, scale);
     if (G == 0.f) continue;
+    const int NZ = DIM == 3 ? 4 : 1;
     float gk[3] = {G * gm[0], G * gm[1], DIM == 3 ? G * gm[2] : 0.f};
     for (int nn = 0; nn < NZ; ++nn)
       for (int m = 0; m < 4; ++m) {

@@ -120,6 +120,8 @@ struct LbfgsWork {
   double* Edev = nullptr;  // device scalar: bending energy at the evaluated point
   double* host = nullptr;  // pinned [3]
   double wp = 0.0;         // penalty weight w_p of Eq. (1)
+  bool rigid = false;      // x holds rigid parameters (angles as angle / ang_scale)
+  double ang_scale = 1.0;
 };
 
 void free_work(LbfgsWork& w) {
@@ -172,8 +174,17 @@ srwcr_status scal(srwcr_ctx* ctx, LbfgsWork& w, float a, const float* x, float* 
 }
 
 // Cost of Eq. (1) at x: f = D + w_p C_p, g = its gradient.
+// The rigid model's bending energy is zero (an affine displacement), so its
+// cost is D alone.
 srwcr_status eval(srwcr_ctx* ctx, int level, LbfgsWork& w, const float* x, float* g, double* f) {
   Level& lv = ctx->lev[level];
+  if (w.rigid) {
+    RET_IF(run_rigid(ctx, lv, x, g, w.ang_scale));
+    CK(cudaMemcpyAsync(w.host + 1, lv.D, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *f = w.host[1];
+    return SRWCR_OK;
+  }
   RET_IF(run_value(ctx, lv, x, true));
   RET_IF(run_grad(ctx, lv, x, nullptr, g, true));
   if (w.wp > 0.0) RET_IF(bending_energy(ctx, level, x, w.Edev, g, (float)w.wp));

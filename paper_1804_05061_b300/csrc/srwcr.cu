@@ -22,6 +22,7 @@
 #include "kernels.cuh"
 #include "kernels_mas_a.cuh"
 #include "kernels_rows.cuh"
+#include "kernels_rigid.cuh"
 
 using namespace srwcr;
 
@@ -129,6 +130,8 @@ struct srwcr_ctx {
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;
   srwcr_bend_levels* bend = nullptr;  // created on first use
+  float* rigid_tab = nullptr;         // rigid model: per-evaluation table (kRigidTab floats)
+  double* rigid_acc = nullptr;        // rigid model: FP64 gradient accumulators [6]
 };
 
 namespace {
@@ -378,6 +381,8 @@ srwcr_status set_smem_limits() {
   CK(cudaFuncSetAttribute(k_accumulate<3, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_accumulate<2, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_accumulate<2, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate<3, T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate<2, T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_accumulate_mas_a<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
@@ -537,6 +542,79 @@ srwcr_status run_grad(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD
                       : launch_adjoint<float>(ctx, lv, c, gD, g, kept_warp));
   prof_end(ctx, kProfAdjoint, ev);
   ctx->launches += 1;
+  return SRWCR_OK;
+}
+
+// Rigid model on the general kernels of the level: value into lv.D (and
+// the tables); with g, dD/dmu (ndim translations, then the angles; an angle
+// is mu * ang_scale radians).
+template <typename T>
+srwcr_status launch_rigid(srwcr_ctx* ctx, Level& lv, const float* g_unused, bool grad) {
+  (void)g_unused;
+  const Geo& gv = lv.gv;
+  const int nblk = gv.ntile[0] * gv.ntile[1] * gv.ntile[2];
+  const T* A = (const T*)lv.A;
+  const T* M = (const T*)lv.M;
+  if (!grad) {
+    if (ctx->cfg.ndim == 3)
+      k_accumulate<3, T, false, true><<<nblk, kBlock, lv.smem_acc, ctx->stream>>>(
+          gv, A, M, ctx->rigid_tab, lv.S, lv.s1, lv.s2);
+    else
+      k_accumulate<2, T, false, true><<<nblk, kBlock, lv.smem_acc, ctx->stream>>>(
+          gv, A, M, ctx->rigid_tab, lv.S, lv.s1, lv.s2);
+  } else {
+    const float invZ = (float)(1.0 / lv.Z);
+    if (ctx->cfg.ndim == 3)
+      k_adjoint_rigid<3, T><<<nblk, kBlock, 0, ctx->stream>>>(gv, A, M, ctx->rigid_tab, lv.U, lv.V,
+                                                              lv.X, nullptr, invZ, ctx->rigid_acc);
+    else
+      k_adjoint_rigid<2, T><<<nblk, kBlock, 0, ctx->stream>>>(gv, A, M, ctx->rigid_tab, lv.U, lv.V,
+                                                              lv.X, nullptr, invZ, ctx->rigid_acc);
+  }
+  CKL();
+  return SRWCR_OK;
+}
+
+srwcr_status ensure_rigid(srwcr_ctx* ctx) {
+  if (ctx->cfg.role != SRWCR_ROLE_M_AS_B)
+    return fail(SRWCR_EINVAL, "the rigid model takes the moving image as B only");
+  if (!ctx->rigid_tab) CK(cudaMalloc((void**)&ctx->rigid_tab, sizeof(float) * kRigidTab));
+  if (!ctx->rigid_acc) CK(cudaMalloc((void**)&ctx->rigid_acc, sizeof(double) * 8));
+  return SRWCR_OK;
+}
+
+// Value (and, with g != NULL, gradient) of the rigid model at mu.
+srwcr_status run_rigid(srwcr_ctx* ctx, Level& lv, const float* mu, float* g, double ang_scale) {
+  RET_IF(ensure_rigid(ctx));
+  const Geo& gv = lv.gv;
+  const int nd = ctx->cfg.ndim;
+  k_rigid_setup<<<1, 32, 0, ctx->stream>>>(mu, nd, 0.5 * (gv.n[0] - 1), 0.5 * (gv.n[1] - 1),
+                                           nd == 3 ? 0.5 * (gv.n[2] - 1) : 0.0, ang_scale,
+                                           ctx->rigid_tab);
+  CKL();
+  CK(cudaMemsetAsync(lv.S, 0, (size_t)lv.g.R * lv.g.nbins * 2 * sizeof(unsigned long long),
+                     ctx->stream));
+  cudaEvent_t ev = prof_begin(ctx);
+  RET_IF(is_bf16(ctx) ? launch_rigid<__nv_bfloat16>(ctx, lv, nullptr, false)
+                      : launch_rigid<float>(ctx, lv, nullptr, false));
+  prof_end(ctx, kProfAccumulate, ev);
+  ev = prof_begin(ctx);
+  launch_finalize_sparse(ctx, lv);
+  CKL();
+  k_reduce_D<<<1, 1024, 0, ctx->stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg);
+  CKL();
+  prof_end(ctx, kProfFinalize, ev);
+  ctx->launches += 4;
+  lv.tables = true;
+  if (!g) return SRWCR_OK;
+  CK(cudaMemsetAsync(ctx->rigid_acc, 0, sizeof(double) * 8, ctx->stream));
+  ev = prof_begin(ctx);
+  RET_IF(is_bf16(ctx) ? launch_rigid<__nv_bfloat16>(ctx, lv, nullptr, true)
+                      : launch_rigid<float>(ctx, lv, nullptr, true));
+  prof_end(ctx, kProfAdjoint, ev);
+  k_rigid_grad_out<<<1, 32, 0, ctx->stream>>>(ctx->rigid_acc, nd, ang_scale, g);
+  CKL();
+  ctx->launches += 2;
   return SRWCR_OK;
 }
 
@@ -700,6 +778,8 @@ const char* srwcr_last_error(void) { return g_err.c_str(); }
 void srwcr_destroy(srwcr_ctx* ctx) {
   if (!ctx) return;
   free_bend(ctx);
+  if (ctx->rigid_tab) cudaFree(ctx->rigid_tab);
+  if (ctx->rigid_acc) cudaFree(ctx->rigid_acc);
   for (int l = 0; l < ctx->nlev; ++l) free_level(ctx->lev[l]);
   if (ctx->D_host) cudaFreeHost(ctx->D_host);
   if (ctx->flag_host) cudaFreeHost(ctx->flag_host);
@@ -1388,5 +1468,6 @@ extern "C" srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c
 }
 
 #include "lbfgs.cuh"
+#include "rigid.cuh"
 #include "bending.cuh"
 #include "batch.cuh"

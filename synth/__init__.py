@@ -438,3 +438,46 @@ def inverse_displacement(v: np.ndarray, iterations: int = 30) -> np.ndarray:
         w = -np.stack([ndimage.map_coordinates(v[k], coords, order=1, mode="nearest")
                        for k in range(d)])
     return w
+
+
+# ----------------------------------------------------------------------------
+# Rigid pre-alignment (known rigid transform)
+# ----------------------------------------------------------------------------
+def rigid_rotation(mu) -> np.ndarray:
+    """Rotation matrix of rigid parameters (x, y[, z] order): 3-D
+    (t_x, t_y, t_z, alpha, beta, gamma) with extrinsic x-y-z Euler angles,
+    2-D (t_x, t_y, theta); via SciPy's Rotation."""
+    from scipy.spatial.transform import Rotation
+    mu = np.asarray(mu, np.float64)
+    if mu.size == 6:
+        return Rotation.from_euler("xyz", mu[3:6]).as_matrix()
+    return Rotation.from_euler("z", mu[2]).as_matrix()[:2, :2]
+
+
+def rigid_pair(kind: str, dims, mu, seed: int, contrast: str = "inverted"):
+    """Fixed phantom F (the 'ct' or 'ellipse' recipe of small_pair) and a
+    moving image M = g(F o T^-1) such that M(T(x)) = g(F(x)) for the rigid
+    map T(x) = R (x - x_c) + x_c + t, x_c = (N - 1) / 2: M is F resampled at
+    T^-1(y) = R^T (y - x_c - t) + x_c (trilinear, clamped) and passed through
+    the intensity map g (inverted contrast: a multi-modal pair)."""
+    nd = len(dims)
+    rng = np.random.default_rng(seed)
+    if kind == "ct":
+        nx, ny, nz = dims
+        f = _ct_phantom(nx, ny, nz, rng, n_vessels=8) + rng.normal(0, 20.0, (nz, ny, nx))
+    elif kind == "ellipse":
+        nx, ny = dims
+        f = _ellipses_2d(max(nx, ny), rng)[:ny, :nx] + rng.normal(0, 0.02, (ny, nx))
+    else:
+        raise ValueError(kind)
+    R = rigid_rotation(mu)
+    t = np.asarray(mu, np.float64)[:nd]
+    ctr = np.array([0.5 * (dims[d] - 1) for d in range(nd)])
+    grids = np.meshgrid(*[np.arange(dims[d]) for d in reversed(range(nd))], indexing="ij")
+    pts = np.stack([g.ravel() for g in reversed(grids)], axis=1).astype(np.float64)  # x, y[, z]
+    src = (pts - ctr - t) @ R + ctr            # R^T (y - x_c - t) + x_c, row-vector form
+    coords = src[:, ::-1].T                    # (z, y, x) order for map_coordinates
+    m = ndimage.map_coordinates(f, coords, order=1, mode="nearest").reshape(f.shape)
+    if contrast == "inverted":
+        m = m.max() - 0.5 * m
+    return np.ascontiguousarray(f, np.float32), np.ascontiguousarray(m, np.float32)
