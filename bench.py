@@ -64,6 +64,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(t: float, dist, device) -> float:
+    """The slowest rank's time (every rank gets it); t itself without a
+    process group.  device: where the collective's tensor lives (a CUDA
+    device under NCCL, "cpu" under gloo)."""
+    if dist is None:
+        return t
+    import torch
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(ws: int, units_per_rank: float, seconds: float) -> float:
+    """Replicas: every rank processes the same units, so the job's rate is
+    ws * units / (the slowest rank's time)."""
+    return ws * units_per_rank / seconds
+
+
 class Clocks:
     """nvidia-smi sampling of SM clock and throttle reasons during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -222,12 +240,7 @@ def bench_batch(args, eng, torch, dist, ws):
         s1.record(stream)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
-        t = s0.elapsed_time(s1) / 1e3
-        if dist is not None:
-            tt = torch.tensor([t], dtype=torch.float64, device=cs[0].device)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return t
+        return max_over_ranks(s0.elapsed_time(s1) / 1e3, dist, cs[0].device)
 
     def plain():
         for i, e in enumerate(engines):
@@ -277,11 +290,11 @@ def bench_batch(args, eng, torch, dist, ws):
                     f"{vox} voxels in all, FFD spacing 8, spatial bins on the FFD grid, 32 "
                     "intensity bins, BF16 storage, autotuned tiles",
         "metric": "pairs/s (value+gradient of every pair)",
-        "plain_pairs_per_s": ws * n * steps / t_plain,
-        "batched_pairs_per_s": ws * n * steps / t_eager,
-        "graph_pairs_per_s": ws * n * steps / t_graph,
+        "plain_pairs_per_s": whole_job_rate(ws, n * steps, t_plain),
+        "batched_pairs_per_s": whole_job_rate(ws, n * steps, t_eager),
+        "graph_pairs_per_s": whole_job_rate(ws, n * steps, t_graph),
         "graph_vs_plain": t_plain / t_graph,
-        "batched_gvoxel_per_s": ws * vox * steps / t_graph / 1e9,
+        "batched_gvoxel_per_s": whole_job_rate(ws, vox * steps, t_graph) / 1e9,
         "launches_per_eval_batched": launches,
         "launches_per_eval_plain": 6 * n,
         "max_abs_D_diff_batched_vs_plain": float(np.abs(D_batch - D_plain).max()),
@@ -481,12 +494,8 @@ def main():
     e.set_profiling(False)
     kms, kcnt, launches = e.profile_read(reset=True)
     step_ms = sum(s.elapsed_time(t) for s, t in zip(starts, ends))
-    t_dev = step_ms / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
-    value = ws * prob.n_voxels * args.steps / t_dev / 1e9
+    t_dev = max_over_ranks(step_ms / 1e3, dist, dev)
+    value = whole_job_rate(ws, prob.n_voxels * args.steps, t_dev) / 1e9
 
     # End to end through the host-buffer entry point: H2D c, compute, D2H g and D.
     c_host = np.ascontiguousarray(c_np.ravel())
@@ -497,12 +506,8 @@ def main():
     n_e2e = max(3, min(args.steps, 20))
     for _ in range(n_e2e):
         e.value_and_grad_host(c_host, g_host)
-    te = time.perf_counter() - te
-    if dist is not None:
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
-    e2e = {"value": ws * prob.n_voxels * n_e2e / te / 1e9, "unit": "Gvoxel/s",
+    te = max_over_ranks(time.perf_counter() - te, dist, dev)
+    e2e = {"value": whole_job_rate(ws, prob.n_voxels * n_e2e, te) / 1e9, "unit": "Gvoxel/s",
            "h2d_bytes_per_step": int(c_host.nbytes), "d2h_bytes_per_step": int(g_host.nbytes + 8),
            "steps": n_e2e}
 
