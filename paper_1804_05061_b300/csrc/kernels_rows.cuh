@@ -373,19 +373,40 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
     const bool multi = cnt > cb;                // CTA-uniform
     for (int i = threadIdx.x; i < 3 * NPY * S; i += blockDim.x) hlo[i] = 0u;
     __syncthreads();
+    // A row's permutation and fixed-image values are loaded in lane order
+    // (independent of each other) one row ahead; the value lane l needs,
+    // that of voxel o + perm[l], comes by shuffle.
+    auto fetch = [&](int r, int* pp, float* aa) {
+      *pp = 0;
+      *aa = 0.f;
+      if (r >= nrows) return false;
+      const int y = TO.o[1] + r % g.tile[1], z = TO.o[2] + r / g.tile[1];
+      if (y >= g.n[1] || z >= g.n[2]) return false;
+      const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
+      *pp = perm[rowid * 32 + lane];
+      const int xn = TO.o[0] + lane;
+      if (xn < g.n[0]) *aa = ldval(A + ((long long)z * g.n[1] + y) * g.n[0] + xn);
+      return true;
+    };
+    int p_next;
+    float a_next;
+    bool ok_next = fetch(warp, &p_next, &a_next);
     for (int row = warp; row < nrows; row += kAccWarps) {
+      const int p = p_next;
+      const float a_lane = a_next;
+      const bool ok = ok_next;
+      ok_next = fetch(row + kAccWarps, &p_next, &a_next);
+      if (!ok) continue;  // warp-uniform
       const int yl = row % g.tile[1], zl = row / g.tile[1];
       const int y = TO.o[1] + yl, z = TO.o[2] + zl;
-      if (y >= g.n[1] || z >= g.n[2]) continue;  // warp-uniform
 
-      const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
-      const int p = perm[rowid * 32 + lane];
       const int x = TO.o[0] + p;
       const bool act = x < g.n[0];
       const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
+      const float av = __shfl_sync(0xffffffffu, a_lane, p);
       float fa = 0.f;
       int key = kSentinel;
-      if (act) key = bin_split(fminf(fmaxf(ldval(A + idx), 0.f), L), nb, &fa);
+      if (act) key = bin_split(fminf(fmaxf(av, 0.f), L), nb, &fa);
       if (multi) {
         // Rows with no voxel whose bins fall in this chunk wait for their pass.
         const bool in = act && ((unsigned)(a2c[key] - c0) < (unsigned)cb ||
@@ -705,33 +726,65 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
   const int xlast = min(TO.o[0] + 31, g.n[0] - 1);
   const int nxn = xlast / g.fsp[0] - TO.f[0] + 4;
   const int nrows = g.tile[1] * g.tile[2];
+  // A row's loads (lane order, lane l reading voxel o + l, so they do not wait
+  // for the permutation) are issued one row ahead of its processing; the
+  // permuted values are then exchanged by shuffles.
+  struct RowLoad {
+    int p;
+    float a;
+    float4 b;
+    bool ok;
+  };
+  auto fetch = [&](int r) {
+    RowLoad f{0, 0.f, make_float4(0.f, 0.f, 0.f, 0.f), false};
+    if (r >= nrows) return f;
+    const int y = TO.o[1] + r % g.tile[1], z = TO.o[2] + r / g.tile[1];
+    if (y >= g.n[1] || z >= g.n[2]) return f;
+    f.ok = true;
+    const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
+    f.p = perm[rowid * 32 + lane];
+    const int xn = TO.o[0] + lane;
+    if (xn < g.n[0]) {
+      const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + xn;
+      f.a = ldval(A + idx);
+      if (bg) f.b = __ldg(bg + idx);
+    }
+    return f;
+  };
+  RowLoad nxt = fetch(warp);
   for (int row = warp; row < nrows; row += kAdjWarps) {
+    const RowLoad cur = nxt;
+    nxt = fetch(row + kAdjWarps);
+    if (!cur.ok) continue;  // warp-uniform
     const int yl = row % g.tile[1], zl = row / g.tile[1];
     const int y = TO.o[1] + yl, z = TO.o[2] + zl;
-    if (y >= g.n[1] || z >= g.n[2]) continue;
     const AxisEntry ye = yt[yl];
     if (!bg) {
       row_cyz<DIM>(g, CZ, zl, ye, nxn, cyz, lane);
       __syncwarp();
     }
 
-    const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
-    const int p = perm[rowid * 32 + lane];
+    const int p = cur.p;
     const int x = TO.o[0] + p;
     const bool act = x < g.n[0];
+    const float av = __shfl_sync(0xffffffffu, cur.a, p);
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (bg) {  // the value pass at the same coefficients stored the warp
+      s.x = __shfl_sync(0xffffffffu, cur.b.x, p);
+      s.y = __shfl_sync(0xffffffffu, cur.b.y, p);
+      s.z = __shfl_sync(0xffffffffu, cur.b.z, p);
+      s.w = __shfl_sync(0xffffffffu, cur.b.w, p);
+    }
     float gm[3] = {0.f, 0.f, 0.f};
     float dm1 = 0.f, dm2 = 0.f, h0 = 0.f, h1 = 0.f;
     int key = kSentinel;
     if (act) {
-      const long long idx = ((long long)z * g.n[1] + y) * g.n[0] + x;
       float fa;
-      key = bin_split(fminf(fmaxf(ldval(A + idx), 0.f), L), nb, &fa);
+      key = bin_split(fminf(fmaxf(av, 0.f), L), nb, &fa);
       h1 = parzen_upper(fa);
       h0 = 1.f - h1;
       float B;
       if (bg) {
-        // The value pass at the same coefficients stored the warp.
-        const float4 s = __ldg(bg + idx);
         B = s.x;
         gm[0] = s.y;
         gm[1] = s.z;
