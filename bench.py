@@ -497,9 +497,11 @@ def main():
     t_dev = max_over_ranks(step_ms / 1e3, dist, dev)
     value = whole_job_rate(ws, prob.n_voxels * args.steps, t_dev) / 1e9
 
-    # End to end through the host-buffer entry point: H2D c, compute, D2H g and D.
-    c_host = np.ascontiguousarray(c_np.ravel())
-    g_host = np.zeros_like(c_host)
+    # End to end through the host-buffer entry point: H2D c from pinned host
+    # memory, compute, D2H g and D into pinned host memory.
+    c_pin = torch.from_numpy(np.ascontiguousarray(c_np.ravel())).pin_memory()
+    g_pin = torch.zeros_like(c_pin).pin_memory()
+    c_host, g_host = c_pin.numpy(), g_pin.numpy()
     for _ in range(2):
         e.value_and_grad_host(c_host, g_host)
     te = time.perf_counter()
@@ -525,19 +527,35 @@ def main():
     peak, peak_kind = hbm_peak()
     achieved = bytes_alg[dom] / (avg[dom] / 1e3) / 1e9 if avg[dom] > 0 else 0.0
     traffic = None
+    warp_inst = None
     prof_file = os.path.join(ROOT, "profiles", f"{dom}_{args.config}_{args.storage}_traffic.json")
     if os.path.exists(prof_file):
         try:
             pj = json.load(open(prof_file))
             if pj.get("kernel_hash") == kernel_hash():
                 traffic = pj.get("dram_bytes_per_launch")
+                warp_inst = pj.get("warp_instructions")
         except Exception:
             traffic = None
+    # The kernel's real limiter is instruction issue (no dense contraction;
+    # HBM-light): executed warp-instructions per launch (ncu, same kernel
+    # source) over its event time, against 4 schedulers x SMs x max SM clock.
+    try:
+        sm_mhz = float(json.load(open(PEAKS_FILE))["sm_max_mhz"])
+    except Exception:
+        sm_mhz = 2032.0
+    issue_peak = 4 * torch.cuda.get_device_properties(dev).multi_processor_count * sm_mhz * 1e6
+    issue = None
+    if warp_inst and avg[dom] > 0:
+        rate = warp_inst / (avg[dom] / 1e3)
+        issue = {"warp_instructions_per_launch": warp_inst, "achieved_per_s": rate,
+                 "peak_per_s": issue_peak, "frac": rate / issue_peak,
+                 "source": os.path.relpath(prof_file, ROOT)}
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "algorithmic_bytes": bytes_alg[dom],
                 "kernel_ms": {k: round(v, 4) for k, v in avg.items()},
-                "algorithmic_bytes_per_voxel_step": 4 * esz}
+                "algorithmic_bytes_per_voxel_step": 4 * esz, "issue": issue}
 
     reg = None
     if not args.no_registration and args.config == "c2":

@@ -174,4 +174,58 @@ __global__ void k_rigid_to_ffd(const Geo g, int ndim, const float* __restrict__ 
   }
 }
 
+// Chain rule through the FFD form of a rigid transform: with c_j =
+// R (p_j - x_c) + x_c + t - p_j at node j, dD/dt_k = sum_j g[k][j] and
+// dD/d(angle) = sum_j sum_k g[k][j] ((dR/d(angle)) (p_j - x_c))_k, reduced
+// per CTA into acc (FP64).  256 threads per CTA.
+template <int DIM>
+__global__ void __launch_bounds__(256)
+k_rigid_chain(const Geo g, const float* __restrict__ tab, const float* __restrict__ grad,
+              double* __restrict__ acc) {
+  constexpr int NA = DIM == 3 ? 3 : 1;
+  constexpr int NP = DIM + NA;
+  __shared__ float red[8][NP];
+  float part[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) part[i] = 0.f;
+  const long long n = g.ncoef;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const int j0 = (int)(i % g.nf[0]);
+    const int j1 = (int)((i / g.nf[0]) % g.nf[1]);
+    const int j2 = (int)(i / ((long long)g.nf[0] * g.nf[1]));
+    const float q[3] = {(float)((j0 - 1) * g.fsp[0]) - __ldg(tab + 12),
+                        (float)((j1 - 1) * g.fsp[1]) - __ldg(tab + 13),
+                        DIM == 3 ? (float)((j2 - 1) * g.fsp[2]) - __ldg(tab + 14) : 0.f};
+    float gk[3];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      gk[k] = __ldg(grad + k * n + i);
+      part[k] += gk[k];
+    }
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      const float* dR = tab + 15 + 9 * a;
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k)
+        s = fmaf(gk[k], fmaf(__ldg(dR + 3 * k), q[0], fmaf(__ldg(dR + 3 * k + 1), q[1], __ldg(dR + 3 * k + 2) * q[2])), s);
+      part[DIM + a] += s;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    float s = part[i];
+#pragma unroll
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) red[warp][i] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NP) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += (double)red[w][threadIdx.x];
+    atomicAdd(acc + threadIdx.x, s);
+  }
+}
+
 }  // namespace srwcr

@@ -132,6 +132,8 @@ struct srwcr_ctx {
   srwcr_bend_levels* bend = nullptr;  // created on first use
   float* rigid_tab = nullptr;         // rigid model: per-evaluation table (kRigidTab floats)
   double* rigid_acc = nullptr;        // rigid model: FP64 gradient accumulators [6]
+  float* rigid_c = nullptr;           // rigid model: FFD form of the transform (level 0 size)
+  float* rigid_g = nullptr;           // rigid model: dD/dc of that FFD form
 };
 
 namespace {
@@ -580,10 +582,18 @@ srwcr_status ensure_rigid(srwcr_ctx* ctx) {
     return fail(SRWCR_EINVAL, "the rigid model takes the moving image as B only");
   if (!ctx->rigid_tab) CK(cudaMalloc((void**)&ctx->rigid_tab, sizeof(float) * kRigidTab));
   if (!ctx->rigid_acc) CK(cudaMalloc((void**)&ctx->rigid_acc, sizeof(double) * 8));
+  const size_t nc = (size_t)ctx->lev[0].g.ncoef * ctx->cfg.ndim;  // level 0 is the largest
+  if (!ctx->rigid_c) CK(cudaMalloc((void**)&ctx->rigid_c, sizeof(float) * nc));
+  if (!ctx->rigid_g) CK(cudaMalloc((void**)&ctx->rigid_g, sizeof(float) * nc));
   return SRWCR_OK;
 }
 
-// Value (and, with g != NULL, gradient) of the rigid model at mu.
+// Value (and, with g != NULL, gradient) of the rigid model at mu.  On a
+// row-parallel level the transform runs through the FFD kernels in its exact
+// FFD form (the affine displacement sampled at the control nodes, which the
+// cubic B-spline reproduces at every voxel, so D is the same function of mu)
+// and dD/dmu is dD/dc chained through that form; otherwise the general
+// per-voxel kernels take the rigid map directly.
 srwcr_status run_rigid(srwcr_ctx* ctx, Level& lv, const float* mu, float* g, double ang_scale) {
   RET_IF(ensure_rigid(ctx));
   const Geo& gv = lv.gv;
@@ -592,6 +602,24 @@ srwcr_status run_rigid(srwcr_ctx* ctx, Level& lv, const float* mu, float* g, dou
                                            nd == 3 ? 0.5 * (gv.n[2] - 1) : 0.0, ang_scale,
                                            ctx->rigid_tab);
   CKL();
+  ctx->launches += 1;
+  if (lv.rows) {
+    const int cb = (int)std::min<long long>(148 * 4, (gv.ncoef + 255) / 256);
+    k_rigid_to_ffd<<<cb, 256, 0, ctx->stream>>>(gv, nd, ctx->rigid_tab, ctx->rigid_c);
+    CKL();
+    ctx->launches += 1;
+    RET_IF(run_value(ctx, lv, ctx->rigid_c, g != nullptr));
+    if (!g) return SRWCR_OK;
+    RET_IF(run_grad(ctx, lv, ctx->rigid_c, nullptr, ctx->rigid_g, true));
+    CK(cudaMemsetAsync(ctx->rigid_acc, 0, sizeof(double) * 8, ctx->stream));
+    if (nd == 3) k_rigid_chain<3><<<cb, 256, 0, ctx->stream>>>(gv, ctx->rigid_tab, ctx->rigid_g, ctx->rigid_acc);
+    else k_rigid_chain<2><<<cb, 256, 0, ctx->stream>>>(gv, ctx->rigid_tab, ctx->rigid_g, ctx->rigid_acc);
+    CKL();
+    k_rigid_grad_out<<<1, 32, 0, ctx->stream>>>(ctx->rigid_acc, nd, ang_scale, g);
+    CKL();
+    ctx->launches += 2;
+    return SRWCR_OK;
+  }
   CK(cudaMemsetAsync(lv.S, 0, (size_t)lv.g.R * lv.g.nbins * 2 * sizeof(unsigned long long),
                      ctx->stream));
   cudaEvent_t ev = prof_begin(ctx);
@@ -604,7 +632,7 @@ srwcr_status run_rigid(srwcr_ctx* ctx, Level& lv, const float* mu, float* g, dou
   k_reduce_D<<<1, 1024, 0, ctx->stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg);
   CKL();
   prof_end(ctx, kProfFinalize, ev);
-  ctx->launches += 4;
+  ctx->launches += 3;
   lv.tables = true;
   if (!g) return SRWCR_OK;
   CK(cudaMemsetAsync(ctx->rigid_acc, 0, sizeof(double) * 8, ctx->stream));
@@ -780,6 +808,8 @@ void srwcr_destroy(srwcr_ctx* ctx) {
   free_bend(ctx);
   if (ctx->rigid_tab) cudaFree(ctx->rigid_tab);
   if (ctx->rigid_acc) cudaFree(ctx->rigid_acc);
+  if (ctx->rigid_c) cudaFree(ctx->rigid_c);
+  if (ctx->rigid_g) cudaFree(ctx->rigid_g);
   for (int l = 0; l < ctx->nlev; ++l) free_level(ctx->lev[l]);
   if (ctx->D_host) cudaFreeHost(ctx->D_host);
   if (ctx->flag_host) cudaFreeHost(ctx->flag_host);

@@ -1,5 +1,8 @@
 """GPU tests of the rigid model (the pre-alignment of Sec. III-D with the
 same measure): T(x) = R (x - x_c) + x_c + t about the level's centre.
+Row-parallel levels evaluate it through the FFD kernels in its exact FFD
+form (dD/dmu chained through that form); general-path levels take the
+rigid map directly.
 
 Against the FP64 oracle (oracle.rigid): D within 1e-5 relative, dD/dmu
 within 1e-4 of its norm per entry (FP32 per-voxel terms summed per CTA,
@@ -58,6 +61,16 @@ def check_against_oracle(prob, f, m, mu, storage="f32", boxcar=None, **kw):
 def test_rigid_value_and_gradient_match_oracle(name, kind, prob):
     f, m = synth.small_pair(kind, prob.dims[:prob.ndim], prob.ffd_spacing[:prob.ndim], 2.0, 700)
     check_against_oracle(prob, f, m, random_mu(prob.ndim, 701))
+
+
+@pytest.mark.parametrize("name,kind,prob", CASES[:2])
+def test_rigid_on_the_general_kernels_matches_oracle(name, kind, prob):
+    # A 16-wide tile puts the level on the general per-voxel kernels, which
+    # take the rigid map directly (row-parallel levels use its FFD form).
+    f, m = synth.small_pair(kind, prob.dims[:prob.ndim], prob.ffd_spacing[:prob.ndim], 2.0, 711)
+    tile = (16, 4, 4) if prob.ndim == 3 else (16, 8)
+    e = check_against_oracle(prob, f, m, random_mu(prob.ndim, 712), tile=tile)
+    assert e.levels[0].kernel_path == 0
 
 
 def test_rigid_bf16_storage_matches_oracle_on_rounded_inputs():
