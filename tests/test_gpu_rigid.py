@@ -128,8 +128,9 @@ def test_rigid_registration_recovers_a_known_transform(kind, dims, mu_true, leve
     err_t = np.abs(mu[:nd] - np.asarray(mu_true[:nd])).max()
     err_a = np.abs(mu[nd:] - np.asarray(mu_true[nd:])).max()
     assert err_t < 0.35 and err_a < 0.01, (mu, mu_true)
-    # the reported value is the value at the returned parameters
-    assert abs(e.rigid_value_and_grad(mu, grad=False) - rep.final_value[0]) <= 1e-9
+    # the reported value is the value at the optimiser's point (t, angle * rho);
+    # the returned angles are that point divided by rho and rounded to FP32
+    assert abs(e.rigid_value_and_grad(mu, grad=False) - rep.final_value[0]) <= 2e-6 * D0
 
 
 def test_rigid_errors():
