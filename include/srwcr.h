@@ -62,8 +62,8 @@ enum { SRWCR_ROLE_M_AS_B = 0, SRWCR_ROLE_M_AS_A = 1 };
  * B-spline bins of Eq. (7), K+3 per axis.  Boxcar: Eq. (6) over a regular
  * partition into K patches per axis, patch floor(x K / N) holding voxel x with
  * weight 1 (the RaPTOR-style distribution of Eqs. 13-14, with the Parzen
- * window of Eq. 5 kept); needs sbin_intervals > 0 and runs on the general
- * per-voxel kernels. */
+ * window of Eq. 5 kept); needs sbin_intervals > 0.  Either distribution
+ * runs on the kernels the level's geometry selects (srwcr_level_desc). */
 enum { SRWCR_SPATIAL_BSPLINE = 0, SRWCR_SPATIAL_BOXCAR = 1 };
 
 /* Problem configuration (Sec. II-F gives the paper's defaults: delta = 5,
@@ -289,8 +289,10 @@ srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n_levels,
  * that order); 2-D (t_x, t_y, theta).  Translations in voxels of the level,
  * angles in radians.  The value is Eq. (9) with B(x) = M(T(x)) (the moving
  * image as B only: SRWCR_EINVAL for SRWCR_ROLE_M_AS_A); the gradient is
- * Eq. (16) with dT/dmu in place of the FFD basis.  Runs on the general
- * per-voxel kernels. */
+ * Eq. (16) with dT/dmu in place of the FFD basis.  On a row-parallel level
+ * the transform is evaluated through the FFD kernels in its exact FFD form
+ * (srwcr_rigid_to_ffd) and dD/dmu is dD/dc chained through that form; on a
+ * general-path level the per-voxel kernels take the rigid map directly. */
 
 /* D (host) and, when g_dev != NULL, dD/dmu (device, 6 or 3 floats) at mu.
  * Synchronises.  Errors: SRWCR_EINVAL, SRWCR_ENUMERIC (non-finite mu or

@@ -42,7 +42,8 @@ constexpr int kSentinel = 0x7fffffff;   // key of lanes past the image edge
 
 // Per-axis geometry of one coordinate: FFD cell (relative to the tile's
 // first node), its 4 weights, spatial-bin cell (relative to the tile's first
-// bin) and its 4 weights.
+// bin) and its 4 weights (cubic B-spline, Eq. 7, or the boxcar patch of
+// Eq. 6 with weights 1, 0, 0, 0).
 struct AxisEntry {
   int frel;
   float bf[4];
@@ -55,8 +56,9 @@ __device__ __forceinline__ void axis_entry(const Geo& g, int d, int v, int f0, i
   float t;
   e->frel = ffd_cell(g, d, v, &t) - f0;
   bspline4(t, e->bf);
-  e->srel = sb_cell(g, d, v, &t) - c0;
-  bspline4(t, e->bs);
+  int sc;
+  axis_weights(g, d, v, &sc, e->bs);
+  e->srel = sc - c0;
 }
 
 // Trivial axis (2-D problems have no z).

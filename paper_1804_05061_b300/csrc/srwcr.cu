@@ -704,11 +704,9 @@ void launch_tile_binmask(srwcr_ctx* ctx, const Geo& g, const void* A, unsigned* 
 // each candidate's per-tile masks are built on the device and the largest
 // per-tile count sizes the histogram.  Levels without such a tile keep the
 // general path.
-// The row-parallel kernels bin the fixed image with cubic B-spline spatial
-// weights; the other roles and distributions run the general kernels.
-bool rows_allowed(const srwcr_config& cfg) {
-  return cfg.role == SRWCR_ROLE_M_AS_B && cfg.spatial == SRWCR_SPATIAL_BSPLINE;
-}
+// The row-parallel kernels order each row by the static fixed-image bin, so
+// they serve the moving image as B only (either spatial distribution).
+bool rows_allowed(const srwcr_config& cfg) { return cfg.role == SRWCR_ROLE_M_AS_B; }
 
 srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv, const int* force_tile = nullptr) {
   const srwcr_config& cfg = ctx->cfg;

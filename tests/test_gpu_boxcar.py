@@ -1,7 +1,9 @@
 """GPU tests of the boxcar spatial distribution (Eq. 6): each voxel belongs
 to one patch of a regular K-per-axis partition, patch floor(x K / N), with
 weight 1; the rest of the method (Parzen window, Eqs. 9-12, gradient
-Eqs. 16-21) is unchanged.  Runs on the general per-voxel kernels.
+Eqs. 16-21) is unchanged.  With the moving image as B it runs on the row
+kernels (their per-axis spatial weights become 1, 0, 0, 0); with the moving
+image as A, or a forced narrow tile, on the general per-voxel kernels.
 
 Against the FP64 oracle (its boxcar geometry): D within 1e-5 relative,
 gradient norm within 1e-4, elementwise within 1e-3 of the largest entry, for
@@ -50,7 +52,7 @@ def test_boxcar_value_gradient_and_regions_match_oracle(name, kind, prob, sig, r
     c = synth.coefficients(prob, 601, sig)
     e = engine(prob, f, m, role=role)
     lv = e.levels[0]
-    assert lv.kernel_path == 0
+    assert lv.kernel_path == (1 if role == "mas_b" else 0)
     assert lv.sbins[:prob.ndim] == tuple(prob.sbin_intervals[:prob.ndim])
     assert lv.n_regions == int(np.prod(prob.sbin_intervals[:prob.ndim]))
     D, g = e.value_and_grad(torch.from_numpy(c).cuda())
@@ -65,6 +67,22 @@ def test_boxcar_value_gradient_and_regions_match_oracle(name, kind, prob, sig, r
     g = g.cpu().numpy().astype(np.float64)
     gn, gon = np.linalg.norm(g), np.linalg.norm(go)
     assert abs(gn - gon) <= GNORM_RTOL * gon, (gn, gon)
+    assert np.abs(g - go).max() <= G_ELEM * np.abs(go).max()
+
+
+@pytest.mark.parametrize("name,kind,prob,sig", CASES[:2])
+def test_boxcar_on_the_general_kernels_matches_oracle(name, kind, prob, sig):
+    # A 16-wide tile puts the level on the general per-voxel kernels.
+    f, m = synth.small_pair(kind, prob.dims[:prob.ndim], prob.ffd_spacing[:prob.ndim], 2.0, 604)
+    c = synth.coefficients(prob, 605, sig)
+    tile = (16, 4, 4) if prob.ndim == 3 else (16, 8)
+    e = engine(prob, f, m, tile=tile)
+    assert e.levels[0].kernel_path == 0
+    D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+    st, go = oracle_case(prob, f, m, c, "mas_b")
+    assert abs(D - st.D) <= D_RTOL * abs(st.D), (D, st.D)
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(np.linalg.norm(g) - np.linalg.norm(go)) <= GNORM_RTOL * np.linalg.norm(go)
     assert np.abs(g - go).max() <= G_ELEM * np.abs(go).max()
 
 
