@@ -369,8 +369,6 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   const int xlast = min(TO.o[0] + 31, g.n[0] - 1);
   const int nxn = xlast / g.fsp[0] - TO.f[0] + 4;   // FFD x-nodes of the row
   const int nrows = g.tile[1] * g.tile[2];
-  // Fold lane roles: item t of a pass (8 per pass), y offset fg (j of the bin).
-  const int ft = lane & 7, fg = lane >> 3;
   for (int c0 = 0; c0 < cnt; c0 += cb) {
     const bool multi = cnt > cb;                // CTA-uniform
     for (int i = threadIdx.x; i < 3 * NPY * S; i += blockDim.x) hlo[i] = 0u;
@@ -530,12 +528,13 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
         mybins[2 * q + 1] = sidx | (1 << 8);
       }
       __syncwarp();
-      // Fold: 8 (bin, moment, x-bin) items per pass, each lane adds its item
-      // to y bin fg of the row's z-plane.
-      const float wyf = ye.bs[fg];
-      const int prow = (zl * g.hb[1] + ye.srel + fg) * S;
+      // Fold: each lane takes whole (bin, moment, x-bin) items (32 per pass)
+      // and adds each to the row's 4 y bins of its z-plane (one item decode
+      // per item; all 32 lanes of an update touch one y row, consecutive
+      // items consecutive columns).
+      const int prow = (zl * g.hb[1] + ye.srel) * S;
       const int per_bin = 2 * NXB;
-      for (int f = ft; f < nbin * per_bin; f += 8) {
+      for (int f = lane; f < nbin * per_bin; f += 32) {
         const int e = f / per_bin, r = f % per_bin;
         const int ch = r / NXB, b = r % NXB;
         if (b >= g.hb[0]) continue;
@@ -544,19 +543,25 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
         const int sg = info & 0xff, slot = (info >> 8) & 1;
         float val = mysegS[seg_at<NV>(sg, 4 * b + 2 * slot + ch)];
         if (info & (1 << 9)) val += mysegS[seg_at<NV>(sg - 1, 4 * b + 2 + ch)];
-        const float u = val * (ch ? s2 : s1) * wyf;
-        if (u == 0.f) continue;
-        // Exact split of u into 20-bit fields (power-of-two scalings, floors
-        // and fused subtractions of FP32 values are exact here).
-        const float hf = floorf(u * 0x1p-40f);
-        const float r1 = fmaf(hf, -0x1p40f, u);
-        const float mf = floorf(r1 * 0x1p-20f);
-        const unsigned lo = __float2uint_rn(fmaf(mf, -0x1p20f, r1));
-        const unsigned mid = (unsigned)mf, hi = (unsigned)hf;
-        const int at = prow + ((a2c[a] - c0) * 2 + ch) * g.hb[0] + b;
-        if (lo) atomicAdd(hlo + at, lo);
-        if (mid) atomicAdd(hmid + at, mid);
-        if (hi) atomicAdd(hhi + at, hi);
+        const float uv = val * (ch ? s2 : s1);
+        if (uv == 0.f) continue;
+        const int col = prow + ((a2c[a] - c0) * 2 + ch) * g.hb[0] + b;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const float u = uv * ye.bs[m];
+          if (u == 0.f) continue;
+          // Exact split of u into 20-bit fields (power-of-two scalings,
+          // floors and fused subtractions of FP32 values are exact here).
+          const float hf = floorf(u * 0x1p-40f);
+          const float r1 = fmaf(hf, -0x1p40f, u);
+          const float mf = floorf(r1 * 0x1p-20f);
+          const unsigned lo = __float2uint_rn(fmaf(mf, -0x1p20f, r1));
+          const unsigned mid = (unsigned)mf, hi = (unsigned)hf;
+          const int at = col + m * S;
+          if (lo) atomicAdd(hlo + at, lo);
+          if (mid) atomicAdd(hmid + at, mid);
+          if (hi) atomicAdd(hhi + at, hi);
+        }
       }
       __syncwarp();
     }
