@@ -344,6 +344,13 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
 
   const TileOrigin TO = tile_setup<DIM>(g, tile);
   const int cb = g.cbin;
+  // Prologue in two phases: the y/z tables, then (independent of each other)
+  // the z-contraction of the coefficients (global loads issued first), the
+  // bin maps, the x table and the clearing of the first pass's accumulators
+  // (16-byte stores; 3 * NPY * S is a multiple of 4 words).
+  build_axis_tables<DIM>(g, TO, yt, zt);
+  __syncthreads();
+  build_cz<DIM>(g, TO, c, zt, CZ);
   int cnt = 0;                                // compacted bins of this tile
   {
     const int words = (nb + 31) >> 5;
@@ -360,9 +367,9 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
     }
   }
   build_xtab<NXB>(g, TO, xt);
-  build_axis_tables<DIM>(g, TO, yt, zt);
-  __syncthreads();
-  build_cz<DIM>(g, TO, c, zt, CZ);
+  const int hwords4 = (3 * NPY * S) >> 2;
+  uint4* h4 = reinterpret_cast<uint4*>(hlo);
+  for (int i = threadIdx.x; i < hwords4; i += blockDim.x) h4[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
 
   const int nxb = (g.n[0] + 31) >> 5;
@@ -371,8 +378,10 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   const int nrows = g.tile[1] * g.tile[2];
   for (int c0 = 0; c0 < cnt; c0 += cb) {
     const bool multi = cnt > cb;                // CTA-uniform
-    for (int i = threadIdx.x; i < 3 * NPY * S; i += blockDim.x) hlo[i] = 0u;
-    __syncthreads();
+    if (c0 > 0) {                               // the first pass was cleared above
+      for (int i = threadIdx.x; i < hwords4; i += blockDim.x) h4[i] = make_uint4(0u, 0u, 0u, 0u);
+      __syncthreads();
+    }
     // A row's permutation and fixed-image values are loaded in lane order
     // (independent of each other) one row ahead; the value lane l needs,
     // that of voxel o + perm[l], comes by shuffle.
@@ -684,10 +693,9 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
   for (int i = threadIdx.x; i < DIM * nodes_tile; i += blockDim.x) gt[i] = 0.f;
   build_xtab<NXB>(g, TO, xt);
   build_axis_tables<DIM>(g, TO, yt, zt);
-  __syncthreads();
-  if (!bg) build_cz<DIM>(g, TO, c, zt, CZ);
   // Region tables contracted over z for each of the tile's z-planes, read
-  // from the per-plane tables of k_zcontract.  X is only needed for the
+  // from the per-plane tables of k_zcontract (in the same phase as the axis
+  // tables, which this does not read).  X is only needed for the
   // fixed-image bins present in the tile (a0 and a0+1 of its voxels, a static
   // mask); other entries are never read.
   const unsigned* tmask = binmask + (size_t)tile * ((nb + 31) >> 5);
@@ -727,6 +735,10 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
     }
   }
   __syncthreads();
+  if (!bg) {
+    build_cz<DIM>(g, TO, c, zt, CZ);
+    __syncthreads();
+  }
   const float scale = (gscale ? __ldg(gscale) : 1.f) * invZ;
 
   const int nxb = (g.n[0] + 31) >> 5;
