@@ -1431,7 +1431,8 @@ extern "C" srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c
   } else {
     static const int cand3[][3] = {{32, 32, 8}, {32, 32, 4}, {32, 16, 8}, {32, 16, 4},
                                    {32, 8, 8},  {32, 8, 4},  {32, 32, 2}, {32, 16, 2},
-                                   {32, 64, 4}, {32, 64, 2}, {32, 128, 2}, {32, 64, 1}};
+                                   {32, 64, 4}, {32, 64, 2}, {32, 128, 2}, {32, 64, 1},
+                                   {32, 128, 1}, {32, 256, 1}};
     static const int cand2[][3] = {{32, 64, 1}, {32, 32, 1}, {32, 16, 1}, {32, 8, 1},
                                    {32, 128, 1}, {32, 256, 1}};
     const int nc = ctx->cfg.ndim == 3 ? (int)(sizeof cand3 / sizeof cand3[0])
