@@ -309,16 +309,20 @@ void launch_batch_rows(srwcr_batch* b, bool lb, const int* active, bool adj) {
       const AdjTable& t = lb ? L.t_lb : L.t;
       if (L.nxb == 4)
         k_adjoint_rows_batch<DIM, T, 4><<<L.nblk, kAdjWarps * 32, L.smem, b->stream>>>(t, active);
-      else
+      else if (L.nxb == 8)
         k_adjoint_rows_batch<DIM, T, 8><<<L.nblk, kAdjWarps * 32, L.smem, b->stream>>>(t, active);
+      else
+        k_adjoint_rows_batch<DIM, T, 12><<<L.nblk, kAdjWarps * 32, L.smem, b->stream>>>(t, active);
     }
   } else {
     for (const auto& L : b->acc_launches) {
       const AccTable& t = lb ? L.t_lb : L.t;
       if (L.nxb == 4)
         k_accumulate_rows_batch<DIM, T, 4><<<L.nblk, kAccWarps * 32, L.smem, b->stream>>>(t, active);
-      else
+      else if (L.nxb == 8)
         k_accumulate_rows_batch<DIM, T, 8><<<L.nblk, kAccWarps * 32, L.smem, b->stream>>>(t, active);
+      else
+        k_accumulate_rows_batch<DIM, T, 12><<<L.nblk, kAccWarps * 32, L.smem, b->stream>>>(t, active);
     }
   }
 }
@@ -339,6 +343,10 @@ srwcr_status set_smem_limits_batch_t() {
   // kernels also hold a few hundred bytes of static descriptors.
   const int mx = 221 * 1024;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  CK(cudaFuncSetAttribute(k_accumulate_rows_batch<3, T, 12>, a, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows_batch<2, T, 12>, a, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_batch<3, T, 12>, a, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_batch<2, T, 12>, a, mx));
   CK(cudaFuncSetAttribute(k_accumulate_rows_batch<3, T, 4>, a, mx));
   CK(cudaFuncSetAttribute(k_accumulate_rows_batch<3, T, 8>, a, mx));
   CK(cudaFuncSetAttribute(k_accumulate_rows_batch<2, T, 4>, a, mx));

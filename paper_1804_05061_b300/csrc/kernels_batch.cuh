@@ -102,7 +102,7 @@ k_accumulate_rows_batch(const __grid_constant__ AccTable tab, const int* __restr
 }
 
 template <int DIM, typename T, int NXB>
-__global__ void __launch_bounds__(kAdjWarps * 32)
+__global__ void __launch_bounds__(kAdjWarps * 32, 4)
 k_adjoint_rows_batch(const __grid_constant__ AdjTable tab, const int* __restrict__ active) {
   extern __shared__ __align__(16) float smem_adj[];
   const int p = batch_find(0, tab.n - 1, blockIdx.x,

@@ -260,7 +260,7 @@ __host__ __device__ inline int hist_yz_stride(const Geo& g) {
 
 __host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int nxb) {
   const size_t npy = (size_t)g.tile[2] * g.hb[1];          // (z-plane, y-bin) rows
-  const size_t nv = (size_t)nxb * 4;
+  const size_t nv = (size_t)(nxb == 12 ? 4 : nxb) * 4;   // segment values per chunk
   size_t b = 3 * npy * hist_yz_stride(g) * sizeof(unsigned);  // plane words (3 per entry)
   b += sizeof(float) * kAccWarps * 32 * nv;                 // segS
   b += sizeof(int) * kAccWarps * 32;                        // segA
@@ -281,13 +281,13 @@ __host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int
 constexpr int kTransposeMaxSeg = 12;
 
 // Position of value q of row (lane or segment) l in a warp's segment buffer
-// of NV floats per row.  With 8 x-bins per row (NV = 32, the only case that
-// takes the transpose route) 16-byte chunks are XOR-swizzled by the row
+// of NV floats per row.  With 8 x-bins per chunk (NV = 32, the only case
+// that takes the transpose route) 16-byte chunks are XOR-swizzled by the row
 // index, so the row stores and the column reads are free of bank conflicts;
 // with 4 the layout is plain.
 template <int NV>
 __device__ __forceinline__ int seg_chunk(int l, int k) {
-  static_assert(NV == 16 || NV == 32, "4 or 8 x-bins per row");
+  static_assert(NV == 16 || NV == 32, "4 or 8 x-bins per chunk");
   return NV == 32 ? (k ^ (l & 7)) : k;
 }
 
@@ -306,7 +306,10 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   const unsigned* __restrict__ binmask = args.binmask;
   unsigned long long* __restrict__ acc = args.acc;
   const float s1 = args.s1, s2 = args.s2;
-  constexpr int NV = NXB * 4;                 // (x-bin, slot, moment): v[4b + 2 slot + ch]
+  // x-bins per chunk of a row (a row with 12 takes three chunks of 4) and
+  // segment-buffer values per chunk: v[4b + 2 slot + ch].
+  constexpr int XC = NXB == 12 ? 4 : NXB;
+  constexpr int NV = XC * 4;
   constexpr int NK = DIM == 3 ? 4 : 1;        // z bins of a row
   const int nb = g.nbins;
   const float L = (float)(nb - 1);
@@ -443,136 +446,146 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
       const bool live = act && (m1 != 0.f || m2 != 0.f);
       if (!__any_sync(0xffffffffu, live)) continue;  // B == 0 on the whole row
 
-      // Per-lane contributions over the row's NXB spatial x-bins.
-      float v[NV];
       const float e0 = live ? h0 * m1 : 0.f, e1 = live ? h0 * m2 : 0.f;
       const float e2 = live ? h1 * m1 : 0.f, e3 = live ? h1 * m2 : 0.f;
-  #pragma unroll
-      for (int b = 0; b < NXB; ++b) {
-        const float w = xt.bsp[b * 32 + p];
-        v[4 * b + 0] = w * e0;
-        v[4 * b + 1] = w * e1;
-        v[4 * b + 2] = w * e2;
-        v[4 * b + 3] = w * e3;
-      }
-      // Segments of equal a0 (lanes are sorted by a0).  Their sums land in row
-      // s of the warp's segment buffer, by one of two warp-uniform routes:
-      //  * transpose (8 x-bins per row, few segments): lane l stores its NV
-      //    values as row l, then lane q < NV adds column q down the rows in
-      //    lane order and writes segment s's total into row s (already read);
-      //  * segmented shuffle reduction toward each head, which then stores its
-      //    segment's NV totals (cost independent of the number of segments).
+      // Segments of equal a0 (lanes are sorted by a0).
       const int prev = __shfl_up_sync(0xffffffffu, key, 1);
       const bool head = lane == 0 || key != prev;
       const unsigned heads = __ballot_sync(0xffffffffu, head);
       const unsigned above = lane == 31 ? 0u : (heads & (0xffffffffu << (lane + 1)));
       const int sidx = __popc(heads & ((1u << lane) - 1u));
-      if (NXB == 8 && __popc(heads) <= kTransposeMaxSeg) {
-        float4* rowp = reinterpret_cast<float4*>(mysegS + lane * NV);
+      // The row's x-bins in chunks of XC (one chunk unless NXB = 12); the bin
+      // list is built after the first chunk's segment sums.
+      int nbin = 0;
+      for (int q0 = 0; q0 < NXB && q0 < g.hb[0]; q0 += XC) {
+        // Per-lane contributions over the chunk's spatial x-bins.
+        float v[NV];
   #pragma unroll
-        for (int k = 0; k < NV / 4; ++k)
-          rowp[seg_chunk<NV>(lane, k)] =
-              make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-        __syncwarp();
-        const unsigned ends = (heads >> 1) | 0x80000000u;  // last lane of each segment
-        if (lane < NV) {
-          float sum = 0.f;
-          int sw = 0;
-  #pragma unroll
-          for (int l = 0; l < 32; ++l) {
-            sum += mysegS[seg_at<NV>(l, lane)];
-            if ((ends >> l) & 1u) {
-              mysegS[seg_at<NV>(sw, lane)] = sum;
-              sum = 0.f;
-              ++sw;
-            }
-          }
+        for (int b = 0; b < XC; ++b) {
+          const float w = xt.bsp[(q0 + b) * 32 + p];
+          v[4 * b + 0] = w * e0;
+          v[4 * b + 1] = w * e1;
+          v[4 * b + 2] = w * e2;
+          v[4 * b + 3] = w * e3;
         }
-      } else {
-        const int seg_end = above ? __ffs(above) - 1 : 32;
-  #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const bool ok = lane + off < seg_end;
-  #pragma unroll
-          for (int q = 0; q < NV; ++q) {
-            const float ov = __shfl_down_sync(0xffffffffu, v[q], off);
-            if (ok) v[q] += ov;
-          }
-        }
-        if (head && key != kSentinel) {
-          float4* rowp = reinterpret_cast<float4*>(mysegS + sidx * NV);
+        // Segment sums land in row s of the warp's segment buffer, by one of
+        // two warp-uniform routes:
+        //  * transpose (8 x-bins per chunk, few segments): lane l stores its NV
+        //    values as row l, then lane q < NV adds column q down the rows in
+        //    lane order and writes segment s's total into row s (already read);
+        //  * segmented shuffle reduction toward each head, which then stores
+        //    its segment's NV totals (cost independent of the number of
+        //    segments).
+        if (XC == 8 && __popc(heads) <= kTransposeMaxSeg) {
+          float4* rowp = reinterpret_cast<float4*>(mysegS + lane * NV);
   #pragma unroll
           for (int k = 0; k < NV / 4; ++k)
-            rowp[seg_chunk<NV>(sidx, k)] =
+            rowp[seg_chunk<NV>(lane, k)] =
                 make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+          __syncwarp();
+          const unsigned ends = (heads >> 1) | 0x80000000u;  // last lane of each segment
+          if (lane < NV) {
+            float sum = 0.f;
+            int sw = 0;
+  #pragma unroll
+            for (int l = 0; l < 32; ++l) {
+              sum += mysegS[seg_at<NV>(l, lane)];
+              if ((ends >> l) & 1u) {
+                mysegS[seg_at<NV>(sw, lane)] = sum;
+                sum = 0.f;
+                ++sw;
+              }
+            }
+          }
+        } else {
+          const int seg_end = above ? __ffs(above) - 1 : 32;
+  #pragma unroll
+          for (int off = 1; off < 32; off <<= 1) {
+            const bool ok = lane + off < seg_end;
+  #pragma unroll
+            for (int q = 0; q < NV; ++q) {
+              const float ov = __shfl_down_sync(0xffffffffu, v[q], off);
+              if (ok) v[q] += ov;
+            }
+          }
+          if (head && key != kSentinel) {
+            float4* rowp = reinterpret_cast<float4*>(mysegS + sidx * NV);
+  #pragma unroll
+            for (int k = 0; k < NV / 4; ++k)
+              rowp[seg_chunk<NV>(sidx, k)] =
+                  make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+          }
         }
-      }
-      __syncwarp();
-      // Bin list.  Segment s (key a) adds bin a (slot 0, plus slot 1 of s-1 when
-      // that segment's key is a-1) and, unless segment s+1 has key a+1, bin a+1
-      // (slot 1 alone).
-      const int next_head = above ? __ffs(above) - 1 : -1;
-      const int next_key = __shfl_sync(0xffffffffu, key, next_head < 0 ? lane : next_head);
-      const bool real = head && key != kSentinel;
-      const bool upper = real && (next_head < 0 || next_key != key + 1);
-      const unsigned below = heads & ((1u << lane) - 1u);
-      const int prev_head = below ? 31 - __clz(below) : lane;
-      const int prev_key = __shfl_sync(0xffffffffu, key, prev_head);
-      const bool merge = real && below && prev_key + 1 == key;
-      // Only bins of the current chunk are listed.
-      const bool in0 = real && (unsigned)(a2c[key] - c0) < (unsigned)cb;
-      const bool in1 = upper && (unsigned)(a2c[key + 1] - c0) < (unsigned)cb;
-      const unsigned emit0 = __ballot_sync(0xffffffffu, in0);
-      const unsigned emit1 = __ballot_sync(0xffffffffu, in1);
-      const unsigned lt = (1u << lane) - 1u;
-      const int pos = __popc(emit0 & lt) + __popc(emit1 & lt);
-      const int nbin = __popc(emit0) + __popc(emit1);
-      if (in0) {
-        mybins[2 * pos] = key;
-        mybins[2 * pos + 1] = sidx | (merge ? (1 << 9) : 0);
-      }
-      if (in1) {
-        const int q = pos + (in0 ? 1 : 0);
-        mybins[2 * q] = key + 1;
-        mybins[2 * q + 1] = sidx | (1 << 8);
-      }
-      __syncwarp();
-      // Fold: each lane takes whole (bin, moment, x-bin) items (32 per pass)
-      // and adds each to the row's 4 y bins of its z-plane (one item decode
-      // per item; all 32 lanes of an update touch one y row, consecutive
-      // items consecutive columns).
-      const int prow = (zl * g.hb[1] + ye.srel) * S;
-      const int per_bin = 2 * NXB;
-      for (int f = lane; f < nbin * per_bin; f += 32) {
-        const int e = f / per_bin, r = f % per_bin;
-        const int ch = r / NXB, b = r % NXB;
-        if (b >= g.hb[0]) continue;
-        const int a = mybins[2 * e];
-        const int info = mybins[2 * e + 1];
-        const int sg = info & 0xff, slot = (info >> 8) & 1;
-        float val = mysegS[seg_at<NV>(sg, 4 * b + 2 * slot + ch)];
-        if (info & (1 << 9)) val += mysegS[seg_at<NV>(sg - 1, 4 * b + 2 + ch)];
-        const float uv = val * (ch ? s2 : s1);
-        if (uv == 0.f) continue;
-        const int col = prow + ((a2c[a] - c0) * 2 + ch) * g.hb[0] + b;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const float u = uv * ye.bs[m];
-          if (u == 0.f) continue;
-          // Exact split of u into 20-bit fields (power-of-two scalings,
-          // floors and fused subtractions of FP32 values are exact here).
-          const float hf = floorf(u * 0x1p-40f);
-          const float r1 = fmaf(hf, -0x1p40f, u);
-          const float mf = floorf(r1 * 0x1p-20f);
-          const unsigned lo = __float2uint_rn(fmaf(mf, -0x1p20f, r1));
-          const unsigned mid = (unsigned)mf, hi = (unsigned)hf;
-          const int at = col + m * S;
-          if (lo) atomicAdd(hlo + at, lo);
-          if (mid) atomicAdd(hmid + at, mid);
-          if (hi) atomicAdd(hhi + at, hi);
+        __syncwarp();
+        if (q0 == 0) {
+          // Bin list.  Segment s (key a) adds bin a (slot 0, plus slot 1 of
+          // s-1 when that segment's key is a-1) and, unless segment s+1 has
+          // key a+1, bin a+1 (slot 1 alone).
+          const int next_head = above ? __ffs(above) - 1 : -1;
+          const int next_key = __shfl_sync(0xffffffffu, key, next_head < 0 ? lane : next_head);
+          const bool real = head && key != kSentinel;
+          const bool upper = real && (next_head < 0 || next_key != key + 1);
+          const unsigned below = heads & ((1u << lane) - 1u);
+          const int prev_head = below ? 31 - __clz(below) : lane;
+          const int prev_key = __shfl_sync(0xffffffffu, key, prev_head);
+          const bool merge = real && below && prev_key + 1 == key;
+          // Only bins of the current bin pass are listed.
+          const bool in0 = real && (unsigned)(a2c[key] - c0) < (unsigned)cb;
+          const bool in1 = upper && (unsigned)(a2c[key + 1] - c0) < (unsigned)cb;
+          const unsigned emit0 = __ballot_sync(0xffffffffu, in0);
+          const unsigned emit1 = __ballot_sync(0xffffffffu, in1);
+          const unsigned lt = (1u << lane) - 1u;
+          const int pos = __popc(emit0 & lt) + __popc(emit1 & lt);
+          nbin = __popc(emit0) + __popc(emit1);
+          if (in0) {
+            mybins[2 * pos] = key;
+            mybins[2 * pos + 1] = sidx | (merge ? (1 << 9) : 0);
+          }
+          if (in1) {
+            const int q = pos + (in0 ? 1 : 0);
+            mybins[2 * q] = key + 1;
+            mybins[2 * q + 1] = sidx | (1 << 8);
+          }
+          __syncwarp();
         }
+        // Fold: each lane takes whole (bin, moment, x-bin) items (32 per
+        // pass) and adds each to the row's 4 y bins of its z-plane (one item
+        // decode per item; all 32 lanes of an update touch one y row,
+        // consecutive items consecutive columns).
+        const int prow = (zl * g.hb[1] + ye.srel) * S;
+        const int per_bin = 2 * XC;
+        for (int f = lane; f < nbin * per_bin; f += 32) {
+          const int e = f / per_bin, r = f % per_bin;
+          const int ch = r / XC, b = r % XC;
+          const int bx_ = q0 + b;                  // the row's x-bin
+          if (bx_ >= g.hb[0]) continue;
+          const int a = mybins[2 * e];
+          const int info = mybins[2 * e + 1];
+          const int sg = info & 0xff, slot = (info >> 8) & 1;
+          float val = mysegS[seg_at<NV>(sg, 4 * b + 2 * slot + ch)];
+          if (info & (1 << 9)) val += mysegS[seg_at<NV>(sg - 1, 4 * b + 2 + ch)];
+          const float uv = val * (ch ? s2 : s1);
+          if (uv == 0.f) continue;
+          const int col = prow + ((a2c[a] - c0) * 2 + ch) * g.hb[0] + bx_;
+  #pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const float u = uv * ye.bs[m];
+            if (u == 0.f) continue;
+            // Exact split of u into 20-bit fields (power-of-two scalings,
+            // floors and fused subtractions of FP32 values are exact here).
+            const float hf = floorf(u * 0x1p-40f);
+            const float r1 = fmaf(hf, -0x1p40f, u);
+            const float mf = floorf(r1 * 0x1p-20f);
+            const unsigned lo = __float2uint_rn(fmaf(mf, -0x1p20f, r1));
+            const unsigned mid = (unsigned)mf, hi = (unsigned)hf;
+            const int at = col + m * S;
+            if (lo) atomicAdd(hlo + at, lo);
+            if (mid) atomicAdd(hmid + at, mid);
+            if (hi) atomicAdd(hhi + at, hi);
+          }
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
     __syncthreads();
     // Flush: one entry per (first plane of a z cell, y bin, column); the

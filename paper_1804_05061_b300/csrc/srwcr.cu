@@ -160,10 +160,10 @@ size_t acc_smem(const Geo& g, int nch) {
   return (size_t)g.hb[0] * g.hb[1] * g.hb[2] * g.nbins * nch * sizeof(unsigned long long);
 }
 
-// Row kernels need 32-wide tiles, at most 8 spatial x-bins and 11 FFD
-// x-nodes per row (FFD spacing >= 5, spatial-bin spacing >= ~5).
+// Row kernels need 32-wide tiles, at most 12 spatial x-bins and 11 FFD
+// x-nodes per row (FFD spacing >= 5, spatial-bin spacing >= 5).
 bool rows_geometry_ok(const Geo& g) {
-  return g.tile[0] == 32 && g.hb[0] <= 8 && g.hf[0] <= kMaxRowNodes && g.tile[1] * g.tile[2] <= 256;
+  return g.tile[0] == 32 && g.hb[0] <= 12 && g.hf[0] <= kMaxRowNodes && g.tile[1] * g.tile[2] <= 256;
 }
 
 void set_tile(Geo& g, int ndim, int tx, int ty, int tz) {
@@ -287,8 +287,10 @@ void launch_rows_acc(srwcr_ctx* ctx, Level& lv, const float* c, int nblk, bool k
   const AccArgs a = acc_args(lv, c, keep);
   if (lv.nxb_rows == 4)
     k_accumulate_rows<DIM, T, 4><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
-  else
+  else if (lv.nxb_rows == 8)
     k_accumulate_rows<DIM, T, 8><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
+  else
+    k_accumulate_rows<DIM, T, 12><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
 }
 
 template <int DIM, typename T>
@@ -297,8 +299,10 @@ void launch_rows_adj(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD,
   const AdjArgs a = adj_args(lv, c, gD, g, kept);
   if (lv.nxb_rows == 4)
     k_adjoint_rows<DIM, T, 4><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a);
-  else
+  else if (lv.nxb_rows == 8)
     k_adjoint_rows<DIM, T, 8><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a);
+  else
+    k_adjoint_rows<DIM, T, 12><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a);
 }
 
 template <typename T>
@@ -391,6 +395,10 @@ srwcr_status set_smem_limits() {
   CK(cudaFuncSetAttribute(k_accumulate_mas_a<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint_mas_a<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint_mas_a<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows<3, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows<2, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
@@ -767,7 +775,7 @@ srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv, const int* force_tile =
       lv.nu = (int)ub.size();
     }
     g.nabin = nab;
-    const int nxb = g.hb[0] <= 4 ? 4 : 8;
+    const int nxb = g.hb[0] <= 4 ? 4 : (g.hb[0] <= 8 ? 8 : 12);
     // Compacted bins per pass of the value kernel: all of them when they fit,
     // else the most that fit (a tile using more takes several passes).
     g.cbin = cfg.bins_per_pass > 0 ? std::min(nab, cfg.bins_per_pass) : nab;

@@ -96,12 +96,45 @@ def test_batched_value_and_gradient_equal_single_pair_and_oracle(specs, storage)
         assert abs(gn - gon) <= GNORM_RTOL * gon, (i, gn, gon)
 
 
+def test_batch_with_twelve_x_bins_per_row_equals_single_pairs():
+    # FFD spacing 5 with the spatial bins on the FFD grid: rows meet up to 11
+    # spatial x-bins, so these pairs run the 12-bin row kernels.
+    import paper_1804_05061_b300 as eng
+    specs5 = []
+    for i, e in enumerate((40, 56)):
+        prob = synth.problem(3, (e, e - 8, e - 16), (5, 5, 5), (0, 0, 0), 32)
+        f, m = synth.small_pair("ct", prob.dims, prob.ffd_spacing, 2.0, 60 + i)
+        specs5.append((prob, f, m))
+    es = [eng.from_problem(p, f, m) for p, f, m in specs5]
+    assert all(e.levels[0].kernel_path == 1 for e in es)
+    b = eng.Batch(es)
+    cs = [synth.coefficients(p, 70 + i, 1.5) for i, (p, _, _) in enumerate(specs5)]
+    for i, c in enumerate(cs):
+        b.coef(i).copy_(torch.from_numpy(c))
+    Db = b.value_and_grad(use_graph=True)
+    lanes = b.info().finalize_lanes
+    for i, e in enumerate(es):
+        D, g = e.value_and_grad(torch.from_numpy(cs[i]).cuda())
+        if e.levels[0].finalize_lanes == lanes:
+            assert Db[i] == D
+        else:
+            assert abs(Db[i] - D) <= 1e-12 * abs(D)
+        assert torch.allclose(b.grad(i), g, rtol=1e-5, atol=1e-5 * float(g.abs().max()))
+        prob, f, m = specs5[i]
+        geo = oracle.Geometry.from_problem(prob)
+        A, M = oracle.prepare(f, m, prob.n_bins)
+        st = oracle.value(geo, A, M, cs[i])
+        assert abs(D - st.D) <= D_RTOL * abs(st.D)
+
+
 def test_batch_rejects_mixed_storage_and_general_path_levels(specs):
     import paper_1804_05061_b300 as eng
     es = make_engines(specs[:1], "f32") + make_engines(specs[1:2], "bf16")
     with pytest.raises(eng.SrwcrError, match="EINVAL"):
         eng.Batch(es)
-    prob = synth.problem(3, (41, 37, 29), (5, 5, 5), (0, 0, 0), 32)
+    # FFD spacing 3: a 32-voxel row meets 14 FFD x-nodes, more than the row
+    # kernels take.
+    prob = synth.problem(3, (41, 37, 29), (3, 3, 3), (0, 0, 0), 32)
     f, m = synth.small_pair("oct", prob.dims, prob.ffd_spacing, 1.0, 9)
     general = eng.from_problem(prob, f, m)
     assert general.levels[0].kernel_path == 0

@@ -38,6 +38,9 @@ SMALL = [
     ("oct_ffd_grid_bins", "oct", synth.problem(3, (41, 37, 29), (5, 5, 5), (0, 0, 0), 32), 1.0),
     ("ct_128_bins", "ct", synth.problem(3, (64, 48, 40), (5, 5, 5), (2, 2, 1), 128), 1.5),
     ("pet_labels", "pet", synth.problem(3, (48, 40, 36), (8, 8, 8), (0, 0, 0), 32), 2.0),
+    # spacing 5 with the bins on the FFD grid (the paper's defaults): a
+    # 32-voxel row meets up to 11 spatial x-bins (the 12-bin row kernels)
+    ("ellipse_2d_spacing5", "ellipse", synth.problem(2, (100, 77), (5, 5), (0, 0), 16), 1.0),
 ]
 
 
@@ -134,8 +137,8 @@ def test_finalisation_lane_count_is_validated(small_cases):
             engine_for(prob, f, m, finalize_lanes=bad)
 
 
-EXPECTED_PATH = {"ellipse_2d_ragged": 1, "ct_3d_ragged": 1, "oct_ffd_grid_bins": 0,
-                 "ct_128_bins": 1, "pet_labels": 1}
+EXPECTED_PATH = {"ellipse_2d_ragged": 1, "ct_3d_ragged": 1, "oct_ffd_grid_bins": 1,
+                 "ct_128_bins": 1, "pet_labels": 1, "ellipse_2d_spacing5": 1}
 
 
 @pytest.mark.parametrize("name", [s[0] for s in SMALL])
