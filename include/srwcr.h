@@ -359,6 +359,13 @@ typedef struct {
  * start at zero.  Errors: SRWCR_EINVAL, SRWCR_ENOMEM, SRWCR_ECUDA. */
 srwcr_status srwcr_batch_create(srwcr_ctx* const* ctxs, int n_pairs, int level, void* stream,
                                 srwcr_batch** out);
+
+/* As srwcr_batch_create, with pair i at pyramid level levels[i] (pairs at
+ * different levels, e.g. the coarse stage of one registration beside the
+ * fine stage of another, share the same launches).  Each pair's level must
+ * run on the row-parallel kernels. */
+srwcr_status srwcr_batch_create_levels(srwcr_ctx* const* ctxs, const int* levels, int n_pairs,
+                                       void* stream, srwcr_batch** out);
 void srwcr_batch_destroy(srwcr_batch* b);
 srwcr_status srwcr_batch_info(const srwcr_batch* b, srwcr_batch_desc* out);
 
@@ -380,7 +387,7 @@ srwcr_status srwcr_batch_sync(srwcr_batch* b, double* D_host);
 
 /* Single-level L-BFGS (Sec. II-F, the method of srwcr_register) for every
  * pair at once, from the coefficients in the packed c buffer, with
- * opts->max_iter[level] iterations at most.  The optimiser state lives on
+ * opts->max_iter[level] iterations at most (each pair's own level).  The optimiser state lives on
  * the device and each round (one batched evaluation plus one decision
  * kernel) is the same launch sequence for every pair, replayed from a CUDA
  * graph when use_graph != 0; pairs that stop drop out of later rounds.  On

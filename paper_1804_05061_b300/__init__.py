@@ -33,7 +33,7 @@ EXPORTS = ("srwcr_create", "srwcr_destroy", "srwcr_last_error", "srwcr_level_inf
            "srwcr_region_stats", "srwcr_debug_bins", "srwcr_debug_warp",
            "srwcr_lbfgs_default_opts", "srwcr_register", "srwcr_set_profiling",
            "srwcr_profile_read", "srwcr_value_noalloc", "srwcr_autotune",
-           "srwcr_batch_create", "srwcr_batch_destroy", "srwcr_batch_info",
+           "srwcr_batch_create", "srwcr_batch_create_levels", "srwcr_batch_destroy", "srwcr_batch_info",
            "srwcr_batch_layout", "srwcr_batch_buffers", "srwcr_batch_value_and_grad",
            "srwcr_batch_sync", "srwcr_batch_register", "srwcr_bending_energy",
            "srwcr_rigid_value_and_grad", "srwcr_rigid_to_ffd", "srwcr_rigid_register")
@@ -124,6 +124,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "srwcr_value_noalloc": (st, [ctypes.POINTER(Config), vp, vp, vp, vp, vp]),
         "srwcr_autotune": (st, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "srwcr_batch_create": (st, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+        "srwcr_batch_create_levels": (st, [vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)]),
         "srwcr_batch_destroy": (None, [vp]),
         "srwcr_batch_info": (st, [vp, ctypes.POINTER(BatchDesc)]),
         "srwcr_batch_layout": (st, [vp, vp, vp]),
@@ -456,18 +457,23 @@ class Batch:
     the current torch stream on entry and before it on exit.
     """
 
-    def __init__(self, engines: Sequence["SRWCR"], level: int = 0):
+    def __init__(self, engines: Sequence["SRWCR"], level=0):
+        """level: one pyramid level for every pair, or one per pair."""
         import torch
         self._torch = torch
         lib = load()
         self.engines = list(engines)
-        self.level = level
+        n = len(self.engines)
+        self.levels = [int(level)] * n if np.isscalar(level) else [int(v) for v in level]
+        if len(self.levels) != n:
+            raise ValueError("one level per engine expected")
         self.stream = torch.cuda.Stream(device=self.engines[0].device)
-        arr = (ctypes.c_void_p * len(self.engines))(*[e._h.value for e in self.engines])
+        arr = (ctypes.c_void_p * n)(*[e._h.value for e in self.engines])
+        lv = (ctypes.c_int * n)(*self.levels)
         h = ctypes.c_void_p()
         self.stream.wait_stream(torch.cuda.current_stream())
-        _check(lib.srwcr_batch_create(arr, len(self.engines), int(level),
-                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        _check(lib.srwcr_batch_create_levels(arr, lv, n, ctypes.c_void_p(self.stream.cuda_stream),
+                                             ctypes.byref(h)))
         self._h = h
         n = len(self.engines)
         off = np.zeros(n + 1, np.int64)
@@ -505,19 +511,19 @@ class Batch:
     def coef(self, i: int):
         """View of pair i's coefficients in the packed buffer."""
         o, n = int(self.offsets[i]), int(self.n_params[i])
-        return self.c[o:o + n].view(self.engines[i].coef_shape(self.level))
+        return self.c[o:o + n].view(self.engines[i].coef_shape(self.levels[i]))
 
     def grad(self, i: int):
         o, n = int(self.offsets[i]), int(self.n_params[i])
-        return self.g[o:o + n].view(self.engines[i].coef_shape(self.level))
+        return self.g[o:o + n].view(self.engines[i].coef_shape(self.levels[i]))
 
     def _enter(self):
         self.stream.wait_stream(self._torch.cuda.current_stream())
 
     def _leave(self):
         self._torch.cuda.current_stream().wait_stream(self.stream)
-        for e in self.engines:
-            e._gen[self.level] += 1
+        for e, lv in zip(self.engines, self.levels):
+            e._gen[lv] += 1
 
     def value_and_grad_async(self, use_graph: bool = True):
         """Queue D_i, dD_i/dc_i for every pair at the packed coefficients."""

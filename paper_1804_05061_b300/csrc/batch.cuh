@@ -35,6 +35,7 @@ struct LbState {
   int nfh;
   int head, hist_len;  // history ring: next slot, entries in use
   int iter, evals, trials, restart, phase, status;
+  int max_iter;        // this pair's iteration limit (its level's entry of the options)
 };
 
 // FP64 inner product over one pair's vectors by one CTA, in a fixed order;
@@ -56,13 +57,14 @@ __device__ double block_dot(const float* __restrict__ a, const float* __restrict
 // Start: trial point = start point, first evaluation pending.
 __global__ void k_lbfgs_init(LbState* __restrict__ st, int* __restrict__ active,
                              const long long* __restrict__ off, const float* __restrict__ x,
-                             float* __restrict__ xn) {
+                             float* __restrict__ xn, const int* __restrict__ max_iter) {
   const int p = blockIdx.x;
   for (long long i = off[p] + threadIdx.x; i < off[p + 1]; i += blockDim.x) xn[i] = x[i];
   if (threadIdx.x == 0) {
     LbState s;
     memset(&s, 0, sizeof s);
     s.restart = 1;
+    s.max_iter = max_iter[p];
     st[p] = s;
     active[p] = 1;
   }
@@ -109,7 +111,7 @@ k_lbfgs_step(LbState* __restrict__ st_all, int* __restrict__ active, LbVectors v
       s.nfh = 1;
     }
     if (!isfinite(fn)) { done = 1; status = SRWCR_ENUMERIC; }
-    else if (o.max_iter <= 0) { done = 1; status = SRWCR_ENOTCONVERGED; }
+    else if (s.max_iter <= 0) { done = 1; status = SRWCR_ENOTCONVERGED; }
   } else {
     if (tid == 0) s.evals += 1;
     int act = 0;  // 0 accept, 1 shrink, 2 grow
@@ -168,7 +170,7 @@ k_lbfgs_step(LbState* __restrict__ st_all, int* __restrict__ active, LbVectors v
               o.rtol * fabs(s.fh[(s.nfh - 1) % kLbHist])) {
         done = 1;
         status = SRWCR_OK;
-      } else if (s.iter >= o.max_iter) {
+      } else if (s.iter >= s.max_iter) {
         done = 1;
         status = SRWCR_ENOTCONVERGED;
       }
@@ -250,7 +252,7 @@ k_lbfgs_step(LbState* __restrict__ st_all, int* __restrict__ active, LbVectors v
 
 struct srwcr_batch {
   int n = 0;
-  int level = 0;
+  std::vector<int> level;      // caller order: each pair's pyramid level
   int ndim = 0;
   bool bf16 = false;
   int device = 0;
@@ -292,6 +294,7 @@ struct srwcr_batch {
   float *xn = nullptr, *gn = nullptr, *d = nullptr, *S = nullptr, *Y = nullptr;
   int lb_m = 0;
   LbState* lbs = nullptr;
+  int* lb_max_iter = nullptr;       // [n] each pair's iteration limit
   int* active = nullptr;
   int* active_host = nullptr;
   cudaGraphExec_t graph_eval = nullptr;
@@ -423,7 +426,7 @@ srwcr_status capture(srwcr_batch* b, cudaGraphExec_t* out, Fn fn) {
 }
 
 void invalidate_member_tables(srwcr_batch* b) {
-  for (srwcr_ctx* c : b->ctx) c->lev[b->level].tables = false;
+  for (int i = 0; i < b->n; ++i) b->ctx[i]->lev[b->level[i]].tables = false;
 }
 
 srwcr_status batch_alloc_lbfgs(srwcr_batch* b, int m) {
@@ -447,6 +450,7 @@ srwcr_status batch_alloc_lbfgs(srwcr_batch* b, int m) {
   CK(cudaMemsetAsync(b->S, 0, sizeof(float) * tot * m, b->stream));
   CK(cudaMemsetAsync(b->Y, 0, sizeof(float) * tot * m, b->stream));
   if (!b->lbs) CK(cudaMalloc((void**)&b->lbs, sizeof(LbState) * b->n));
+  if (!b->lb_max_iter) CK(cudaMalloc((void**)&b->lb_max_iter, sizeof(int) * b->n));
   // Evaluation table of the optimiser: reads xn, writes gn.
   std::vector<BatchPair> tab = b->host_tab;
   for (auto& bp : tab) {
@@ -477,7 +481,7 @@ void srwcr_batch_destroy(srwcr_batch* b) {
   if (b->graph_eval) cudaGraphExecDestroy(b->graph_eval);
   if (b->graph_round) cudaGraphExecDestroy(b->graph_round);
   void* ptrs[] = {b->c, b->g, b->D, b->ndeg, b->off_dev, b->tab_eval, b->tab_lb, b->xn, b->gn,
-                  b->d, b->S, b->Y, b->lbs, b->active};
+                  b->d, b->S, b->Y, b->lbs, b->lb_max_iter, b->active};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (b->active_host) cudaFreeHost(b->active_host);
@@ -485,10 +489,10 @@ void srwcr_batch_destroy(srwcr_batch* b) {
   delete b;
 }
 
-static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, int n, int level,
-                                      void* stream) {
+static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, const int* levels,
+                                      int n, void* stream) {
   b->n = n;
-  b->level = level;
+  b->level.assign(levels, levels + n);
   b->ctx.assign(ctxs, ctxs + n);
   CK(cudaGetDevice(&b->device));
   if (stream) {
@@ -505,7 +509,8 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
     if (c->device != b->device) return fail(SRWCR_EINVAL, "pair %d: context on another device", i);
     if (c->cfg.ndim != b->ndim || is_bf16(c) != b->bf16)
       return fail(SRWCR_EINVAL, "pair %d: dimension or storage differs from pair 0", i);
-    if (level >= c->nlev) return fail(SRWCR_EINVAL, "pair %d has no level %d", i, level);
+    const int level = levels[i];
+    if (level < 0 || level >= c->nlev) return fail(SRWCR_EINVAL, "pair %d has no level %d", i, level);
     if (!c->lev[level].rows)
       return fail(SRWCR_EINVAL, "pair %d: level %d is not on the row-parallel kernels", i, level);
     for (int j = 0; j < i; ++j)
@@ -514,7 +519,7 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
   // Packed coefficient layout (caller order), 64-float aligned per pair.
   b->off.assign(n + 1, 0);
   for (int i = 0; i < n; ++i) {
-    const Geo& g = ctxs[i]->lev[level].g;
+    const Geo& g = ctxs[i]->lev[levels[i]].g;
     const long long np = g.ncoef * b->ndim;
     b->off[i + 1] = b->off[i] + (np + 63) / 64 * 64;
   }
@@ -535,8 +540,8 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-    const Level& la = ctxs[a]->lev[level];
-    const Level& lc = ctxs[c]->lev[level];
+    const Level& la = ctxs[a]->lev[levels[a]];
+    const Level& lc = ctxs[c]->lev[levels[c]];
     if (la.nxb_rows != lc.nxb_rows) return la.nxb_rows < lc.nxb_rows;
     return la.g.nvox > lc.g.nvox;
   });
@@ -544,7 +549,7 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
   long long region = 0;
   for (int t = 0; t < n; ++t) {
     const int i = order[t];
-    Level& lv = ctxs[i]->lev[level];
+    Level& lv = ctxs[i]->lev[levels[i]];
     BatchPair& bp = b->host_tab[t];
     memset(&bp, 0, sizeof bp);
     bp.g = lv.g;
@@ -580,7 +585,7 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
     // else the cost model over all pairs' region lists.
     const int req = ctxs[0]->cfg.finalize_lanes;
     std::vector<const std::vector<int>*> lists;
-    for (int i = 0; i < n; ++i) lists.push_back(&ctxs[i]->lev[level].nz_ptr_host);
+    for (int i = 0; i < n; ++i) lists.push_back(&ctxs[i]->lev[levels[i]].nz_ptr_host);
     b->fin_lanes = req > 0 ? req : finalize_lanes_auto(lists, ctxs[0]->device);
   }
   // Row-kernel launches: pairs bucketed by (x-bins per row, CTAs per SM),
@@ -594,7 +599,7 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
       bs.push_back({key, {t}});
     };
     for (int t = 0; t < n; ++t) {
-      const Level& lv = ctxs[order[t]]->lev[level];
+      const Level& lv = ctxs[order[t]]->lev[levels[order[t]]];
       bucket(acc_b, {lv.nxb_rows, ctas_per_sm(lv.smem_acc_rows)}, t);
       bucket(adj_b, {lv.nxb_rows, ctas_per_sm(lv.smem_adj_rows)}, t);
     }
@@ -613,7 +618,7 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
           it.id = bp.id;
           it.tile_begin = tile;
           tile += bp.g.ntile[0] * bp.g.ntile[1] * bp.g.ntile[2];
-          L.smem = std::max(L.smem, ctxs[order[t]]->lev[level].smem_acc_rows);
+          L.smem = std::max(L.smem, ctxs[order[t]]->lev[levels[order[t]]].smem_acc_rows);
         }
         L.nblk = tile;
         L.t_lb = L.t;
@@ -636,7 +641,7 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
           it.id = bp.id;
           it.tile_begin = tile;
           tile += bp.g.ntile[0] * bp.g.ntile[1] * bp.g.ntile[2];
-          L.smem = std::max(L.smem, ctxs[order[t]]->lev[level].smem_adj_rows);
+          L.smem = std::max(L.smem, ctxs[order[t]]->lev[levels[order[t]]].smem_adj_rows);
         }
         L.nblk = tile;
         L.t_lb = L.t;
@@ -651,15 +656,15 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, in
   return SRWCR_OK;
 }
 
-srwcr_status srwcr_batch_create(srwcr_ctx* const* ctxs, int n_pairs, int level, void* stream,
-                                srwcr_batch** out) {
+srwcr_status srwcr_batch_create_levels(srwcr_ctx* const* ctxs, const int* levels, int n_pairs,
+                                       void* stream, srwcr_batch** out) {
   if (!out) return fail(SRWCR_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!ctxs || n_pairs < 1 || n_pairs > 65535) return fail(SRWCR_EINVAL, "need 1..65535 contexts");
-  if (level < 0 || level > 3) return fail(SRWCR_EINVAL, "level %d out of range", level);
+  if (!ctxs || !levels || n_pairs < 1 || n_pairs > 65535)
+    return fail(SRWCR_EINVAL, "need 1..65535 contexts and their levels");
   srwcr_batch* b = new (std::nothrow) srwcr_batch();
   if (!b) return fail(SRWCR_ENOMEM, "host allocation failed");
-  srwcr_status st = batch_create_impl(b, ctxs, n_pairs, level, stream);
+  srwcr_status st = batch_create_impl(b, ctxs, levels, n_pairs, stream);
   if (st != SRWCR_OK) {
     std::string keep = g_err;
     srwcr_batch_destroy(b);
@@ -668,6 +673,16 @@ srwcr_status srwcr_batch_create(srwcr_ctx* const* ctxs, int n_pairs, int level, 
   }
   *out = b;
   return SRWCR_OK;
+}
+
+srwcr_status srwcr_batch_create(srwcr_ctx* const* ctxs, int n_pairs, int level, void* stream,
+                                srwcr_batch** out) {
+  if (n_pairs < 1 || n_pairs > 65535) {
+    if (out) *out = nullptr;
+    return fail(SRWCR_EINVAL, "need 1..65535 contexts");
+  }
+  std::vector<int> levels(n_pairs, level);
+  return srwcr_batch_create_levels(ctxs, levels.data(), n_pairs, stream, out);
 }
 
 srwcr_status srwcr_batch_info(const srwcr_batch* b, srwcr_batch_desc* out) {
@@ -686,7 +701,7 @@ srwcr_status srwcr_batch_layout(const srwcr_batch* b, int64_t* offsets, int64_t*
   if (!b) return fail(SRWCR_EINVAL, "null batch");
   for (int i = 0; i <= b->n && offsets; ++i) offsets[i] = b->off[i];
   for (int i = 0; i < b->n && n_params; ++i)
-    n_params[i] = b->ctx[i]->lev[b->level].g.ncoef * b->ndim;
+    n_params[i] = b->ctx[i]->lev[b->level[i]].g.ncoef * b->ndim;
   return SRWCR_OK;
 }
 
@@ -726,14 +741,24 @@ srwcr_status srwcr_batch_register(srwcr_batch* b, const srwcr_lbfgs_opts* opts, 
   srwcr_lbfgs_opts oo;
   srwcr_lbfgs_default_opts(&oo);
   if (opts) oo = *opts;
-  if (oo.m < 1 || oo.m > 16 || oo.max_ls < 1 || oo.stable_window >= kLbHist ||
-      oo.max_iter[b->level] < 0)
+  // Each pair runs at most opts->max_iter[its level] iterations.
+  std::vector<int> mi(b->n);
+  int mi_max = 0;
+  for (int i = 0; i < b->n; ++i) {
+    mi[i] = oo.max_iter[b->level[i]];
+    mi_max = std::max(mi_max, mi[i]);
+    if (mi[i] < 0) return fail(SRWCR_EINVAL, "negative max_iter for level %d", b->level[i]);
+  }
+  if (oo.m < 1 || oo.m > 16 || oo.max_ls < 1 || oo.stable_window >= kLbHist)
     return fail(SRWCR_EINVAL, "bad L-BFGS options (m in 1..16, max_ls >= 1, window < %d)", kLbHist);
   if (oo.penalty_weight != 0.0)
     return fail(SRWCR_EINVAL, "the batched driver minimises D alone (penalty_weight must be 0)");
-  LbOpts o{oo.m, oo.max_iter[b->level], oo.stable_window, oo.max_ls, oo.stable_rtol, oo.c1, oo.c2};
+  LbOpts o{oo.m, mi_max, oo.stable_window, oo.max_ls, oo.stable_rtol, oo.c1, oo.c2};
   RET_IF(batch_alloc_lbfgs(b, o.m));
-  k_lbfgs_init<<<b->n, 256, 0, b->stream>>>(b->lbs, b->active, b->off_dev, b->c, b->xn);
+  CK(cudaMemcpyAsync(b->lb_max_iter, mi.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice,
+                     b->stream));
+  k_lbfgs_init<<<b->n, 256, 0, b->stream>>>(b->lbs, b->active, b->off_dev, b->c, b->xn,
+                                             b->lb_max_iter);
   CKL();
   b->launches += 1;
   if (use_graph && b->graph_round &&

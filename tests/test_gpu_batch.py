@@ -127,6 +127,42 @@ def test_batch_with_twelve_x_bins_per_row_equals_single_pairs():
         assert abs(D - st.D) <= D_RTOL * abs(st.D)
 
 
+def test_batch_with_pairs_at_different_pyramid_levels(specs):
+    # Pairs at level 0 and level 1 of their pyramids in one batch: each pair's
+    # batched value equals its single-pair value at its own level, and the
+    # batched L-BFGS stops each pair at its own level's iteration limit.
+    import paper_1804_05061_b300 as eng
+    es = [eng.from_problem(s.prob, s.fixed, s.moving, pyramid_levels=2) for s in specs[:4]]
+    levels = [0, 1, 1, 0]
+    assert all(e.levels[l].kernel_path == 1 for e, l in zip(es, levels))
+    b = eng.Batch(es, level=levels)
+    cs = [synth.coefficients(synth.problem(3, e.levels[l].dims, s.prob.ffd_spacing, (0, 0, 0), 32),
+                             90 + i, 1.0)
+          for i, (e, l, s) in enumerate(zip(es, levels, specs))]
+    for i, c in enumerate(cs):
+        assert tuple(b.coef(i).shape) == tuple(es[i].coef_shape(levels[i]))
+        b.coef(i).copy_(torch.from_numpy(c))
+    Db = b.value_and_grad(use_graph=True)
+    lanes = b.info().finalize_lanes
+    for i, (e, l) in enumerate(zip(es, levels)):
+        D, g = e.value_and_grad(torch.from_numpy(cs[i]).cuda(), level=l)
+        if e.levels[l].finalize_lanes == lanes:
+            assert Db[i] == D
+        else:
+            assert abs(Db[i] - D) <= 1e-12 * abs(D)
+        assert torch.allclose(b.grad(i), g, rtol=1e-5, atol=1e-5 * float(g.abs().max()))
+    o = eng.SRWCR.default_opts()
+    o.max_iter[0], o.max_iter[1] = 2, 4
+    o.stable_window = 0
+    for i in range(len(es)):
+        b.coef(i).zero_()
+    rep = b.register(o, use_graph=True, check=False)
+    for i, l in enumerate(levels):
+        assert rep["iterations"][i] <= (2 if l == 0 else 4)
+        if rep["status"][i] == 7:  # iteration limit
+            assert rep["iterations"][i] == (2 if l == 0 else 4)
+
+
 def test_batch_rejects_mixed_storage_and_general_path_levels(specs):
     import paper_1804_05061_b300 as eng
     es = make_engines(specs[:1], "f32") + make_engines(specs[1:2], "bf16")
