@@ -144,12 +144,15 @@ srwcr_status srwcr_value_and_grad_async(srwcr_ctx* ctx, int level, const float* 
 
 /* End-to-end form with host buffers: copies c_host (n_params floats) to the
  * device, evaluates, copies g back to g_host and D to D_host.  Uses
- * context-owned staging buffers; host buffers may be pageable or pinned. */
+ * context-owned staging buffers; host buffers may be pageable or pinned.
+ * With page-locked buffers the whole call is captured as a CUDA graph on
+ * first use for this (level, c_host, g_host) and replayed afterwards; the
+ * graph is dropped when srwcr_autotune re-selects a level's kernels. */
 srwcr_status srwcr_value_and_grad_host(srwcr_ctx* ctx, int level, const float* c_host,
                                        double* D_host, float* g_host);
 
 /* Forward half used by the autograd form: evaluates D (to D_dev) and keeps
- * the per-region tables of the finalisation (Table I lines 4-18) in the
+ * the per-region tables of the finalisation (Table I) in the
  * context for a later srwcr_backward at the same level. */
 srwcr_status srwcr_forward(srwcr_ctx* ctx, int level, const float* c_dev, double* D_dev);
 

@@ -147,7 +147,7 @@ __global__ void k_fixed_to_double(const unsigned long long* __restrict__ in, dou
     out[i] = (double)in[i] * inv_scale;
 }
 
-// (b) One warp per spatial bin r, FP64 throughout (Table I lines 5-17):
+// (b) One warp per spatial bin r, FP64 throughout (Table I):
 //   W_r = sum_a P, T1 = sum_a S1, T2 = sum_a S2, mu_r = T1/W, sigma_r^2 = T2/W - mu^2,
 //   Q_r = sum_a (S2 - S1^2/P) = W_r sum_a sigma_r^2(a) p_r(a)        (Eqs. 9, 10)
 //   1 - CR_r = Q_r/(W_r sigma_r^2),  share of D = Q_r/(Z sigma_r^2)      (Eq. 9)

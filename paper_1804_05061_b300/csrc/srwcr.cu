@@ -134,6 +134,15 @@ struct srwcr_ctx {
   double* rigid_acc = nullptr;        // rigid model: FP64 gradient accumulators [6]
   float* rigid_c = nullptr;           // rigid model: FFD form of the transform (level 0 size)
   float* rigid_g = nullptr;           // rigid model: dD/dc of that FFD form
+  // Host-buffer entry point: the whole call (copies, check, value, gradient,
+  // copies back) as one CUDA graph for the last (level, c, g) it served with
+  // page-locked host buffers; dropped when a level's kernels are re-selected.
+  cudaGraphExec_t host_graph = nullptr;
+  cudaStream_t capture_stream = nullptr;  // the legacy default stream cannot be captured
+  int host_graph_level = -1;
+  const float* host_graph_c = nullptr;
+  float* host_graph_g = nullptr;
+  long long host_graph_launches = 0;  // kernels per replay
 };
 
 namespace {
@@ -414,6 +423,16 @@ bool is_bf16(const srwcr_ctx* ctx) { return ctx->cfg.storage == SRWCR_STORAGE_BF
 
 // Kernel kinds reported by srwcr_profile_read.
 enum { kProfAccumulate = 0, kProfFinalize = 1, kProfAdjoint = 2, kProfKinds = 3 };
+
+// The cached host-call graph holds the kernels and buffers a level had when
+// it was captured.
+void drop_host_graph(srwcr_ctx* ctx) {
+  if (ctx->host_graph) cudaGraphExecDestroy(ctx->host_graph);
+  ctx->host_graph = nullptr;
+  ctx->host_graph_level = -1;
+  ctx->host_graph_c = nullptr;
+  ctx->host_graph_g = nullptr;
+}
 
 cudaEvent_t prof_begin(srwcr_ctx* ctx) {
   if (!ctx->profiling) return nullptr;
@@ -816,6 +835,8 @@ void srwcr_destroy(srwcr_ctx* ctx) {
   if (ctx->rigid_acc) cudaFree(ctx->rigid_acc);
   if (ctx->rigid_c) cudaFree(ctx->rigid_c);
   if (ctx->rigid_g) cudaFree(ctx->rigid_g);
+  if (ctx->host_graph) cudaGraphExecDestroy(ctx->host_graph);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   for (int l = 0; l < ctx->nlev; ++l) free_level(ctx->lev[l]);
   if (ctx->D_host) cudaFreeHost(ctx->D_host);
   if (ctx->flag_host) cudaFreeHost(ctx->flag_host);
@@ -1097,6 +1118,65 @@ srwcr_status srwcr_value_and_grad_async(srwcr_ctx* ctx, int level, const float* 
   return SRWCR_OK;
 }
 
+namespace {
+
+bool host_page_locked(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// One host-buffer call on ctx->stream: copy c in, check it, value and
+// gradient, copy g and D out (the caller synchronises).
+srwcr_status queue_host_call(srwcr_ctx* ctx, Level& lv, int64_t np, const float* c_host,
+                             float* g_host) {
+  CK(cudaMemcpyAsync(ctx->c_stage, c_host, sizeof(float) * np, cudaMemcpyHostToDevice, ctx->stream));
+  RET_IF(check_finite_async(ctx, ctx->c_stage, np));
+  RET_IF(run_value(ctx, lv, ctx->c_stage, true));
+  RET_IF(run_grad(ctx, lv, ctx->c_stage, nullptr, ctx->g_stage, true));
+  CK(cudaMemcpyAsync(g_host, ctx->g_stage, sizeof(float) * np, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->D_host, lv.D, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return SRWCR_OK;
+}
+
+// Captures queue_host_call into ctx->host_graph (on a private stream).  On
+// failure the graph stays empty and the caller queues the call directly.
+void capture_host_call(srwcr_ctx* ctx, int level, int64_t np, const float* c_host, float* g_host) {
+  drop_host_graph(ctx);
+  if (!ctx->capture_stream &&
+      cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->capture_stream = nullptr;
+    return;
+  }
+  cudaStream_t user = ctx->stream;
+  const long long launches = ctx->launches;
+  ctx->stream = ctx->capture_stream;
+  cudaGraph_t graph = nullptr;
+  srwcr_status st = SRWCR_ECUDA;
+  if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    st = queue_host_call(ctx, ctx->lev[level], np, c_host, g_host);
+    if (cudaStreamEndCapture(ctx->stream, &graph) != cudaSuccess) st = SRWCR_ECUDA;
+  }
+  ctx->stream = user;
+  ctx->host_graph_launches = ctx->launches - launches;
+  ctx->launches = launches;  // nothing ran during the capture
+  cudaGraphExec_t exec = nullptr;
+  if (st == SRWCR_OK && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+    ctx->host_graph = exec;
+    ctx->host_graph_level = level;
+    ctx->host_graph_c = c_host;
+    ctx->host_graph_g = g_host;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+}
+
+}  // namespace
+
 srwcr_status srwcr_value_and_grad_host(srwcr_ctx* ctx, int level, const float* c_host,
                                        double* D_host, float* g_host) {
   RET_IF(check_level(ctx, level));
@@ -1104,6 +1184,7 @@ srwcr_status srwcr_value_and_grad_host(srwcr_ctx* ctx, int level, const float* c
   Level& lv = ctx->lev[level];
   const int64_t np = lv.g.ncoef * ctx->cfg.ndim;
   if (ctx->stage_len < np) {
+    drop_host_graph(ctx);
     if (ctx->c_stage) cudaFree(ctx->c_stage);
     if (ctx->g_stage) cudaFree(ctx->g_stage);
     ctx->c_stage = ctx->g_stage = nullptr;
@@ -1111,12 +1192,24 @@ srwcr_status srwcr_value_and_grad_host(srwcr_ctx* ctx, int level, const float* c
     CK(cudaMalloc((void**)&ctx->g_stage, sizeof(float) * np));
     ctx->stage_len = np;
   }
-  CK(cudaMemcpyAsync(ctx->c_stage, c_host, sizeof(float) * np, cudaMemcpyHostToDevice, ctx->stream));
-  RET_IF(check_finite_async(ctx, ctx->c_stage, np));
-  RET_IF(run_value(ctx, lv, ctx->c_stage, true));
-  RET_IF(run_grad(ctx, lv, ctx->c_stage, nullptr, ctx->g_stage, true));
-  CK(cudaMemcpyAsync(g_host, ctx->g_stage, sizeof(float) * np, cudaMemcpyDeviceToHost, ctx->stream));
-  return finish_sync(ctx, lv, D_host);
+  // Page-locked host buffers: replay the call from a CUDA graph (captured on
+  // first use for this level and these buffers); otherwise queue it.
+  const bool graph_ok = !ctx->profiling && host_page_locked(c_host) && host_page_locked(g_host);
+  if (graph_ok && !(ctx->host_graph && ctx->host_graph_level == level &&
+                    ctx->host_graph_c == c_host && ctx->host_graph_g == g_host))
+    capture_host_call(ctx, level, np, c_host, g_host);
+  if (graph_ok && ctx->host_graph) {
+    CK(cudaGraphLaunch(ctx->host_graph, ctx->stream));
+    ctx->launches += ctx->host_graph_launches;
+  } else {
+    RET_IF(queue_host_call(ctx, lv, np, c_host, g_host));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->flag_host[0]) return fail(SRWCR_ENUMERIC, "non-finite FFD coefficients");
+  if (!std::isfinite(ctx->D_host[0])) return fail(SRWCR_ENUMERIC, "non-finite SRWCR value");
+  if (D_host) *D_host = ctx->D_host[0];
+  lv.tables = true;
+  return SRWCR_OK;
 }
 
 srwcr_status srwcr_forward(srwcr_ctx* ctx, int level, const float* c_dev, double* D_dev) {
@@ -1425,6 +1518,7 @@ extern "C" srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c
   if (!c_dev) return fail(SRWCR_EINVAL, "c_dev is NULL");
   if (reps < 1) reps = 3;
   Level& lv = ctx->lev[level];
+  drop_host_graph(ctx);  // the level's kernels may change
   if (!rows_allowed(ctx->cfg)) {
     // Only the row-parallel tiles are tuned; this level runs the general kernels.
     for (int d = 0; d < 3 && tile_out; ++d) tile_out[d] = lv.g.tile[d];

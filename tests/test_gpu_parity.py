@@ -228,6 +228,36 @@ def test_host_buffer_entry_point_equals_device_entry_point(small_cases):
     assert np.allclose(gh, g.cpu().numpy().ravel(), rtol=1e-5, atol=1e-7 * np.abs(gh).max())
 
 
+def test_host_buffer_entry_point_with_page_locked_buffers_replays_one_graph(small_cases):
+    # Page-locked host buffers: the call is captured once per (level, buffers)
+    # and replayed; results equal the device entry point's, a new buffer or a
+    # re-tuned level is captured again, and a bad input is still reported.
+    import paper_1804_05061_b300 as eng
+    prob, f, m, c = small_cases["pet_labels"]   # a problem no other test autotunes
+    e = engine_for(prob, f, m)
+    ct = torch.from_numpy(c).cuda()
+    D, g = e.value_and_grad(ct)
+    cp = torch.from_numpy(np.ascontiguousarray(c.ravel())).pin_memory()
+    gp = torch.zeros_like(cp).pin_memory()
+    for _ in range(3):
+        gp.zero_()
+        assert e.value_and_grad_host(cp.numpy(), gp.numpy()) == D
+        assert np.allclose(gp.numpy(), g.cpu().numpy().ravel(), rtol=1e-5,
+                           atol=1e-7 * float(g.abs().max()))
+    gp2 = torch.zeros_like(cp).pin_memory()
+    assert e.value_and_grad_host(cp.numpy(), gp2.numpy()) == D
+    # (the gradient's FP32 atomics make it reproducible to rounding only)
+    assert np.allclose(gp2.numpy(), gp.numpy(), rtol=1e-5, atol=1e-7 * float(g.abs().max()))
+    e.autotune(ct, reps=1)
+    D2, _ = e.value_and_grad(ct)
+    assert e.value_and_grad_host(cp.numpy(), gp.numpy()) == D2
+    bad = cp.clone().pin_memory()
+    bad[3] = float("nan")
+    with pytest.raises(eng.SrwcrError, match="ENUMERIC"):
+        e.value_and_grad_host(bad.numpy(), gp.numpy())
+    assert e.value_and_grad_host(cp.numpy(), gp.numpy()) == D2
+
+
 def test_exact_functional_dependence_gives_zero_on_gpu():
     prob = synth.problem(3, (40, 36, 20), (5, 5, 5), (3, 3, 2), 16)
     rng = np.random.default_rng(3)
