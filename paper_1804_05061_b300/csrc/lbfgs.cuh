@@ -6,8 +6,11 @@
 //
 // Vectors (coefficients, gradients, the m (s, y) pairs) live on the device
 // in FP32; every inner product is accumulated in FP64 on the device with a
-// fixed reduction order, then read by the host, which runs the control flow.
-// Included once, at the end of srwcr.cu.
+// fixed reduction order into a device scalar.  The two-loop recursion takes
+// its coefficients from those scalars on the device, so the host, which runs
+// the control flow, synchronises only for its decisions: once per iteration
+// (g.g, g.d, d.d) and once per line-search trial (the cost, g_new.d and, for
+// the history, s.y).  Included once, at the end of srwcr.cu.
 #pragma once
 
 namespace {
@@ -50,6 +53,40 @@ __global__ void k_axpby(float a, const float* __restrict__ x, float b, float* __
 
 // y = a*x (x and y may alias)
 __global__ void k_scal(float a, const float* __restrict__ x, float* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// Device scalars of one L-BFGS level (FP64): the decision values read by the
+// host and the two-loop coefficients.
+enum : int {
+  kScGG = 0, kScGD, kScDD, kScSYN, kScYY, kScGND, kScSY,
+  kScSQ = 8,              // [16] s_i . q of the first loop
+  kScYQ = kScSQ + 16,     // [16] y_i . d of the second loop
+  kScAlpha = kScYQ + 16,  // [16] alpha_i = rho_i s_i . q
+  kScCount = kScAlpha + 16
+};
+
+// Two-loop updates with the coefficient formed from device scalars in FP64
+// and rounded to FP32 as the host would: mode 0 (first loop) a = -(rho q_i),
+// also storing alpha_i = rho q_i; mode 1 (second loop) a = alpha_i - rho q_i.
+// y = a*x + b*y.
+__global__ void k_axpby_sc(int mode, double rho, int iq, int ialpha, double* __restrict__ sc,
+                           const float* __restrict__ x, float b, float* __restrict__ y,
+                           long long n) {
+  const double t = rho * sc[iq];
+  const float a = mode == 0 ? (float)-t : (float)(sc[ialpha] - t);
+  if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) sc[ialpha] = t;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+// y = (sc[inum] / sc[iden]) * x, the ratio rounded to FP32 (x, y may alias).
+__global__ void k_scal_sc(const double* __restrict__ sc, int inum, int iden, const float* x,
+                          float* y, long long n) {
+  const float a = (float)(sc[inum] / sc[iden]);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     y[i] = a * x[i];
@@ -115,20 +152,21 @@ struct LbfgsWork {
   float* S = nullptr;  // [m][n]
   float* Y = nullptr;  // [m][n]
   double* part = nullptr;
-  double* dot = nullptr;   // device scalar
-  double* Ddev = nullptr;  // device scalar
   double* Edev = nullptr;  // device scalar: bending energy at the evaluated point
   double* host = nullptr;  // pinned [3]
+  double* sc = nullptr;    // device scalars [kScCount]
+  double* hsc = nullptr;   // pinned copies of the decision scalars [8]
   double wp = 0.0;         // penalty weight w_p of Eq. (1)
   bool rigid = false;      // x holds rigid parameters (angles as angle / ang_scale)
   double ang_scale = 1.0;
 };
 
 void free_work(LbfgsWork& w) {
-  void* p[] = {w.x, w.g, w.d, w.xn, w.gn, w.S, w.Y, w.part, w.dot, w.Ddev, w.Edev};
+  void* p[] = {w.x, w.g, w.d, w.xn, w.gn, w.S, w.Y, w.part, w.Edev, w.sc};
   for (void* q : p)
     if (q) cudaFree(q);
   if (w.host) cudaFreeHost(w.host);
+  if (w.hsc) cudaFreeHost(w.hsc);
   w = LbfgsWork();
 }
 
@@ -143,27 +181,27 @@ srwcr_status alloc_work(LbfgsWork& w, long long n, int m) {
   CK(cudaMalloc((void**)&w.S, sizeof(float) * n * m));
   CK(cudaMalloc((void**)&w.Y, sizeof(float) * n * m));
   CK(cudaMalloc((void**)&w.part, sizeof(double) * kDotBlocks));
-  CK(cudaMalloc((void**)&w.dot, sizeof(double)));
-  CK(cudaMalloc((void**)&w.Ddev, sizeof(double)));
   CK(cudaMalloc((void**)&w.Edev, sizeof(double)));
   CK(cudaMallocHost((void**)&w.host, sizeof(double) * 3));
+  CK(cudaMalloc((void**)&w.sc, sizeof(double) * kScCount));
+  CK(cudaMallocHost((void**)&w.hsc, sizeof(double) * 8));
   return SRWCR_OK;
 }
 
-srwcr_status dot(srwcr_ctx* ctx, LbfgsWork& w, const float* a, const float* b, double* out) {
+// Queue an FP64 inner product into the device scalar sc[idx].
+srwcr_status dot_sc(srwcr_ctx* ctx, LbfgsWork& w, const float* a, const float* b, int idx) {
   k_dot_partial<<<kDotBlocks, 256, 0, ctx->stream>>>(a, b, w.n, w.part);
   CKL();
-  k_dot_final<<<1, 32, 0, ctx->stream>>>(w.part, kDotBlocks, w.dot);
+  k_dot_final<<<1, 32, 0, ctx->stream>>>(w.part, kDotBlocks, w.sc + idx);
   CKL();
-  CK(cudaMemcpyAsync(w.host, w.dot, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  *out = w.host[0];
   return SRWCR_OK;
 }
 
-srwcr_status axpby(srwcr_ctx* ctx, LbfgsWork& w, float a, const float* x, float b, float* y) {
-  k_axpby<<<kDotBlocks, 256, 0, ctx->stream>>>(a, x, b, y, w.n);
-  CKL();
+// Copy sc[first, first + count) to hsc[first ...] and wait.
+srwcr_status read_sc(srwcr_ctx* ctx, LbfgsWork& w, int first, int count) {
+  CK(cudaMemcpyAsync(w.hsc + first, w.sc + first, sizeof(double) * count, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return SRWCR_OK;
 }
 
@@ -173,26 +211,33 @@ srwcr_status scal(srwcr_ctx* ctx, LbfgsWork& w, float a, const float* x, float* 
   return SRWCR_OK;
 }
 
-// Cost of Eq. (1) at x: f = D + w_p C_p, g = its gradient.
-// The rigid model's bending energy is zero (an affine displacement), so its
-// cost is D alone.
-srwcr_status eval(srwcr_ctx* ctx, int level, LbfgsWork& w, const float* x, float* g, double* f) {
+// Cost of Eq. (1) at x: f = D + w_p C_p, g = its gradient; queued, the
+// cost's terms copied to w.host[1], w.host[2] (read after a synchronise with
+// eval_cost).  The rigid model's bending energy is zero (an affine
+// displacement), so its cost is D alone.
+srwcr_status eval_queue(srwcr_ctx* ctx, int level, LbfgsWork& w, const float* x, float* g) {
   Level& lv = ctx->lev[level];
   if (w.rigid) {
     RET_IF(run_rigid(ctx, lv, x, g, w.ang_scale));
-    CK(cudaMemcpyAsync(w.host + 1, lv.D, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    *f = w.host[1];
-    return SRWCR_OK;
+  } else {
+    RET_IF(run_value(ctx, lv, x, true));
+    RET_IF(run_grad(ctx, lv, x, nullptr, g, true));
+    if (w.wp > 0.0) RET_IF(bending_energy(ctx, level, x, w.Edev, g, (float)w.wp));
   }
-  RET_IF(run_value(ctx, lv, x, true));
-  RET_IF(run_grad(ctx, lv, x, nullptr, g, true));
-  if (w.wp > 0.0) RET_IF(bending_energy(ctx, level, x, w.Edev, g, (float)w.wp));
   CK(cudaMemcpyAsync(w.host + 1, lv.D, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  if (w.wp > 0.0)
+  if (!w.rigid && w.wp > 0.0)
     CK(cudaMemcpyAsync(w.host + 2, w.Edev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return SRWCR_OK;
+}
+
+double eval_cost(const LbfgsWork& w) {
+  return w.host[1] + (!w.rigid && w.wp > 0.0 ? w.wp * w.host[2] : 0.0);
+}
+
+srwcr_status eval(srwcr_ctx* ctx, int level, LbfgsWork& w, const float* x, float* g, double* f) {
+  RET_IF(eval_queue(ctx, level, w, x, g));
   CK(cudaStreamSynchronize(ctx->stream));
-  *f = w.host[1] + (w.wp > 0.0 ? w.wp * w.host[2] : 0.0);
+  *f = eval_cost(w);
   return SRWCR_OK;
 }
 
@@ -202,79 +247,83 @@ srwcr_status lbfgs_level(srwcr_ctx* ctx, int level, LbfgsWork& w, const srwcr_lb
   double f;
   RET_IF(eval(ctx, level, w, w.x, w.g, &f));
   int ne = 1, hist_len = 0, head = 0;  // ring buffer of (s, y); head = next slot
-  double rho[16], alpha_k[16];
+  double rho[16];
   std::vector<double> fh{f};
   bool restart = true;
   srwcr_status status = SRWCR_ENOTCONVERGED;
   int it = 0;
   const long long n = w.n;
   for (it = 1; it <= max_iter; ++it) {
-    double gg;
-    RET_IF(dot(ctx, w, w.g, w.g, &gg));
-    if (!(gg > 0.0)) { status = SRWCR_OK; --it; break; }
-    // Two-loop recursion on d = q.
+    // d = -H g by the two-loop recursion, all on the device.
+    RET_IF(dot_sc(ctx, w, w.g, w.g, kScGG));
     CK(cudaMemcpyAsync(w.d, w.g, sizeof(float) * n, cudaMemcpyDeviceToDevice, ctx->stream));
     for (int t = 0; t < hist_len; ++t) {
       const int slot = (head - 1 - t + o.m) % o.m;
-      double sq;
-      RET_IF(dot(ctx, w, w.S + slot * n, w.d, &sq));
-      alpha_k[slot] = rho[slot] * sq;
-      RET_IF(axpby(ctx, w, (float)-alpha_k[slot], w.Y + slot * n, 1.f, w.d));
+      RET_IF(dot_sc(ctx, w, w.S + slot * n, w.d, kScSQ + slot));
+      k_axpby_sc<<<kDotBlocks, 256, 0, ctx->stream>>>(0, rho[slot], kScSQ + slot, kScAlpha + slot,
+                                                       w.sc, w.Y + slot * n, 1.f, w.d, n);
+      CKL();
     }
     if (hist_len > 0) {
       const int newest = (head - 1 + o.m) % o.m;
-      double sy, yy;
-      RET_IF(dot(ctx, w, w.S + newest * n, w.Y + newest * n, &sy));
-      RET_IF(dot(ctx, w, w.Y + newest * n, w.Y + newest * n, &yy));
-      RET_IF(scal(ctx, w, (float)(sy / yy), w.d, w.d));
+      RET_IF(dot_sc(ctx, w, w.S + newest * n, w.Y + newest * n, kScSYN));
+      RET_IF(dot_sc(ctx, w, w.Y + newest * n, w.Y + newest * n, kScYY));
+      k_scal_sc<<<kDotBlocks, 256, 0, ctx->stream>>>(w.sc, kScSYN, kScYY, w.d, w.d, n);
+      CKL();
     }
     for (int t = hist_len - 1; t >= 0; --t) {
       const int slot = (head - 1 - t + o.m) % o.m;
-      double yq;
-      RET_IF(dot(ctx, w, w.Y + slot * n, w.d, &yq));
-      const double beta = rho[slot] * yq;
-      RET_IF(axpby(ctx, w, (float)(alpha_k[slot] - beta), w.S + slot * n, 1.f, w.d));
+      RET_IF(dot_sc(ctx, w, w.Y + slot * n, w.d, kScYQ + slot));
+      k_axpby_sc<<<kDotBlocks, 256, 0, ctx->stream>>>(1, rho[slot], kScYQ + slot, kScAlpha + slot,
+                                                       w.sc, w.S + slot * n, 1.f, w.d, n);
+      CKL();
     }
     RET_IF(scal(ctx, w, -1.f, w.d, w.d));  // d = -H g
-    double gd;
-    RET_IF(dot(ctx, w, w.g, w.d, &gd));
+    RET_IF(dot_sc(ctx, w, w.g, w.d, kScGD));
+    RET_IF(dot_sc(ctx, w, w.d, w.d, kScDD));
+    RET_IF(read_sc(ctx, w, kScGG, 3));
+    const double gg = w.hsc[kScGG];
+    double gd = w.hsc[kScGD], dd = w.hsc[kScDD];
+    if (!(gg > 0.0)) { status = SRWCR_OK; --it; break; }
     if (!(gd < 0.0)) {
       hist_len = 0;
       head = 0;
       RET_IF(scal(ctx, w, -1.f, w.g, w.d));
       gd = -gg;
+      dd = gg;  // d = -g: the same products, summed in the same order
       restart = true;
     }
-    double dd;
-    RET_IF(dot(ctx, w, w.d, w.d, &dd));
     double alpha = restart ? 1.0 / std::sqrt(dd) : 1.0;
     bool accepted = false;
-    double fn = f;
+    double fn = f, sy = 0.0;
+    // Each trial also forms s = xn - x, y = gn - g in the history slot head
+    // (the two-loop above is done with it) and s.y, so an accepted trial
+    // needs no further round trip.
+    float* s = w.S + head * n;
+    float* y = w.Y + head * n;
     for (int ls = 0; ls < o.max_ls; ++ls) {
       k_xpay<<<kDotBlocks, 256, 0, ctx->stream>>>(w.x, (float)alpha, w.d, w.xn, n);
       CKL();
-      RET_IF(eval(ctx, level, w, w.xn, w.gn, &fn));
+      RET_IF(eval_queue(ctx, level, w, w.xn, w.gn));
       ++ne;
+      RET_IF(dot_sc(ctx, w, w.gn, w.d, kScGND));
+      k_xpay<<<kDotBlocks, 256, 0, ctx->stream>>>(w.xn, -1.f, w.x, s, n);
+      CKL();
+      k_xpay<<<kDotBlocks, 256, 0, ctx->stream>>>(w.gn, -1.f, w.g, y, n);
+      CKL();
+      RET_IF(dot_sc(ctx, w, s, y, kScSY));
+      RET_IF(read_sc(ctx, w, kScGND, 2));
+      fn = eval_cost(w);
       if (!std::isfinite(fn) || fn > f + o.c1 * alpha * gd) { alpha *= 0.5; continue; }
-      double gnd;
-      RET_IF(dot(ctx, w, w.gn, w.d, &gnd));
-      if (gnd < o.c2 * gd) { alpha *= 2.0; continue; }
+      if (w.hsc[kScGND] < o.c2 * gd) { alpha *= 2.0; continue; }
       accepted = true;
+      sy = w.hsc[kScSY];
       break;
     }
     if (!accepted) { status = SRWCR_ELINESEARCH; --it; break; }
-    // s = xn - x into slot head, y = gn - g; then x = xn, g = gn.
-    float* s = w.S + head * n;
-    float* y = w.Y + head * n;
-    k_xpay<<<kDotBlocks, 256, 0, ctx->stream>>>(w.xn, -1.f, w.x, s, n);
-    CKL();
-    k_xpay<<<kDotBlocks, 256, 0, ctx->stream>>>(w.gn, -1.f, w.g, y, n);
-    CKL();
     std::swap(w.x, w.xn);
     std::swap(w.g, w.gn);
     f = fn;
-    double sy;
-    RET_IF(dot(ctx, w, s, y, &sy));
     if (sy > 0.0) {
       rho[head] = 1.0 / sy;
       head = (head + 1) % o.m;
