@@ -100,8 +100,9 @@ typedef struct {
   int64_t n_params;       /* ndim * prod(ffd_nodes) = length of c and g */
   int64_t n_regions;      /* prod(sbins) */
   int tile[3];            /* voxel tile used by the kernels */
-  int kernel_path;        /* 1: row-parallel kernels (32-wide tiles, FFD and
-                             spatial-bin spacing >= ~5 voxels along x);
+  int kernel_path;        /* 1: row-parallel kernels (32-wide tiles; a row
+                             meets at most 11 FFD x-nodes and 12 spatial
+                             x-bins: spacings >= 4 voxels along x);
                              0: general per-voxel kernels */
   int finalize_lanes;     /* lanes per spatial bin in the finalisation */
 } srwcr_level_desc;

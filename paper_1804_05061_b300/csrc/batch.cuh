@@ -260,7 +260,7 @@ struct srwcr_batch {
   bool own_stream = false;
   std::vector<srwcr_ctx*> ctx;
   std::vector<long long> off;  // caller order, n+1 float offsets into c and g
-  // Row-kernel launches.  Pairs are grouped by x-bins per row (4 or 8, a
+  // Row-kernel launches.  Pairs are grouped by x-bins per row (4, 8 or 12, a
   // template parameter) and by how many CTAs of their shared-memory size fit
   // on an SM (a launch's dynamic shared memory is the largest of its pairs',
   // so mixing sizes would lower the occupancy of the smaller ones); at most

@@ -17,7 +17,7 @@ struct BatchPair {
   AccArgs acc;
   AdjArgs adj;
   int id;                        // caller's index of the pair (active flags, D)
-  int group;                     // launch group (x-bins per row, 4 or 8)
+  int group;                     // launch group (x-bins per row, 4, 8 or 12)
   long long region_begin;        // first finalisation warp of this pair
   RegionStatic rs;               // static per-region data of the fixed image
   double inv_s1, inv_s2, invZ;

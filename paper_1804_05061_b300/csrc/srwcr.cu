@@ -93,7 +93,7 @@ struct Level {
   size_t smem_acc = 0, smem_adj = 0;
   bool tables = false;
   // Row-parallel fast path (32-wide tiles): static per-row lane permutation
-  // ordering voxels by fixed-image bin, x-bins per row (4 or 8), smem sizes.
+  // ordering voxels by fixed-image bin, x-bins per row (4, 8 or 12), smem sizes.
   bool rows = false;
   int nxb_rows = 0;
   unsigned char* perm = nullptr;
