@@ -39,6 +39,9 @@ constexpr int kAccWarps = 16;           // value pass: 512 threads per CTA
 constexpr int kAdjWarps = 8;            // adjoint: 256 threads per CTA
 constexpr int kMaxRowNodes = 11;        // FFD x-nodes a 32-voxel row may touch
 constexpr int kSentinel = 0x7fffffff;   // key of lanes past the image edge
+// Adjoint: rows whose per-segment X table (segments x x-bins x 2 entries)
+// would exceed this form X per lane instead.
+constexpr int kAdjLaneXMin = 64;
 
 // Per-axis geometry of one coordinate: FFD cell (relative to the tile's
 // first node), its 4 weights, spatial-bin cell (relative to the tile's first
@@ -276,9 +279,6 @@ __host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int
 // ---------------------------------------------------------------------------
 // (a) value pass: fused FFD + warp + joint statistics, row-parallel.
 // ---------------------------------------------------------------------------
-// Rows with at most this many segments take the transpose route of the
-// value kernel's segment sums (8 x-bins per row); others the shuffle route.
-constexpr int kTransposeMaxSeg = 12;
 
 // Position of value q of row (lane or segment) l in a warp's segment buffer
 // of NV floats per row.  With 8 x-bins per chunk (NV = 32, the only case
@@ -469,14 +469,16 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
           v[4 * b + 3] = w * e3;
         }
         // Segment sums land in row s of the warp's segment buffer, by one of
-        // two warp-uniform routes:
-        //  * transpose (8 x-bins per chunk, few segments): lane l stores its NV
-        //    values as row l, then lane q < NV adds column q down the rows in
-        //    lane order and writes segment s's total into row s (already read);
-        //  * segmented shuffle reduction toward each head, which then stores
-        //    its segment's NV totals (cost independent of the number of
-        //    segments).
-        if (XC == 8 && __popc(heads) <= kTransposeMaxSeg) {
+        // two routes fixed by the chunk width:
+        //  * transpose (8 x-bins per chunk): lane l stores its NV values as
+        //    row l, then lane q < NV adds column q down the rows in lane order
+        //    and writes segment s's total into row s (already read); one
+        //    extra store per segment, so it stays cheaper than the 5-level
+        //    shuffle over 32 values even when every lane is its own segment;
+        //  * 4 x-bins per chunk: segmented shuffle reduction toward each head,
+        //    which then stores its segment's NV totals (with 16 values the
+        //    half-idle transpose is not cheaper).
+        if (XC == 8) {
           float4* rowp = reinterpret_cast<float4*>(mysegS + lane * NV);
   #pragma unroll
           for (int k = 0; k < NV / 4; ++k)
@@ -845,35 +847,63 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
         for (int jj = 0; jj < 4; ++jj) s += ye.bs[jj] * tab[(ye.srel + jj) * g.hb[0] + b];
       rowt[tt] = s;
     }
-    // Segments of equal a0; X over the y bins for each segment's two bins.
+    // Segments of equal a0.  X summed over the row's y bins is formed either
+    // once per segment for every x-bin of the row (few segments), or, in rows
+    // with many segments (speckled fixed images), by each lane for its own
+    // 4 x-bins and 2 a-bins only (warp-uniform choice; the same sums in the
+    // same order either way).
     const int prev = __shfl_up_sync(0xffffffffu, key, 1);
     const bool head = lane == 0 || key != prev;
     const unsigned heads = __ballot_sync(0xffffffffu, head);
     const int nseg = __popc(heads);
-    if (head) mysegA[__popc(heads & ((1u << lane) - 1u))] = key;
-    __syncwarp();
     const float* XZr = XZ + (size_t)zl * p01 * nb;
-    for (int it = lane; it < nseg * NXB * 2; it += 32) {
-      const int s = it / (NXB * 2), rem = it % (NXB * 2), b = rem >> 1, slot = rem & 1;
-      const int a = mysegA[s];
-      float acc_x = 0.f;
-      if (a != kSentinel && b < g.hb[0]) {
-        for (int jj = 0; jj < 4; ++jj)
-          acc_x += ye.bs[jj] * XZr[(size_t)((ye.srel + jj) * g.hb[0] + b) * nb + a + slot];
+    const bool xlane = nseg * NXB * 2 > kAdjLaneXMin;
+    if (!xlane) {
+      if (head) mysegA[__popc(heads & ((1u << lane) - 1u))] = key;
+      __syncwarp();
+      for (int it = lane; it < nseg * NXB * 2; it += 32) {
+        const int s = it / (NXB * 2), rem = it % (NXB * 2), b = rem >> 1, slot = rem & 1;
+        const int a = mysegA[s];
+        float acc_x = 0.f;
+        if (a != kSentinel && b < g.hb[0]) {
+          for (int jj = 0; jj < 4; ++jj)
+            acc_x += ye.bs[jj] * XZr[(size_t)((ye.srel + jj) * g.hb[0] + b) * nb + a + slot];
+        }
+        xy[(s * NXB + b) * 2 + slot] = acc_x;
       }
-      xy[(s * NXB + b) * 2 + slot] = acc_x;
     }
     __syncwarp();
     float G = 0.f;
     if (live) {
-      const int sidx = __popc(heads & ((2u << lane) - 1u)) - 1;
       float su = 0.f, sv = 0.f, sxr = 0.f;
+      if (xlane) {
+        const int sp = xt.srel[p];
+        const size_t ystep = (size_t)g.hb[0] * nb;
 #pragma unroll
-      for (int b = 0; b < NXB; ++b) {
-        const float w = xt.bsp[b * 32 + p];
-        su += w * rowt[b];
-        sv += w * rowt[NXB + b];
-        sxr += w * (h0 * xy[(sidx * NXB + b) * 2] + h1 * xy[(sidx * NXB + b) * 2 + 1]);
+        for (int i = 0; i < 4; ++i) {
+          const int b = sp + i;
+          const float w = xt.bs[i * 32 + p];
+          if (w == 0.f || b >= g.hb[0]) continue;
+          su += w * rowt[b];
+          sv += w * rowt[NXB + b];
+          const float* xr = XZr + ((size_t)ye.srel * g.hb[0] + b) * nb + key;
+          float x0 = 0.f, x1 = 0.f;
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            x0 += ye.bs[jj] * xr[jj * ystep];
+            x1 += ye.bs[jj] * xr[jj * ystep + 1];
+          }
+          sxr += w * (h0 * x0 + h1 * x1);
+        }
+      } else {
+        const int sidx = __popc(heads & ((2u << lane) - 1u)) - 1;
+#pragma unroll
+        for (int b = 0; b < NXB; ++b) {
+          const float w = xt.bsp[b * 32 + p];
+          su += w * rowt[b];
+          sv += w * rowt[NXB + b];
+          sxr += w * (h0 * xy[(sidx * NXB + b) * 2] + h1 * xy[(sidx * NXB + b) * 2 + 1]);
+        }
       }
       G = scale * (dm2 * su + 2.f * dm1 * (sv - sxr));
     }

@@ -351,3 +351,48 @@ def test_c3_full_value_and_sampled_gradient():
     go = oracle.gradient_at(geo, A, M, c, st, idx)
     gs = g.cpu().numpy().ravel()[idx].astype(np.float64)
     assert np.abs(gs - go).max() <= G_ELEM * np.abs(g.cpu().numpy()).max()
+
+
+# Speckled fixed images put many fixed-image bins into one 32-voxel row (5 to
+# 19 here): the value pass forms the segment sums of 8-bin chunks by the
+# transpose route with up to 32 segments, and the adjoint forms the X sums
+# per lane in rows whose per-segment table would exceed 64 entries.  One
+# case per row width (4, 8 and 12 spatial x-bins); the 4-bin case mixes rows
+# of both adjoint routes.
+SPECKLE = [
+    ("oct_rows4", synth.problem(3, (64, 30, 12), (8, 8, 8), (2, 2, 2), 32), 4, "f32"),
+    ("oct_rows8", synth.problem(3, (64, 30, 14), (10, 10, 10), (0, 0, 0), 32), 8, "f32"),
+    ("oct_rows8_bf16", synth.problem(3, (64, 30, 14), (10, 10, 10), (0, 0, 0), 32), 8, "bf16"),
+    ("oct_rows12", synth.problem(3, (64, 26, 12), (5, 5, 5), (0, 0, 0), 32), 12, "f32"),
+]
+
+
+def lane_route_rows(fixed, nbins, nxb):
+    """Share of 32-voxel rows whose segments x x-bins x 2 exceeds 64 (the
+    adjoint's per-lane route), from the fixed image's bins on the host."""
+    L = nbins - 1
+    f = fixed.astype(np.float64)
+    k = np.clip(np.floor(L * (f - f.min()) / (f.max() - f.min())), 0, L - 1).astype(int)
+    rows = k.reshape(-1, 32)
+    nseg = np.array([len(np.unique(r)) for r in rows])
+    return float(np.mean(nseg * nxb * 2 > 64))
+
+
+@pytest.mark.parametrize("name,prob,nxb,storage", SPECKLE, ids=[s[0] for s in SPECKLE])
+def test_speckle_rows_match_oracle(name, prob, nxb, storage):
+    i = [s[0] for s in SPECKLE].index(name)
+    f, m = synth.small_pair("oct", prob.dims[:prob.ndim], prob.ffd_spacing[:prob.ndim], 2.0, 300 + i)
+    c = synth.coefficients(prob, 400 + i, 1.5)
+    share = lane_route_rows(f, prob.n_bins, nxb)
+    assert share >= 0.5, share
+    if nxb == 4:
+        assert share < 1.0, share          # both adjoint routes run
+    e = engine_for(prob, f, m, storage=storage)
+    assert e.levels[0].kernel_path == 1
+    D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+    st, go, _, _, _ = oracle_eval(prob, f, m, c, storage=storage)
+    assert abs(D - st.D) <= D_RTOL * abs(st.D), (D, st.D)
+    g = g.cpu().numpy().astype(np.float64)
+    gn, gon = np.linalg.norm(g), np.linalg.norm(go)
+    assert abs(gn - gon) <= GNORM_RTOL * gon, (gn, gon)
+    assert np.abs(g - go).max() <= G_ELEM * np.abs(go).max()
