@@ -139,7 +139,12 @@ srwcr_status srwcr_value_and_grad(srwcr_ctx* ctx, int level, const float* c_dev,
                                   float* g_dev);
 
 /* Same, without synchronising: D is written to D_dev (device double).
- * Safe to capture in a CUDA graph once the context exists. */
+ * Safe to capture in a CUDA graph once the context exists.  From the second
+ * consecutive call with the same (level, c_dev, D_dev, g_dev) the library
+ * captures the call once as its own CUDA graph (on a private stream) and
+ * replays it on the context's stream while the arguments stay the same;
+ * not while the context's stream is being captured by the caller or the
+ * benchmark profiling events are on.  srwcr_autotune drops the graph. */
 srwcr_status srwcr_value_and_grad_async(srwcr_ctx* ctx, int level, const float* c_dev,
                                         double* D_dev, float* g_dev);
 

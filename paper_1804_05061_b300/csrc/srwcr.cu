@@ -143,6 +143,16 @@ struct srwcr_ctx {
   const float* host_graph_c = nullptr;
   float* host_graph_g = nullptr;
   long long host_graph_launches = 0;  // kernels per replay
+  // Device entry point (srwcr_value_and_grad_async): the second consecutive
+  // call with the same (level, c, D, g) captures the call as one CUDA graph,
+  // replayed while the arguments stay the same; dropped with the host graph.
+  cudaGraphExec_t async_graph = nullptr;
+  int async_level = -1;
+  const float* async_c = nullptr;
+  double* async_D = nullptr;
+  float* async_g = nullptr;
+  int async_repeats = 0;               // consecutive calls with these arguments (-1: capture failed)
+  long long async_graph_launches = 0;  // kernels per replay
 };
 
 namespace {
@@ -426,12 +436,23 @@ enum { kProfAccumulate = 0, kProfFinalize = 1, kProfAdjoint = 2, kProfKinds = 3 
 
 // The cached host-call graph holds the kernels and buffers a level had when
 // it was captured.
+void drop_async_graph(srwcr_ctx* ctx) {
+  if (ctx->async_graph) cudaGraphExecDestroy(ctx->async_graph);
+  ctx->async_graph = nullptr;
+  ctx->async_level = -1;
+  ctx->async_c = nullptr;
+  ctx->async_D = nullptr;
+  ctx->async_g = nullptr;
+  ctx->async_repeats = 0;
+}
+
 void drop_host_graph(srwcr_ctx* ctx) {
   if (ctx->host_graph) cudaGraphExecDestroy(ctx->host_graph);
   ctx->host_graph = nullptr;
   ctx->host_graph_level = -1;
   ctx->host_graph_c = nullptr;
   ctx->host_graph_g = nullptr;
+  drop_async_graph(ctx);
 }
 
 cudaEvent_t prof_begin(srwcr_ctx* ctx) {
@@ -836,6 +857,7 @@ void srwcr_destroy(srwcr_ctx* ctx) {
   if (ctx->rigid_c) cudaFree(ctx->rigid_c);
   if (ctx->rigid_g) cudaFree(ctx->rigid_g);
   if (ctx->host_graph) cudaGraphExecDestroy(ctx->host_graph);
+  if (ctx->async_graph) cudaGraphExecDestroy(ctx->async_graph);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   for (int l = 0; l < ctx->nlev; ++l) free_level(ctx->lev[l]);
   if (ctx->D_host) cudaFreeHost(ctx->D_host);
@@ -1107,15 +1129,83 @@ srwcr_status srwcr_value_and_grad(srwcr_ctx* ctx, int level, const float* c_dev,
   return finish_sync(ctx, lv, D_host);
 }
 
+namespace {
+
+// One device-buffer call on ctx->stream: value (keeping the warp), gradient,
+// D copied out.
+srwcr_status queue_async_call(srwcr_ctx* ctx, Level& lv, const float* c_dev, double* D_dev,
+                              float* g_dev) {
+  RET_IF(run_value(ctx, lv, c_dev, true));
+  RET_IF(run_grad(ctx, lv, c_dev, nullptr, g_dev, true));
+  CK(cudaMemcpyAsync(D_dev, lv.D, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  return SRWCR_OK;
+}
+
+// Captures queue_async_call into ctx->async_graph on the private capture
+// stream (nothing runs); on failure the graph stays empty.
+void capture_async_call(srwcr_ctx* ctx, int level, const float* c_dev, double* D_dev,
+                        float* g_dev) {
+  if (!ctx->capture_stream &&
+      cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->capture_stream = nullptr;
+    return;
+  }
+  cudaStream_t user = ctx->stream;
+  const long long launches = ctx->launches;
+  ctx->stream = ctx->capture_stream;
+  cudaGraph_t graph = nullptr;
+  srwcr_status st = SRWCR_ECUDA;
+  if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    st = queue_async_call(ctx, ctx->lev[level], c_dev, D_dev, g_dev);
+    if (cudaStreamEndCapture(ctx->stream, &graph) != cudaSuccess) st = SRWCR_ECUDA;
+  }
+  ctx->stream = user;
+  ctx->async_graph_launches = ctx->launches - launches;
+  ctx->launches = launches;
+  cudaGraphExec_t exec = nullptr;
+  if (st == SRWCR_OK && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
+    ctx->async_graph = exec;
+  else
+    ctx->async_repeats = -1;  // no further attempt for these arguments
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+}
+
+}  // namespace
+
 srwcr_status srwcr_value_and_grad_async(srwcr_ctx* ctx, int level, const float* c_dev,
                                         double* D_dev, float* g_dev) {
   RET_IF(check_level(ctx, level));
   if (!c_dev || !g_dev || !D_dev) return fail(SRWCR_EINVAL, "null device pointer");
   Level& lv = ctx->lev[level];
-  RET_IF(run_value(ctx, lv, c_dev, true));
-  RET_IF(run_grad(ctx, lv, c_dev, nullptr, g_dev, true));
-  CK(cudaMemcpyAsync(D_dev, lv.D, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-  return SRWCR_OK;
+  // Repeated calls with the same buffers (an optimiser's loop) replay one
+  // graph: fewer launch gaps.  Not while the caller's stream is being
+  // captured (the call then becomes part of the caller's graph as it is) or
+  // while the per-kernel profiling events are on.
+  if (!(ctx->async_level == level && ctx->async_c == c_dev && ctx->async_D == D_dev &&
+        ctx->async_g == g_dev)) {
+    drop_async_graph(ctx);
+    ctx->async_level = level;
+    ctx->async_c = c_dev;
+    ctx->async_D = D_dev;
+    ctx->async_g = g_dev;
+  }
+  if (ctx->async_repeats >= 0 && ctx->async_repeats < 2) ++ctx->async_repeats;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(ctx->stream, &cap) != cudaSuccess ||
+                         cap != cudaStreamCaptureStatusNone;
+  if (capturing) cudaGetLastError();
+  if (!capturing && !ctx->profiling && ctx->async_repeats >= 2) {
+    if (!ctx->async_graph) capture_async_call(ctx, level, c_dev, D_dev, g_dev);
+    if (ctx->async_graph) {
+      CK(cudaGraphLaunch(ctx->async_graph, ctx->stream));
+      ctx->launches += ctx->async_graph_launches;
+      lv.tables = true;
+      return SRWCR_OK;
+    }
+  }
+  return queue_async_call(ctx, lv, c_dev, D_dev, g_dev);
 }
 
 namespace {
