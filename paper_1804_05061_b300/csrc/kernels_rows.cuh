@@ -280,20 +280,15 @@ __host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int
 // (a) value pass: fused FFD + warp + joint statistics, row-parallel.
 // ---------------------------------------------------------------------------
 
-// Position of value q of row (lane or segment) l in a warp's segment buffer
-// of NV floats per row.  With 8 x-bins per chunk (NV = 32, the only case
-// that takes the transpose route) 16-byte chunks are XOR-swizzled by the row
-// index, so the row stores and the column reads are free of bank conflicts;
-// with 4 the layout is plain.
-template <int NV>
-__device__ __forceinline__ int seg_chunk(int l, int k) {
-  static_assert(NV == 16 || NV == 32, "4 or 8 x-bins per chunk");
-  return NV == 32 ? (k ^ (l & 7)) : k;
-}
-
+// Position of value q of row l in a warp's segment buffer of NV floats per
+// row (a segment's totals sit in the row of its last lane).  With 8 x-bins
+// per chunk (NV = 32, the transpose) 16-byte chunks are XOR-swizzled by the
+// row index, so the row stores and the column reads are free of bank
+// conflicts; with 4 the layout is plain.
 template <int NV>
 __device__ __forceinline__ int seg_at(int l, int q) {
-  return l * NV + (seg_chunk<NV>(l, q >> 2) << 2) + (q & 3);
+  static_assert(NV == 16 || NV == 32, "4 or 8 x-bins per chunk");
+  return NV == 32 ? l * 32 + (((q >> 2) ^ (l & 7)) << 2) + (q & 3) : l * 16 + q;
 }
 
 template <int DIM, typename T, int NXB>
@@ -333,7 +328,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   unsigned* hhi = hmid + (size_t)NPY * S;
   float* segS = reinterpret_cast<float*>(hhi + (size_t)NPY * S);
   int* segA = reinterpret_cast<int*>(segS + kAccWarps * 32 * NV);
-  int* binl = segA + kAccWarps * 32;          // [warp][64][2]: a, (s | slot<<8 | merge<<9)
+  int* binl = segA + kAccWarps * 32;          // [warp][64][2]: a, (row | slot<<8 | merge<<9 | prev row<<10)
   int* a2c = binl + kAccWarps * 64 * 2;       // fixed-image bin -> compact index (-1: unused)
   int* c2a = a2c + nb;                        // compact index -> bin
   float* cyz_all = reinterpret_cast<float*>(c2a + g.nabin);
@@ -453,7 +448,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
       const bool head = lane == 0 || key != prev;
       const unsigned heads = __ballot_sync(0xffffffffu, head);
       const unsigned above = lane == 31 ? 0u : (heads & (0xffffffffu << (lane + 1)));
-      const int sidx = __popc(heads & ((1u << lane) - 1u));
+      const unsigned ends = (heads >> 1) | 0x80000000u;   // last lane of each segment
       // The row's x-bins in chunks of XC (one chunk unless NXB = 12); the bin
       // list is built after the first chunk's segment sums.
       int nbin = 0;
@@ -468,35 +463,32 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
           v[4 * b + 2] = w * e2;
           v[4 * b + 3] = w * e3;
         }
-        // Segment sums land in row s of the warp's segment buffer, by one of
-        // two routes fixed by the chunk width:
-        //  * transpose (8 x-bins per chunk): lane l stores its NV values as
-        //    row l, then lane q < NV adds column q down the rows in lane order
-        //    and writes segment s's total into row s (already read); one
-        //    extra store per segment, so it stays cheaper than the 5-level
-        //    shuffle over 32 values even when every lane is its own segment;
-        //  * 4 x-bins per chunk: segmented shuffle reduction toward each head,
-        //    which then stores its segment's NV totals (with 16 values the
-        //    half-idle transpose is not cheaper).
-        if (XC == 8) {
-          float4* rowp = reinterpret_cast<float4*>(mysegS + lane * NV);
+        // Segment sums; a segment's NV totals end up in the row of its last
+        // lane in the warp's segment buffer.
+        //  * 8 x-bins per chunk: transpose.  Lane l stores its NV values as
+        //    row l, then lane q sums column q down the rows in lane order and,
+        //    at the last lane of each segment, writes the running sum (the
+        //    segment's total) back into that row (already read): 32 loads and
+        //    one store per segment instead of a 5-level shuffle over 32
+        //    values, however many segments the row has.
+        //  * 4 x-bins: segmented shuffle reduction toward each head, which
+        //    stores its segment's totals (with 16 values the shuffle tree
+        //    beats a transpose).
+        if (NV == 32) {
+          float4* rowp = reinterpret_cast<float4*>(mysegS);
   #pragma unroll
           for (int k = 0; k < NV / 4; ++k)
-            rowp[seg_chunk<NV>(lane, k)] =
+            rowp[seg_at<NV>(lane, 4 * k) >> 2] =
                 make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
           __syncwarp();
-          const unsigned ends = (heads >> 1) | 0x80000000u;  // last lane of each segment
-          if (lane < NV) {
-            float sum = 0.f;
-            int sw = 0;
+          float sum = 0.f;
   #pragma unroll
-            for (int l = 0; l < 32; ++l) {
-              sum += mysegS[seg_at<NV>(l, lane)];
-              if ((ends >> l) & 1u) {
-                mysegS[seg_at<NV>(sw, lane)] = sum;
-                sum = 0.f;
-                ++sw;
-              }
+          for (int l = 0; l < 32; ++l) {
+            const int at = seg_at<NV>(l, lane);
+            sum += mysegS[at];
+            if ((ends >> l) & 1u) {
+              mysegS[at] = sum;
+              sum = 0.f;
             }
           }
         } else {
@@ -511,10 +503,10 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
             }
           }
           if (head && key != kSentinel) {
-            float4* rowp = reinterpret_cast<float4*>(mysegS + sidx * NV);
+            float4* rowp = reinterpret_cast<float4*>(mysegS);
   #pragma unroll
             for (int k = 0; k < NV / 4; ++k)
-              rowp[seg_chunk<NV>(sidx, k)] =
+              rowp[seg_at<NV>(seg_end - 1, 4 * k) >> 2] =
                   make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
           }
         }
@@ -522,8 +514,11 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
         if (q0 == 0) {
           // Bin list.  Segment s (key a) adds bin a (slot 0, plus slot 1 of
           // s-1 when that segment's key is a-1) and, unless segment s+1 has
-          // key a+1, bin a+1 (slot 1 alone).
+          // key a+1, bin a+1 (slot 1 alone).  An entry names the rows holding
+          // the totals: its segment's last lane and, when merged, the last
+          // lane of segment s-1 (the head's left neighbour).
           const int next_head = above ? __ffs(above) - 1 : -1;
+          const int last = next_head < 0 ? 31 : next_head - 1;
           const int next_key = __shfl_sync(0xffffffffu, key, next_head < 0 ? lane : next_head);
           const bool real = head && key != kSentinel;
           const bool upper = real && (next_head < 0 || next_key != key + 1);
@@ -541,12 +536,12 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
           nbin = __popc(emit0) + __popc(emit1);
           if (in0) {
             mybins[2 * pos] = key;
-            mybins[2 * pos + 1] = sidx | (merge ? (1 << 9) : 0);
+            mybins[2 * pos + 1] = last | (merge ? (1 << 9) | ((lane - 1) << 10) : 0);
           }
           if (in1) {
             const int q = pos + (in0 ? 1 : 0);
             mybins[2 * q] = key + 1;
-            mybins[2 * q + 1] = sidx | (1 << 8);
+            mybins[2 * q + 1] = last | (1 << 8);
           }
           __syncwarp();
         }
@@ -565,7 +560,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
           const int info = mybins[2 * e + 1];
           const int sg = info & 0xff, slot = (info >> 8) & 1;
           float val = mysegS[seg_at<NV>(sg, 4 * b + 2 * slot + ch)];
-          if (info & (1 << 9)) val += mysegS[seg_at<NV>(sg - 1, 4 * b + 2 + ch)];
+          if (info & (1 << 9)) val += mysegS[seg_at<NV>((info >> 10) & 31, 4 * b + 2 + ch)];
           const float uv = val * (ch ? s2 : s1);
           if (uv == 0.f) continue;
           const int col = prow + ((a2c[a] - c0) * 2 + ch) * g.hb[0] + bx_;
