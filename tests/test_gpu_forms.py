@@ -220,14 +220,22 @@ def test_synthetic_grid_registration_recovers_the_known_displacement():
     assert rmse < 0.55 * rmse0, (rmse0, rmse)
 
 
-def test_async_repeated_calls_replay_one_graph_with_current_inputs():
+ASYNC_CASES = [
+    ("ct_rows", "ct", synth.problem(3, (70, 45, 23), (6, 5, 4), (3, 2, 2), 24), {}),
+    ("ct_bf16", "ct", synth.problem(3, (70, 45, 23), (6, 5, 4), (3, 2, 2), 24), {"storage": "bf16"}),
+    ("ct_mas_a", "ct", synth.problem(3, (48, 40, 20), (6, 6, 5), (2, 2, 2), 24), {"role": "mas_a"}),
+    ("ellipse_2d", "ellipse", synth.problem(2, (100, 77), (7, 7), (3, 2), 16), {}),
+]
+
+
+@pytest.mark.parametrize("name,kind,prob,kw", ASYNC_CASES, ids=[a[0] for a in ASYNC_CASES])
+def test_async_repeated_calls_replay_one_graph_with_current_inputs(name, kind, prob, kw):
     """srwcr_value_and_grad_async with the same buffers replays one captured
     graph from the second call on: each call still reads the buffers'
     current contents, launches the same kernels, and after autotune (which
     drops the graph) the replay matches the synchronous entry point again."""
-    prob = synth.problem(3, (70, 45, 23), (6, 5, 4), (3, 2, 2), 24)
-    f, m = synth.small_pair("ct", prob.dims, prob.ffd_spacing, 2.0, 71)
-    e = engine(prob, f, m)
+    f, m = synth.small_pair(kind, prob.dims[:prob.ndim], prob.ffd_spacing[:prob.ndim], 2.0, 71)
+    e = engine(prob, f, m, **kw)
     cs = [torch.from_numpy(synth.coefficients(prob, 72 + k, 1.5)).cuda() for k in range(2)]
     ref = [e.value_and_grad(ck) for ck in cs]
     c = torch.empty_like(cs[0])
@@ -242,9 +250,15 @@ def test_async_repeated_calls_replay_one_graph_with_current_inputs():
         torch.cuda.synchronize()
         D0, g0 = ref[k]
         assert float(D.item()) == D0, (call, float(D.item()), D0)   # fixed-point sums: exact
-        assert torch.allclose(g, g0, rtol=1e-5, atol=1e-6 * float(g0.abs().max())), call
+        # The gradient's FP32 atomics add in any order: compare to rounding.
+        assert torch.allclose(g, g0, rtol=1e-5, atol=1e-5 * float(g0.abs().max())), call
     _, _, launches = e.profile_read(reset=True)
-    assert launches == 5 * 5                   # 5 kernels per call, replayed or not
+    e.set_profiling(True)                      # the events force call-by-call launches
+    e.value_and_grad_async(c, D, g)
+    torch.cuda.synchronize()
+    e.set_profiling(False)
+    _, _, per_call = e.profile_read(reset=True)
+    assert per_call >= 4 and launches == 5 * per_call   # replayed or not, the same kernels
     tile = e.autotune(cs[0], reps=2)
     assert tuple(e.levels[0].tile) == tile
     ref = [e.value_and_grad(ck) for ck in cs]
@@ -254,4 +268,4 @@ def test_async_repeated_calls_replay_one_graph_with_current_inputs():
         e.value_and_grad_async(c, D, g)
         torch.cuda.synchronize()
         assert float(D.item()) == ref[k][0], call
-        assert torch.allclose(g, ref[k][1], rtol=1e-5, atol=1e-6 * float(ref[k][1].abs().max()))
+        assert torch.allclose(g, ref[k][1], rtol=1e-5, atol=1e-5 * float(ref[k][1].abs().max()))
