@@ -492,6 +492,18 @@ def main():
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     _, _, launches = e.profile_read(reset=True)
+    # The same steps with the L2 warm (no flush between them).
+    warm0 = torch.cuda.Event(enable_timing=True)
+    warm1 = torch.cuda.Event(enable_timing=True)
+    warm0.record(stream)
+    for _ in range(args.steps):
+        e.value_and_grad_async(c, D, g)
+    warm1.record(stream)
+    torch.cuda.synchronize()
+    t_warm = max_over_ranks(warm0.elapsed_time(warm1) / 1e3, dist, dev)
+    l2_warm = {"value": whole_job_rate(ws, prob.n_voxels * args.steps, t_warm) / 1e9,
+               "unit": "Gvoxel/s", "ms_per_step": t_warm * 1e3 / args.steps}
+    e.profile_read(reset=True)
     # Per-kernel split (CUDA events around each kernel on the context's
     # stream) in a separate pass: with the events on, the library launches
     # the kernels one by one instead of replaying its graph.
@@ -563,6 +575,8 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "algorithmic_bytes": bytes_alg[dom],
+                "dram_frac": (traffic / (avg[dom] / 1e3) / 1e9 / peak
+                              if traffic and avg[dom] > 0 else None),
                 "kernel_ms": {k: round(v, 4) for k, v in avg.items()},
                 "algorithmic_bytes_per_voxel_step": 4 * esz, "issue": issue}
 
@@ -597,7 +611,8 @@ def main():
                        "n_params": prob.n_params, "parallelism": f"replicas x{ws}",
                        "l2": "flushed between steps (256 MB write, outside the timed events)",
                        "wall_ms_per_step_incl_flush": wall / args.steps * 1e3},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "l2_warm": l2_warm,
+            "clocks": clk,
             "gpu_launches": launches, "batched": batch, "registration": reg, "accuracy": acc,
             "rigid": rig}
     if rank == 0:
