@@ -172,23 +172,32 @@ __device__ __forceinline__ void build_axis_tables(const Geo& g, const TileOrigin
 template <int DIM>
 __device__ __forceinline__ void build_cz(const Geo& g, const TileOrigin& T, const float* __restrict__ c,
                                          const AxisEntry* zt, float* CZ) {
-  const int per_z = DIM * g.hf[1] * g.hf[0];
-  const int n = g.tile[2] * per_z;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int zl = i / per_z, r = i % per_z;
-    const int k = r / (g.hf[1] * g.hf[0]), m = (r / g.hf[0]) % g.hf[1], l = r % g.hf[0];
+  // Threads are spread over the (y-node m, x-node l) pairs and, when there
+  // are fewer pairs than threads, over the (plane, component) entries of a
+  // pair; the index divisions are done once per thread.
+  const int per_k = g.hf[1] * g.hf[0];
+  const int per_z = DIM * per_k;
+  const int nzk = g.tile[2] * DIM;
+  const int tpp = per_k < (int)blockDim.x ? min((int)blockDim.x / per_k, nzk) : 1;
+  for (int t = threadIdx.x; t < per_k * tpp; t += blockDim.x) {
+    const int sub = t / per_k, i = t - sub * per_k;
+    const int m = i / g.hf[0], l = i - m * g.hf[0];
     const int n0 = T.f[0] + l, n1 = T.f[1] + m;
-    float s = 0.f;
-    if (n0 < g.nf[0] && n1 < g.nf[1]) {
+    const bool in = n0 < g.nf[0] && n1 < g.nf[1];
+    for (int zk = sub; zk < nzk; zk += tpp) {
+      const int zl = zk / DIM, k = zk - zl * DIM;
       const AxisEntry& e = zt[zl];
-      const int NZ = DIM == 3 ? 4 : 1;
-      for (int q = 0; q < NZ; ++q) {
-        const int n2 = T.f[2] + e.frel + q;
-        if (n2 < g.nf[2])
-          s += e.bf[q] * __ldg(c + k * g.ncoef + ((long long)n2 * g.nf[1] + n1) * g.nf[0] + n0);
+      float s = 0.f;
+      if (in) {
+        const int NZ = DIM == 3 ? 4 : 1;
+        for (int q = 0; q < NZ; ++q) {
+          const int n2 = T.f[2] + e.frel + q;
+          if (n2 < g.nf[2])
+            s += e.bf[q] * __ldg(c + k * g.ncoef + ((long long)n2 * g.nf[1] + n1) * g.nf[0] + n0);
+        }
       }
+      CZ[zl * per_z + k * per_k + i] = s;
     }
-    CZ[i] = s;
   }
 }
 
@@ -588,39 +597,48 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
     // Flush: one entry per (first plane of a z cell, y bin, column); the
     // planes of that cell are combined with their z weights, then the NK z
     // bins are added to the global accumulators.
+    // Threads are spread over the columns (bin, moment, x bin) and, when
+    // there are fewer columns than threads, over the y bins of a column; each
+    // loops over the first planes of the z cells and its y bins (the index
+    // divisions are done once per thread).
     const int wcols = 2 * cb * g.hb[0];
-    for (int i = threadIdx.x; i < NPY * S; i += blockDim.x) {
-      const int pz = i / S, col = i % S;
-      if (col >= wcols) continue;
-      const int zl = pz / g.hb[1], l1 = pz - zl * g.hb[1];
-      const int cz = zt[zl].srel;
-      if (zl > 0 && zt[zl - 1].srel == cz) continue;
-      const int b = col % g.hb[0], ach = col / g.hb[0];
+    const int tpc = wcols < (int)blockDim.x ? min((int)blockDim.x / wcols, g.hb[1]) : 1;
+    for (int t = threadIdx.x; t < wcols * tpc; t += blockDim.x) {
+      const int sub = t / wcols, col = t - sub * wcols;
+      const int ach = col / g.hb[0], b = col - ach * g.hb[0];
       if (c0 + (ach >> 1) >= cnt) continue;
-      float u[NK];
-#pragma unroll
-      for (int m = 0; m < NK; ++m) u[m] = 0.f;
-      bool any = false;
-      for (int pl = zl; pl < g.tile[2] && zt[pl].srel == cz; ++pl) {
-        const int j = (pl * g.hb[1] + l1) * S + col;
-        const unsigned long long h =
-            ((unsigned long long)hhi[j] << 40) + ((unsigned long long)hmid[j] << 20) + hlo[j];
-        if (!h) continue;
-        any = true;
-        const float hv = __ull2float_rn(h);
-#pragma unroll
-        for (int m = 0; m < NK; ++m) u[m] = fmaf(zt[pl].bs[m], hv, u[m]);
-      }
-      if (!any) continue;
+      const int r0 = TO.cb[0] + b;
+      if (r0 >= g.nsb[0]) continue;
       const int a = c2a[c0 + (ach >> 1)], ch = ach & 1;
-      const int r0 = TO.cb[0] + b, r1 = TO.cb[1] + l1;
-      if (r0 >= g.nsb[0] || r1 >= g.nsb[1]) continue;
+      for (int zl = 0; zl < g.tile[2]; ++zl) {
+        const int cz = zt[zl].srel;
+        if (zl > 0 && zt[zl - 1].srel == cz) continue;
+        for (int l1 = sub; l1 < g.hb[1]; l1 += tpc) {
+          const int r1 = TO.cb[1] + l1;
+          if (r1 >= g.nsb[1]) break;
+          float u[NK];
 #pragma unroll
-      for (int m = 0; m < NK; ++m) {
-        const int r2 = TO.cb[2] + cz + m;
-        if (u[m] == 0.f || r2 >= g.nsb[2]) continue;
-        const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
-        atomicAdd(acc + ((size_t)r * nb + a) * 2 + ch, __float2ull_rn(u[m]));
+          for (int m = 0; m < NK; ++m) u[m] = 0.f;
+          bool any = false;
+          for (int pl = zl; pl < g.tile[2] && zt[pl].srel == cz; ++pl) {
+            const int j = (pl * g.hb[1] + l1) * S + col;
+            const unsigned long long h =
+                ((unsigned long long)hhi[j] << 40) + ((unsigned long long)hmid[j] << 20) + hlo[j];
+            if (!h) continue;
+            any = true;
+            const float hv = __ull2float_rn(h);
+#pragma unroll
+            for (int m = 0; m < NK; ++m) u[m] = fmaf(zt[pl].bs[m], hv, u[m]);
+          }
+          if (!any) continue;
+#pragma unroll
+          for (int m = 0; m < NK; ++m) {
+            const int r2 = TO.cb[2] + cz + m;
+            if (u[m] == 0.f || r2 >= g.nsb[2]) continue;
+            const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
+            atomicAdd(acc + ((size_t)r * nb + a) * 2 + ch, __float2ull_rn(u[m]));
+          }
+        }
       }
     }
     __syncthreads();                            // the next pass clears the accumulators

