@@ -202,15 +202,47 @@ __device__ __forceinline__ void build_cz(const Geo& g, const TileOrigin& T, cons
 }
 
 // Per-row FFD table: cyz[k][l] = sum_m beta_m(y) CZ[z][k][ly + m][l].
+// The lane's entries (component k, x-node l) of that table: t = lane and
+// t = lane + 32, t < DIM * nxn (fixed for a tile, so decoded once).
+struct CyzSlots {
+  int n;        // entries of this lane (0, 1 or 2)
+  int k[2], l[2];
+};
+
+template <int DIM>
+__device__ __forceinline__ CyzSlots cyz_slots(int nxn, int lane) {
+  CyzSlots s;
+  s.n = (lane < DIM * nxn) + (lane + 32 < DIM * nxn);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int t = lane + 32 * j;
+    s.k[j] = t / nxn;
+    s.l[j] = t - s.k[j] * nxn;
+  }
+  return s;
+}
+
 template <int DIM>
 __device__ __forceinline__ void row_cyz(const Geo& g, const float* CZ, int zl, const AxisEntry& ye,
-                                        int nxn, float* cyz, int lane) {
+                                        const CyzSlots& cs, float* cyz) {
   const int per_z = DIM * g.hf[1] * g.hf[0];
-  for (int t = lane; t < DIM * nxn; t += 32) {
-    const int k = t / nxn, l = t % nxn;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (j >= cs.n) break;
+    const int k = cs.k[j], l = cs.l[j];
     const float* base = CZ + zl * per_z + (k * g.hf[1] + ye.frel) * g.hf[0] + l;
     cyz[k * kMaxRowNodes + l] = ye.bf[0] * base[0] + ye.bf[1] * base[g.hf[0]] +
                                 ye.bf[2] * base[2 * g.hf[0]] + ye.bf[3] * base[3 * g.hf[0]];
+  }
+}
+
+// A warp's next row (y, z within the tile), advanced by the number of warps
+// without a division.
+__device__ __forceinline__ void row_step(int step, int ty, int* yl, int* zl) {
+  *yl += step;
+  while (*yl >= ty) {
+    *yl -= ty;
+    ++*zl;
   }
 }
 
@@ -383,6 +415,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   const int xlast = min(TO.o[0] + 31, g.n[0] - 1);
   const int nxn = xlast / g.fsp[0] - TO.f[0] + 4;   // FFD x-nodes of the row
   const int nrows = g.tile[1] * g.tile[2];
+  const CyzSlots cslots = cyz_slots<DIM>(nxn, lane);
   for (int c0 = 0; c0 < cnt; c0 += cb) {
     const bool multi = cnt > cb;                // CTA-uniform
     if (c0 > 0) {                               // the first pass was cleared above
@@ -392,11 +425,11 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
     // A row's permutation and fixed-image values are loaded in lane order
     // (independent of each other) one row ahead; the value lane l needs,
     // that of voxel o + perm[l], comes by shuffle.
-    auto fetch = [&](int r, int* pp, float* aa) {
+    auto fetch = [&](int yr, int zr, int* pp, float* aa) {
       *pp = 0;
       *aa = 0.f;
-      if (r >= nrows) return false;
-      const int y = TO.o[1] + r % g.tile[1], z = TO.o[2] + r / g.tile[1];
+      if (zr >= g.tile[2]) return false;          // past the tile's last row
+      const int y = TO.o[1] + yr, z = TO.o[2] + zr;
       if (y >= g.n[1] || z >= g.n[2]) return false;
       const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
       *pp = perm[rowid * 32 + lane];
@@ -406,14 +439,17 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
     };
     int p_next;
     float a_next;
-    bool ok_next = fetch(warp, &p_next, &a_next);
+    int yn = 0, zn = 0;                         // row = zn * tile[1] + yn
+    row_step(warp, g.tile[1], &yn, &zn);
+    bool ok_next = fetch(yn, zn, &p_next, &a_next);
     for (int row = warp; row < nrows; row += kAccWarps) {
       const int p = p_next;
       const float a_lane = a_next;
       const bool ok = ok_next;
-      ok_next = fetch(row + kAccWarps, &p_next, &a_next);
+      const int yl = yn, zl = zn;
+      row_step(kAccWarps, g.tile[1], &yn, &zn);
+      ok_next = fetch(yn, zn, &p_next, &a_next);
       if (!ok) continue;  // warp-uniform
-      const int yl = row % g.tile[1], zl = row / g.tile[1];
       const int y = TO.o[1] + yl, z = TO.o[2] + zl;
 
       const int x = TO.o[0] + p;
@@ -430,7 +466,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
         if (!__any_sync(0xffffffffu, in)) continue;
       }
       const AxisEntry ye = yt[yl];
-      row_cyz<DIM>(g, CZ, zl, ye, nxn, cyz, lane);
+      row_cyz<DIM>(g, CZ, zl, ye, cslots, cyz);
       __syncwarp();
       float m1 = 0.f, m2 = 0.f, h0 = 0.f, h1 = 0.f;
       if (act) {
@@ -782,10 +818,10 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
     float4 b;
     bool ok;
   };
-  auto fetch = [&](int r) {
+  auto fetch = [&](int yr, int zr) {
     RowLoad f{0, 0.f, make_float4(0.f, 0.f, 0.f, 0.f), false};
-    if (r >= nrows) return f;
-    const int y = TO.o[1] + r % g.tile[1], z = TO.o[2] + r / g.tile[1];
+    if (zr >= g.tile[2]) return f;              // past the tile's last row
+    const int y = TO.o[1] + yr, z = TO.o[2] + zr;
     if (y >= g.n[1] || z >= g.n[2]) return f;
     f.ok = true;
     const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
@@ -798,16 +834,20 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
     }
     return f;
   };
-  RowLoad nxt = fetch(warp);
+  int yn = 0, zn = 0;                           // row = zn * tile[1] + yn
+  row_step(warp, g.tile[1], &yn, &zn);
+  const CyzSlots cslots = cyz_slots<DIM>(nxn, lane);
+  RowLoad nxt = fetch(yn, zn);
   for (int row = warp; row < nrows; row += kAdjWarps) {
     const RowLoad cur = nxt;
-    nxt = fetch(row + kAdjWarps);
+    const int yl = yn, zl = zn;
+    row_step(kAdjWarps, g.tile[1], &yn, &zn);
+    nxt = fetch(yn, zn);
     if (!cur.ok) continue;  // warp-uniform
-    const int yl = row % g.tile[1], zl = row / g.tile[1];
     const int y = TO.o[1] + yl, z = TO.o[2] + zl;
     const AxisEntry ye = yt[yl];
     if (!bg) {
-      row_cyz<DIM>(g, CZ, zl, ye, nxn, cyz, lane);
+      row_cyz<DIM>(g, CZ, zl, ye, cslots, cyz);
       __syncwarp();
     }
 
@@ -1002,7 +1042,7 @@ k_accumulate_rows(const Geo g, const AccArgs args) {
 }
 
 template <int DIM, typename T, int NXB>
-__global__ void __launch_bounds__(kAdjWarps * 32)
+__global__ void __launch_bounds__(kAdjWarps * 32, 4)
 k_adjoint_rows(const Geo g, const AdjArgs args) {
   extern __shared__ __align__(16) float smem_adj[];
   adj_rows_body<DIM, T, NXB>(g, args, blockIdx.x, smem_adj);
