@@ -768,34 +768,31 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
     const float* __restrict__ UZg = args.uvxz;
     const float* __restrict__ VZg = UZg + nzp_g;
     const float* __restrict__ XZg = UZg + 2 * nzp_g;
+    // Threads are spread over the (plane, y/x bin) entries and, when there
+    // are fewer entries than threads, over the columns (U, V, X[a]) of an
+    // entry; the index divisions are done once per thread.
     const int nzp = g.tile[2] * p01;
-    const int n = nzp * (2 + nb);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      int zl, hb01, col;  // col: 0 = U, 1 = V, 2 + a = X[a]
-      if (i < 2 * nzp) {
-        col = i / nzp;
-        const int r = i - col * nzp;
-        zl = r / p01;
-        hb01 = r - zl * p01;
-      } else {
-        const int r = i - 2 * nzp;
-        const int zh = r / nb;
-        col = 2 + (r - zh * nb);
-        zl = zh / p01;
-        hb01 = zh - zl * p01;
-        const int a = col - 2;
-        if (!((__ldg(tmask + (a >> 5)) >> (a & 31)) & 1u)) continue;
-      }
-      const int r0 = TO.cb[0] + hb01 % g.hb[0], r1 = TO.cb[1] + hb01 / g.hb[0];
+    const int ncol = 2 + nb;                  // 0 = U, 1 = V, 2 + a = X[a]
+    const int tpe = nzp < (int)blockDim.x ? min((int)blockDim.x / nzp, ncol) : 1;
+    for (int t = threadIdx.x; t < nzp * tpe; t += blockDim.x) {
+      const int sub = t / nzp, e = t - sub * nzp;
+      const int zl = e / p01, hb01 = e - zl * p01;
+      const int l1 = hb01 / g.hb[0], l0 = hb01 - l1 * g.hb[0];
+      const int r0 = TO.cb[0] + l0, r1 = TO.cb[1] + l1;
       const int z = TO.o[2] + zl;
-      float s = 0.f;
-      if (r0 < g.nsb[0] && r1 < g.nsb[1] && z < g.n[2]) {
-        const long long zr = ((long long)z * g.nsb[1] + r1) * g.nsb[0] + r0;
-        s = col == 0 ? __ldg(UZg + zr) : (col == 1 ? __ldg(VZg + zr) : __ldg(XZg + zr * nb + (col - 2)));
+      const bool in = r0 < g.nsb[0] && r1 < g.nsb[1] && z < g.n[2];
+      const long long zr = in ? ((long long)z * g.nsb[1] + r1) * g.nsb[0] + r0 : 0;
+      for (int col = sub; col < ncol; col += tpe) {
+        if (col >= 2) {
+          const int a = col - 2;
+          if (!((__ldg(tmask + (a >> 5)) >> (a & 31)) & 1u)) continue;
+        }
+        float s = 0.f;
+        if (in) s = col == 0 ? __ldg(UZg + zr) : (col == 1 ? __ldg(VZg + zr) : __ldg(XZg + zr * nb + (col - 2)));
+        if (col == 0) UZ[e] = s;
+        else if (col == 1) VZ[e] = s;
+        else XZ[(size_t)e * nb + (col - 2)] = s;
       }
-      if (col == 0) UZ[zl * p01 + hb01] = s;
-      else if (col == 1) VZ[zl * p01 + hb01] = s;
-      else XZ[((size_t)zl * p01 + hb01) * nb + (col - 2)] = s;
     }
   }
   __syncthreads();
