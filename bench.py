@@ -461,7 +461,7 @@ def main():
     e = eng.from_problem(prob, pair.fixed, pair.moving, storage=args.storage)
     stream = e.stream
     c = torch.from_numpy(c_np).to(dev)
-    tile = e.autotune(c, reps=3)
+    tile = e.autotune(c, reps=10)    # more repetitions: a steadier choice between close tiles
     g = torch.empty_like(c)
     D = torch.empty((), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2

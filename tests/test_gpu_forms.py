@@ -269,3 +269,35 @@ def test_async_repeated_calls_replay_one_graph_with_current_inputs(name, kind, p
         torch.cuda.synchronize()
         assert float(D.item()) == ref[k][0], call
         assert torch.allclose(g, ref[k][1], rtol=1e-5, atol=1e-5 * float(ref[k][1].abs().max()))
+
+
+def test_async_call_captured_in_a_caller_graph():
+    """srwcr_value_and_grad_async issued while the caller captures the
+    context's stream into its own CUDA graph (here torch.cuda.graph) becomes
+    part of that graph: replays read the current coefficients and give the
+    synchronous entry point's value and gradient."""
+    prob = synth.problem(3, (70, 45, 23), (6, 5, 4), (3, 2, 2), 24)
+    f, m = synth.small_pair("ct", prob.dims, prob.ffd_spacing, 2.0, 81)
+    s = torch.cuda.Stream()
+    e = engine(prob, f, m, stream=s)
+    cs = [torch.from_numpy(synth.coefficients(prob, 82 + k, 1.5)).cuda() for k in range(2)]
+    ref = [e.value_and_grad(ck) for ck in cs]
+    c = cs[0].clone()
+    g = torch.empty_like(c)
+    D = torch.empty((), dtype=torch.float64, device="cuda")
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(3):                      # warm-up, incl. the library's own graph
+            e.value_and_grad_async(c, D, g)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        e.value_and_grad_async(c, D, g)
+    for call in range(4):
+        k = call % 2
+        c.copy_(cs[k])
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert float(D.item()) == ref[k][0], (call, float(D.item()), ref[k][0])
+        assert torch.allclose(g, ref[k][1], rtol=1e-5, atol=1e-5 * float(ref[k][1].abs().max()))
