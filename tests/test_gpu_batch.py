@@ -127,6 +127,43 @@ def test_batch_with_twelve_x_bins_per_row_equals_single_pairs():
         assert abs(D - st.D) <= D_RTOL * abs(st.D)
 
 
+@pytest.mark.parametrize("spacing", [8, 10, 5])
+def test_batch_of_speckled_pairs_equals_single_pairs(spacing):
+    # Speckled (OCT-shaped) fixed images put about 11 fixed-image bins in a
+    # 32-voxel row: the batched value kernel runs the many-segment transpose
+    # and the batched adjoint the per-lane X route; spacings 8, 10 and 5 with
+    # the bins on the FFD grid give 8- and 12-bin rows.
+    import paper_1804_05061_b300 as eng
+    specs_o = []
+    for i, e in enumerate((40, 64)):
+        prob = synth.problem(3, (e, e - 8, e - 12), (spacing,) * 3, (0, 0, 0), 32)
+        f, m = synth.small_pair("oct", prob.dims, prob.ffd_spacing, 2.0, 90 + i)
+        specs_o.append((prob, f, m))
+    es = [eng.from_problem(p, f, m) for p, f, m in specs_o]
+    assert all(e.levels[0].kernel_path == 1 for e in es)
+    b = eng.Batch(es)
+    cs = [synth.coefficients(p, 95 + i, 1.5) for i, (p, _, _) in enumerate(specs_o)]
+    for i, c in enumerate(cs):
+        b.coef(i).copy_(torch.from_numpy(c))
+    Db = b.value_and_grad(use_graph=True)
+    lanes = b.info().finalize_lanes
+    for i, e in enumerate(es):
+        D, g = e.value_and_grad(torch.from_numpy(cs[i]).cuda())
+        if e.levels[0].finalize_lanes == lanes:
+            assert Db[i] == D
+        else:
+            assert abs(Db[i] - D) <= 1e-12 * abs(D)
+        assert torch.allclose(b.grad(i), g, rtol=1e-5, atol=1e-5 * float(g.abs().max()))
+        prob, f, m = specs_o[i]
+        geo = oracle.Geometry.from_problem(prob)
+        A, M = oracle.prepare(f, m, prob.n_bins)
+        st = oracle.value(geo, A, M, cs[i])
+        go = oracle.gradient(geo, A, M, cs[i], st)
+        assert abs(D - st.D) <= D_RTOL * abs(st.D)
+        gb = b.grad(i).cpu().numpy().astype(np.float64)
+        assert abs(np.linalg.norm(gb) - np.linalg.norm(go)) <= GNORM_RTOL * np.linalg.norm(go)
+
+
 def test_batch_with_pairs_at_different_pyramid_levels(specs):
     # Pairs at level 0 and level 1 of their pyramids in one batch: each pair's
     # batched value equals its single-pair value at its own level, and the
