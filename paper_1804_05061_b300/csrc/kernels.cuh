@@ -26,6 +26,21 @@ __device__ __forceinline__ unsigned long long to_fixed(float v) {
   return __float2ull_rn(v);
 }
 
+// Exact 64-bit add into a shared-memory word with two native 32-bit atomics
+// (a 64-bit shared atomic add is not a single instruction): the low word's
+// wrap-around, seen in the value the first atomic returns, is carried into
+// the high word.  Once all adds are done the word holds the exact sum.
+__device__ __forceinline__ void shared_add_u64(unsigned long long* p, unsigned long long v) {
+  unsigned* w = reinterpret_cast<unsigned*>(p);       // little-endian: low word first
+  const unsigned lo = (unsigned)v, hi = (unsigned)(v >> 32);
+  unsigned carry = 0u;
+  if (lo) {
+    const unsigned old = atomicAdd(w, lo);
+    carry = old + lo < old ? 1u : 0u;
+  }
+  if (hi + carry) atomicAdd(w + 1, hi + carry);
+}
+
 template <int DIM>
 __device__ __forceinline__ void tile_origin(const Geo& g, int b, int o[3]) {
   const int t0 = b % g.ntile[0];
@@ -107,16 +122,16 @@ k_accumulate(const Geo g, const T* __restrict__ A, const T* __restrict__ M,
           unsigned long long* hp = hist + (size_t)(hrow + i) * nb * NCH;
           const float wa0 = w * h0, wa1 = w * h1;
           if (STATIC) {
-            if (wa0 != 0.f) atomicAdd(hp + a0, to_fixed(wa0 * s0));
-            if (wa1 != 0.f) atomicAdd(hp + a0 + 1, to_fixed(wa1 * s0));
+            if (wa0 != 0.f) shared_add_u64(hp + a0, to_fixed(wa0 * s0));
+            if (wa1 != 0.f) shared_add_u64(hp + a0 + 1, to_fixed(wa1 * s0));
           } else {
             if (wa0 != 0.f) {
-              atomicAdd(hp + 2 * a0, to_fixed(wa0 * m1 * s0));
-              atomicAdd(hp + 2 * a0 + 1, to_fixed(wa0 * m2 * s1));
+              shared_add_u64(hp + 2 * a0, to_fixed(wa0 * m1 * s0));
+              shared_add_u64(hp + 2 * a0 + 1, to_fixed(wa0 * m2 * s1));
             }
             if (wa1 != 0.f) {
-              atomicAdd(hp + 2 * a0 + 2, to_fixed(wa1 * m1 * s0));
-              atomicAdd(hp + 2 * a0 + 3, to_fixed(wa1 * m2 * s1));
+              shared_add_u64(hp + 2 * a0 + 2, to_fixed(wa1 * m1 * s0));
+              shared_add_u64(hp + 2 * a0 + 3, to_fixed(wa1 * m2 * s1));
             }
           }
         }

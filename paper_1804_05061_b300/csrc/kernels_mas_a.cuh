@@ -75,14 +75,14 @@ k_accumulate_mas_a(const Geo g, const T* __restrict__ F, const T* __restrict__ M
           unsigned long long* hp = hist + (size_t)(hrow + i) * nb * NCH;
           const float wa0 = w * h0, wa1 = w * h1;
           if (wa0 != 0.f) {
-            atomicAdd(hp + 3 * a0, to_fixed(wa0 * s0));
-            atomicAdd(hp + 3 * a0 + 1, to_fixed(wa0 * m1 * s1));
-            atomicAdd(hp + 3 * a0 + 2, to_fixed(wa0 * m2 * s2));
+            shared_add_u64(hp + 3 * a0, to_fixed(wa0 * s0));
+            shared_add_u64(hp + 3 * a0 + 1, to_fixed(wa0 * m1 * s1));
+            shared_add_u64(hp + 3 * a0 + 2, to_fixed(wa0 * m2 * s2));
           }
           if (wa1 != 0.f) {
-            atomicAdd(hp + 3 * a0 + 3, to_fixed(wa1 * s0));
-            atomicAdd(hp + 3 * a0 + 4, to_fixed(wa1 * m1 * s1));
-            atomicAdd(hp + 3 * a0 + 5, to_fixed(wa1 * m2 * s2));
+            shared_add_u64(hp + 3 * a0 + 3, to_fixed(wa1 * s0));
+            shared_add_u64(hp + 3 * a0 + 4, to_fixed(wa1 * m1 * s1));
+            shared_add_u64(hp + 3 * a0 + 5, to_fixed(wa1 * m2 * s2));
           }
         }
       }
