@@ -37,8 +37,9 @@ CONFIG_NAMES = {"c1": "c1_2d_128", "c2": "c2_ct_256x256x96", "c3": "c3_oct_160",
                 "c5": "c5_ct_512x512x300"}
 METRIC = "SRWCR value+grad Gvoxel/s & HBM-roofline % at 256²×96; batched vs plain pairs/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-KERNEL_SOURCES = ["paper_1804_05061_b300/csrc/kernels.cuh",
-                  "paper_1804_05061_b300/csrc/kernels_rows.cuh",
+# The sources of the row kernels the committed ncu counters describe (the
+# counters are used only while these files hash the same).
+KERNEL_SOURCES = ["paper_1804_05061_b300/csrc/kernels_rows.cuh",
                   "paper_1804_05061_b300/csrc/device_math.cuh"]
 
 
