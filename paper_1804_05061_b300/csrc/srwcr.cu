@@ -83,6 +83,7 @@ struct Level {
   float* V = nullptr;                 // [R]
   float* X = nullptr;                 // [R][nbins] (M as A: mu_r(a) / sigma_r^2)
   float* Y2 = nullptr;                // M as A: [R][nbins] mu_r(a)^2 / sigma_r^2
+  float2* DY = nullptr;               // M as A: [R][nbins] (Y2[a+1] - Y2[a], X[a+1] - X[a])
   double* Dr = nullptr;               // [R] share of D
   double* stats = nullptr;            // [R][4]
   double* D = nullptr;                // device scalar
@@ -382,10 +383,10 @@ srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const flo
   if (ctx->cfg.role == SRWCR_ROLE_M_AS_A) {
     if (ctx->cfg.ndim == 3)
       k_adjoint_mas_a<3, T><<<nblk, kBlock, lv.smem_adj, ctx->stream>>>(
-          lv.g, (const T*)lv.A, (const T*)lv.M, c, lv.X, lv.Y2, gD, invZ, g);
+          lv.g, (const T*)lv.A, (const T*)lv.M, c, lv.DY, gD, invZ, g);
     else
       k_adjoint_mas_a<2, T><<<nblk, kBlock, lv.smem_adj, ctx->stream>>>(
-          lv.g, (const T*)lv.A, (const T*)lv.M, c, lv.X, lv.Y2, gD, invZ, g);
+          lv.g, (const T*)lv.A, (const T*)lv.M, c, lv.DY, gD, invZ, g);
     CKL();
     return SRWCR_OK;
   }
@@ -569,7 +570,7 @@ srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c, bool keep_warp
   ev = prof_begin(ctx);
   if (mas_a)
     k_finalize_mas_a<<<fblk, kBlock, 0, ctx->stream>>>(lv.g, lv.S, 1.0 / lv.s0, 1.0 / lv.s1,
-                                                       1.0 / lv.s2, 1.0 / lv.Z, lv.X, lv.Y2, lv.Dr,
+                                                       1.0 / lv.s2, 1.0 / lv.Z, lv.X, lv.Y2, lv.DY, lv.Dr,
                                                        lv.stats);
   else
     launch_finalize_sparse(ctx, lv);
@@ -720,7 +721,7 @@ srwcr_status finish_sync(srwcr_ctx* ctx, Level& lv, double* D_host) {
 void free_level(Level& lv) {
   void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg, lv.perm,
                   lv.binmask, lv.Wr, lv.nz_ptr, lv.nz_bin, lv.nz_inv_p, lv.bg, lv.uvxz,
-                  lv.ubins, lv.Y2};
+                  lv.ubins, lv.Y2, lv.DY};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   lv = Level();
@@ -904,6 +905,7 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     CK(cudaMalloc((void**)&lv.V, sizeof(float) * g.R));
     CK(cudaMalloc((void**)&lv.X, sizeof(float) * g.R * g.nbins));
     if (nch == 3) CK(cudaMalloc((void**)&lv.Y2, sizeof(float) * g.R * g.nbins));
+    if (nch == 3) CK(cudaMalloc((void**)&lv.DY, sizeof(float2) * g.R * g.nbins));
     CK(cudaMalloc((void**)&lv.Dr, sizeof(double) * g.R));
     CK(cudaMalloc((void**)&lv.stats, sizeof(double) * g.R * 4));
     CK(cudaMalloc((void**)&lv.D, sizeof(double)));
