@@ -187,6 +187,20 @@ srwcr_status srwcr_debug_bins(srwcr_ctx* ctx, int level, int32_t* out_dev);
  * the kernels compute it, to out_dev (device float, n_voxels). */
 srwcr_status srwcr_debug_warp(srwcr_ctx* ctx, int level, const float* c_dev, float* out_dev);
 
+/* Debug: the warped moving image and the gradient of its interpolant at the
+ * warped point, as the kernels compute them (Sec. II-F; the gradient is the
+ * dM/dT(x) factor of Eq. 16): out_dev[4*i + 0..3] = (B, dM/dy_x, dM/dy_y,
+ * dM/dy_z) for voxel i (y_z = 0 in 2-D).  out_dev: device float array of
+ * 4*n_voxels, 16-byte aligned.  Synchronises. */
+srwcr_status srwcr_debug_warp_grad(srwcr_ctx* ctx, int level, const float* c_dev, float* out_dev);
+
+/* The normalised images of pyramid level `level` as the kernels read them
+ * (Sec. II: [0, L_eps]; coarser levels are 2^d box averages with floor sizes,
+ * the multi-resolution scheme of Sec. II-F), converted to float32.
+ * fixed_dev, moving_dev: device float arrays of n_voxels (either may be
+ * NULL).  Synchronises. */
+srwcr_status srwcr_level_images(srwcr_ctx* ctx, int level, float* fixed_dev, float* moving_dev);
+
 /* Benchmark hooks.  With profiling enabled the library brackets each of its
  * kernels with CUDA events on the context's stream.  srwcr_profile_read
  * synchronises the stream and reports, per kernel kind (0 = fused warp and
@@ -225,10 +239,15 @@ srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c_dev, int r
  *   stream         cudaStream_t (NULL = legacy default)
  * Work is queued on `stream`; the call does not synchronise.  Scratch is a
  * file-scope device array of 16 MiB that every device that loads the library
- * holds until exit; problems needing more (about 28 bytes per spatial bin
- * and intensity bin) are rejected with SRWCR_EINVAL.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) and
- * caches it, so make that first call before any stream capture.  Every call
+ * holds until exit.  A problem needs 28 bytes per (spatial bin, intensity
+ * bin) pair plus 48 bytes per spatial bin, each of 8 blocks rounded up to 256
+ * bytes: up to about 590 k pairs (the 512x512x300 workload with 3971 spatial
+ * bins and 128 intensity bins needs 14.4 MB); larger problems are rejected
+ * with SRWCR_EINVAL, the message stating the bytes needed.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it, so make that first call before any stream capture.  The
+ * cache assumes one primary context per device for the life of the process:
+ * do not call this entry point on a device after cudaDeviceReset.  Every call
  * shares the array and re-zeroes the parts it accumulates into: calls that
  * overlap on the GPU (other streams, other host threads) race.  The
  * normalising factor Z is the voxel count (weights sum to one per voxel),
@@ -287,6 +306,32 @@ srwcr_status srwcr_bending_energy(srwcr_ctx* ctx, int level, const float* c_dev,
  * n_levels <= the context's pyramid_levels.  report may be NULL. */
 srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n_levels,
                             const srwcr_lbfgs_opts* opts, srwcr_report* report);
+
+/* Coefficients of pyramid level `level` (>= 1) refined to level - 1, the
+ * coarse-to-fine transfer of srwcr_register (Sec. II-F: the control grids of
+ * the levels are concatenated): dyadic subdivision of the uniform cubic
+ * B-spline (fine node 2i-1 takes (c[i-1] + 6 c[i] + c[i+1]) / 8, fine node
+ * 2i takes (c[i] + c[i+1]) / 2, coarse indices clamped to the grid), values
+ * doubled because displacements are in voxels of their level.  Where no
+ * index is clamped, the fine displacement at fine voxel 2x equals twice the
+ * coarse displacement at coarse voxel x.
+ *   c_coarse_dev  device, n_params of `level`
+ *   c_fine_dev    device, n_params of level - 1 (overwritten)
+ * Queued on the context's stream.  Errors: SRWCR_EINVAL, SRWCR_ECUDA. */
+srwcr_status srwcr_refine(srwcr_ctx* ctx, int level, const float* c_coarse_dev, float* c_fine_dev);
+
+/* One L-BFGS search direction d = -H g (Sec. II-F) from the two-loop
+ * recursion srwcr_register runs (Nocedal & Wright, Alg. 7.4: H0 = (s.y /
+ * y.y) I from the newest pair, rho_i = 1 / s_i.y_i, FP32 vectors with FP64
+ * inner products on the device), for an explicit history.
+ *   n             vector length
+ *   hist_len      number of (s, y) pairs, 0..16 (0 gives d = -g)
+ *   S_dev, Y_dev  device float [hist_len][n], oldest pair first; each
+ *                 s_i.y_i must be > 0 (else SRWCR_EINVAL)
+ *   g_dev         device float [n]; d_dev device float [n] (overwritten)
+ * Runs on the context's stream with scratch of its own; synchronises. */
+srwcr_status srwcr_lbfgs_direction(srwcr_ctx* ctx, int64_t n, int hist_len, const float* S_dev,
+                                   const float* Y_dev, const float* g_dev, float* d_dev);
 
 /* ------------------------------------------------------------------------
  * Rigid model: the pre-alignment the paper runs with the same measure before

@@ -47,6 +47,26 @@ class LbfgsResult:
     history: List[Tuple[int, float, float, float, int]] = field(default_factory=list)
 
 
+def two_loop(g: np.ndarray, S: List[np.ndarray], Y: List[np.ndarray]) -> np.ndarray:
+    """d = -H g by the two-loop recursion over the pairs (S, Y), oldest
+    first: the first loop runs newest to oldest with rho_i = 1 / y_i's_i, the
+    initial matrix is (s'y / y'y) I of the newest pair, and the second loop
+    runs oldest to newest."""
+    q = np.array(g, dtype=np.float64, copy=True)
+    alphas = []
+    for s, y in zip(reversed(S), reversed(Y)):
+        rho = 1.0 / float(y @ s)
+        a = rho * float(s @ q)
+        alphas.append((a, rho))
+        q -= a * y
+    if S:
+        q *= float(S[-1] @ Y[-1]) / float(Y[-1] @ Y[-1])
+    for (s, y), (a, rho) in zip(zip(S, Y), reversed(alphas)):
+        b = rho * float(y @ q)
+        q += s * (a - b)
+    return -q
+
+
 def minimise(fg: Callable[[np.ndarray], Tuple[float, np.ndarray]], x0: np.ndarray,
              opts: LbfgsOptions = LbfgsOptions()) -> LbfgsResult:
     """Minimise f with gradient from ``fg(x) -> (f, g)`` (all float64)."""
@@ -67,20 +87,7 @@ def minimise(fg: Callable[[np.ndarray], Tuple[float, np.ndarray]], x0: np.ndarra
             status = "zero_gradient"
             it -= 1
             break
-        # Two-loop recursion: d = -H g.
-        q = g.copy()
-        alphas = []
-        for s, y in zip(reversed(S), reversed(Y)):
-            rho = 1.0 / float(y @ s)
-            a = rho * float(s @ q)
-            alphas.append((a, rho))
-            q -= a * y
-        if S:
-            q *= float(S[-1] @ Y[-1]) / float(Y[-1] @ Y[-1])
-        for (s, y), (a, rho) in zip(zip(S, Y), reversed(alphas)):
-            b = rho * float(y @ q)
-            q += s * (a - b)
-        d = -q
+        d = two_loop(g, S, Y)
         gd = float(g @ d)
         if not gd < 0.0:
             S.clear(); Y.clear()

@@ -36,7 +36,9 @@ EXPORTS = ("srwcr_create", "srwcr_destroy", "srwcr_last_error", "srwcr_level_inf
            "srwcr_batch_create", "srwcr_batch_create_levels", "srwcr_batch_destroy", "srwcr_batch_info",
            "srwcr_batch_layout", "srwcr_batch_buffers", "srwcr_batch_value_and_grad",
            "srwcr_batch_sync", "srwcr_batch_register", "srwcr_bending_energy",
-           "srwcr_rigid_value_and_grad", "srwcr_rigid_to_ffd", "srwcr_rigid_register")
+           "srwcr_rigid_value_and_grad", "srwcr_rigid_to_ffd", "srwcr_rigid_register",
+           "srwcr_debug_warp_grad", "srwcr_level_images", "srwcr_refine",
+           "srwcr_lbfgs_direction")
 
 
 class SrwcrError(RuntimeError):
@@ -116,6 +118,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "srwcr_region_stats": (st, [vp, ctypes.c_int, vp, i64p]),
         "srwcr_debug_bins": (st, [vp, ctypes.c_int, vp]),
         "srwcr_debug_warp": (st, [vp, ctypes.c_int, vp, vp]),
+        "srwcr_debug_warp_grad": (st, [vp, ctypes.c_int, vp, vp]),
+        "srwcr_level_images": (st, [vp, ctypes.c_int, vp, vp]),
+        "srwcr_refine": (st, [vp, ctypes.c_int, vp, vp]),
+        "srwcr_lbfgs_direction": (st, [vp, ctypes.c_int64, ctypes.c_int, vp, vp, vp, vp]),
         "srwcr_lbfgs_default_opts": (None, [ctypes.POINTER(LbfgsOpts)]),
         "srwcr_set_profiling": (st, [vp, ctypes.c_int]),
         "srwcr_profile_read": (st, [vp, vp, vp, i64p, ctypes.c_int]),
@@ -329,6 +335,47 @@ class SRWCR:
                                 device=self.device)
         _check(load().srwcr_debug_warp(self._h, level, _ptr(c), _ptr(out)))
         return out
+
+    def debug_warp_grad(self, c, level: int = 0):
+        """(n_voxels, 4) float32: B and the interpolant's gradient at T(x)."""
+        c = self._c(c, level)
+        out = self._torch.empty((self.levels[level].n_voxels, 4), dtype=self._torch.float32,
+                                device=self.device)
+        _check(load().srwcr_debug_warp_grad(self._h, level, _ptr(c), _ptr(out)))
+        return out
+
+    def level_images(self, level: int = 0):
+        """The level's normalised fixed and moving images as float32 tensors
+        shaped like the inputs at that level."""
+        d = self.levels[level].dims
+        shape = (d[1], d[0]) if self.ndim == 2 else (d[2], d[1], d[0])
+        A = self._torch.empty(shape, dtype=self._torch.float32, device=self.device)
+        M = self._torch.empty_like(A)
+        _check(load().srwcr_level_images(self._h, level, _ptr(A), _ptr(M)))
+        return A, M
+
+    def refine(self, c_coarse, level: int):
+        """Coefficients of `level` refined to level - 1 (dyadic subdivision,
+        values doubled)."""
+        c_coarse = self._c(c_coarse, level)
+        out = self.zeros(level - 1)
+        _check(load().srwcr_refine(self._h, level, _ptr(c_coarse), _ptr(out)))
+        self._torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return out
+
+    def lbfgs_direction(self, g, S=None, Y=None):
+        """d = -H g from the library's two-loop recursion; S, Y: (k, n)
+        float32 CUDA tensors of (s, y) pairs, oldest first."""
+        t = self._torch
+        g = g.contiguous().view(-1)
+        k = 0 if S is None else int(S.shape[0])
+        d = t.empty_like(g)
+        S = S.contiguous() if k else None
+        Y = Y.contiguous() if k else None
+        t.cuda.current_stream(self.device).synchronize()
+        _check(load().srwcr_lbfgs_direction(self._h, g.numel(), k, _ptr(S) if k else None,
+                                            _ptr(Y) if k else None, _ptr(g), _ptr(d)))
+        return d
 
     # -- benchmark hooks ---------------------------------------------------
     def set_profiling(self, on: bool = True):

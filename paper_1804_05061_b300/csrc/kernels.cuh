@@ -563,9 +563,11 @@ __global__ void k_debug_bins(const Geo g, const T* __restrict__ A, int* __restri
   }
 }
 
+// B(x) = M(T(x)) per voxel; with out4 != NULL, (B, dM/dy_x, dM/dy_y, dM/dy_z)
+// per voxel instead.
 template <int DIM, typename T>
 __global__ void k_debug_warp(const Geo g, const T* __restrict__ M, const float* __restrict__ c,
-                             float* __restrict__ out) {
+                             float* __restrict__ out, float4* __restrict__ out4) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.nvox;
        i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % g.n[0]), y = (int)((i / g.n[0]) % g.n[1]),
@@ -573,8 +575,18 @@ __global__ void k_debug_warp(const Geo g, const T* __restrict__ M, const float* 
     float u[3], bw[3][4], gm[3];
     int fc[3];
     ffd_displacement<DIM>(g, c, x, y, z, u, fc, bw);
-    out[i] = sample_moving<DIM, T>(g, M, (float)x + u[0], (float)y + u[1], (float)z + u[2], gm);
+    const float B = sample_moving<DIM, T>(g, M, (float)x + u[0], (float)y + u[1], (float)z + u[2], gm);
+    if (out4) out4[i] = make_float4(B, gm[0], gm[1], gm[2]);
+    else out[i] = B;
   }
+}
+
+// Storage-type image to float32.
+template <typename T>
+__global__ void k_to_float(const T* __restrict__ in, long long n, float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = ldval(in + i);
 }
 
 }  // namespace srwcr

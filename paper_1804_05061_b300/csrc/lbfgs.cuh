@@ -211,6 +211,49 @@ srwcr_status scal(srwcr_ctx* ctx, LbfgsWork& w, float a, const float* x, float* 
   return SRWCR_OK;
 }
 
+// w.d = -H w.g by the two-loop recursion (Nocedal & Wright, Alg. 7.4), all
+// on the device: the hist_len newest (s, y) pairs sit in ring slots of w.S /
+// w.Y (m slots, the newest at head - 1), rho[slot] = 1 / s.y, and the
+// initial matrix is H0 = (s.y / y.y) I from the newest pair.  Queued.
+srwcr_status two_loop(srwcr_ctx* ctx, LbfgsWork& w, int m, int hist_len, int head,
+                      const double* rho) {
+  const long long n = w.n;
+  CK(cudaMemcpyAsync(w.d, w.g, sizeof(float) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  for (int t = 0; t < hist_len; ++t) {
+    const int slot = (head - 1 - t + m) % m;
+    RET_IF(dot_sc(ctx, w, w.S + slot * n, w.d, kScSQ + slot));
+    k_axpby_sc<<<kDotBlocks, 256, 0, ctx->stream>>>(0, rho[slot], kScSQ + slot, kScAlpha + slot,
+                                                     w.sc, w.Y + slot * n, 1.f, w.d, n);
+    CKL();
+  }
+  if (hist_len > 0) {
+    const int newest = (head - 1 + m) % m;
+    RET_IF(dot_sc(ctx, w, w.S + newest * n, w.Y + newest * n, kScSYN));
+    RET_IF(dot_sc(ctx, w, w.Y + newest * n, w.Y + newest * n, kScYY));
+    k_scal_sc<<<kDotBlocks, 256, 0, ctx->stream>>>(w.sc, kScSYN, kScYY, w.d, w.d, n);
+    CKL();
+  }
+  for (int t = hist_len - 1; t >= 0; --t) {
+    const int slot = (head - 1 - t + m) % m;
+    RET_IF(dot_sc(ctx, w, w.Y + slot * n, w.d, kScYQ + slot));
+    k_axpby_sc<<<kDotBlocks, 256, 0, ctx->stream>>>(1, rho[slot], kScYQ + slot, kScAlpha + slot,
+                                                     w.sc, w.S + slot * n, 1.f, w.d, n);
+    CKL();
+  }
+  return scal(ctx, w, -1.f, w.d, w.d);
+}
+
+// Coarse level `level` coefficients cc -> the next finer level's cf by dyadic
+// cubic B-spline subdivision, values doubled.  Queued.
+srwcr_status refine_queue(srwcr_ctx* ctx, int level, const float* cc, float* cf) {
+  const Geo& gc = ctx->lev[level].g;
+  const Geo& gf = ctx->lev[level - 1].g;
+  k_subdivide<<<256, 256, 0, ctx->stream>>>(cc, ctx->cfg.ndim, gc.nf[0], gc.nf[1], gc.nf[2], cf,
+                                            gf.nf[0], gf.nf[1], gf.nf[2]);
+  CKL();
+  return SRWCR_OK;
+}
+
 // Cost of Eq. (1) at x: f = D + w_p C_p, g = its gradient; queued, the
 // cost's terms copied to w.host[1], w.host[2] (read after a synchronise with
 // eval_cost).  The rigid model's bending energy is zero (an affine
@@ -254,31 +297,8 @@ srwcr_status lbfgs_level(srwcr_ctx* ctx, int level, LbfgsWork& w, const srwcr_lb
   int it = 0;
   const long long n = w.n;
   for (it = 1; it <= max_iter; ++it) {
-    // d = -H g by the two-loop recursion, all on the device.
     RET_IF(dot_sc(ctx, w, w.g, w.g, kScGG));
-    CK(cudaMemcpyAsync(w.d, w.g, sizeof(float) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-    for (int t = 0; t < hist_len; ++t) {
-      const int slot = (head - 1 - t + o.m) % o.m;
-      RET_IF(dot_sc(ctx, w, w.S + slot * n, w.d, kScSQ + slot));
-      k_axpby_sc<<<kDotBlocks, 256, 0, ctx->stream>>>(0, rho[slot], kScSQ + slot, kScAlpha + slot,
-                                                       w.sc, w.Y + slot * n, 1.f, w.d, n);
-      CKL();
-    }
-    if (hist_len > 0) {
-      const int newest = (head - 1 + o.m) % o.m;
-      RET_IF(dot_sc(ctx, w, w.S + newest * n, w.Y + newest * n, kScSYN));
-      RET_IF(dot_sc(ctx, w, w.Y + newest * n, w.Y + newest * n, kScYY));
-      k_scal_sc<<<kDotBlocks, 256, 0, ctx->stream>>>(w.sc, kScSYN, kScYY, w.d, w.d, n);
-      CKL();
-    }
-    for (int t = hist_len - 1; t >= 0; --t) {
-      const int slot = (head - 1 - t + o.m) % o.m;
-      RET_IF(dot_sc(ctx, w, w.Y + slot * n, w.d, kScYQ + slot));
-      k_axpby_sc<<<kDotBlocks, 256, 0, ctx->stream>>>(1, rho[slot], kScYQ + slot, kScAlpha + slot,
-                                                       w.sc, w.S + slot * n, 1.f, w.d, n);
-      CKL();
-    }
-    RET_IF(scal(ctx, w, -1.f, w.d, w.d));  // d = -H g
+    RET_IF(two_loop(ctx, w, o.m, hist_len, head, rho));  // w.d = -H g
     RET_IF(dot_sc(ctx, w, w.g, w.d, kScGD));
     RET_IF(dot_sc(ctx, w, w.d, w.d, kScDD));
     RET_IF(read_sc(ctx, w, kScGG, 3));
@@ -363,7 +383,6 @@ extern "C" srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n
   const int nd = ctx->cfg.ndim;
   srwcr_status final_status = SRWCR_OK;
   float* prev = nullptr;  // coarse result (device), owned here
-  const Geo* prev_g = nullptr;
   for (int level = n_levels - 1; level >= 0; --level) {
     const Geo& g = ctx->lev[level].g;
     LbfgsWork w;
@@ -375,8 +394,8 @@ extern "C" srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n
     } else if (level == n_levels - 1) {
       cudaMemcpyAsync(w.x, c_dev_inout, sizeof(float) * w.n, cudaMemcpyDeviceToDevice, ctx->stream);
     } else {
-      k_subdivide<<<256, 256, 0, ctx->stream>>>(prev, nd, prev_g->nf[0], prev_g->nf[1],
-                                                prev_g->nf[2], w.x, g.nf[0], g.nf[1], g.nf[2]);
+      st = refine_queue(ctx, level + 1, prev, w.x);
+      if (st != SRWCR_OK) { free_work(w); cudaFree(prev); return st; }
     }
     int iters = 0, evals = 0;
     double f = 0.0;
@@ -404,7 +423,6 @@ extern "C" srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n
         return fail(SRWCR_ENOMEM, "cudaMalloc failed");
       }
       cudaMemcpyAsync(prev, w.x, sizeof(float) * w.n, cudaMemcpyDeviceToDevice, ctx->stream);
-      prev_g = &g;
     } else {
       cudaMemcpyAsync(c_dev_inout, w.x, sizeof(float) * w.n, cudaMemcpyDeviceToDevice, ctx->stream);
     }
@@ -420,4 +438,49 @@ extern "C" srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n
   if (final_status == SRWCR_ENOTCONVERGED)
     return fail(SRWCR_ENOTCONVERGED, "iteration limit reached at the finest level");
   return SRWCR_OK;
+}
+
+extern "C" srwcr_status srwcr_lbfgs_direction(srwcr_ctx* ctx, int64_t n, int hist_len,
+                                              const float* S_dev, const float* Y_dev,
+                                              const float* g_dev, float* d_dev) {
+  if (!ctx) return fail(SRWCR_EINVAL, "null context");
+  if (n < 1 || hist_len < 0 || hist_len > 16) return fail(SRWCR_EINVAL, "bad n or hist_len");
+  if (!g_dev || !d_dev || (hist_len > 0 && (!S_dev || !Y_dev)))
+    return fail(SRWCR_EINVAL, "null device pointer");
+  const int m = hist_len > 0 ? hist_len : 1;
+  LbfgsWork w;
+  srwcr_status st = alloc_work(w, n, m);
+  if (st != SRWCR_OK) { free_work(w); return st; }
+  double rho[16];
+  cudaError_t e = cudaMemcpyAsync(w.g, g_dev, sizeof(float) * n, cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess && hist_len > 0)
+    e = cudaMemcpyAsync(w.S, S_dev, sizeof(float) * n * hist_len, cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess && hist_len > 0)
+    e = cudaMemcpyAsync(w.Y, Y_dev, sizeof(float) * n * hist_len, cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e != cudaSuccess) st = fail(SRWCR_ECUDA, "copy: %s", cudaGetErrorString(e));
+  // rho_i = 1 / s_i.y_i from the same FP64 device dot the driver forms.
+  for (int i = 0; i < hist_len && st == SRWCR_OK; ++i) {
+    st = dot_sc(ctx, w, w.S + i * n, w.Y + i * n, kScSY);
+    if (st == SRWCR_OK) st = read_sc(ctx, w, kScSY, 1);
+    if (st == SRWCR_OK && !(w.hsc[kScSY] > 0.0)) st = fail(SRWCR_EINVAL, "pair %d has s.y <= 0", i);
+    if (st == SRWCR_OK) rho[i] = 1.0 / w.hsc[kScSY];
+  }
+  // Slots 0 .. hist_len-1 hold the pairs oldest first: the newest is at
+  // head - 1 with head = 0 (mod m).
+  if (st == SRWCR_OK) st = two_loop(ctx, w, m, hist_len, 0, rho);
+  if (st == SRWCR_OK) {
+    e = cudaMemcpyAsync(d_dev, w.d, sizeof(float) * n, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = fail(SRWCR_ECUDA, "two-loop: %s", cudaGetErrorString(e));
+  }
+  free_work(w);
+  return st;
+}
+
+extern "C" srwcr_status srwcr_refine(srwcr_ctx* ctx, int level, const float* c_coarse_dev,
+                                     float* c_fine_dev) {
+  RET_IF(check_level(ctx, level));
+  if (level < 1) return fail(SRWCR_EINVAL, "level %d has no finer level", level);
+  if (!c_coarse_dev || !c_fine_dev) return fail(SRWCR_EINVAL, "null device pointer");
+  return refine_queue(ctx, level, c_coarse_dev, c_fine_dev);
 }

@@ -1352,18 +1352,54 @@ srwcr_status srwcr_debug_bins(srwcr_ctx* ctx, int level, int32_t* out_dev) {
   return SRWCR_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+srwcr_status debug_warp(srwcr_ctx* ctx, int level, const float* c_dev, float* out, float4* out4) {
+  Level& lv = ctx->lev[level];
+  if (ctx->cfg.ndim == 3) {
+    if (is_bf16(ctx)) k_debug_warp<3, __nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(lv.g, (const __nv_bfloat16*)lv.M, c_dev, out, out4);
+    else k_debug_warp<3, float><<<1024, 256, 0, ctx->stream>>>(lv.g, (const float*)lv.M, c_dev, out, out4);
+  } else {
+    if (is_bf16(ctx)) k_debug_warp<2, __nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(lv.g, (const __nv_bfloat16*)lv.M, c_dev, out, out4);
+    else k_debug_warp<2, float><<<1024, 256, 0, ctx->stream>>>(lv.g, (const float*)lv.M, c_dev, out, out4);
+  }
+  CKL();
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SRWCR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 srwcr_status srwcr_debug_warp(srwcr_ctx* ctx, int level, const float* c_dev, float* out_dev) {
   RET_IF(check_level(ctx, level));
   if (!c_dev || !out_dev) return fail(SRWCR_EINVAL, "null device pointer");
+  return debug_warp(ctx, level, c_dev, out_dev, nullptr);
+}
+
+srwcr_status srwcr_debug_warp_grad(srwcr_ctx* ctx, int level, const float* c_dev, float* out_dev) {
+  RET_IF(check_level(ctx, level));
+  if (!c_dev || !out_dev) return fail(SRWCR_EINVAL, "null device pointer");
+  if (reinterpret_cast<uintptr_t>(out_dev) % 16) return fail(SRWCR_EINVAL, "out_dev must be 16-byte aligned");
+  return debug_warp(ctx, level, c_dev, nullptr, reinterpret_cast<float4*>(out_dev));
+}
+
+srwcr_status srwcr_level_images(srwcr_ctx* ctx, int level, float* fixed_dev, float* moving_dev) {
+  RET_IF(check_level(ctx, level));
   Level& lv = ctx->lev[level];
-  if (ctx->cfg.ndim == 3) {
-    if (is_bf16(ctx)) k_debug_warp<3, __nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(lv.g, (const __nv_bfloat16*)lv.M, c_dev, out_dev);
-    else k_debug_warp<3, float><<<1024, 256, 0, ctx->stream>>>(lv.g, (const float*)lv.M, c_dev, out_dev);
-  } else {
-    if (is_bf16(ctx)) k_debug_warp<2, __nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(lv.g, (const __nv_bfloat16*)lv.M, c_dev, out_dev);
-    else k_debug_warp<2, float><<<1024, 256, 0, ctx->stream>>>(lv.g, (const float*)lv.M, c_dev, out_dev);
+  float* out[2] = {fixed_dev, moving_dev};
+  const void* in[2] = {lv.A, lv.M};
+  for (int i = 0; i < 2; ++i) {
+    if (!out[i]) continue;
+    if (is_bf16(ctx))
+      k_to_float<__nv_bfloat16><<<1024, 256, 0, ctx->stream>>>((const __nv_bfloat16*)in[i], lv.g.nvox, out[i]);
+    else
+      k_to_float<float><<<1024, 256, 0, ctx->stream>>>((const float*)in[i], lv.g.nvox, out[i]);
+    CKL();
   }
-  CKL();
   CK(cudaStreamSynchronize(ctx->stream));
   return SRWCR_OK;
 }
@@ -1427,7 +1463,11 @@ void srwcr_lbfgs_default_opts(srwcr_lbfgs_opts* o) {
 // kNoAllocScratchBytes, which every device that loads this library keeps
 // until the process exits.  Host code only sees that array's name as a
 // host-side stand-in, never as a device address, so the device address is
-// obtained once per device with cudaGetSymbolAddress and cached.
+// obtained once per device with cudaGetSymbolAddress and cached.  The cache
+// assumes that each device keeps one primary context for the life of the
+// process: after cudaDeviceReset (a new context, the array at a new address)
+// the cached address is stale, so a process that resets a device must not
+// call this entry point on it again.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1462,8 +1502,6 @@ extern "C" srwcr_status srwcr_value_noalloc(const srwcr_config* cfg, const float
   if (cfg->tile[0] < 0 || cfg->tile[1] < 0 || cfg->tile[2] < 0)
     return fail(SRWCR_EINVAL, "negative tile size");
   if (cfg->bins_per_pass < 0) return fail(SRWCR_EINVAL, "negative bins_per_pass");
-  if (cfg->role != SRWCR_ROLE_M_AS_B && cfg->role != SRWCR_ROLE_M_AS_A)
-    return fail(SRWCR_EINVAL, "unknown role");
   cudaStream_t st = (cudaStream_t)stream;
 
   // Device address of the scratch array, looked up once per device.
@@ -1488,10 +1526,12 @@ extern "C" srwcr_status srwcr_value_noalloc(const srwcr_config* cfg, const float
   Geo g;
   const int dims[3] = {cfg->dims[0], cfg->dims[1], cfg->ndim == 3 ? cfg->dims[2] : 1};
   RET_IF(make_geo(*cfg, dims, g));
+  // Scratch layout (28 bytes per spatial bin x intensity bin, 48 per spatial
+  // bin): S holds first the fixed-image statistics (R*nb u64), converted to P
+  // in FP64, and then, cleared again, the two moving-image moments.
   const size_t R = (size_t)g.R, nb = (size_t)g.nbins;
   const size_t offS = 0;
-  const size_t offPf = align256(offS + sizeof(unsigned long long) * R * nb * 2);
-  const size_t offP = align256(offPf + sizeof(unsigned long long) * R * nb);
+  const size_t offP = align256(offS + sizeof(unsigned long long) * R * nb * 2);
   const size_t offX = align256(offP + sizeof(double) * R * nb);
   const size_t offU = align256(offX + sizeof(float) * R * nb);
   const size_t offV = align256(offU + sizeof(float) * R);
@@ -1505,7 +1545,6 @@ extern "C" srwcr_status srwcr_value_noalloc(const srwcr_config* cfg, const float
                 "the allocation-free entry point holds %zu bytes",
                 need, R, nb, kNoAllocScratchBytes);
   unsigned long long* S = reinterpret_cast<unsigned long long*>(scratch + offS);
-  unsigned long long* Pfix = reinterpret_cast<unsigned long long*>(scratch + offPf);
   double* P = reinterpret_cast<double*>(scratch + offP);
   float* X = reinterpret_cast<float*>(scratch + offX);
   float* U = reinterpret_cast<float*>(scratch + offU);
@@ -1517,23 +1556,26 @@ extern "C" srwcr_status srwcr_value_noalloc(const srwcr_config* cfg, const float
   RET_IF(set_smem_limits<float>());
   double sP, s1, s2;
   fixed_scales(g, cfg->ndim, &sP, &s1, &s2);
-  // Everything the kernels accumulate into starts at zero on every call.
-  CK(cudaMemsetAsync(S, 0, sizeof(unsigned long long) * R * nb * 2, st));
-  CK(cudaMemsetAsync(Pfix, 0, sizeof(unsigned long long) * R * nb, st));
   const int nblk = g.ntile[0] * g.ntile[1] * g.ntile[2];
-  if (cfg->ndim == 3) {
+  // Everything the kernels accumulate into starts at zero on every call; the
+  // steps are ordered on `st`, so S can serve both accumulations in turn.
+  CK(cudaMemsetAsync(S, 0, sizeof(unsigned long long) * R * nb, st));
+  if (cfg->ndim == 3)
     k_accumulate<3, float, true><<<nblk, kBlock, acc_smem(g, 1), st>>>(
-        g, fixed_dev, moving_dev, nullptr, Pfix, (float)sP, 0.f);
+        g, fixed_dev, moving_dev, nullptr, S, (float)sP, 0.f);
+  else
+    k_accumulate<2, float, true><<<nblk, kBlock, acc_smem(g, 1), st>>>(
+        g, fixed_dev, moving_dev, nullptr, S, (float)sP, 0.f);
+  CKL();
+  k_fixed_to_double<<<256, 256, 0, st>>>(S, 1.0 / sP, P, (long long)(R * nb));
+  CKL();
+  CK(cudaMemsetAsync(S, 0, sizeof(unsigned long long) * R * nb * 2, st));
+  if (cfg->ndim == 3)
     k_accumulate<3, float, false><<<nblk, kBlock, acc_smem(g, 2), st>>>(
         g, fixed_dev, moving_dev, c_dev, S, (float)s1, (float)s2);
-  } else {
-    k_accumulate<2, float, true><<<nblk, kBlock, acc_smem(g, 1), st>>>(
-        g, fixed_dev, moving_dev, nullptr, Pfix, (float)sP, 0.f);
+  else
     k_accumulate<2, float, false><<<nblk, kBlock, acc_smem(g, 2), st>>>(
         g, fixed_dev, moving_dev, c_dev, S, (float)s1, (float)s2);
-  }
-  CKL();
-  k_fixed_to_double<<<256, 256, 0, st>>>(Pfix, 1.0 / sP, P, (long long)(R * nb));
   CKL();
   // Z = N: the spatial weights and Parzen weights each sum to one per voxel.
   const double invZ = 1.0 / (double)g.nvox;
