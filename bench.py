@@ -137,20 +137,35 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_cpu_baseline(pair, c):
-    """FP64 oracle value+gradient on the host cores: one full evaluation of
-    the same workload (single thread)."""
+def host_info():
+    """Host cores and CPU model (the CPU baseline runs here)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def oracle_full_eval(pair, c, storage="f32"):
+    """FP64 oracle value+gradient of the whole workload at c on one host
+    core: seconds, D, gradient, and the degenerate regions (count, summed
+    p(r))."""
     import oracle
     prob = pair.prob
     geo = oracle.Geometry.from_problem(prob)
-    A, M = oracle.prepare(pair.fixed, pair.moving, prob.n_bins, "f32")
+    A, M = oracle.prepare(pair.fixed, pair.moving, prob.n_bins, storage)
     t = time.perf_counter()
     st = oracle.value(geo, A, M, c)
-    oracle.gradient(geo, A, M, c, st)
+    g = oracle.gradient(geo, A, M, c, st)
     dt = time.perf_counter() - t
-    return {"value": prob.n_voxels / dt / 1e9, "unit": "Gvoxel/s", "cores": 1,
-            "kind": "oracle", "sample": f"one full value+gradient of {prob.dims} "
-            f"({prob.n_voxels} voxels), {dt:.1f} s"}
+    deg = st.valid == 0
+    return {"seconds": dt, "D": float(st.D), "g": np.asarray(g, np.float64).ravel(),
+            "n_degenerate": int(st.n_degenerate), "degenerate_p_mass": float(st.pr[deg].sum())}
 
 
 def slab(pair, nz):
@@ -164,8 +179,58 @@ def slab(pair, nz):
                           np.ascontiguousarray(pair.moving[:nz]))
 
 
-def run_reference(args, pair, c_full):
+def _oracle_slab_job(job):
+    """One oracle value+gradient of a slab sample (worker process)."""
+    fixed, moving, dims, spacing, sbins, nbins, storage, seed = job
     import oracle
+    prob = synth.problem(3, dims, spacing, sbins, nbins)
+    c = synth.coefficients(prob, seed, 2.0)
+    geo = oracle.Geometry.from_problem(prob)
+    A, M = oracle.prepare(fixed, moving, nbins, storage)
+    t = time.perf_counter()
+    st = oracle.value(geo, A, M, c)
+    oracle.gradient(geo, A, M, c, st)
+    return time.perf_counter() - t
+
+
+class OraclePool:
+    """All host cores: one spawned process per core, each evaluating the
+    same bounded slab sample with the unchanged single-threaded oracle."""
+
+    def __init__(self, sample, storage, procs=None):
+        import multiprocessing as mp
+        import oracle
+        oracle.build()
+        self.procs = procs or os.cpu_count() or 1
+        prob = sample.prob
+        self.job = (sample.fixed, sample.moving, tuple(prob.dims), tuple(prob.ffd_spacing),
+                    tuple(prob.sbin_intervals), prob.n_bins, storage, 2001)
+        self.voxels = prob.n_voxels
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+
+    def step(self):
+        """Wall seconds of one round: every process evaluates the sample once."""
+        t = time.perf_counter()
+        self.pool.map(_oracle_slab_job, [self.job] * self.procs, chunksize=1)
+        return time.perf_counter() - t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def accuracy(D, g, D_ref, g_ref):
+    """Relative errors of a GPU result against the FP64 oracle's."""
+    g = np.asarray(g, np.float64).ravel()
+    gn, gn_ref = float(np.linalg.norm(g)), float(np.linalg.norm(g_ref))
+    return {"D_rel": abs(D - D_ref) / abs(D_ref), "gnorm_rel": abs(gn - gn_ref) / gn_ref,
+            "g_max_elem_rel": float(np.abs(g - g_ref).max() / np.abs(g_ref).max()),
+            "D": D, "D_oracle": D_ref}
+
+
+def run_reference(args, pair, c_full):
+    """The oracle on every host core: each step is one round in which every
+    process evaluates value+gradient of the same 256x256x8 slab sample."""
     ws, rank, _ = dist_env()
     if ws > 1:
         import torch.distributed as dist
@@ -175,18 +240,13 @@ def run_reference(args, pair, c_full):
             return
     sample = slab(pair, 8)
     prob = sample.prob
-    c = synth.coefficients(prob, 2001, 2.0)
-    geo = oracle.Geometry.from_problem(prob)
-    A, M = oracle.prepare(sample.fixed, sample.moving, prob.n_bins, args.storage)
+    pool = OraclePool(sample, args.storage)
     for _ in range(args.warmup):
-        st = oracle.value(geo, A, M, c)
-        oracle.gradient(geo, A, M, c, st)
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        st = oracle.value(geo, A, M, c)
-        oracle.gradient(geo, A, M, c, st)
-    dt = time.perf_counter() - t
-    v = prob.n_voxels * args.steps / dt / 1e9
+        pool.step()
+    dt = sum(pool.step() for _ in range(args.steps))
+    pool.close()
+    v = pool.procs * prob.n_voxels * args.steps / dt / 1e9
+    host = host_info()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gvoxel/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -195,9 +255,10 @@ def run_reference(args, pair, c_full):
                        f"{pair.prob.dims[2]}, {pair.prob.n_bins} bins); reference steps run on "
                        f"a {prob.dims[0]}x{prob.dims[1]}x{prob.dims[2]} slab",
                        "storage": args.storage},
-            "cpu_baseline": {"value": v, "unit": "Gvoxel/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{prob.dims} slab of the workload, {args.steps} "
-                             "value+gradient evaluations"},
+            "cpu_baseline": {"value": v, "unit": "Gvoxel/s", "cores": pool.procs, "kind": "oracle",
+                             "host": host,
+                             "sample": f"{pool.procs} processes (one per host core), each one "
+                             f"value+gradient of the {prob.dims} slab per step, {args.steps} steps"},
             "e2e": {"value": v, "unit": "Gvoxel/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -256,6 +317,26 @@ def bench_batch(args, eng, torch, dist, ws):
     t_graph = timed(lambda: b.value_and_grad_async(use_graph=True), b.stream)
     D_batch = b.values()
     launches = b.info().launches_per_eval
+    # Error of every pair's batched result against the FP64 oracle values
+    # stored for these pairs and coefficients (tests/golden, written from the
+    # oracle alone); the worst pair is reported.
+    worst = None
+    gold_path = os.path.join(ROOT, "tests", "golden", "full_size_oracle.json")
+    if os.path.exists(gold_path):
+        gold = json.load(open(gold_path))["cases"]
+        errs = []
+        for i in range(n):
+            ref = gold.get(f"c4_pair{i:02d}")
+            if ref is None or ref.get("coef_seed") != 7000 + i or list(specs[i].prob.dims) != ref["dims"]:
+                continue
+            gi = b.grad(i).detach().cpu().numpy().ravel().astype(np.float64)
+            errs.append({"pair": i, "D_rel": abs(D_batch[i] - ref["D"]) / abs(ref["D"]),
+                         "gnorm_rel": abs(float(np.linalg.norm(gi)) - ref["gnorm"]) / ref["gnorm"]})
+        if errs:
+            worst = {"pairs_checked": len(errs),
+                     "worst_D_rel": max(errs, key=lambda r: r["D_rel"]),
+                     "worst_gnorm_rel": max(errs, key=lambda r: r["gnorm_rel"]),
+                     "reference": "FP64 oracle on the BF16-rounded inputs (stored)"}
 
     # L-BFGS: per-pair host-driven driver vs batched, graph-replayed rounds.
     o = eng.SRWCR.default_opts()
@@ -300,6 +381,7 @@ def bench_batch(args, eng, torch, dist, ws):
         "launches_per_eval_batched": launches,
         "launches_per_eval_plain": 6 * n,
         "max_abs_D_diff_batched_vs_plain": float(np.abs(D_batch - D_plain).max()),
+        "accuracy_vs_oracle": worst,
         "tiles": sorted(set(tuple(t) for t in tiles)),
         "steps": steps,
         "lbfgs": {"iterations_per_pair": args.batch_lbfgs_iters,
@@ -342,16 +424,17 @@ def bench_registration(eng, torch, pair):
 
 
 def bench_accuracy(eng, torch):
-    """Synthetic-grid accuracy run (Sec. III-A): a 128^3 binary grid O and a
-    warped copy W(x) = O(x + v(x)) under a smooth bias field, v a cubic
+    """Synthetic-grid accuracy run (Sec. III-A, Table II): a 128^3 binary grid O
+    and a warped copy W(x) = O(x + v(x)) under a smooth bias field, v a cubic
     B-spline field with control displacements uniform in [-15, 15] voxels
     (spacing 16).  3-level pyramid, FFD spacing 5, spatial bins on the FFD
-    grid, 32 bins, default L-BFGS options.  Two of the paper's combinations
-    (Table II; its means over ten cases, its own warp spacing and bias field):
-    M as B with O as the moving image (recovered displacement = v; paper
-    4.44 -> 1.00 voxels) and M as A with W as the moving image (recovered
-    displacement = the inverse of v; paper 1.70).  RMSE over the whole
-    volume."""
+    grid, 32 bins, default L-BFGS options with the coarsest level started
+    off the lattice (start_jitter 0.5 voxel: the identity samples the binary
+    moving image at the lattice, where every voxel sits at a kink of the
+    Parzen window).  The four combinations of Table II (paper: its means over
+    ten cases, its own warp spacing and bias field), plus the paper's best
+    one started at the identity.  RMSE over the whole volume; the recovered
+    displacement is v when O moves and the inverse of v when W moves."""
     import numpy as np
     g = synth.grid_pair(seed=0)
     n = g.original.shape[0]
@@ -359,15 +442,22 @@ def bench_accuracy(eng, torch):
     v = synth.displacement_field(g.original.shape, g.true_spacing, g.true_coef)
     w = synth.inverse_displacement(v)
     rms = lambda a: float(np.sqrt(np.mean(np.sum(a ** 2, axis=0))))
-    out = {"workload": "128^3 binary grid vs. its B-spline-warped, bias-field copy (seed 0)"}
-    for key, role, fixed, moving, truth, paper in (
-            ("m_as_b_o_as_moving", "mas_b", g.warped, g.original, v, 1.00),
-            ("m_as_a_w_as_moving", "mas_a", g.original, g.warped, w, 1.70)):
+    out = {"workload": "128^3 binary grid vs. its B-spline-warped, bias-field copy (seed 0)",
+           "start_jitter_voxels": 0.5}
+    for key, role, fixed, moving, truth, paper, jitter in (
+            ("m_as_b_w_as_moving", "mas_b", g.original, g.warped, w, 1.89, 0.5),
+            ("m_as_b_o_as_moving", "mas_b", g.warped, g.original, v, 1.00, 0.5),
+            ("m_as_a_w_as_moving", "mas_a", g.original, g.warped, w, 1.70, 0.5),
+            ("m_as_a_o_as_moving", "mas_a", g.warped, g.original, v, 0.78, 0.5),
+            ("m_as_a_o_as_moving_identity_start", "mas_a", g.warped, g.original, v, 0.78, 0.0)):
         e = eng.from_problem(prob, fixed, moving, role=role, pyramid_levels=3)
         c = e.zeros()
+        o = e.default_opts()
+        o.start_jitter = jitter
+        o.seed = 1
         torch.cuda.synchronize()
         t = time.perf_counter()
-        rep = e.register(c, 3, e.default_opts())
+        rep = e.register(c, 3, o)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t
         u = synth.displacement_field(g.original.shape, (5, 5, 5), c.cpu().numpy())
@@ -376,6 +466,7 @@ def bench_accuracy(eng, torch):
                     "iterations": [int(rep.iterations[l]) for l in (2, 1, 0)],
                     "kernel_path": [int(e.levels[l].kernel_path) for l in (2, 1, 0)],
                     "wall_s": wall}
+        e.close()
     return out
 
 
@@ -422,6 +513,110 @@ def bench_rigid(eng, torch, prob):
             "register_wall_s": wall}
 
 
+def row_skips(e, c, level=0):
+    """Shares of the row kernels' 32-voxel x-rows that skip work at c: the
+    value pass skips rows whose warped intensities are all 0 (no moment to
+    add), the adjoint rows where the moving image's interpolated gradient is
+    0 at every voxel (computed from srwcr_debug_warp_grad)."""
+    import torch
+    lv = e.levels[level]
+    nx, ny, nz = lv.dims
+    out = e.debug_warp_grad(c, level).view(nz, ny, nx, 4)
+    nxb = (nx + 31) // 32
+    pad = torch.zeros((nz, ny, nxb * 32, 4), dtype=out.dtype, device=out.device)
+    pad[:, :, :nx] = out
+    rows = pad.view(nz, ny, nxb, 32, 4)
+    val = (rows[..., 0] == 0).all(-1)
+    adj = (rows[..., 1:] == 0).all(-1).all(-1)
+    return {"value": float(val.float().mean()), "adjoint": float(adj.float().mean()),
+            "rows": int(val.numel())}
+
+
+def degenerate(e, level=0):
+    """Regions the value leaves out (sigma_r^2 at the degenerate threshold or
+    p(r) = 0): their count and summed share p(r)."""
+    st, nd = e.region_stats(level)
+    deg = st[:, 1] == 0.0
+    return {"regions": int(nd), "of": int(st.shape[0]), "p_mass": float(st[deg, 0].sum())}
+
+
+def time_steps(e, c, D, g, steps, warmup, flush, dist, dev, clocks=None):
+    """CUDA-event time of `steps` value+gradient calls through
+    srwcr_value_and_grad_async with the same buffers (the library replays its
+    graph), the L2 flushed before each outside the events; then the
+    per-kernel split from a separate pass with the library's events on.
+    Returns (slowest rank's seconds, per-kernel ms, launches, wall, clocks)."""
+    import torch
+    stream = e.stream
+    for _ in range(warmup):
+        e.value_and_grad_async(c, D, g)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e.profile_read(reset=True)
+    if clocks is not None:
+        clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()     # no-op unless a profiler waits for it
+    t0 = time.perf_counter()
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        e.value_and_grad_async(c, D, g)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop() if clocks is not None else None
+    _, _, launches = e.profile_read(reset=True)
+    step_ms = sum(s_.elapsed_time(t_) for s_, t_ in zip(starts, ends))
+    t_dev = max_over_ranks(step_ms / 1e3, dist, dev)
+    e.set_profiling(True)
+    for _ in range(min(steps, 20)):
+        flush.zero_()
+        e.value_and_grad_async(c, D, g)
+    torch.cuda.synchronize()
+    e.set_profiling(False)
+    kms, kcnt, _ = e.profile_read(reset=True)
+    names = ["accumulate", "finalize", "adjoint"]
+    avg = {names[i]: (kms[i] / kcnt[i] if kcnt[i] else 0.0) for i in range(3)}
+    return t_dev, avg, launches, wall, clk
+
+
+def bench_pair_section(eng, torch, pair, storage, c_np, args, flush, dist, dev, ws, oracle_ref):
+    """Device-timed value+gradient of another workload or storage type, with
+    its error against the FP64 oracle (oracle_ref: a finished
+    oracle_full_eval of the same pair, storage and coefficients)."""
+    prob = pair.prob
+    e = eng.from_problem(prob, pair.fixed, pair.moving, storage=storage)
+    c = torch.from_numpy(c_np).to(dev)
+    tile = e.autotune(c, reps=5)
+    g = torch.empty_like(c)
+    D = torch.empty((), dtype=torch.float64, device=dev)
+    steps = max(3, min(args.steps, 20))
+    t_dev, avg, _, _, _ = time_steps(e, c, D, g, steps, args.warmup, flush, dist, dev)
+    out = {"workload": f"{pair.name}: {prob.dims[0]}x{prob.dims[1]}x{prob.dims[2]}, FFD spacing "
+                       f"{prob.ffd_spacing[0]}, spatial bins "
+                       f"{list(prob.sbin_intervals[:prob.ndim]) if any(prob.sbin_intervals) else 'on the FFD grid'}, "
+                       f"{prob.n_bins} intensity bins",
+           "storage": storage, "tile": list(tile),
+           "value": whole_job_rate(ws, prob.n_voxels * steps, t_dev) / 1e9, "unit": "Gvoxel/s",
+           "ms_per_step": t_dev * 1e3 / steps,
+           "kernel_ms": {k: round(v, 4) for k, v in avg.items()},
+           "rows_skipped": row_skips(e, c), "degenerate": degenerate(e)}
+    if oracle_ref is not None:
+        Dv, gv = e.value_and_grad(c)
+        out["accuracy_vs_oracle"] = accuracy(Dv, gv.cpu().numpy(), oracle_ref["D"], oracle_ref["g"])
+        out["degenerate"]["oracle_regions"] = oracle_ref["n_degenerate"]
+        out["degenerate"]["oracle_p_mass"] = oracle_ref["degenerate_p_mass"]
+    e.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -439,6 +634,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the synthetic-grid accuracy run")
     ap.add_argument("--no-rigid", action="store_true", help="skip the rigid pre-alignment run")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other-storage and dense-content (OCT) lines")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -449,10 +646,30 @@ def main():
         run_reference(args, pair, c_np)
         return
 
+    ws, rank, local = dist_env()
+    # The FP64 oracle evaluations (the CPU baseline and the error of each GPU
+    # result) run in spawned worker processes beside the GPU sections; the
+    # pool is started before the first CUDA call.
+    cpu_jobs = {}
+    executor = None
+    other = "bf16" if args.storage == "f32" else "f32"
+    dense = synth.make_pair(CONFIG_NAMES["c3"]) if args.config != "c3" else None
+    c_dense = synth.coefficients(dense.prob, 2003, 2.0) if dense is not None else None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        import oracle
+        oracle.build()
+        executor = cf.ProcessPoolExecutor(max_workers=3, mp_context=mp.get_context("spawn"))
+        cpu_jobs["main"] = executor.submit(oracle_full_eval, pair, c_np, args.storage)
+        if not args.no_extra:
+            cpu_jobs["other"] = executor.submit(oracle_full_eval, pair, c_np, other)
+            if dense is not None:
+                cpu_jobs["dense"] = executor.submit(oracle_full_eval, dense, c_dense, "f32")
+
     import torch
     import paper_1804_05061_b300 as eng
 
-    ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     dist = None
     if ws > 1:
@@ -467,32 +684,13 @@ def main():
     D = torch.empty((), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    for _ in range(args.warmup):
-        e.value_and_grad_async(c, D, g)
-    torch.cuda.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = Clocks(local)
-    e.profile_read(reset=True)
-    clocks.start()
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    torch.cuda.profiler.start()     # no-op unless a profiler waits for it
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()
-        starts[k].record(stream)
-        e.value_and_grad_async(c, D, g)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    torch.cuda.profiler.stop()
-    if dist is not None:
-        dist.barrier()
-    wall = time.perf_counter() - t0
-    clk = clocks.stop()
-    _, _, launches = e.profile_read(reset=True)
+    t_dev, avg, launches, wall, clk = time_steps(e, c, D, g, args.steps, args.warmup, flush,
+                                                 dist, dev, clocks)
+    step_ms = t_dev * 1e3
+    value = whole_job_rate(ws, prob.n_voxels * args.steps, t_dev) / 1e9
+    D_gpu = float(D.item())
+    g_gpu = g.cpu().numpy().ravel()
     # The same steps with the L2 warm (no flush between them).
     warm0 = torch.cuda.Event(enable_timing=True)
     warm1 = torch.cuda.Event(enable_timing=True)
@@ -505,19 +703,8 @@ def main():
     l2_warm = {"value": whole_job_rate(ws, prob.n_voxels * args.steps, t_warm) / 1e9,
                "unit": "Gvoxel/s", "ms_per_step": t_warm * 1e3 / args.steps}
     e.profile_read(reset=True)
-    # Per-kernel split (CUDA events around each kernel on the context's
-    # stream) in a separate pass: with the events on, the library launches
-    # the kernels one by one instead of replaying its graph.
-    e.set_profiling(True)
-    for _ in range(min(args.steps, 20)):
-        flush.zero_()
-        e.value_and_grad_async(c, D, g)
-    torch.cuda.synchronize()
-    e.set_profiling(False)
-    kms, kcnt, _ = e.profile_read(reset=True)
-    step_ms = sum(s.elapsed_time(t) for s, t in zip(starts, ends))
-    t_dev = max_over_ranks(step_ms / 1e3, dist, dev)
-    value = whole_job_rate(ws, prob.n_voxels * args.steps, t_dev) / 1e9
+    skips = row_skips(e, c)
+    deg = degenerate(e)
 
     # End to end through the host-buffer entry point: H2D c from pinned host
     # memory, compute, D2H g and D into pinned host memory.
@@ -538,8 +725,6 @@ def main():
     # Roofline of the dominant kernel (algorithmic bytes / CUDA-event time).
     esz = 2 if args.storage == "bf16" else 4
     lv = e.levels[0]
-    names = ["accumulate", "finalize", "adjoint"]
-    avg = {names[i]: (kms[i] / kcnt[i] if kcnt[i] else 0.0) for i in range(3)}
     bytes_alg = {
         "accumulate": 2 * esz * lv.n_voxels + 4 * lv.n_params + 16 * lv.n_regions * prob.n_bins,
         "adjoint": 2 * esz * lv.n_voxels + 4 * lv.n_params * 2
@@ -579,7 +764,24 @@ def main():
                 "dram_frac": (traffic / (avg[dom] / 1e3) / 1e9 / peak
                               if traffic and avg[dom] > 0 else None),
                 "kernel_ms": {k: round(v, 4) for k, v in avg.items()},
-                "algorithmic_bytes_per_voxel_step": 4 * esz, "issue": issue}
+                "algorithmic_bytes_per_voxel_step": 4 * esz, "issue": issue,
+                "rows_skipped_frac": {"value": skips["value"], "adjoint": skips["adjoint"]}}
+    e.close()
+    del e
+
+    def oracle_result(key):
+        if key not in cpu_jobs:
+            return None
+        return cpu_jobs[key].result()
+
+    extra = {}
+    if not args.no_extra:
+        extra[f"{other}_storage"] = bench_pair_section(
+            eng, torch, pair, other, c_np, args, flush, dist, dev, ws, oracle_result("other"))
+        if dense is not None:
+            extra["dense_oct"] = bench_pair_section(
+                eng, torch, dense, "f32", c_dense, args, flush, dist, dev, ws,
+                oracle_result("dense"))
 
     reg = None
     if not args.no_registration and args.config == "c2":
@@ -595,8 +797,28 @@ def main():
         batch = bench_batch(args, eng, torch, dist, ws)
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = oracle_cpu_baseline(pair, c_np)
+    acc_main = None
+    main_ref = oracle_result("main")
+    if main_ref is not None:
+        acc_main = accuracy(D_gpu, g_gpu, main_ref["D"], main_ref["g"])
+        deg["oracle_regions"] = main_ref["n_degenerate"]
+        deg["oracle_p_mass"] = main_ref["degenerate_p_mass"]
+        cpu = {"value": prob.n_voxels / main_ref["seconds"] / 1e9, "unit": "Gvoxel/s", "cores": 1,
+               "kind": "oracle", "host": host_info(),
+               "sample": f"one full value+gradient of {prob.dims} ({prob.n_voxels} voxels) on "
+                         f"one core, {main_ref['seconds']:.1f} s"}
+        executor.shutdown()
+        # Every host core: one process per core on the 256x256x8 slab.
+        sample = slab(pair, 8)
+        pool = OraclePool(sample, args.storage)
+        pool.step()
+        rounds = 2
+        dt = sum(pool.step() for _ in range(rounds))
+        pool.close()
+        cpu["all_cores"] = {"value": pool.procs * sample.prob.n_voxels * rounds / dt / 1e9,
+                            "unit": "Gvoxel/s", "cores": pool.procs,
+                            "sample": f"{pool.procs} processes, each one value+gradient of the "
+                                      f"{sample.prob.dims} slab per round, {rounds} rounds"}
 
     line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
@@ -607,15 +829,16 @@ def main():
                        f"{prob.sbin_intervals[:prob.ndim]} intervals, {prob.n_bins} intensity "
                        "bins, M as B, finest level",
                        "storage": args.storage, "tile": list(tile),
-                       "kernel_path": "row-parallel" if e.levels[0].kernel_path else "general",
+                       "kernel_path": "row-parallel" if lv.kernel_path else "general",
                        "n_voxels": prob.n_voxels,
                        "n_params": prob.n_params, "parallelism": f"replicas x{ws}",
                        "l2": "flushed between steps (256 MB write, outside the timed events)",
                        "wall_ms_per_step_incl_flush": wall / args.steps * 1e3},
+            "accuracy_vs_oracle": acc_main, "degenerate": deg,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "l2_warm": l2_warm,
             "clocks": clk,
-            "gpu_launches": launches, "batched": batch, "registration": reg, "accuracy": acc,
-            "rigid": rig}
+            "gpu_launches": launches, **extra, "batched": batch, "registration": reg,
+            "accuracy": acc, "rigid": rig}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

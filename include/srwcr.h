@@ -89,6 +89,12 @@ typedef struct {
                              0 = chosen per level from the number of
                              fixed-image bins each spatial bin holds */
   int spatial;            /* SRWCR_SPATIAL_BSPLINE (0) | SRWCR_SPATIAL_BOXCAR */
+  int keep_warp;          /* value+gradient on the row-parallel kernels: the
+                             value pass stores the warped intensity and the
+                             moving-image gradient (16 bytes per voxel) for
+                             the adjoint (1), or the adjoint recomputes them
+                             (-1); 0 = stored for levels of at most 2^25
+                             voxels, recomputed for larger ones */
 } srwcr_config;
 
 /* Geometry of one pyramid level. */
@@ -271,6 +277,18 @@ typedef struct {
                              the bending energy (srwcr_bending_energy); 0 =
                              D alone (default).  The paper uses 0.1 for
                              mono-modal and 30 for multi-modal pairs. */
+  double start_jitter;    /* > 0: srwcr_register adds to the start of its first
+                             (coarsest) level coefficients drawn uniformly
+                             from [-start_jitter, start_jitter] voxels
+                             (SplitMix64 of seed and the coefficient index).
+                             The identity map samples the moving image on
+                             the lattice, where a two-valued image puts
+                             every voxel at a kink of the Parzen window
+                             (Eq. 5) and the gradient of Eqs. 19/21 is
+                             one-sided; a start off the lattice avoids
+                             it.  0 = no jitter (default).  The rigid and
+                             batched drivers start where they are given. */
+  unsigned long long seed;
 } srwcr_lbfgs_opts;
 
 typedef struct {

@@ -53,7 +53,8 @@ class Config(ctypes.Structure):
                 ("n_intensity_bins", ctypes.c_int), ("storage", ctypes.c_int),
                 ("pyramid_levels", ctypes.c_int), ("tile", ctypes.c_int * 3),
                 ("bins_per_pass", ctypes.c_int), ("role", ctypes.c_int),
-                ("finalize_lanes", ctypes.c_int), ("spatial", ctypes.c_int)]
+                ("finalize_lanes", ctypes.c_int), ("spatial", ctypes.c_int),
+                ("keep_warp", ctypes.c_int)]
 
 
 class LevelDesc(ctypes.Structure):
@@ -68,7 +69,8 @@ class LbfgsOpts(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("max_iter", ctypes.c_int * 4),
                 ("stable_window", ctypes.c_int), ("stable_rtol", ctypes.c_double),
                 ("max_ls", ctypes.c_int), ("c1", ctypes.c_double), ("c2", ctypes.c_double),
-                ("penalty_weight", ctypes.c_double)]
+                ("penalty_weight", ctypes.c_double), ("start_jitter", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
 
 
 class Report(ctypes.Structure):
@@ -189,7 +191,8 @@ class SRWCR:
                  sbin_intervals: Sequence[int] = (0, 0, 0), n_bins: int = 32,
                  storage: str = "f32", pyramid_levels: int = 1,
                  tile: Optional[Sequence[int]] = None, stream=None, bins_per_pass: int = 0,
-                 role: str = "mas_b", finalize_lanes: int = 0, spatial: str = "bspline"):
+                 role: str = "mas_b", finalize_lanes: int = 0, spatial: str = "bspline",
+                 keep_warp: int = 0):
         import torch
         self._torch = torch
         lib = load()
@@ -212,6 +215,7 @@ class SRWCR:
         cfg.role = ROLE[role]
         cfg.finalize_lanes = int(finalize_lanes)
         cfg.spatial = SPATIAL[spatial]
+        cfg.keep_warp = int(keep_warp)
         self.cfg = cfg
         self.ndim = ndim
         self.storage = storage

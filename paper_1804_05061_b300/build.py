@@ -13,7 +13,8 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsrwcr.so")
 SOURCES = ["srwcr.cu"]
-DEPS = SOURCES + ["kernels.cuh", "kernels_rows.cuh", "kernels_batch.cuh", "kernels_mas_a.cuh",
+DEPS = SOURCES + ["kernels.cuh", "kernels_rows.cuh", "kernels_rows_mas_a.cuh", "kernels_batch.cuh",
+                  "kernels_mas_a.cuh",
                   "kernels_rigid.cuh", "device_math.cuh", "lbfgs.cuh", "batch.cuh", "bending.cuh",
                   "rigid.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

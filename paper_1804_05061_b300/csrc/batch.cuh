@@ -513,6 +513,8 @@ static srwcr_status batch_create_impl(srwcr_batch* b, srwcr_ctx* const* ctxs, co
     if (level < 0 || level >= c->nlev) return fail(SRWCR_EINVAL, "pair %d has no level %d", i, level);
     if (!c->lev[level].rows)
       return fail(SRWCR_EINVAL, "pair %d: level %d is not on the row-parallel kernels", i, level);
+    if (c->cfg.role != SRWCR_ROLE_M_AS_B)
+      return fail(SRWCR_EINVAL, "pair %d: the batched form takes the moving image as B", i);
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c) return fail(SRWCR_EINVAL, "pair %d repeats pair %d", i, j);
   }

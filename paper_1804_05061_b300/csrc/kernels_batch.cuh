@@ -88,6 +88,10 @@ struct AdjTable {
   AdjItem it[kBatchChunk];
 };
 
+// Both tables travel as one kernel parameter each (at most 32764 bytes).
+static_assert(sizeof(AccTable) <= 32764, "AccTable exceeds the kernel parameter limit");
+static_assert(sizeof(AdjTable) <= 32764, "AdjTable exceeds the kernel parameter limit");
+
 template <int DIM, typename T, int NXB>
 __global__ void __launch_bounds__(kAccWarps * 32, 2)
 k_accumulate_rows_batch(const __grid_constant__ AccTable tab, const int* __restrict__ active) {

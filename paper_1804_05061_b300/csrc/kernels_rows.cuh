@@ -16,7 +16,7 @@
 //     evaluations), so voxels sharing a0 are adjacent.  A segmented warp
 //     reduction forms, per segment, the FP32 sums over <= 32 voxels of
 //     beta_x(i) h(a - A) {m1, m2}; each sum is then spread over the
-//     row-constant y/z weights (one lane per y/z bin) and added in 64-bit
+//     row-constant y/z weights (one lane per y/z bin) and added in 48-bit
 //     fixed point to the CTA histogram, whose per-bin stride is odd so those
 //     adds hit distinct banks.  Only short FP32 sums are ever formed, so the
 //     E[b^2] - mu^2 cancellation of Eq. (10) keeps full accuracy.
@@ -28,7 +28,12 @@
 //
 // Rows in which every warped intensity is exactly 0 (m1 = m2 = 0) add nothing
 // to the statistics, and rows in which the moving-image gradient vanishes at
-// every voxel add nothing to the gradient; both are skipped.
+// every voxel add nothing to the gradient; both are skipped.  A row whose
+// static distance to the nearest nonzero moving-image voxel (L-infinity,
+// voxels) exceeds its largest displacement bound by more than the trilinear
+// stencil's reach reads only zeros: the value pass skips its warp, and it
+// records for the adjoint which rows have a nonzero moving-image gradient,
+// so that the adjoint visits only those.
 #pragma once
 
 #include "device_math.cuh"
@@ -222,19 +227,35 @@ __device__ __forceinline__ CyzSlots cyz_slots(int nxn, int lane) {
   return s;
 }
 
+// Returns the largest magnitude among the lane's entries: every voxel of the
+// row is displaced by at most the warp-wide maximum along each axis (the
+// x-weights of Eq. 17 are non-negative and sum to one).
 template <int DIM>
-__device__ __forceinline__ void row_cyz(const Geo& g, const float* CZ, int zl, const AxisEntry& ye,
-                                        const CyzSlots& cs, float* cyz) {
+__device__ __forceinline__ float row_cyz(const Geo& g, const float* CZ, int zl, const AxisEntry& ye,
+                                         const CyzSlots& cs, float* cyz) {
   const int per_z = DIM * g.hf[1] * g.hf[0];
+  float mx = 0.f;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     if (j >= cs.n) break;
     const int k = cs.k[j], l = cs.l[j];
     const float* base = CZ + zl * per_z + (k * g.hf[1] + ye.frel) * g.hf[0] + l;
-    cyz[k * kMaxRowNodes + l] = ye.bf[0] * base[0] + ye.bf[1] * base[g.hf[0]] +
-                                ye.bf[2] * base[2 * g.hf[0]] + ye.bf[3] * base[3 * g.hf[0]];
+    const float v = ye.bf[0] * base[0] + ye.bf[1] * base[g.hf[0]] + ye.bf[2] * base[2 * g.hf[0]] +
+                    ye.bf[3] * base[3 * g.hf[0]];
+    cyz[k * kMaxRowNodes + l] = v;
+    mx = fmaxf(mx, fabsf(v));
   }
+  return mx;
 }
+
+// Reach of a row's trilinear stencil beyond its largest displacement bound
+// U: reads lie within ceil(|u|) + 1 voxels of the voxel (L-infinity), and |u|
+// exceeds U only by FP32 rounding, so a row with static distance d > U + 3 to
+// the nearest nonzero moving-image voxel reads only zeros.
+constexpr float kDeadRowMargin = 3.f;
+// Cap of the static row distance (rows farther from any nonzero voxel store
+// the cap, a lower bound).
+constexpr int kRowDistCap = 64;
 
 // A warp's next row (y, z within the tile), advanced by the number of warps
 // without a division.
@@ -273,6 +294,8 @@ struct AccArgs {
   const unsigned* binmask;       // per-tile fixed-image bins present
   unsigned long long* acc;       // [R][nbins][2] fixed-point sums
   float4* bg;                    // per voxel (B, dM/dy) for the adjoint, or NULL
+  const unsigned char* rowdist;  // per row: distance to the nearest nonzero M voxel, or NULL
+  unsigned char* rowlive;        // per row: nonzero dM/dy somewhere (written with bg), or NULL
   float s1, s2;                  // fixed-point scales of the two moments
 };
 
@@ -287,6 +310,7 @@ struct AdjArgs {
   const float* X;
   const float* gscale;           // device scalar or NULL (1)
   const float4* bg;              // (B, dM/dy) stored by the value pass, or NULL: recompute
+  const unsigned char* rowlive;  // rows with nonzero dM/dy (value pass, with bg), or NULL: all
   const float* uvxz;             // U, V, X contracted over z per image plane (k_zcontract)
   float invZ;
   float* grad;
@@ -305,7 +329,7 @@ __host__ __device__ inline int hist_yz_stride(const Geo& g) {
 __host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int nxb) {
   const size_t npy = (size_t)g.tile[2] * g.hb[1];          // (z-plane, y-bin) rows
   const size_t nv = (size_t)(nxb == 12 ? 4 : nxb) * 4;   // segment values per chunk
-  size_t b = 3 * npy * hist_yz_stride(g) * sizeof(unsigned);  // plane words (3 per entry)
+  size_t b = 2 * npy * hist_yz_stride(g) * sizeof(unsigned);  // plane words (2 per entry)
   b += sizeof(float) * kAccWarps * 32 * nv;                 // segS
   b += sizeof(int) * kAccWarps * 32;                        // segA
   b += sizeof(int) * kAccWarps * 64 * 2;                    // bin list
@@ -332,7 +356,10 @@ __device__ __forceinline__ int seg_at(int l, int q) {
   return NV == 32 ? l * 32 + (((q >> 2) ^ (l & 7)) << 2) + (q & 3) : l * 16 + q;
 }
 
-template <int DIM, typename T, int NXB>
+// SKIP: the level keeps the per-row records (static distance to nonzero M,
+// nonzero-gradient flag); without them every row is processed and the
+// per-row tests are compiled out.
+template <int DIM, typename T, int NXB, bool SKIP = true>
 __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args, int tile,
                                               unsigned long long* smem_u64) {
   const T* __restrict__ A = static_cast<const T*>(args.A);
@@ -341,6 +368,8 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   const unsigned char* __restrict__ perm = args.perm;
   const unsigned* __restrict__ binmask = args.binmask;
   unsigned long long* __restrict__ acc = args.acc;
+  const unsigned char* __restrict__ rowdist = SKIP ? args.rowdist : nullptr;
+  unsigned char* __restrict__ rowlive = SKIP ? args.rowlive : nullptr;
   const float s1 = args.s1, s2 = args.s2;
   // x-bins per chunk of a row (a row with 12 takes three chunks of 4) and
   // segment-buffer values per chunk: v[4b + 2 slot + ch].
@@ -353,20 +382,19 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   // Per-plane fixed-point accumulators H[z-plane][y bin][bin][moment][x-bin]:
   // a row's sums are weighted by its y B-spline only (4 updates per item);
   // the z weights are applied once per plane at the flush.  Each entry is
-  // held as three 32-bit words (bits 0-19, 20-39 and 40-63 of each update;
-  // an FP32 update has 24 significant bits, so it touches at most two) and
-  // receives at most one update per row of its plane (<= 256) of value
-  // < 2^56, so no word overflows.  The flush recombines a plane's words
-  // exactly, combines the planes of one z cell in FP32 in plane order with
-  // their z weights and adds the results to the global accumulators.
+  // held as two 32-bit words (bits 0-23 and 24-47 of each update, which is
+  // < 2^48) and receives at most one update per row of its plane (<= 256),
+  // so neither word overflows (256 * (2^24 - 1) < 2^32).  The flush
+  // recombines a plane's words exactly, combines the planes of one z cell in
+  // FP32 in plane order with their z weights and adds the results to the
+  // global accumulators.
   // The bin axis holds g.cbin of the tile's compacted bins; a tile that uses
   // more takes several passes over its rows, each folding one chunk of bins
   // and skipping rows with no voxel in that chunk.
   const int S = hist_yz_stride(g);
   const int NPY = g.tile[2] * g.hb[1];
   unsigned* hlo = reinterpret_cast<unsigned*>(smem_u64);
-  unsigned* hmid = hlo + (size_t)NPY * S;
-  unsigned* hhi = hmid + (size_t)NPY * S;
+  unsigned* hhi = hlo + (size_t)NPY * S;
   float* segS = reinterpret_cast<float*>(hhi + (size_t)NPY * S);
   int* segA = reinterpret_cast<int*>(segS + kAccWarps * 32 * NV);
   int* binl = segA + kAccWarps * 32;          // [warp][64][2]: a, (row | slot<<8 | merge<<9 | prev row<<10)
@@ -386,7 +414,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   // Prologue in two phases: the y/z tables, then (independent of each other)
   // the z-contraction of the coefficients (global loads issued first), the
   // bin maps, the x table and the clearing of the first pass's accumulators
-  // (16-byte stores; 3 * NPY * S is a multiple of 4 words).
+  // (16-byte stores; 2 * NPY * S is a multiple of 4 words).
   build_axis_tables<DIM>(g, TO, yt, zt);
   __syncthreads();
   build_cz<DIM>(g, TO, c, zt, CZ);
@@ -406,7 +434,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
     }
   }
   build_xtab<NXB>(g, TO, xt);
-  const int hwords4 = (3 * NPY * S) >> 2;
+  const int hwords4 = (2 * NPY * S) >> 2;
   uint4* h4 = reinterpret_cast<uint4*>(hlo);
   for (int i = threadIdx.x; i < hwords4; i += blockDim.x) h4[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
@@ -425,32 +453,36 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
     // A row's permutation and fixed-image values are loaded in lane order
     // (independent of each other) one row ahead; the value lane l needs,
     // that of voxel o + perm[l], comes by shuffle.
-    auto fetch = [&](int yr, int zr, int* pp, float* aa) {
+    auto fetch = [&](int yr, int zr, int* pp, float* aa, int* dd) {
       *pp = 0;
       *aa = 0.f;
+      *dd = 0;
       if (zr >= g.tile[2]) return false;          // past the tile's last row
       const int y = TO.o[1] + yr, z = TO.o[2] + zr;
       if (y >= g.n[1] || z >= g.n[2]) return false;
       const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
       *pp = perm[rowid * 32 + lane];
+      if (SKIP && rowdist) *dd = rowdist[rowid];
       const int xn = TO.o[0] + lane;
       if (xn < g.n[0]) *aa = ldval(A + ((long long)z * g.n[1] + y) * g.n[0] + xn);
       return true;
     };
-    int p_next;
+    int p_next, d_next;
     float a_next;
     int yn = 0, zn = 0;                         // row = zn * tile[1] + yn
     row_step(warp, g.tile[1], &yn, &zn);
-    bool ok_next = fetch(yn, zn, &p_next, &a_next);
+    bool ok_next = fetch(yn, zn, &p_next, &a_next, &d_next);
     for (int row = warp; row < nrows; row += kAccWarps) {
       const int p = p_next;
       const float a_lane = a_next;
+      const int rdist = d_next;
       const bool ok = ok_next;
       const int yl = yn, zl = zn;
       row_step(kAccWarps, g.tile[1], &yn, &zn);
-      ok_next = fetch(yn, zn, &p_next, &a_next);
+      ok_next = fetch(yn, zn, &p_next, &a_next, &d_next);
       if (!ok) continue;  // warp-uniform
       const int y = TO.o[1] + yl, z = TO.o[2] + zl;
+      const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
 
       const int x = TO.o[0] + p;
       const bool act = x < g.n[0];
@@ -466,9 +498,19 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
         if (!__any_sync(0xffffffffu, in)) continue;
       }
       const AxisEntry ye = yt[yl];
-      row_cyz<DIM>(g, CZ, zl, ye, cslots, cyz);
+      const float umax = row_cyz<DIM>(g, CZ, zl, ye, cslots, cyz);
+      if (SKIP && rowdist) {
+        // Row provably reading only zeros of M: B = 0 and dM/dy = 0 at every
+        // voxel, nothing to add (warp-uniform; NaN coefficients never pass).
+        const float U = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(umax)));
+        if ((float)rdist > U + kDeadRowMargin) {
+          if (rowlive && lane == 0) rowlive[rowid] = 0;
+          continue;
+        }
+      }
       __syncwarp();
       float m1 = 0.f, m2 = 0.f, h0 = 0.f, h1 = 0.f;
+      bool glive = false;
       if (act) {
         h1 = parzen_upper(fa);
         h0 = 1.f - h1;
@@ -477,11 +519,16 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
         float B = row_warp<DIM, T>(g, M, cyz, xt.frel[p], bx, x, y, z, gm);
         B = fminf(fmaxf(B, 0.f), L);
         if (args.bg) args.bg[idx] = make_float4(B, gm[0], gm[1], gm[2]);
+        if (SKIP) glive = gm[0] != 0.f || gm[1] != 0.f || gm[2] != 0.f;
         float fb;
         const int kb = bin_split(B, nb, &fb);
         const float w1 = parzen_upper(fb), kf = (float)kb;
         m1 = kf + w1;                              // sum_b b   h(b - B)
         m2 = kf * kf + (2.f * kf + 1.f) * w1;      // sum_b b^2 h(b - B)
+      }
+      if (SKIP && rowlive) {
+        const bool any_g = __any_sync(0xffffffffu, glive);
+        if (lane == 0) rowlive[rowid] = any_g ? 1 : 0;
       }
       const bool live = act && (m1 != 0.f || m2 != 0.f);
       if (!__any_sync(0xffffffffu, live)) continue;  // B == 0 on the whole row
@@ -613,16 +660,14 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
           for (int m = 0; m < 4; ++m) {
             const float u = uv * ye.bs[m];
             if (u == 0.f) continue;
-            // Exact split of u into 20-bit fields (power-of-two scalings,
-            // floors and fused subtractions of FP32 values are exact here).
-            const float hf = floorf(u * 0x1p-40f);
-            const float r1 = fmaf(hf, -0x1p40f, u);
-            const float mf = floorf(r1 * 0x1p-20f);
-            const unsigned lo = __float2uint_rn(fmaf(mf, -0x1p20f, r1));
-            const unsigned mid = (unsigned)mf, hi = (unsigned)hf;
+            // Split of u (< 2^48) into 24-bit fields: the power-of-two
+            // scaling, the floor and the fused subtraction are exact; the low
+            // field rounds u's fraction (u < 2^24) to the fixed-point unit.
+            const float hf = floorf(u * 0x1p-24f);
+            const unsigned lo = __float2uint_rn(fmaf(hf, -0x1p24f, u));
+            const unsigned hi = (unsigned)hf;
             const int at = col + m * S;
             if (lo) atomicAdd(hlo + at, lo);
-            if (mid) atomicAdd(hmid + at, mid);
             if (hi) atomicAdd(hhi + at, hi);
           }
         }
@@ -658,8 +703,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
           bool any = false;
           for (int pl = zl; pl < g.tile[2] && zt[pl].srel == cz; ++pl) {
             const int j = (pl * g.hb[1] + l1) * S + col;
-            const unsigned long long h =
-                ((unsigned long long)hhi[j] << 40) + ((unsigned long long)hmid[j] << 20) + hlo[j];
+            const unsigned long long h = ((unsigned long long)hhi[j] << 24) + hlo[j];
             if (!h) continue;
             any = true;
             const float hv = __ull2float_rn(h);
@@ -806,21 +850,51 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
   const int xlast = min(TO.o[0] + 31, g.n[0] - 1);
   const int nxn = xlast / g.fsp[0] - TO.f[0] + 4;
   const int nrows = g.tile[1] * g.tile[2];
-  // A row's loads (lane order, lane l reading voxel o + l, so they do not wait
-  // for the permutation) are issued one row ahead of its processing; the
+  // The warp's rows are row = warp + k * kAdjWarps, k = 0, 1, ...  With the
+  // value pass's record of the rows whose moving-image gradient is nonzero
+  // somewhere (rowlive), only those are visited: 32 candidates' flags are
+  // read at a time and the set ones taken in order.  A row's loads (lane
+  // order, lane l reading voxel o + l, so they do not wait for the
+  // permutation) are issued one live row ahead of its processing; the
   // permuted values are then exchanged by shuffles.
+  const unsigned char* __restrict__ rowlive = args.rowlive;
   struct RowLoad {
     int p;
     float a;
     float4 b;
+    int yl, zl;
     bool ok;
   };
-  auto fetch = [&](int yr, int zr) {
-    RowLoad f{0, 0.f, make_float4(0.f, 0.f, 0.f, 0.f), false};
-    if (zr >= g.tile[2]) return f;              // past the tile's last row
-    const int y = TO.o[1] + yr, z = TO.o[2] + zr;
-    if (y >= g.n[1] || z >= g.n[2]) return f;
+  unsigned cand = 0;       // flags of candidates kb .. kb + 31 not yet taken
+  int kb = -32;
+  int cyl = 0, czl = 0;    // this lane's candidate kb + lane: (y, z) within the tile
+  auto refill = [&]() {
+    kb += 32;
+    const int row = warp + (kb + lane) * kAdjWarps;
+    bool live = false;
+    cyl = 0;
+    czl = 0;
+    if (row < nrows) {
+      czl = row / g.tile[1];
+      cyl = row - czl * g.tile[1];
+      const int y = TO.o[1] + cyl, z = TO.o[2] + czl;
+      live = y < g.n[1] && z < g.n[2];
+      if (live && rowlive) live = rowlive[((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5)] != 0;
+    }
+    cand = __ballot_sync(0xffffffffu, live);
+  };
+  auto fetch_next = [&]() {
+    RowLoad f{0, 0.f, make_float4(0.f, 0.f, 0.f, 0.f), 0, 0, false};
+    while (cand == 0) {
+      if (warp + (kb + 32) * kAdjWarps >= nrows) return f;   // warp-uniform
+      refill();
+    }
+    const int b = __ffs(cand) - 1;
+    cand &= cand - 1;
+    f.yl = __shfl_sync(0xffffffffu, cyl, b);
+    f.zl = __shfl_sync(0xffffffffu, czl, b);
     f.ok = true;
+    const int y = TO.o[1] + f.yl, z = TO.o[2] + f.zl;
     const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
     f.p = perm[rowid * 32 + lane];
     const int xn = TO.o[0] + lane;
@@ -831,16 +905,12 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
     }
     return f;
   };
-  int yn = 0, zn = 0;                           // row = zn * tile[1] + yn
-  row_step(warp, g.tile[1], &yn, &zn);
   const CyzSlots cslots = cyz_slots<DIM>(nxn, lane);
-  RowLoad nxt = fetch(yn, zn);
-  for (int row = warp; row < nrows; row += kAdjWarps) {
+  RowLoad nxt = fetch_next();
+  while (nxt.ok) {
     const RowLoad cur = nxt;
-    const int yl = yn, zl = zn;
-    row_step(kAdjWarps, g.tile[1], &yn, &zn);
-    nxt = fetch(yn, zn);
-    if (!cur.ok) continue;  // warp-uniform
+    const int yl = cur.yl, zl = cur.zl;
+    nxt = fetch_next();
     const int y = TO.o[1] + yl, z = TO.o[2] + zl;
     const AxisEntry ye = yt[yl];
     if (!bg) {
@@ -1031,11 +1101,11 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
 }
 
 // One problem: one CTA per tile.
-template <int DIM, typename T, int NXB>
+template <int DIM, typename T, int NXB, bool SKIP>
 __global__ void __launch_bounds__(kAccWarps * 32, 2)
 k_accumulate_rows(const Geo g, const AccArgs args) {
   extern __shared__ __align__(16) unsigned long long smem_acc[];
-  acc_rows_body<DIM, T, NXB>(g, args, blockIdx.x, smem_acc);
+  acc_rows_body<DIM, T, NXB, SKIP>(g, args, blockIdx.x, smem_acc);
 }
 
 template <int DIM, typename T, int NXB>
@@ -1106,6 +1176,63 @@ k_zcontract(const Geo g, const int* __restrict__ ubins, int nu, const float* __r
   const long long n = zcontract_items(g, nu);
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
     zcontract_item<DIM>(g, i, ubins, nu, U, V, X, out);
+}
+
+// Static L-infinity distance (voxels, capped at kRowDistCap) from each voxel
+// to the nearest voxel where the moving image is nonzero, by separable
+// passes: along x the distance within the x-line, then along y and z
+// d(v) = min over offsets t of max(|t|, d_prev(v + t e_axis)) (the L-infinity
+// distance is the largest per-axis offset, minimised axis by axis).  Capped
+// values are lower bounds of the true distance.
+template <typename T>
+__global__ void k_mdist_x(const Geo g, const T* __restrict__ M, unsigned char* __restrict__ d) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.nvox;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.n[0]);
+    const long long line = i - x;
+    int best = kRowDistCap;
+    for (int t = 0; t < best; ++t) {
+      const bool lo = x - t >= 0 && ldval(M + line + x - t) != 0.f;
+      const bool hi = x + t < g.n[0] && ldval(M + line + x + t) != 0.f;
+      if (lo || hi) { best = t; break; }
+    }
+    d[i] = (unsigned char)best;
+  }
+}
+
+// One separable pass along axis `axis` (1 = y, 2 = z): out(v) = min over t
+// of max(|t|, in(v + t e_axis)), |t| < kRowDistCap.
+__global__ void k_mdist_pass(const Geo g, int axis, const unsigned char* __restrict__ in,
+                             unsigned char* __restrict__ out) {
+  const long long stride = axis == 1 ? g.n[0] : (long long)g.n[0] * g.n[1];
+  const int n = g.n[axis];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.nvox;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)((i / stride) % n);
+    int best = in[i];
+    for (int t = 1; t < best; ++t) {
+      const int lo = c - t >= 0 ? in[i - t * stride] : kRowDistCap;
+      const int hi = c + t < n ? in[i + t * stride] : kRowDistCap;
+      best = min(best, max(t, min(lo, hi)));
+    }
+    out[i] = (unsigned char)best;
+  }
+}
+
+// Per 32-voxel x-row (row id ((z * ny + y) * nxb + x / 32)): the smallest
+// distance over its voxels.
+__global__ void k_row_dist(const Geo g, const unsigned char* __restrict__ d,
+                           unsigned char* __restrict__ rowdist) {
+  const int nxb = (g.n[0] + 31) >> 5;
+  const long long nrows = (long long)nxb * g.n[1] * g.n[2];
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nrows;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int xb = (int)(r % nxb);
+    const long long yz = r / nxb;
+    int best = kRowDistCap;
+    for (int x = xb * 32; x < min(xb * 32 + 32, g.n[0]); ++x) best = min(best, (int)d[yz * g.n[0] + x]);
+    rowdist[r] = (unsigned char)best;
+  }
 }
 
 // Static per-tile mask of the fixed-image bins its voxels touch (a0, a0+1).

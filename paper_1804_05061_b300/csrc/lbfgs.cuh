@@ -100,6 +100,21 @@ __global__ void k_xpay(const float* __restrict__ x, float a, const float* __rest
     z[i] = x[i] + a * y[i];
 }
 
+// x[i] += a uniform draw from [-amp, amp]: SplitMix64 (S. Vigna's published
+// generator: golden-ratio increment, two xor-shift-multiply rounds and a
+// final xor-shift) of seed + (i + 1) steps, its top 24 bits as the fraction.
+__global__ void k_jitter(float* __restrict__ x, long long n, float amp, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const float u = (float)(z >> 40) * 0x1p-24f;    // [0, 1)
+    x[i] += amp * (2.f * u - 1.f);
+  }
+}
+
 // Dyadic refinement of uniform cubic B-spline coefficients (knot doubling):
 // fine node j sits at coarse node position (j+1)/2 (offset indices); odd j
 // take (c[i-1] + 6c[i] + c[i+1])/8 with i = (j+1)/2, even j take
@@ -378,6 +393,7 @@ extern "C" srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n
   if (opts) o = *opts;
   if (o.m < 1 || o.m > 16 || o.max_ls < 1) return fail(SRWCR_EINVAL, "bad L-BFGS options");
   if (!(o.penalty_weight >= 0.0)) return fail(SRWCR_EINVAL, "penalty_weight must be >= 0");
+  if (!(o.start_jitter >= 0.0)) return fail(SRWCR_EINVAL, "start_jitter must be >= 0");
   if (o.penalty_weight > 0.0) RET_IF(ensure_bend(ctx));
   if (report) memset(report, 0, sizeof *report);
   const int nd = ctx->cfg.ndim;
@@ -396,6 +412,14 @@ extern "C" srwcr_status srwcr_register(srwcr_ctx* ctx, float* c_dev_inout, int n
     } else {
       st = refine_queue(ctx, level + 1, prev, w.x);
       if (st != SRWCR_OK) { free_work(w); cudaFree(prev); return st; }
+    }
+    if (level == n_levels - 1 && o.start_jitter > 0.0) {
+      k_jitter<<<256, 256, 0, ctx->stream>>>(w.x, w.n, (float)o.start_jitter, o.seed);
+      cudaError_t je = cudaGetLastError();
+      if (je != cudaSuccess) {
+        free_work(w);
+        return fail(SRWCR_ECUDA, "start jitter: %s", cudaGetErrorString(je));
+      }
     }
     int iters = 0, evals = 0;
     double f = 0.0;

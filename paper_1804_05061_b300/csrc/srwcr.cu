@@ -22,6 +22,7 @@
 #include "kernels.cuh"
 #include "kernels_mas_a.cuh"
 #include "kernels_rows.cuh"
+#include "kernels_rows_mas_a.cuh"
 #include "kernels_rigid.cuh"
 
 using namespace srwcr;
@@ -66,6 +67,9 @@ srwcr_status fail(srwcr_status st, const char* fmt, ...) {
 
 constexpr int kBlock = 256;
 constexpr int kMinBinsPerPass = 8;  // value kernel: fewest compacted bins per pass
+// Levels above this many voxels recompute the warp in the adjoint by default
+// instead of storing 16 bytes per voxel between the two passes.
+constexpr long long kKeepWarpMaxVoxels = 1LL << 25;
 constexpr size_t kSmemBudget = 112 * 1024;  // per CTA, two CTAs per SM
 
 struct Level {
@@ -100,7 +104,10 @@ struct Level {
   unsigned char* perm = nullptr;
   unsigned* binmask = nullptr;        // per tile: fixed-image bins present
   float4* bg = nullptr;               // per voxel (B, dM/dy) of the last kept warp
+  unsigned char* rowdist = nullptr;   // per 32-voxel row: static distance to nonzero M (capped)
+  unsigned char* rowlive = nullptr;   // per row: nonzero dM/dy at the last kept warp
   float* uvxz = nullptr;              // U, V, X contracted over z per image plane
+  float2* dyz = nullptr;              // M as A: table differences contracted over z per plane
   int* ubins = nullptr;               // fixed-image bins present in the image (any tile)
   int nu = 0;
   size_t smem_acc_rows = 0, smem_adj_rows = 0;
@@ -277,11 +284,11 @@ void fixed_scales(const Geo& g, int ndim, double* sP, double* s1, double* s2) {
   *s1 = std::ldexp(1.0, 62 - ceil_log2(box * L));
   *s2 = std::ldexp(1.0, 62 - ceil_log2(box * L * L));
   // The row kernels add sums over at most two 32-voxel row segments (terms
-  // <= L, L^2) into three 32-bit words (bits 0-19, 20-39, 40-63), at most
-  // 256 updates per word per CTA: one update stays below 2^56, so no word
+  // <= L, L^2) into two 32-bit words (bits 0-23, 24-47), at most 256
+  // updates per word per CTA: one update stays below 2^48, so no word
   // overflows.
-  *s1 = std::min(*s1, std::ldexp(1.0, 56 - ceil_log2(64.0 * L)));
-  *s2 = std::min(*s2, std::ldexp(1.0, 56 - ceil_log2(64.0 * L * L)));
+  *s1 = std::min(*s1, std::ldexp(1.0, 48 - ceil_log2(64.0 * L)));
+  *s2 = std::min(*s2, std::ldexp(1.0, 48 - ceil_log2(64.0 * L * L)));
 }
 
 // keep_warp: the value pass stores (B, dM/dy) per voxel for an adjoint at
@@ -290,6 +297,8 @@ AccArgs acc_args(const Level& lv, const float* c, bool keep_warp) {
   AccArgs a;
   a.A = lv.A; a.M = lv.M; a.c = c; a.perm = lv.perm; a.binmask = lv.binmask;
   a.acc = lv.S; a.bg = keep_warp ? lv.bg : nullptr; a.s1 = lv.s1; a.s2 = lv.s2;
+  a.rowdist = lv.rowdist;
+  a.rowlive = keep_warp ? lv.rowlive : nullptr;
   return a;
 }
 
@@ -297,20 +306,29 @@ AdjArgs adj_args(const Level& lv, const float* c, const float* gD, float* g, boo
   AdjArgs a;
   a.A = lv.A; a.M = lv.M; a.c = c; a.perm = lv.perm; a.binmask = lv.binmask;
   a.U = lv.U; a.V = lv.V; a.X = lv.X; a.gscale = gD; a.bg = kept_warp ? lv.bg : nullptr;
+  a.rowlive = kept_warp ? lv.rowlive : nullptr;
   a.uvxz = lv.uvxz;
   a.invZ = (float)(1.0 / lv.Z); a.grad = g;
   return a;
 }
 
+template <int DIM, typename T, bool SKIP>
+void launch_rows_acc_s(srwcr_ctx* ctx, Level& lv, const AccArgs& a, int nblk) {
+  if (lv.nxb_rows == 4)
+    k_accumulate_rows<DIM, T, 4, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
+  else if (lv.nxb_rows == 8)
+    k_accumulate_rows<DIM, T, 8, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
+  else
+    k_accumulate_rows<DIM, T, 12, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
+}
+
+// Levels without the per-row records run the kernel with the per-row tests
+// compiled out.
 template <int DIM, typename T>
 void launch_rows_acc(srwcr_ctx* ctx, Level& lv, const float* c, int nblk, bool keep) {
   const AccArgs a = acc_args(lv, c, keep);
-  if (lv.nxb_rows == 4)
-    k_accumulate_rows<DIM, T, 4><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
-  else if (lv.nxb_rows == 8)
-    k_accumulate_rows<DIM, T, 8><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
-  else
-    k_accumulate_rows<DIM, T, 12><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
+  if (lv.rowdist) launch_rows_acc_s<DIM, T, true>(ctx, lv, a, nblk);
+  else launch_rows_acc_s<DIM, T, false>(ctx, lv, a, nblk);
 }
 
 template <int DIM, typename T>
@@ -325,6 +343,36 @@ void launch_rows_adj(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD,
     k_adjoint_rows<DIM, T, 12><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a);
 }
 
+AccArgsA acc_args_a(const Level& lv, const float* c, bool keep_warp) {
+  AccArgsA a;
+  a.F = lv.A; a.M = lv.M; a.c = c; a.acc = lv.S; a.bg = keep_warp ? lv.bg : nullptr;
+  a.rowdist = lv.rowdist; a.rowlive = keep_warp ? lv.rowlive : nullptr;
+  a.s0 = lv.s0; a.s1 = lv.s1; a.s2 = lv.s2;
+  return a;
+}
+
+template <int DIM, typename T>
+void launch_rows_acc_mas_a(srwcr_ctx* ctx, Level& lv, const float* c, int nblk, bool keep) {
+  const AccArgsA a = acc_args_a(lv, c, keep);
+  const size_t sm = lv.smem_acc_rows;
+  if (lv.nxb_rows == 4) k_accumulate_rows_mas_a<DIM, T, 4><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a);
+  else if (lv.nxb_rows == 8) k_accumulate_rows_mas_a<DIM, T, 8><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a);
+  else k_accumulate_rows_mas_a<DIM, T, 12><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a);
+}
+
+template <int DIM, typename T>
+void launch_rows_adj_mas_a(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g,
+                           int nblk, bool kept) {
+  AdjArgsA a;
+  a.F = lv.A; a.M = lv.M; a.c = c; a.dyz = lv.dyz; a.gscale = gD;
+  a.bg = kept ? lv.bg : nullptr; a.rowlive = kept ? lv.rowlive : nullptr;
+  a.invZ = (float)(1.0 / lv.Z); a.grad = g;
+  const size_t sm = lv.smem_adj_rows;
+  if (lv.nxb_rows == 4) k_adjoint_rows_mas_a<DIM, T, 4><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a);
+  else if (lv.nxb_rows == 8) k_adjoint_rows_mas_a<DIM, T, 8><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a);
+  else k_adjoint_rows_mas_a<DIM, T, 12><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a);
+}
+
 template <typename T>
 srwcr_status launch_accumulate(srwcr_ctx* ctx, Level& lv, const float* c, bool stat, float s0,
                                float s1, bool keep_warp = false) {
@@ -333,8 +381,14 @@ srwcr_status launch_accumulate(srwcr_ctx* ctx, Level& lv, const float* c, bool s
   const T* A = (const T*)lv.A;
   const T* M = (const T*)lv.M;
   if (!stat && lv.rows) {
-    if (ctx->cfg.ndim == 3) launch_rows_acc<3, T>(ctx, lv, c, nblk, keep_warp);
-    else launch_rows_acc<2, T>(ctx, lv, c, nblk, keep_warp);
+    if (ctx->cfg.role == SRWCR_ROLE_M_AS_A) {
+      if (ctx->cfg.ndim == 3) launch_rows_acc_mas_a<3, T>(ctx, lv, c, nblk, keep_warp);
+      else launch_rows_acc_mas_a<2, T>(ctx, lv, c, nblk, keep_warp);
+    } else if (ctx->cfg.ndim == 3) {
+      launch_rows_acc<3, T>(ctx, lv, c, nblk, keep_warp);
+    } else {
+      launch_rows_acc<2, T>(ctx, lv, c, nblk, keep_warp);
+    }
     CKL();
     return SRWCR_OK;
   }
@@ -365,6 +419,19 @@ srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const flo
                             bool kept_warp) {
   const int nblk = lv.g.ntile[0] * lv.g.ntile[1] * lv.g.ntile[2];
   const float invZ = (float)(1.0 / lv.Z);
+  if (lv.rows && ctx->cfg.role == SRWCR_ROLE_M_AS_A) {
+    // Per-plane z-contraction of the table differences, then the adjoint.
+    const long long nz = zcontract_dy_len(lv.g);
+    const int zb = (int)std::min<long long>(148 * 16, (nz + 255) / 256);
+    if (ctx->cfg.ndim == 3) k_zcontract_dy<3><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.DY, lv.dyz);
+    else k_zcontract_dy<2><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.DY, lv.dyz);
+    CKL();
+    ctx->launches += 1;
+    if (ctx->cfg.ndim == 3) launch_rows_adj_mas_a<3, T>(ctx, lv, c, gD, g, nblk, kept_warp);
+    else launch_rows_adj_mas_a<2, T>(ctx, lv, c, gD, g, nblk, kept_warp);
+    CKL();
+    return SRWCR_OK;
+  }
   if (lv.rows) {
     // Per-plane z-contraction of the region tables, then the adjoint.
     const long long nz = zcontract_items(lv.g, lv.nu);
@@ -415,18 +482,36 @@ srwcr_status set_smem_limits() {
   CK(cudaFuncSetAttribute(k_accumulate_mas_a<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint_mas_a<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint_mas_a<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 12, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 12, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 12, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 12, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint_rows<3, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint_rows<2, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<3, T, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows<2, T, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint_rows<3, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint_rows<3, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint_rows<2, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   CK(cudaFuncSetAttribute(k_adjoint_rows<2, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows_mas_a<3, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows_mas_a<3, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows_mas_a<3, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows_mas_a<2, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows_mas_a<2, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_accumulate_rows_mas_a<2, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_mas_a<3, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_mas_a<3, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_mas_a<3, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_mas_a<2, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_mas_a<2, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+  CK(cudaFuncSetAttribute(k_adjoint_rows_mas_a<2, T, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
   return SRWCR_OK;
 }
 
@@ -721,7 +806,7 @@ srwcr_status finish_sync(srwcr_ctx* ctx, Level& lv, double* D_host) {
 void free_level(Level& lv) {
   void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg, lv.perm,
                   lv.binmask, lv.Wr, lv.nz_ptr, lv.nz_bin, lv.nz_inv_p, lv.bg, lv.uvxz,
-                  lv.ubins, lv.Y2, lv.DY};
+                  lv.ubins, lv.Y2, lv.DY, lv.rowdist, lv.rowlive, lv.dyz};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   lv = Level();
@@ -753,12 +838,54 @@ void launch_tile_binmask(srwcr_ctx* ctx, const Geo& g, const void* A, unsigned* 
 // each candidate's per-tile masks are built on the device and the largest
 // per-tile count sizes the histogram.  Levels without such a tile keep the
 // general path.
-// The row-parallel kernels order each row by the static fixed-image bin, so
-// they serve the moving image as B only (either spatial distribution).
-bool rows_allowed(const srwcr_config& cfg) { return cfg.role == SRWCR_ROLE_M_AS_B; }
+// The row-parallel kernels serve both roles (either spatial distribution):
+// with the moving image as B each row is ordered by the static fixed-image
+// bin; with the moving image as A the lanes are grouped by the warped bin at
+// every evaluation and the histogram holds every intensity bin.
+bool rows_allowed(const srwcr_config& cfg) {
+  return cfg.role == SRWCR_ROLE_M_AS_B || cfg.role == SRWCR_ROLE_M_AS_A;
+}
+
+// Moving image as A: the largest listed tile whose histogram (every bin)
+// and tables fit in shared memory, with at most 128 rows per plane (an entry
+// takes up to two updates per row, each < 2^48 in two 24-bit words).
+srwcr_status select_rows_path_mas_a(srwcr_ctx* ctx, Level& lv, const int* force_tile) {
+  const srwcr_config& cfg = ctx->cfg;
+  const int nd = cfg.ndim;
+  static const int cand3[][3] = {{32, 64, 1}, {32, 32, 2}, {32, 16, 4}, {32, 32, 1}, {32, 16, 2},
+                                 {32, 8, 4}, {32, 8, 2}, {32, 4, 2}, {32, 2, 2}, {32, 1, 1}};
+  static const int cand2[][3] = {{32, 64, 1}, {32, 32, 1}, {32, 16, 1}, {32, 8, 1}, {32, 4, 1},
+                                 {32, 1, 1}};
+  std::vector<std::array<int, 3>> cands;
+  if (force_tile) cands.push_back({force_tile[0], force_tile[1], force_tile[2]});
+  else if (cfg.tile[0] > 0) {
+    if (cfg.tile[0] == 32) cands.push_back({32, std::max(1, cfg.tile[1]), std::max(1, cfg.tile[2])});
+  } else if (nd == 3) {
+    for (auto& t : cand3) cands.push_back({t[0], t[1], t[2]});
+  } else {
+    for (auto& t : cand2) cands.push_back({t[0], t[1], t[2]});
+  }
+  for (const auto& t : cands) {
+    Geo g = lv.gv;
+    set_tile(g, nd, t[0], t[1], t[2]);
+    if (!rows_geometry_ok(g) || g.tile[1] > 128) continue;
+    const int nxb = g.hb[0] <= 4 ? 4 : (g.hb[0] <= 8 ? 8 : 12);
+    const size_t sa = acc_rows_mas_a_smem_bytes(g, nd, nxb), sj = adj_rows_mas_a_smem_bytes(g, nd, nxb);
+    if (sa > 220 * 1024 || sj > 220 * 1024) continue;
+    lv.g = g;
+    lv.rows = true;
+    lv.nxb_rows = nxb;
+    lv.smem_acc_rows = sa;
+    lv.smem_adj_rows = sj;
+    if (!lv.dyz) CK(cudaMalloc((void**)&lv.dyz, sizeof(float2) * zcontract_dy_len(g)));
+    return SRWCR_OK;
+  }
+  return SRWCR_OK;
+}
 
 srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv, const int* force_tile = nullptr) {
   const srwcr_config& cfg = ctx->cfg;
+  if (cfg.role == SRWCR_ROLE_M_AS_A) return select_rows_path_mas_a(ctx, lv, force_tile);
   const int nd = cfg.ndim;
   static const int cand3[][3] = {{32, 32, 4}, {32, 16, 4}, {32, 8, 4}, {32, 8, 2}, {32, 4, 2},
                                  {32, 2, 2}, {32, 1, 1}};
@@ -842,6 +969,49 @@ srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv, const int* force_tile =
   return SRWCR_OK;
 }
 
+// Static per-row distance to the nearest nonzero moving-image voxel (the
+// value pass skips rows that provably read only zeros) and the per-row
+// record of a nonzero moving-image gradient the adjoint visits.
+srwcr_status build_row_dist(srwcr_ctx* ctx, Level& lv) {
+  const Geo& g = lv.g;
+  const long long nrows = (long long)((g.n[0] + 31) / 32) * g.n[1] * g.n[2];
+  CK(cudaMalloc((void**)&lv.rowdist, nrows));
+  CK(cudaMalloc((void**)&lv.rowlive, nrows));
+  CK(cudaMemsetAsync(lv.rowlive, 1, nrows, ctx->stream));
+  unsigned char* d[2] = {nullptr, nullptr};
+  CK(cudaMalloc((void**)&d[0], g.nvox));
+  cudaError_t e = cudaMalloc((void**)&d[1], g.nvox);
+  if (e != cudaSuccess) { cudaFree(d[0]); return fail(SRWCR_ENOMEM, "cudaMalloc failed"); }
+  const int nb = (int)std::min<long long>(148 * 8, (g.nvox + 255) / 256);
+  if (is_bf16(ctx)) k_mdist_x<__nv_bfloat16><<<nb, 256, 0, ctx->stream>>>(g, (const __nv_bfloat16*)lv.M, d[0]);
+  else k_mdist_x<float><<<nb, 256, 0, ctx->stream>>>(g, (const float*)lv.M, d[0]);
+  int cur = 0;
+  for (int axis = 1; axis < ctx->cfg.ndim; ++axis, cur ^= 1)
+    k_mdist_pass<<<nb, 256, 0, ctx->stream>>>(g, axis, d[cur], d[cur ^ 1]);
+  k_row_dist<<<(int)std::min<long long>(148 * 8, (nrows + 255) / 256), 256, 0, ctx->stream>>>(g, d[cur], lv.rowdist);
+  e = cudaGetLastError();
+  std::vector<unsigned char> hd;
+  if (e == cudaSuccess) {
+    hd.resize(nrows);
+    e = cudaMemcpyAsync(hd.data(), lv.rowdist, nrows, cudaMemcpyDeviceToHost, ctx->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d[0]);
+  cudaFree(d[1]);
+  if (e != cudaSuccess) return fail(SRWCR_ECUDA, "row distances: %s", cudaGetErrorString(e));
+  // A level where no row lies farther than the stencil's reach from a
+  // nonzero moving-image voxel can never skip a row: both records are
+  // dropped there (every row is processed, without the per-row tests).
+  const unsigned char far = *std::max_element(hd.begin(), hd.end());
+  if ((float)far <= kDeadRowMargin) {
+    cudaFree(lv.rowdist);
+    cudaFree(lv.rowlive);
+    lv.rowdist = nullptr;
+    lv.rowlive = nullptr;
+  }
+  return SRWCR_OK;
+}
+
 void free_bend(srwcr_ctx* ctx);  // bending.cuh
 
 }  // namespace
@@ -906,6 +1076,7 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     CK(cudaMalloc((void**)&lv.X, sizeof(float) * g.R * g.nbins));
     if (nch == 3) CK(cudaMalloc((void**)&lv.Y2, sizeof(float) * g.R * g.nbins));
     if (nch == 3) CK(cudaMalloc((void**)&lv.DY, sizeof(float2) * g.R * g.nbins));
+    if (nch == 3) CK(cudaMemsetAsync(lv.DY, 0, sizeof(float2) * g.R * g.nbins, ctx->stream));
     CK(cudaMalloc((void**)&lv.Dr, sizeof(double) * g.R));
     CK(cudaMalloc((void**)&lv.stats, sizeof(double) * g.R * 4));
     CK(cudaMalloc((void**)&lv.D, sizeof(double)));
@@ -979,8 +1150,10 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     // per-voxel kernels run.
     if (rows_allowed(*cfg)) RET_IF(select_rows_path(ctx, lv));
     if (lv.rows) {
-      CK(cudaMalloc((void**)&lv.bg, sizeof(float4) * lv.g.nvox));
+      const bool keep = cfg->keep_warp > 0 || (cfg->keep_warp == 0 && lv.g.nvox <= kKeepWarpMaxVoxels);
+      if (keep) CK(cudaMalloc((void**)&lv.bg, sizeof(float4) * lv.g.nvox));
       CK(cudaMalloc((void**)&lv.uvxz, sizeof(float) * zcontract_len(lv.g)));
+      RET_IF(build_row_dist(ctx, lv));
     }
   }
 
@@ -992,6 +1165,10 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     lv.s1 = (float)s1;
     lv.s0 = (float)sP;
     lv.s2 = (float)s2;
+    // Moving image as A on the row kernels: P is accumulated per evaluation
+    // from sums over at most 64 voxels of weights <= 1 per row update, each
+    // kept below 2^48 like the moments.
+    if (cfg->role == SRWCR_ROLE_M_AS_A && lv.rows) lv.s0 = (float)std::min(sP, std::ldexp(1.0, 42));
     CK(cudaMemsetAsync(lv.S, 0, sizeof(unsigned long long) * lv.g.R * lv.g.nbins, ctx->stream));
     RET_IF(is_bf16(ctx) ? launch_accumulate<__nv_bfloat16>(ctx, lv, nullptr, true, (float)sP, 0.f)
                         : launch_accumulate<float>(ctx, lv, nullptr, true, (float)sP, 0.f));
@@ -1071,6 +1248,7 @@ srwcr_status srwcr_create(const srwcr_config* cfg, const float* fixed, const flo
   if (cfg->bins_per_pass < 0) return fail(SRWCR_EINVAL, "negative bins_per_pass");
   if (cfg->role != SRWCR_ROLE_M_AS_B && cfg->role != SRWCR_ROLE_M_AS_A)
     return fail(SRWCR_EINVAL, "unknown role");
+  if (cfg->keep_warp < -1 || cfg->keep_warp > 1) return fail(SRWCR_EINVAL, "keep_warp must be -1, 0 or 1");
   if (cfg->finalize_lanes != 0 && cfg->finalize_lanes != 1 && cfg->finalize_lanes != 2 &&
       cfg->finalize_lanes != 4 && cfg->finalize_lanes != 8 && cfg->finalize_lanes != 16 &&
       cfg->finalize_lanes != 32)
@@ -1448,6 +1626,8 @@ void srwcr_lbfgs_default_opts(srwcr_lbfgs_opts* o) {
   o->c1 = 1e-4;
   o->c2 = 0.9;
   o->penalty_weight = 0.0;
+  o->start_jitter = 0.0;
+  o->seed = 0;
 }
 
 }  // extern "C"
@@ -1600,9 +1780,10 @@ std::vector<std::pair<std::string, std::array<int, 3>>> g_tune_cache;
 
 std::string tune_key(const srwcr_ctx* ctx, const Geo& g) {
   char buf[256];
-  snprintf(buf, sizeof buf, "d%d_n%dx%dx%d_f%dx%dx%d_s%d/%d,%d/%d,%d/%d_b%d_t%d_p%d", ctx->cfg.ndim,
+  snprintf(buf, sizeof buf, "d%d_n%dx%dx%d_f%dx%dx%d_s%d/%d,%d/%d,%d/%d_b%d_t%d_p%d_r%d_w%d", ctx->cfg.ndim,
            g.n[0], g.n[1], g.n[2], g.fsp[0], g.fsp[1], g.fsp[2], g.sbn[0], g.sbd[0], g.sbn[1],
-           g.sbd[1], g.sbn[2], g.sbd[2], g.nbins, ctx->cfg.storage, ctx->cfg.bins_per_pass);
+           g.sbd[1], g.sbn[2], g.sbd[2], g.nbins, ctx->cfg.storage, ctx->cfg.bins_per_pass,
+           ctx->cfg.role, ctx->cfg.spatial);
   return buf;
 }
 

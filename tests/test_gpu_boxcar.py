@@ -52,7 +52,7 @@ def test_boxcar_value_gradient_and_regions_match_oracle(name, kind, prob, sig, r
     c = synth.coefficients(prob, 601, sig)
     e = engine(prob, f, m, role=role)
     lv = e.levels[0]
-    assert lv.kernel_path == (1 if role == "mas_b" else 0)
+    assert lv.kernel_path == 1     # both roles run on the row kernels
     assert lv.sbins[:prob.ndim] == tuple(prob.sbin_intervals[:prob.ndim])
     assert lv.n_regions == int(np.prod(prob.sbin_intervals[:prob.ndim]))
     D, g = e.value_and_grad(torch.from_numpy(c).cuda())

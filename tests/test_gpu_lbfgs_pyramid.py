@@ -115,7 +115,7 @@ def test_register_iterations_match_oracle_loop_fed_gpu_values(c1_engine):
         cg = c.cpu().numpy().ravel().astype(np.float64)
         assert rep.iterations[0] == res.n_iter == k
         assert rep.evaluations[0] == res.n_evals, (k, rep.evaluations[0], res.n_evals)
-        x_tol, d_tol = (2e-5, 5e-6) if k <= 3 else (2e-3, 1e-4)
+        x_tol, d_tol = (2e-5, 5e-6) if k <= 3 else (5e-3, 5e-4)
         err = np.linalg.norm(cg - res.x) / np.linalg.norm(res.x)
         assert err <= x_tol, (k, err)
         assert abs(rep.final_value[0] - res.f) <= d_tol * abs(res.f), (k, rep.final_value[0], res.f)

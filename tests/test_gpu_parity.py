@@ -63,12 +63,22 @@ def test_value_gradient_and_regions_match_oracle(small_cases, name):
     st, go, _, _, _ = oracle_eval(prob, f, m, c)
     assert abs(D - st.D) <= D_RTOL * abs(st.D), (D, st.D)
     assert ndeg == st.n_degenerate
-    v = st.valid.astype(bool)
     # p(r): FP32 products w*h summed exactly in fixed point -> ~1e-7 relative.
     assert np.allclose(stats[:, 0], st.pr, rtol=1e-6, atol=1e-15)
     # sigma_r^2 = E[b^2] - mu^2 is formed from FP32 per-voxel moments whose
     # rounding (~1e-7 of E[b^2]) survives the cancellation: compare on the
     # scale of E_r[b^2]; CR inherits that error divided by sigma_r^2.
+    # The moment sums are fixed point with one quantum per level, so the
+    # quantisation error of a region's sigma^2 is about (a few half quanta) /
+    # W_r, W_r = p(r) Z its total weight: above the 1e-6 bar only for regions
+    # whose support meets the image in a few voxels at B-spline weights near
+    # 1e-3 per axis (p(r) ~ 1e-10, W_r ~ 1e-5 voxels).  Regions with p(r) <
+    # 1e-8 are checked loosely and shown to hold a negligible share of D.
+    v = st.valid.astype(bool)
+    tiny = v & (st.pr < 1e-8)
+    assert np.sum(st.pr[tiny] * (1.0 - st.cr[tiny])) <= 1e-6 * abs(st.D)
+    assert np.all(np.abs(stats[tiny, 1] - st.var_r[tiny]) <= 1e-3 * np.maximum(st.var_r[tiny], 1.0))
+    v = v & ~tiny
     ms = st.var_r[v] + st.mu_r[v] ** 2
     assert np.all(np.abs(stats[v, 1] - st.var_r[v]) <= 1e-6 * np.maximum(ms, 1.0))
     assert np.all(np.abs(stats[v, 2] - st.cr[v]) <= 1e-6 + 4e-6 * np.maximum(ms, 1.0) / st.var_r[v])
@@ -333,9 +343,12 @@ def test_c2_bf16_storage(c2_case):
     pair, c = c2_case
     prob = pair.prob
     e = engine_for(prob, pair.fixed, pair.moving, storage="bf16")
-    D = e.value(torch.from_numpy(c).cuda())
-    st, _, _, _, _ = oracle_eval(prob, pair.fixed, pair.moving, c, storage="bf16", grad=False)
+    D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+    st, go, _, _, _ = oracle_eval(prob, pair.fixed, pair.moving, c, storage="bf16")
     assert abs(D - st.D) <= D_RTOL * st.D, (D, st.D)
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(np.linalg.norm(g) - np.linalg.norm(go)) <= GNORM_RTOL * np.linalg.norm(go)
+    assert np.abs(g - go).max() <= G_ELEM * np.abs(go).max()
 
 
 def test_c3_full_value_and_sampled_gradient():
