@@ -169,14 +169,17 @@ def oracle_full_eval(pair, c, storage="f32"):
 
 
 def slab(pair, nz):
-    """Sub-volume (first nz slices) as a bounded sample of a 3-D workload."""
+    """Sub-volume (the middle nz slices) as a bounded sample of a 3-D
+    workload."""
     prob = pair.prob
     if prob.ndim == 2:
         return pair
+    z0 = (prob.dims[2] - nz) // 2
     p2 = synth.problem(3, (prob.dims[0], prob.dims[1], nz), prob.ffd_spacing,
                        prob.sbin_intervals, prob.n_bins)
-    return synth.PairSpec(pair.name + f"_slab{nz}", p2, np.ascontiguousarray(pair.fixed[:nz]),
-                          np.ascontiguousarray(pair.moving[:nz]))
+    return synth.PairSpec(pair.name + f"_slab{nz}", p2,
+                          np.ascontiguousarray(pair.fixed[z0:z0 + nz]),
+                          np.ascontiguousarray(pair.moving[z0:z0 + nz]))
 
 
 def _oracle_slab_job(job):
