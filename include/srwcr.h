@@ -207,6 +207,21 @@ srwcr_status srwcr_debug_warp_grad(srwcr_ctx* ctx, int level, const float* c_dev
  * NULL).  Synchronises. */
 srwcr_status srwcr_level_images(srwcr_ctx* ctx, int level, float* fixed_dev, float* moving_dev);
 
+/* Debug: the fixed-point conversions of the histogram flushes, written with
+ * 32-bit operations (64-bit integer <-> float conversions run on this GPU's
+ * narrow FP64 unit).  For i < n: fixed_dev[i] = the nearest integer to
+ * v_dev[i] (ties to even), for 0 <= v < 2^64.  For i < m: float_dev[i] = the
+ * nearest float (ties to even) to hi_dev[i] * 2^24 + lo_dev[i], for
+ * hi <= 256 * (2^24 - 1) (the 48-bit word pairs of the row kernels' plane
+ * histograms).  reference != 0 computes the same with CUDA's 64-bit
+ * conversions instead, so a caller can compare the two bit for bit.  All
+ * pointers are device arrays (may be NULL where their count is 0); runs on
+ * the legacy default stream and synchronises the device.  SRWCR_EINVAL on a
+ * negative count or a missing array. */
+srwcr_status srwcr_debug_fixed_point(const float* v_dev, int64_t n, const uint32_t* hi_dev,
+                                     const uint32_t* lo_dev, int64_t m, uint64_t* fixed_dev,
+                                     float* float_dev, int reference);
+
 /* Benchmark hooks.  With profiling enabled the library brackets each of its
  * kernels with CUDA events on the context's stream.  srwcr_profile_read
  * synchronises the stream and reports, per kernel kind (0 = fused warp and

@@ -38,7 +38,7 @@ EXPORTS = ("srwcr_create", "srwcr_destroy", "srwcr_last_error", "srwcr_level_inf
            "srwcr_batch_sync", "srwcr_batch_register", "srwcr_bending_energy",
            "srwcr_rigid_value_and_grad", "srwcr_rigid_to_ffd", "srwcr_rigid_register",
            "srwcr_debug_warp_grad", "srwcr_level_images", "srwcr_refine",
-           "srwcr_lbfgs_direction")
+           "srwcr_lbfgs_direction", "srwcr_debug_fixed_point")
 
 
 class SrwcrError(RuntimeError):
@@ -124,6 +124,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "srwcr_level_images": (st, [vp, ctypes.c_int, vp, vp]),
         "srwcr_refine": (st, [vp, ctypes.c_int, vp, vp]),
         "srwcr_lbfgs_direction": (st, [vp, ctypes.c_int64, ctypes.c_int, vp, vp, vp, vp]),
+        "srwcr_debug_fixed_point": (st, [vp, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, vp,
+                                         ctypes.c_int]),
         "srwcr_lbfgs_default_opts": (None, [ctypes.POINTER(LbfgsOpts)]),
         "srwcr_set_profiling": (st, [vp, ctypes.c_int]),
         "srwcr_profile_read": (st, [vp, vp, vp, i64p, ctypes.c_int]),
@@ -614,3 +616,19 @@ def from_problem(prob, fixed, moving, storage: str = "f32", pyramid_levels: int 
     """Build an engine from a ``synth.Problem``-like description."""
     return SRWCR(fixed, moving, prob.ffd_spacing[:prob.ndim], prob.sbin_intervals[:prob.ndim],
                  prob.n_bins, storage=storage, pyramid_levels=pyramid_levels, **kw)
+
+
+def debug_fixed_point(v, hi, lo, reference: bool = False):
+    """The flushes' fixed-point conversions on CUDA tensors: v (float32) ->
+    nearest integer (int64 tensor holding the uint64 bits), and
+    (hi, lo) (int32 tensors holding uint32 bits) -> nearest float32 to
+    hi * 2^24 + lo.  reference=True takes CUDA's 64-bit conversions."""
+    import torch
+    v = v.contiguous(); hi = hi.contiguous(); lo = lo.contiguous()
+    assert v.dtype == torch.float32 and hi.dtype == torch.int32 and lo.dtype == torch.int32
+    assert hi.numel() == lo.numel()
+    fixed = torch.empty(v.numel(), dtype=torch.int64, device=v.device)
+    flt = torch.empty(hi.numel(), dtype=torch.float32, device=v.device)
+    _check(load().srwcr_debug_fixed_point(_ptr(v), v.numel(), _ptr(hi), _ptr(lo), hi.numel(),
+                                          _ptr(fixed), _ptr(flt), int(bool(reference))))
+    return fixed, flt

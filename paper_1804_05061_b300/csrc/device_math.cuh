@@ -41,6 +41,32 @@ struct Geo {
 __device__ __forceinline__ float ldval(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldval(const __nv_bfloat16* p) { return __bfloat162float(p[0]); }
 
+// Fixed-point conversions done with 32-bit operations only: conversions
+// between 64-bit integers and floats run on the narrow FP64 unit of this
+// GPU, and a histogram flush issues one per entry.
+//
+// Nearest 64-bit integer to v, 0 <= v < 2^64 (ties to even), the value
+// __float2ull_rn returns.  hf = floor(v / 2^32) is exact (power-of-two
+// scaling, then floor); v - hf 2^32 is exact in the FMA and lies in
+// [0, 2^32); below 2^32 the conversion rounds the fraction of v, from 2^32
+// up v is a multiple of 2^9 and the remainder an integer.
+__device__ __forceinline__ unsigned long long fixed_from_float(float v) {
+  const float hf = floorf(v * 0x1p-32f);
+  const unsigned lo = __float2uint_rn(fmaf(hf, -0x1p32f, v));
+  return ((unsigned long long)__float2uint_rz(hf) << 32) | lo;
+}
+
+// Nearest float to hi 2^24 + lo for hi <= 256 (2^24 - 1) and lo < 2^32 (a
+// 48-bit histogram word pair), the value __ull2float_rn returns for that
+// sum.  After the carry of lo's top byte into hi the sum is hn 2^24 + l with
+// l < 2^24; below 2^48 (hn < 2^24) both halves are exact floats and the FMA
+// rounds their exact sum once.  Larger sums take the 64-bit conversion.
+__device__ __forceinline__ float fields_to_float(unsigned hi, unsigned lo) {
+  const unsigned hn = hi + (lo >> 24);
+  if (hn < (1u << 24)) return fmaf((float)hn, 0x1p24f, (float)(lo & 0xffffffu));
+  return __ull2float_rn(((unsigned long long)hi << 24) + lo);
+}
+
 // Eq. (8): w[l] = beta_l(t), t in [0, 1].
 __device__ __forceinline__ void bspline4(float t, float w[4]) {
   const float s = 1.0f / 6.0f;

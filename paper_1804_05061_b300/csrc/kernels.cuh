@@ -23,7 +23,7 @@ namespace srwcr {
 
 // Non-negative float -> 64-bit fixed point (round to nearest).
 __device__ __forceinline__ unsigned long long to_fixed(float v) {
-  return __float2ull_rn(v);
+  return fixed_from_float(v);
 }
 
 // Exact 64-bit add into a shared-memory word with two native 32-bit atomics
@@ -587,6 +587,21 @@ __global__ void k_to_float(const T* __restrict__ in, long long n, float* __restr
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     out[i] = ldval(in + i);
+}
+
+// The fixed-point conversions of the histogram flushes on n floats v and on
+// m word pairs (hi, lo); reference != 0 takes CUDA's 64-bit conversions
+// instead, the values the 32-bit forms must reproduce.
+__global__ void k_debug_fixed(const float* __restrict__ v, long long n, const unsigned* __restrict__ hi,
+                              const unsigned* __restrict__ lo, long long m,
+                              unsigned long long* __restrict__ fixed, float* __restrict__ flt,
+                              int reference) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
+    fixed[i] = reference ? __float2ull_rn(v[i]) : fixed_from_float(v[i]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += stride)
+    flt[i] = reference ? __ull2float_rn(((unsigned long long)hi[i] << 24) + lo[i])
+                       : fields_to_float(hi[i], lo[i]);
 }
 
 }  // namespace srwcr

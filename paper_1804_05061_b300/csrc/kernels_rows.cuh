@@ -680,20 +680,31 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
     // bins are added to the global accumulators.
     // Threads are spread over the columns (bin, moment, x bin) and, when
     // there are fewer columns than threads, over the y bins of a column; each
-    // loops over the first planes of the z cells and its y bins (the index
-    // divisions are done once per thread).
-    const int wcols = 2 * cb * g.hb[0];
+    // loops over the first planes of the z cells and its y bins.  Consecutive
+    // threads take consecutive (bin, moment) pairs of one x bin, so a warp's
+    // global additions fall on consecutive words of one region's record.
+    // Their shared-memory stride is then the x-bin count; when that is a
+    // multiple of 4, each group of 8 pairs starts at another x bin, which
+    // spreads a warp's reads over all 32 banks.
+    const int nach = 2 * cb;
+    const int wcols = nach * g.hb[0];
     const int tpc = wcols < (int)blockDim.x ? min((int)blockDim.x / wcols, g.hb[1]) : 1;
+    const bool rotate = (g.hb[0] & 3) == 0;
+    const size_t ystride = (size_t)g.nsb[0] * nb * 2, zstride = ystride * g.nsb[1];
     for (int t = threadIdx.x; t < wcols * tpc; t += blockDim.x) {
-      const int sub = t / wcols, col = t - sub * wcols;
-      const int ach = col / g.hb[0], b = col - ach * g.hb[0];
+      const int sub = t / wcols, i = t - sub * wcols;
+      const int bq = i / nach, ach = i - bq * nach;
       if (c0 + (ach >> 1) >= cnt) continue;
+      const int b = rotate ? (bq + (ach >> 3)) % g.hb[0] : bq;
       const int r0 = TO.cb[0] + b;
       if (r0 >= g.nsb[0]) continue;
+      const int col = ach * g.hb[0] + b;
       const int a = c2a[c0 + (ach >> 1)], ch = ach & 1;
+      unsigned long long* accx = acc + ((size_t)r0 * nb + a) * 2 + ch;
       for (int zl = 0; zl < g.tile[2]; ++zl) {
         const int cz = zt[zl].srel;
         if (zl > 0 && zt[zl - 1].srel == cz) continue;
+        const int r2b = TO.cb[2] + cz;
         for (int l1 = sub; l1 < g.hb[1]; l1 += tpc) {
           const int r1 = TO.cb[1] + l1;
           if (r1 >= g.nsb[1]) break;
@@ -703,20 +714,19 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
           bool any = false;
           for (int pl = zl; pl < g.tile[2] && zt[pl].srel == cz; ++pl) {
             const int j = (pl * g.hb[1] + l1) * S + col;
-            const unsigned long long h = ((unsigned long long)hhi[j] << 24) + hlo[j];
-            if (!h) continue;
+            const unsigned lo = hlo[j], hi = hhi[j];
+            if (!(lo | hi)) continue;
             any = true;
-            const float hv = __ull2float_rn(h);
+            const float hv = fields_to_float(hi, lo);
 #pragma unroll
             for (int m = 0; m < NK; ++m) u[m] = fmaf(zt[pl].bs[m], hv, u[m]);
           }
           if (!any) continue;
+          unsigned long long* accy = accx + (size_t)r1 * ystride + (size_t)r2b * zstride;
 #pragma unroll
           for (int m = 0; m < NK; ++m) {
-            const int r2 = TO.cb[2] + cz + m;
-            if (u[m] == 0.f || r2 >= g.nsb[2]) continue;
-            const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
-            atomicAdd(acc + ((size_t)r * nb + a) * 2 + ch, __float2ull_rn(u[m]));
+            if (u[m] == 0.f || r2b + m >= g.nsb[2]) continue;
+            atomicAdd(accy + (size_t)m * zstride, fixed_from_float(u[m]));
           }
         }
       }

@@ -270,10 +270,10 @@ __device__ __forceinline__ void acc_rows_mas_a_body(const Geo& g, const AccArgsA
         bool any = false;
         for (int pl = zl; pl < g.tile[2] && zt[pl].srel == cz; ++pl) {
           const int j = (pl * g.hb[1] + l1) * S + col;
-          const unsigned long long h = ((unsigned long long)hhi[j] << 24) + hlo[j];
-          if (!h) continue;
+          const unsigned lo = hlo[j], hi = hhi[j];
+          if (!(lo | hi)) continue;
           any = true;
-          const float hv = __ull2float_rn(h);
+          const float hv = fields_to_float(hi, lo);
 #pragma unroll
           for (int m = 0; m < NK; ++m) u[m] = fmaf(zt[pl].bs[m], hv, u[m]);
         }
@@ -283,7 +283,7 @@ __device__ __forceinline__ void acc_rows_mas_a_body(const Geo& g, const AccArgsA
           const int r2 = TO.cb[2] + cz + m;
           if (u[m] == 0.f || r2 >= g.nsb[2]) continue;
           const long long r = ((long long)r2 * g.nsb[1] + r1) * g.nsb[0] + r0;
-          atomicAdd(acc + ((size_t)r * nb + a) * 3 + ch, __float2ull_rn(u[m]));
+          atomicAdd(acc + ((size_t)r * nb + a) * 3 + ch, fixed_from_float(u[m]));
         }
       }
     }

@@ -210,9 +210,12 @@ void set_tile(Geo& g, int ndim, int tx, int ty, int tz) {
 srwcr_status choose_tile(Geo& g, int ndim, const int* req, int nch) {
   if (req[0] > 0) {
     set_tile(g, ndim, req[0], std::max(1, req[1]), std::max(1, req[2]));
-    if (acc_smem(g, nch) > 220 * 1024)
-      return fail(SRWCR_EINVAL, "requested tile needs %zu bytes of shared memory",
-                  acc_smem(g, nch));
+    // The create-time statistics always run on the general kernels (one
+    // channel); a 32-wide tile may leave the evaluations to the row kernels,
+    // which is checked once those are selected.
+    const size_t need = acc_smem(g, req[0] == 32 ? 1 : nch);
+    if (need > 220 * 1024)
+      return fail(SRWCR_EINVAL, "requested tile needs %zu bytes of shared memory", need);
     return SRWCR_OK;
   }
   static const int cand3[][3] = {{32, 32, 8}, {32, 16, 8}, {32, 8, 8}, {32, 8, 4}, {32, 4, 4}, {32, 4, 2},
@@ -1149,6 +1152,10 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
     // with the moving image as A the binned image moves, so the general
     // per-voxel kernels run.
     if (rows_allowed(*cfg)) RET_IF(select_rows_path(ctx, lv));
+    if (!lv.rows && lv.smem_acc > 220 * 1024)
+      return fail(SRWCR_EINVAL,
+                  "requested tile needs %zu bytes of shared memory on the general kernels, and the "
+                  "row kernels cannot take level %d", lv.smem_acc, l);
     if (lv.rows) {
       const bool keep = cfg->keep_warp > 0 || (cfg->keep_warp == 0 && lv.g.nvox <= kKeepWarpMaxVoxels);
       if (keep) CK(cudaMalloc((void**)&lv.bg, sizeof(float4) * lv.g.nvox));
@@ -1579,6 +1586,20 @@ srwcr_status srwcr_level_images(srwcr_ctx* ctx, int level, float* fixed_dev, flo
     CKL();
   }
   CK(cudaStreamSynchronize(ctx->stream));
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_debug_fixed_point(const float* v_dev, int64_t n, const uint32_t* hi_dev,
+                                     const uint32_t* lo_dev, int64_t m, uint64_t* fixed_dev,
+                                     float* float_dev, int reference) {
+  if (n < 0 || m < 0) return fail(SRWCR_EINVAL, "negative count");
+  if (n > 0 && (!v_dev || !fixed_dev)) return fail(SRWCR_EINVAL, "null device pointer");
+  if (m > 0 && (!hi_dev || !lo_dev || !float_dev)) return fail(SRWCR_EINVAL, "null device pointer");
+  if (n == 0 && m == 0) return SRWCR_OK;
+  k_debug_fixed<<<256, 256>>>(v_dev, n, hi_dev, lo_dev, m,
+                              reinterpret_cast<unsigned long long*>(fixed_dev), float_dev, reference);
+  CKL();
+  CK(cudaDeviceSynchronize());
   return SRWCR_OK;
 }
 
