@@ -322,8 +322,10 @@ struct AdjArgs {
 // The intensity axis holds only the fixed-image bins the tile uses (a static
 // per-tile mask), in compact order.
 __host__ __device__ inline int hist_yz_stride(const Geo& g) {
+  // At least 4 words past the row's last column (the value kernel's fold
+  // adds zeros up to 3 words past it); 8 modulo 32.
   const int w = 2 * g.cbin * g.hb[0];
-  return ((w + 23) / 32) * 32 + 8;
+  return ((w + 27) / 32) * 32 + 8;
 }
 
 __host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int nxb) {
@@ -643,32 +645,35 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
         // consecutive items consecutive columns).
         const int prow = (zl * g.hb[1] + ye.srel) * S;
         const int per_bin = 2 * XC;
+        // The body has no branch: an item past the row's x-bins or with a
+        // zero sum carries uv = 0 and adds zeros, which costs fewer
+        // instructions than skipping the additions.  Past the x-bins a
+        // column lies at most 3 words beyond the last one of its y row
+        // (NXB - hb0 <= 3), inside the row's spare words.
         for (int f = lane; f < nbin * per_bin; f += 32) {
           const int e = f / per_bin, r = f % per_bin;
           const int ch = r / XC, b = r % XC;
           const int bx_ = q0 + b;                  // the row's x-bin
-          if (bx_ >= g.hb[0]) continue;
           const int a = mybins[2 * e];
           const int info = mybins[2 * e + 1];
           const int sg = info & 0xff, slot = (info >> 8) & 1;
-          float val = mysegS[seg_at<NV>(sg, 4 * b + 2 * slot + ch)];
-          if (info & (1 << 9)) val += mysegS[seg_at<NV>((info >> 10) & 31, 4 * b + 2 + ch)];
-          const float uv = val * (ch ? s2 : s1);
-          if (uv == 0.f) continue;
+          const float v0 = mysegS[seg_at<NV>(sg, 4 * b + 2 * slot + ch)];
+          const float v1 = mysegS[seg_at<NV>((info >> 10) & 31, 4 * b + 2 + ch)];
+          const float val = (info & (1 << 9)) ? v0 + v1 : v0;
+          const float uv = bx_ < g.hb[0] ? val * (ch ? s2 : s1) : 0.f;
           const int col = prow + ((a2c[a] - c0) * 2 + ch) * g.hb[0] + bx_;
   #pragma unroll
           for (int m = 0; m < 4; ++m) {
             const float u = uv * ye.bs[m];
-            if (u == 0.f) continue;
             // Split of u (< 2^48) into 24-bit fields: the power-of-two
             // scaling, the floor and the fused subtraction are exact; the low
             // field rounds u's fraction (u < 2^24) to the fixed-point unit.
             const float hf = floorf(u * 0x1p-24f);
             const unsigned lo = __float2uint_rn(fmaf(hf, -0x1p24f, u));
-            const unsigned hi = (unsigned)hf;
+            const unsigned hi = __float2uint_rz(hf);
             const int at = col + m * S;
-            if (lo) atomicAdd(hlo + at, lo);
-            if (hi) atomicAdd(hhi + at, hi);
+            atomicAdd(hlo + at, lo);
+            atomicAdd(hhi + at, hi);
           }
         }
         __syncwarp();
@@ -752,12 +757,17 @@ __device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
   return v[0];
 }
 
+// Words per (plane, y bin, x bin) entry of the adjoint's X table: the bin
+// count made odd, so lanes reading one bin at different x or y bins fall
+// in different shared-memory banks.
+__host__ __device__ inline int adj_xz_stride(const Geo& g) { return g.nbins | 1; }
+
 // Bytes of the adjoint's shared memory (must match the carve-up below).
 __host__ __device__ inline size_t adj_rows_smem_bytes(const Geo& g, int dim, int nxb) {
   const size_t hf = (size_t)g.hf[0] * g.hf[1] * g.tile[2];         // per-plane nodes
   const size_t p01 = (size_t)g.hb[0] * g.hb[1];
   size_t b = sizeof(float) * dim * hf;                               // gt
-  b += sizeof(float) * g.tile[2] * p01 * (2 + g.nbins);              // UZ, VZ, XZ
+  b += sizeof(float) * g.tile[2] * p01 * (2 + adj_xz_stride(g));     // UZ, VZ, XZ
   b += sizeof(float) * kAdjWarps * (2 * nxb + 32 * nxb * 2);         // rowt, xy
   b += sizeof(int) * kAdjWarps * 32;                                 // segA
   b += sizeof(float) * kAdjWarps * dim * kMaxRowNodes;               // cyz
@@ -792,8 +802,9 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
   float* gt = smem_f32;
   float* UZ = gt + DIM * nodes_tile;                 // [TZ][hb1][hb0]
   float* VZ = UZ + g.tile[2] * p01;
-  float* XZ = VZ + g.tile[2] * p01;                  // [TZ][hb1][hb0][nb]
-  float* rowt_all = XZ + (size_t)g.tile[2] * p01 * nb;
+  const int nbx = adj_xz_stride(g);
+  float* XZ = VZ + g.tile[2] * p01;                  // [TZ][hb1][hb0][nbx]
+  float* rowt_all = XZ + (size_t)g.tile[2] * p01 * nbx;
   float* xy_all = rowt_all + kAdjWarps * 2 * NXB;
   int* segA_all = reinterpret_cast<int*>(xy_all + kAdjWarps * 32 * NXB * 2);
   float* cyz_all = reinterpret_cast<float*>(segA_all + kAdjWarps * 32);
@@ -845,7 +856,7 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
         if (in) s = col == 0 ? __ldg(UZg + zr) : (col == 1 ? __ldg(VZg + zr) : __ldg(XZg + zr * nb + (col - 2)));
         if (col == 0) UZ[e] = s;
         else if (col == 1) VZ[e] = s;
-        else XZ[(size_t)e * nb + (col - 2)] = s;
+        else XZ[(size_t)e * nbx + (col - 2)] = s;
       }
     }
   }
@@ -986,7 +997,7 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
     const bool head = lane == 0 || key != prev;
     const unsigned heads = __ballot_sync(0xffffffffu, head);
     const int nseg = __popc(heads);
-    const float* XZr = XZ + (size_t)zl * p01 * nb;
+    const float* XZr = XZ + (size_t)zl * p01 * nbx;
     const bool xlane = nseg * NXB * 2 > kAdjLaneXMin;
     if (!xlane) {
       if (head) mysegA[__popc(heads & ((1u << lane) - 1u))] = key;
@@ -997,7 +1008,7 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
         float acc_x = 0.f;
         if (a != kSentinel && b < g.hb[0]) {
           for (int jj = 0; jj < 4; ++jj)
-            acc_x += ye.bs[jj] * XZr[(size_t)((ye.srel + jj) * g.hb[0] + b) * nb + a + slot];
+            acc_x += ye.bs[jj] * XZr[(size_t)((ye.srel + jj) * g.hb[0] + b) * nbx + a + slot];
         }
         xy[(s * NXB + b) * 2 + slot] = acc_x;
       }
@@ -1008,7 +1019,7 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
       float su = 0.f, sv = 0.f, sxr = 0.f;
       if (xlane) {
         const int sp = xt.srel[p];
-        const size_t ystep = (size_t)g.hb[0] * nb;
+        const size_t ystep = (size_t)g.hb[0] * nbx;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int b = sp + i;
@@ -1016,7 +1027,7 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
           if (w == 0.f || b >= g.hb[0]) continue;
           su += w * rowt[b];
           sv += w * rowt[NXB + b];
-          const float* xr = XZr + ((size_t)ye.srel * g.hb[0] + b) * nb + key;
+          const float* xr = XZr + ((size_t)ye.srel * g.hb[0] + b) * nbx + key;
           float x0 = 0.f, x1 = 0.f;
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj) {
