@@ -758,9 +758,10 @@ __device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
 }
 
 // Words per (plane, y bin, x bin) entry of the adjoint's X table: the bin
-// count made odd, so lanes reading one bin at different x or y bins fall
-// in different shared-memory banks.
-__host__ __device__ inline int adj_xz_stride(const Geo& g) { return g.nbins | 1; }
+// count rounded up to 2 modulo 32, so the (x bin b, bin a + slot) entries a
+// warp reads for one bin a, at offsets 2 b + slot modulo 32, and one bin at
+// different x or y bins fall in different shared-memory banks.
+__host__ __device__ inline int adj_xz_stride(const Geo& g) { return ((g.nbins + 29) / 32) * 32 + 2; }
 
 // Bytes of the adjoint's shared memory (must match the carve-up below).
 __host__ __device__ inline size_t adj_rows_smem_bytes(const Geo& g, int dim, int nxb) {
