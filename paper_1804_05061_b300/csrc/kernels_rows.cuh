@@ -757,18 +757,20 @@ __device__ __forceinline__ float warp_reduce_scatter32(float v[32], int lane) {
   return v[0];
 }
 
-// Words per (plane, y bin, x bin) entry of the adjoint's X table: the bin
-// count rounded up to 2 modulo 32, so the (x bin b, bin a + slot) entries a
-// warp reads for one bin a, at offsets 2 b + slot modulo 32, and one bin at
-// different x or y bins fall in different shared-memory banks.
-__host__ __device__ inline int adj_xz_stride(const Geo& g) { return ((g.nbins + 29) / 32) * 32 + 2; }
+// The adjoint's X table is X[plane][y bin][bin a][x bin] with the x-bin
+// stride made odd: a warp's reads of one (y bin, x bin) for lanes of
+// different bins and neighbouring x bins (a row's bins are few and close)
+// then fall in different shared-memory banks unless the bins are about
+// 32 / stride apart, and one bin at neighbouring x bins is contiguous.
+__host__ __device__ inline int adj_x_stride(const Geo& g) { return g.hb[0] | 1; }
 
 // Bytes of the adjoint's shared memory (must match the carve-up below).
 __host__ __device__ inline size_t adj_rows_smem_bytes(const Geo& g, int dim, int nxb) {
   const size_t hf = (size_t)g.hf[0] * g.hf[1] * g.tile[2];         // per-plane nodes
   const size_t p01 = (size_t)g.hb[0] * g.hb[1];
   size_t b = sizeof(float) * dim * hf;                               // gt
-  b += sizeof(float) * g.tile[2] * p01 * (2 + adj_xz_stride(g));     // UZ, VZ, XZ
+  b += sizeof(float) * g.tile[2] * p01 * 2;                          // UZ, VZ
+  b += sizeof(float) * g.tile[2] * g.hb[1] * g.nbins * adj_x_stride(g);  // XZ
   b += sizeof(float) * kAdjWarps * (2 * nxb + 32 * nxb * 2);         // rowt, xy
   b += sizeof(int) * kAdjWarps * 32;                                 // segA
   b += sizeof(float) * kAdjWarps * dim * kMaxRowNodes;               // cyz
@@ -803,9 +805,10 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
   float* gt = smem_f32;
   float* UZ = gt + DIM * nodes_tile;                 // [TZ][hb1][hb0]
   float* VZ = UZ + g.tile[2] * p01;
-  const int nbx = adj_xz_stride(g);
-  float* XZ = VZ + g.tile[2] * p01;                  // [TZ][hb1][hb0][nbx]
-  float* rowt_all = XZ + (size_t)g.tile[2] * p01 * nbx;
+  const int hx = adj_x_stride(g);
+  const int xzy = nb * hx;                           // words per (plane, y bin) of XZ
+  float* XZ = VZ + g.tile[2] * p01;                  // [TZ][hb1][nb][hx]
+  float* rowt_all = XZ + (size_t)g.tile[2] * g.hb[1] * xzy;
   float* xy_all = rowt_all + kAdjWarps * 2 * NXB;
   int* segA_all = reinterpret_cast<int*>(xy_all + kAdjWarps * 32 * NXB * 2);
   float* cyz_all = reinterpret_cast<float*>(segA_all + kAdjWarps * 32);
@@ -857,7 +860,7 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
         if (in) s = col == 0 ? __ldg(UZg + zr) : (col == 1 ? __ldg(VZg + zr) : __ldg(XZg + zr * nb + (col - 2)));
         if (col == 0) UZ[e] = s;
         else if (col == 1) VZ[e] = s;
-        else XZ[(size_t)e * nbx + (col - 2)] = s;
+        else XZ[(size_t)(zl * g.hb[1] + l1) * xzy + (col - 2) * hx + l0] = s;
       }
     }
   }
@@ -998,7 +1001,7 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
     const bool head = lane == 0 || key != prev;
     const unsigned heads = __ballot_sync(0xffffffffu, head);
     const int nseg = __popc(heads);
-    const float* XZr = XZ + (size_t)zl * p01 * nbx;
+    const float* XZr = XZ + (size_t)zl * g.hb[1] * xzy;
     const bool xlane = nseg * NXB * 2 > kAdjLaneXMin;
     if (!xlane) {
       if (head) mysegA[__popc(heads & ((1u << lane) - 1u))] = key;
@@ -1009,7 +1012,7 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
         float acc_x = 0.f;
         if (a != kSentinel && b < g.hb[0]) {
           for (int jj = 0; jj < 4; ++jj)
-            acc_x += ye.bs[jj] * XZr[(size_t)((ye.srel + jj) * g.hb[0] + b) * nbx + a + slot];
+            acc_x += ye.bs[jj] * XZr[(size_t)(ye.srel + jj) * xzy + (a + slot) * hx + b];
         }
         xy[(s * NXB + b) * 2 + slot] = acc_x;
       }
@@ -1020,7 +1023,7 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
       float su = 0.f, sv = 0.f, sxr = 0.f;
       if (xlane) {
         const int sp = xt.srel[p];
-        const size_t ystep = (size_t)g.hb[0] * nbx;
+        const int ystep = xzy;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int b = sp + i;
@@ -1028,12 +1031,12 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
           if (w == 0.f || b >= g.hb[0]) continue;
           su += w * rowt[b];
           sv += w * rowt[NXB + b];
-          const float* xr = XZr + ((size_t)ye.srel * g.hb[0] + b) * nbx + key;
+          const float* xr = XZr + (size_t)ye.srel * xzy + key * hx + b;
           float x0 = 0.f, x1 = 0.f;
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj) {
             x0 += ye.bs[jj] * xr[jj * ystep];
-            x1 += ye.bs[jj] * xr[jj * ystep + 1];
+            x1 += ye.bs[jj] * xr[jj * ystep + hx];
           }
           sxr += w * (h0 * x0 + h1 * x1);
         }
