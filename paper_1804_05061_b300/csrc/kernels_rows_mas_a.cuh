@@ -56,11 +56,12 @@ struct AdjArgsA {
 
 constexpr int kMasARowStride = 28;   // floats per lane row of the transpose (24 used)
 
-// Words per y/z row of the histogram: 3 * nbins * hb0 columns, rounded to
-// 8 mod 32 as in the M-as-B kernel.
+// Words per y/z row of the histogram: 3 * nbins * hb0 columns and at least
+// 8 spare words (the fold's lanes without a column add zeros there),
+// rounded to 8 mod 32 as in the M-as-B kernel.
 __host__ __device__ inline int mas_a_yz_stride(const Geo& g) {
   const int w = 3 * g.nbins * g.hb[0];
-  return ((w + 23) / 32) * 32 + 8;
+  return ((w + 31) / 32) * 32 + 8;
 }
 
 __host__ __device__ inline size_t acc_rows_mas_a_smem_bytes(const Geo& g, int dim, int nxb) {
@@ -225,22 +226,24 @@ __device__ __forceinline__ void acc_rows_mas_a_body(const Geo& g, const AccArgsA
         float sum = 0.f;
         for (unsigned mm = members; mm; mm &= mm - 1)
           if (lane < 24) sum += tr[(__ffs(mm) - 1) * kMasARowStride + lane];
+        // No branch, as in the M-as-B value kernel: lanes without a column
+        // (lane >= 24, or an x-bin past the row's) add zeros to a spare
+        // word of their own past the row's columns, zero sums add zeros.
         const int bx_ = q0 + qb;
-        if (lane >= 24 || bx_ >= g.hb[0]) continue;
-        const float uv = sum * qscale;
-        if (uv == 0.f) continue;
-        const int col = prow + ((a0 + qslot) * 3 + qch) * g.hb[0] + bx_;
+        const bool inq = lane < 24 && bx_ < g.hb[0];
+        const float uv = inq ? sum * qscale : 0.f;
+        const int col = prow + (inq ? ((a0 + qslot) * 3 + qch) * g.hb[0] + bx_
+                                    : 3 * g.nbins * g.hb[0] + (lane & 7));
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           const float u = uv * ye.bs[m];
-          if (u == 0.f) continue;
           // Two 24-bit fields of u (< 2^48), as in the M-as-B value kernel.
           const float hf = floorf(u * 0x1p-24f);
           const unsigned lo = __float2uint_rn(fmaf(hf, -0x1p24f, u));
-          const unsigned hi = (unsigned)hf;
+          const unsigned hi = __float2uint_rz(hf);
           const int at = col + m * S;
-          if (lo) atomicAdd(hlo + at, lo);
-          if (hi) atomicAdd(hhi + at, hi);
+          atomicAdd(hlo + at, lo);
+          atomicAdd(hhi + at, hi);
         }
       }
       __syncwarp();
