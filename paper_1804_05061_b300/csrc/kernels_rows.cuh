@@ -174,9 +174,11 @@ __device__ __forceinline__ void build_axis_tables(const Geo& g, const TileOrigin
 
 // z-contracted FFD coefficients: CZ[z][k][m][l] for the tile's z-planes,
 // components k, y-nodes m < hf1, x-nodes l < hf0 (read through L1/L2).
+// Returns the bit pattern of the largest |entry| this thread wrote (as an
+// unsigned, so a NaN entry makes it NaN; 0 if none).
 template <int DIM>
-__device__ __forceinline__ void build_cz(const Geo& g, const TileOrigin& T, const float* __restrict__ c,
-                                         const AxisEntry* zt, float* CZ) {
+__device__ __forceinline__ unsigned build_cz(const Geo& g, const TileOrigin& T, const float* __restrict__ c,
+                                             const AxisEntry* zt, float* CZ) {
   // Threads are spread over the (y-node m, x-node l) pairs and, when there
   // are fewer pairs than threads, over the (plane, component) entries of a
   // pair; the index divisions are done once per thread.
@@ -184,6 +186,7 @@ __device__ __forceinline__ void build_cz(const Geo& g, const TileOrigin& T, cons
   const int per_z = DIM * per_k;
   const int nzk = g.tile[2] * DIM;
   const int tpp = per_k < (int)blockDim.x ? min((int)blockDim.x / per_k, nzk) : 1;
+  unsigned mx = 0u;
   for (int t = threadIdx.x; t < per_k * tpp; t += blockDim.x) {
     const int sub = t / per_k, i = t - sub * per_k;
     const int m = i / g.hf[0], l = i - m * g.hf[0];
@@ -202,8 +205,10 @@ __device__ __forceinline__ void build_cz(const Geo& g, const TileOrigin& T, cons
         }
       }
       CZ[zl * per_z + k * per_k + i] = s;
+      mx = max(mx, __float_as_uint(fabsf(s)));
     }
   }
+  return mx;
 }
 
 // Per-row FFD table: cyz[k][l] = sum_m beta_m(y) CZ[z][k][ly + m][l].
@@ -340,6 +345,7 @@ __host__ __device__ inline size_t acc_rows_smem_bytes(const Geo& g, int dim, int
   b += sizeof(float) * xtab_words(nxb);                     // x tables
   b += sizeof(AxisEntry) * (g.tile[1] + g.tile[2]);         // y, z tables
   b += sizeof(float) * g.tile[2] * dim * g.hf[1] * g.hf[0]; // CZ
+  b += sizeof(unsigned);                                    // tile displacement bound
   return b;
 }
 
@@ -417,9 +423,19 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
   // the z-contraction of the coefficients (global loads issued first), the
   // bin maps, the x table and the clearing of the first pass's accumulators
   // (16-byte stores; 2 * NPY * S is a multiple of 4 words).
+  // The tile's displacement bound: the largest |entry| of CZ bounds every
+  // row's coefficient table (non-negative y weights summing to one).
+  unsigned* tile_u = reinterpret_cast<unsigned*>(CZ + g.tile[2] * DIM * g.hf[1] * g.hf[0]);
+  if (threadIdx.x == 0) *tile_u = 0u;
   build_axis_tables<DIM>(g, TO, yt, zt);
   __syncthreads();
-  build_cz<DIM>(g, TO, c, zt, CZ);
+  {
+    const unsigned mx = build_cz<DIM>(g, TO, c, zt, CZ);
+    if (SKIP && rowdist) {
+      const unsigned wmx = __reduce_max_sync(0xffffffffu, mx);
+      if (lane == 0) atomicMax(tile_u, wmx);
+    }
+  }
   int cnt = 0;                                // compacted bins of this tile
   {
     const int words = (nb + 31) >> 5;
@@ -469,18 +485,60 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
       if (xn < g.n[0]) *aa = ldval(A + ((long long)z * g.n[1] + y) * g.n[0] + xn);
       return true;
     };
+    // The warp's rows are row = warp + k * kAccWarps.  On levels with the
+    // per-row distances, a row farther than the tile's displacement bound
+    // + 3 from the nonzero moving image is empty whatever its own bound (it
+    // is at most the tile's): the warp reads the distances of 32 of its
+    // rows at a time, records those rows as having no moving-image
+    // gradient and visits only the others (each then takes the exact
+    // per-row test below).
+    const bool scan = SKIP && rowdist != nullptr;   // CTA-uniform
+    const float Ut = __uint_as_float(*tile_u);
+    unsigned cand = 0;                          // candidates kb .. kb + 31 not yet visited
+    int kb = -32;
+    auto refill = [&]() {
+      kb += 32;
+      const int r = warp + (kb + lane) * kAccWarps;
+      bool cnd = false;
+      if (r < nrows) {
+        const int zr = r / g.tile[1], yr = r - zr * g.tile[1];
+        const int y = TO.o[1] + yr, z = TO.o[2] + zr;
+        if (y < g.n[1] && z < g.n[2]) {
+          const long long rowid = ((long long)z * g.n[1] + y) * nxb + (TO.o[0] >> 5);
+          cnd = !((float)rowdist[rowid] > Ut + kDeadRowMargin);   // NaN bound: kept
+          if (!cnd && rowlive) rowlive[rowid] = 0;
+        }
+      }
+      cand = __ballot_sync(0xffffffffu, cnd);
+    };
+    auto next_candidate = [&]() {
+      while (cand == 0) {
+        if (warp + (kb + 32) * kAccWarps >= nrows) return nrows;   // warp-uniform
+        refill();
+      }
+      const int b = __ffs(cand) - 1;
+      cand &= cand - 1;
+      return warp + (kb + b) * kAccWarps;
+    };
     int p_next, d_next;
     float a_next;
-    int yn = 0, zn = 0;                         // row = zn * tile[1] + yn
-    row_step(warp, g.tile[1], &yn, &zn);
+    int row = scan ? next_candidate() : warp;   // row = zn * tile[1] + yn
+    int zn = row / g.tile[1], yn = row - zn * g.tile[1];
     bool ok_next = fetch(yn, zn, &p_next, &a_next, &d_next);
-    for (int row = warp; row < nrows; row += kAccWarps) {
+    while (row < nrows) {
       const int p = p_next;
       const float a_lane = a_next;
       const int rdist = d_next;
       const bool ok = ok_next;
       const int yl = yn, zl = zn;
-      row_step(kAccWarps, g.tile[1], &yn, &zn);
+      if (scan) {
+        row = next_candidate();
+        zn = row / g.tile[1];
+        yn = row - zn * g.tile[1];
+      } else {
+        row += kAccWarps;
+        row_step(kAccWarps, g.tile[1], &yn, &zn);
+      }
       ok_next = fetch(yn, zn, &p_next, &a_next, &d_next);
       if (!ok) continue;  // warp-uniform
       const int y = TO.o[1] + yl, z = TO.o[2] + zl;
