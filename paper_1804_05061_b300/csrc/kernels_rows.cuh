@@ -128,9 +128,12 @@ __device__ __forceinline__ XTab xtab_carve(float* base, int nxb) {
   return t;
 }
 
+// Built by the 32 threads from `first` on (the callers pass the last warp,
+// whose share of the other prologue work is the smallest).
 template <int NXB>
-__device__ __forceinline__ void build_xtab(const Geo& g, const TileOrigin& T, XTab xt) {
-  for (int p = threadIdx.x; p < 32; p += blockDim.x) {
+__device__ __forceinline__ void build_xtab(const Geo& g, const TileOrigin& T, XTab xt, int first) {
+  const int p = (int)threadIdx.x - first;
+  if (p >= 0 && p < 32) {
     AxisEntry e;
     axis_entry(g, 0, min(T.o[0] + p, g.n[0] - 1), T.f[0], T.cb[0], &e);
     xt.frel[p] = e.frel;
@@ -451,7 +454,7 @@ __device__ __forceinline__ void acc_rows_body(const Geo& g, const AccArgs& args,
       if (used) c2a[before] = a;
     }
   }
-  build_xtab<NXB>(g, TO, xt);
+  build_xtab<NXB>(g, TO, xt, (int)blockDim.x - 32);
   const int hwords4 = (2 * NPY * S) >> 2;
   uint4* h4 = reinterpret_cast<uint4*>(hlo);
   for (int i = threadIdx.x; i < hwords4; i += blockDim.x) h4[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -882,7 +885,7 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
   const float4* __restrict__ bg = args.bg;  // CTA-uniform: stored warp or recompute
   const TileOrigin TO = tile_setup<DIM>(g, tile);
   for (int i = threadIdx.x; i < DIM * nodes_tile; i += blockDim.x) gt[i] = 0.f;
-  build_xtab<NXB>(g, TO, xt);
+  build_xtab<NXB>(g, TO, xt, (int)blockDim.x - 32);
   build_axis_tables<DIM>(g, TO, yt, zt);
   // Region tables contracted over z for each of the tile's z-planes, read
   // from the per-plane tables of k_zcontract (in the same phase as the axis

@@ -115,7 +115,7 @@ __device__ __forceinline__ void acc_rows_mas_a_body(const Geo& g, const AccArgsA
   build_axis_tables<DIM>(g, TO, yt, zt);
   __syncthreads();
   build_cz<DIM>(g, TO, c, zt, CZ);
-  build_xtab<NXB>(g, TO, xt);
+  build_xtab<NXB>(g, TO, xt, (int)blockDim.x - 32);
   const int hwords4 = (2 * NPY * S) >> 2;
   uint4* h4 = reinterpret_cast<uint4*>(hlo);
   for (int i = threadIdx.x; i < hwords4; i += blockDim.x) h4[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -369,7 +369,7 @@ __device__ __forceinline__ void adj_rows_mas_a_body(const Geo& g, const AdjArgsA
 
   const TileOrigin TO = tile_setup<DIM>(g, tile);
   for (int i = threadIdx.x; i < DIM * nodes_tile; i += blockDim.x) gt[i] = 0.f;
-  build_xtab<NXB>(g, TO, xt);
+  build_xtab<NXB>(g, TO, xt, (int)blockDim.x - 32);
   build_axis_tables<DIM>(g, TO, yt, zt);
   {
     // The tile's planes of the z-contracted table differences, every bin.
