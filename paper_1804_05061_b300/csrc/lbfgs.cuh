@@ -278,8 +278,7 @@ srwcr_status eval_queue(srwcr_ctx* ctx, int level, LbfgsWork& w, const float* x,
   if (w.rigid) {
     RET_IF(run_rigid(ctx, lv, x, g, w.ang_scale));
   } else {
-    RET_IF(run_value(ctx, lv, x, true));
-    RET_IF(run_grad(ctx, lv, x, nullptr, g, true));
+    RET_IF(run_value_and_grad(ctx, lv, x, g));
     if (w.wp > 0.0) RET_IF(bending_energy(ctx, level, x, w.Edev, g, (float)w.wp));
   }
   CK(cudaMemcpyAsync(w.host + 1, lv.D, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

@@ -124,6 +124,10 @@ struct srwcr_ctx {
   int nlev = 0;
   Level lev[4];
   cudaStream_t stream = nullptr;
+  // A value+gradient call sums D on this second stream while the gradient
+  // runs (fork after the finalisation, join before anything reads D).
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int device = 0;
   double* D_host = nullptr;   // pinned
   int* flag_host = nullptr;   // pinned
@@ -644,7 +648,8 @@ void launch_finalize_sparse(srwcr_ctx* ctx, const Level& lv) {
 
 // (a) + (b): value into lv.D, tables into lv.U/V/X.  keep_warp: also store
 // the per-voxel warp for a following run_grad(..., true) at the same c.
-srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c, bool keep_warp) {
+srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c, bool keep_warp,
+                       bool reduce = true) {
   const bool mas_a = ctx->cfg.role == SRWCR_ROLE_M_AS_A;
   const size_t sbytes = (size_t)lv.g.R * lv.g.nbins * (mas_a ? 3 : 2) * sizeof(unsigned long long);
   CK(cudaMemsetAsync(lv.S, 0, sbytes, ctx->stream));
@@ -663,8 +668,10 @@ srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c, bool keep_warp
   else
     launch_finalize_sparse(ctx, lv);
   CKL();
-  k_reduce_D<<<1, 1024, 0, ctx->stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg);
-  CKL();
+  if (reduce) {
+    k_reduce_D<<<1, 1024, 0, ctx->stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg);
+    CKL();
+  }
   prof_end(ctx, kProfFinalize, ev);
   ctx->launches += 3;
   lv.tables = true;
@@ -682,6 +689,24 @@ srwcr_status run_grad(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD
   prof_end(ctx, kProfAdjoint, ev);
   ctx->launches += 1;
   return SRWCR_OK;
+}
+
+// Value and gradient at the same c (the warp kept by the value pass where
+// the level keeps it).  The value's final sum only feeds D, so it runs on
+// the auxiliary stream beside the table contraction and the adjoint; the
+// context's stream waits for it before returning, so whatever follows on
+// that stream (D copies, line-search tests, a graph's end) sees D.  Inside
+// a stream capture the fork and join become graph edges.
+srwcr_status run_value_and_grad(srwcr_ctx* ctx, Level& lv, const float* c, float* g) {
+  RET_IF(run_value(ctx, lv, c, true, false));
+  CK(cudaEventRecord(ctx->fork_ev, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->aux_stream, ctx->fork_ev, 0));
+  k_reduce_D<<<1, 1024, 0, ctx->aux_stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg);
+  CKL();
+  CK(cudaEventRecord(ctx->join_ev, ctx->aux_stream));
+  const srwcr_status st = run_grad(ctx, lv, c, nullptr, g, true);
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0));
+  return st;
 }
 
 // Rigid model on the general kernels of the level: value into lv.D (and
@@ -1033,6 +1058,9 @@ void srwcr_destroy(srwcr_ctx* ctx) {
   if (ctx->host_graph) cudaGraphExecDestroy(ctx->host_graph);
   if (ctx->async_graph) cudaGraphExecDestroy(ctx->async_graph);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   for (int l = 0; l < ctx->nlev; ++l) free_level(ctx->lev[l]);
   if (ctx->D_host) cudaFreeHost(ctx->D_host);
   if (ctx->flag_host) cudaFreeHost(ctx->flag_host);
@@ -1056,6 +1084,9 @@ static srwcr_status create_impl(const srwcr_config* cfg, const float* fixed, con
   CK(cudaMallocHost((void**)&ctx->flag_host, sizeof(int)));
   ctx->flag_host[0] = 0;
   CK(cudaMalloc((void**)&ctx->flag_dev, sizeof(int)));
+  CK(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming));
   RET_IF(set_smem_limits<float>());
   RET_IF(set_smem_limits<__nv_bfloat16>());
   const size_t esz = is_bf16(ctx) ? 2 : 4;
@@ -1311,8 +1342,7 @@ srwcr_status srwcr_value_and_grad(srwcr_ctx* ctx, int level, const float* c_dev,
   if (!c_dev || !g_dev) return fail(SRWCR_EINVAL, "null device pointer");
   Level& lv = ctx->lev[level];
   RET_IF(check_finite_async(ctx, c_dev, lv.g.ncoef * ctx->cfg.ndim));
-  RET_IF(run_value(ctx, lv, c_dev, true));
-  RET_IF(run_grad(ctx, lv, c_dev, nullptr, g_dev, true));
+  RET_IF(run_value_and_grad(ctx, lv, c_dev, g_dev));
   return finish_sync(ctx, lv, D_host);
 }
 
@@ -1322,8 +1352,7 @@ namespace {
 // D copied out.
 srwcr_status queue_async_call(srwcr_ctx* ctx, Level& lv, const float* c_dev, double* D_dev,
                               float* g_dev) {
-  RET_IF(run_value(ctx, lv, c_dev, true));
-  RET_IF(run_grad(ctx, lv, c_dev, nullptr, g_dev, true));
+  RET_IF(run_value_and_grad(ctx, lv, c_dev, g_dev));
   CK(cudaMemcpyAsync(D_dev, lv.D, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   return SRWCR_OK;
 }
@@ -1412,8 +1441,7 @@ srwcr_status queue_host_call(srwcr_ctx* ctx, Level& lv, int64_t np, const float*
                              float* g_host) {
   CK(cudaMemcpyAsync(ctx->c_stage, c_host, sizeof(float) * np, cudaMemcpyHostToDevice, ctx->stream));
   RET_IF(check_finite_async(ctx, ctx->c_stage, np));
-  RET_IF(run_value(ctx, lv, ctx->c_stage, true));
-  RET_IF(run_grad(ctx, lv, ctx->c_stage, nullptr, ctx->g_stage, true));
+  RET_IF(run_value_and_grad(ctx, lv, ctx->c_stage, ctx->g_stage));
   CK(cudaMemcpyAsync(g_host, ctx->g_stage, sizeof(float) * np, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(ctx->D_host, lv.D, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   return SRWCR_OK;
@@ -1893,13 +1921,11 @@ extern "C" srwcr_status srwcr_autotune(srwcr_ctx* ctx, int level, const float* c
       st = select_rows_path(ctx, lv, cand[i]);
       if (st != SRWCR_OK || !lv.rows) continue;
       for (int w = 0; w < 2 && st == SRWCR_OK; ++w) {
-        st = run_value(ctx, lv, c_dev, true);
-        if (st == SRWCR_OK) st = run_grad(ctx, lv, c_dev, nullptr, g, true);
+        st = run_value_and_grad(ctx, lv, c_dev, g);
       }
       cudaEventRecord(e0, ctx->stream);
       for (int r = 0; r < reps && st == SRWCR_OK; ++r) {
-        st = run_value(ctx, lv, c_dev, true);
-        if (st == SRWCR_OK) st = run_grad(ctx, lv, c_dev, nullptr, g, true);
+        st = run_value_and_grad(ctx, lv, c_dev, g);
       }
       cudaEventRecord(e1, ctx->stream);
       if (st != SRWCR_OK) break;
