@@ -697,11 +697,13 @@ srwcr_status run_grad(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD
 // context's stream waits for it before returning, so whatever follows on
 // that stream (D copies, line-search tests, a graph's end) sees D.  Inside
 // a stream capture the fork and join become graph edges.
-srwcr_status run_value_and_grad(srwcr_ctx* ctx, Level& lv, const float* c, float* g) {
+// D_host: optional device-mapped page-locked copy of D (see reduce_D_block).
+srwcr_status run_value_and_grad(srwcr_ctx* ctx, Level& lv, const float* c, float* g,
+                                double* D_host = nullptr) {
   RET_IF(run_value(ctx, lv, c, true, false));
   CK(cudaEventRecord(ctx->fork_ev, ctx->stream));
   CK(cudaStreamWaitEvent(ctx->aux_stream, ctx->fork_ev, 0));
-  k_reduce_D<<<1, 1024, 0, ctx->aux_stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg);
+  k_reduce_D<<<1, 1024, 0, ctx->aux_stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg, D_host);
   CKL();
   CK(cudaEventRecord(ctx->join_ev, ctx->aux_stream));
   const srwcr_status st = run_grad(ctx, lv, c, nullptr, g, true);
@@ -812,6 +814,21 @@ __global__ void k_check_finite(const float* __restrict__ c, long long n, int* __
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     if (!isfinite(c[i])) flag[0] = 1;
+}
+
+// Copies n coefficients from page-locked host memory (read through its
+// device mapping) into the device staging buffer, and stores 1 into the
+// mapped host flag if any is not finite (the host clears the flag before
+// the launch): the upload and the check of a host-buffer call in one kernel.
+__global__ void k_stage_checked(const float* src, float* __restrict__ dst, long long n, int* flag) {
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float v = src[i];
+    dst[i] = v;
+    bad |= !isfinite(v);
+  }
+  if (bad) *reinterpret_cast<volatile int*>(flag) = 1;
 }
 
 srwcr_status check_finite_async(srwcr_ctx* ctx, const float* c, long long n) {
@@ -1435,10 +1452,35 @@ bool host_page_locked(const void* p) {
   return a.type == cudaMemoryTypeHost;
 }
 
+// The device address of page-locked host memory (null if it has none).
+void* host_device_alias(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // One host-buffer call on ctx->stream: copy c in, check it, value and
 // gradient, copy g and D out (the caller synchronises).
+// With c_host and the context's flag and D words device-mapped (page-locked
+// buffers), one kernel uploads and checks c and the value's sum stores D
+// into host memory itself, so the call holds one copy (g) instead of four
+// copies and a memset; the host clears the flag before each launch.
 srwcr_status queue_host_call(srwcr_ctx* ctx, Level& lv, int64_t np, const float* c_host,
                              float* g_host) {
+  const float* c_map = static_cast<const float*>(host_device_alias(c_host));
+  int* flag_map = static_cast<int*>(host_device_alias(ctx->flag_host));
+  double* D_map = static_cast<double*>(host_device_alias(ctx->D_host));
+  if (c_map && flag_map && D_map) {
+    const int blocks = (int)std::min<int64_t>(4 * 148, (np + 255) / 256);
+    k_stage_checked<<<blocks, 256, 0, ctx->stream>>>(c_map, ctx->c_stage, np, flag_map);
+    CKL();
+    RET_IF(run_value_and_grad(ctx, lv, ctx->c_stage, ctx->g_stage, D_map));
+    CK(cudaMemcpyAsync(g_host, ctx->g_stage, sizeof(float) * np, cudaMemcpyDeviceToHost, ctx->stream));
+    return SRWCR_OK;
+  }
   CK(cudaMemcpyAsync(ctx->c_stage, c_host, sizeof(float) * np, cudaMemcpyHostToDevice, ctx->stream));
   RET_IF(check_finite_async(ctx, ctx->c_stage, np));
   RET_IF(run_value_and_grad(ctx, lv, ctx->c_stage, ctx->g_stage));
@@ -1503,6 +1545,7 @@ srwcr_status srwcr_value_and_grad_host(srwcr_ctx* ctx, int level, const float* c
   if (graph_ok && !(ctx->host_graph && ctx->host_graph_level == level &&
                     ctx->host_graph_c == c_host && ctx->host_graph_g == g_host))
     capture_host_call(ctx, level, np, c_host, g_host);
+  ctx->flag_host[0] = 0;   // set by the check if c holds a non-finite value
   if (graph_ok && ctx->host_graph) {
     CK(cudaGraphLaunch(ctx->host_graph, ctx->stream));
     ctx->launches += ctx->host_graph_launches;
