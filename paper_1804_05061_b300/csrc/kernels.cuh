@@ -338,12 +338,12 @@ __global__ void k_finalize(const Geo g, const double* __restrict__ P,
 }
 
 // Deterministic sum of the regions' shares (fixed partition, fixed tree).
-// D_host (may be null): page-locked host memory, device-mapped, that
-// receives D as well (a host-buffer call then needs no copy of D).
+// D_copy (may be null): a second place for D (the caller's device buffer,
+// or device-mapped page-locked host memory), so no copy of D follows.
 __device__ __forceinline__ void reduce_D_block(const double* __restrict__ Dr,
                                                const double* __restrict__ stats, long long R,
                                                double* __restrict__ D, int* __restrict__ ndeg,
-                                               double* D_host = nullptr) {
+                                               double* D_copy = nullptr) {
   __shared__ double sh[1024];
   __shared__ int shn[1024];
   double s = 0.0;
@@ -365,14 +365,14 @@ __device__ __forceinline__ void reduce_D_block(const double* __restrict__ Dr,
   if (threadIdx.x == 0) {
     D[0] = sh[0];
     ndeg[0] = shn[0];
-    if (D_host) *reinterpret_cast<volatile double*>(D_host) = sh[0];
+    if (D_copy) *reinterpret_cast<volatile double*>(D_copy) = sh[0];
   }
 }
 
 __global__ void __launch_bounds__(1024)
 k_reduce_D(const double* __restrict__ Dr, const double* __restrict__ stats, long long R,
-           double* __restrict__ D, int* __restrict__ ndeg, double* D_host = nullptr) {
-  reduce_D_block(Dr, stats, R, D, ndeg, D_host);
+           double* __restrict__ D, int* __restrict__ ndeg, double* D_copy = nullptr) {
+  reduce_D_block(Dr, stats, R, D, ndeg, D_copy);
 }
 
 // (c) Adjoint.  dD/dB(x) of Eq. (19) with the b-sums in closed form:

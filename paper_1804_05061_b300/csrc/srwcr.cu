@@ -697,13 +697,13 @@ srwcr_status run_grad(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD
 // context's stream waits for it before returning, so whatever follows on
 // that stream (D copies, line-search tests, a graph's end) sees D.  Inside
 // a stream capture the fork and join become graph edges.
-// D_host: optional device-mapped page-locked copy of D (see reduce_D_block).
+// D_copy: optional second place for D (see reduce_D_block).
 srwcr_status run_value_and_grad(srwcr_ctx* ctx, Level& lv, const float* c, float* g,
-                                double* D_host = nullptr) {
+                                double* D_copy = nullptr) {
   RET_IF(run_value(ctx, lv, c, true, false));
   CK(cudaEventRecord(ctx->fork_ev, ctx->stream));
   CK(cudaStreamWaitEvent(ctx->aux_stream, ctx->fork_ev, 0));
-  k_reduce_D<<<1, 1024, 0, ctx->aux_stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg, D_host);
+  k_reduce_D<<<1, 1024, 0, ctx->aux_stream>>>(lv.Dr, lv.stats, lv.g.R, lv.D, lv.ndeg, D_copy);
   CKL();
   CK(cudaEventRecord(ctx->join_ev, ctx->aux_stream));
   const srwcr_status st = run_grad(ctx, lv, c, nullptr, g, true);
@@ -1366,11 +1366,10 @@ srwcr_status srwcr_value_and_grad(srwcr_ctx* ctx, int level, const float* c_dev,
 namespace {
 
 // One device-buffer call on ctx->stream: value (keeping the warp), gradient,
-// D copied out.
+// and D, which the value's final sum also stores into D_dev.
 srwcr_status queue_async_call(srwcr_ctx* ctx, Level& lv, const float* c_dev, double* D_dev,
                               float* g_dev) {
-  RET_IF(run_value_and_grad(ctx, lv, c_dev, g_dev));
-  CK(cudaMemcpyAsync(D_dev, lv.D, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  RET_IF(run_value_and_grad(ctx, lv, c_dev, g_dev, D_dev));
   return SRWCR_OK;
 }
 
