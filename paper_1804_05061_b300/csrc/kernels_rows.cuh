@@ -1258,10 +1258,16 @@ __device__ __forceinline__ void zcontract_item(const Geo& g, long long i, const 
 template <int DIM>
 __global__ void __launch_bounds__(256)
 k_zcontract(const Geo g, const int* __restrict__ ubins, int nu, const float* __restrict__ U,
-            const float* __restrict__ V, const float* __restrict__ X, float* __restrict__ out) {
+            const float* __restrict__ V, const float* __restrict__ X, float* __restrict__ out,
+            float* __restrict__ zero, long long nzero) {
+  // Also clears the nzero floats at `zero` (the gradient the adjoint that
+  // follows accumulates into), which saves the step a memset.
   const long long n = zcontract_items(g, nu);
-  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
-    zcontract_item<DIM>(g, i, ubins, nu, U, V, X, out);
+  const long long m = n > nzero ? n : nzero;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < m; i += (long long)gridDim.x * 256) {
+    if (i < n) zcontract_item<DIM>(g, i, ubins, nu, U, V, X, out);
+    if (i < nzero) zero[i] = 0.f;
+  }
 }
 
 // Static L-infinity distance (voxels, capped at kRowDistCap) from each voxel

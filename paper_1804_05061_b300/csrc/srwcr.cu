@@ -441,12 +441,16 @@ srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const flo
   }
   if (lv.rows) {
     // Per-plane z-contraction of the region tables, then the adjoint.
-    const long long nz = zcontract_items(lv.g, lv.nu);
+    // The contraction also clears g (see run_grad).
+    const long long ng = lv.g.ncoef * ctx->cfg.ndim;
+    const long long nz = std::max(zcontract_items(lv.g, lv.nu), ng);
     const int zb = (int)std::min<long long>(148 * 16, (nz + 255) / 256);
     if (ctx->cfg.ndim == 3)
-      k_zcontract<3><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.ubins, lv.nu, lv.U, lv.V, lv.X, lv.uvxz);
+      k_zcontract<3><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.ubins, lv.nu, lv.U, lv.V, lv.X, lv.uvxz,
+                                                  g, ng);
     else
-      k_zcontract<2><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.ubins, lv.nu, lv.U, lv.V, lv.X, lv.uvxz);
+      k_zcontract<2><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.ubins, lv.nu, lv.U, lv.V, lv.X, lv.uvxz,
+                                                  g, ng);
     CKL();
     ctx->launches += 1;
     if (ctx->cfg.ndim == 3) launch_rows_adj<3, T>(ctx, lv, c, gD, g, nblk, kept_warp);
@@ -682,7 +686,10 @@ srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c, bool keep_warp
 // at the same coefficients instead of recomputing it.
 srwcr_status run_grad(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g,
                       bool kept_warp) {
-  CK(cudaMemsetAsync(g, 0, sizeof(float) * lv.g.ncoef * ctx->cfg.ndim, ctx->stream));
+  // On row-kernel levels with the moving image as B the table contraction
+  // that precedes the adjoint clears g itself.
+  if (!(lv.rows && ctx->cfg.role == SRWCR_ROLE_M_AS_B))
+    CK(cudaMemsetAsync(g, 0, sizeof(float) * lv.g.ncoef * ctx->cfg.ndim, ctx->stream));
   cudaEvent_t ev = prof_begin(ctx);
   RET_IF(is_bf16(ctx) ? launch_adjoint<__nv_bfloat16>(ctx, lv, c, gD, g, kept_warp)
                       : launch_adjoint<float>(ctx, lv, c, gD, g, kept_warp));
