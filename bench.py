@@ -168,6 +168,19 @@ def oracle_full_eval(pair, c, storage="f32"):
             "n_degenerate": int(st.n_degenerate), "degenerate_p_mass": float(st.pr[deg].sum())}
 
 
+def workload_text(pair):
+    """What the workload is: image shape, content, FFD spacing, spatial and
+    intensity bins."""
+    prob = pair.prob
+    kind = {"c1": "2-D ellipse phantom pair", "c2": "CT-shaped pair", "c3": "OCT-shaped pair (speckled layers)",
+            "c5": "CT-shaped pair"}.get(pair.name[:2], "pair")
+    shape = "x".join(str(d) for d in prob.dims[:prob.ndim])
+    sb = prob.sbin_intervals[:prob.ndim]
+    bins = "spatial bins on the FFD grid" if not any(sb) else f"spatial bins {tuple(sb)} intervals"
+    return (f"{shape} {kind}, FFD spacing {prob.ffd_spacing[0]}, {bins}, "
+            f"{prob.n_bins} intensity bins")
+
+
 def slab(pair, nz):
     """Sub-volume (the middle nz slices) as a bounded sample of a 3-D
     workload."""
@@ -827,10 +840,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-            "config": {"workload": f"{pair.name}: {prob.dims[0]}x{prob.dims[1]}x{prob.dims[2]} "
-                       f"CT-shaped pair, FFD spacing {prob.ffd_spacing[0]}, spatial bins "
-                       f"{prob.sbin_intervals[:prob.ndim]} intervals, {prob.n_bins} intensity "
-                       "bins, M as B, finest level",
+            "config": {"workload": f"{pair.name}: {workload_text(pair)}, M as B, finest level",
                        "storage": args.storage, "tile": list(tile),
                        "kernel_path": "row-parallel" if lv.kernel_path else "general",
                        "n_voxels": prob.n_voxels,
