@@ -79,7 +79,13 @@ def test_fifty_lbfgs_iterations_decrease_and_agree_with_oracle(c1):
     assert all(f1 <= f0 for f0, f1 in zip(fs, fs[1:]))
     assert Dg < 0.9 * D0 and res.f < 0.9 * D0
     # Same method, different arithmetic (FP32 vectors vs FP64): the runs end
-    # at nearby values.
+    # at nearby values.  The iteration is chaotic at the rounding level (the
+    # FP64 oracle with its iterate rounded to FP32 drifts from itself by 5e-3
+    # in D after 9 iterations, and three identical 50-iteration GPU runs end
+    # at D = 0.19207, 0.19270, 0.19247 because the gradient's FP32 atomics add
+    # in a run-dependent order), so after 50 iterations only closeness of the
+    # final values is a meaningful bar; iterations 1-6 and the two-loop
+    # direction are pinned tightly in test_gpu_lbfgs_pyramid.py.
     assert abs(Dg - res.f) <= 2e-2 * res.f, (Dg, res.f)
 
 
