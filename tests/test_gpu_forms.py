@@ -84,8 +84,9 @@ def test_fifty_lbfgs_iterations_decrease_and_agree_with_oracle(c1):
     # in D after 9 iterations, and three identical 50-iteration GPU runs end
     # at D = 0.19207, 0.19270, 0.19247 because the gradient's FP32 atomics add
     # in a run-dependent order), so after 50 iterations only closeness of the
-    # final values is a meaningful bar; iterations 1-6 and the two-loop
-    # direction are pinned tightly in test_gpu_lbfgs_pyramid.py.
+    # final values is a meaningful bar (four GPU runs measured 2.6e-4, 8.0e-3,
+    # 1.8e-3 and 3.6e-3 from the oracle's final D); iterations 1-6 and the
+    # two-loop direction are pinned tightly in test_gpu_lbfgs_pyramid.py.
     assert abs(Dg - res.f) <= 2e-2 * res.f, (Dg, res.f)
 
 
