@@ -268,6 +268,33 @@ def test_host_buffer_entry_point_with_page_locked_buffers_replays_one_graph(smal
     assert e.value_and_grad_host(cp.numpy(), gp.numpy()) == D2
 
 
+def test_host_buffer_entry_point_with_one_page_locked_buffer(small_cases):
+    # A page-locked c with a pageable g: no graph (that needs both buffers
+    # page-locked), c uploaded and checked through its device mapping, D
+    # stored into mapped host memory; a pageable c with a page-locked g takes
+    # the copy path.  Both equal the device entry point, and a non-finite c is
+    # reported on either path.
+    import paper_1804_05061_b300 as eng
+    prob, f, m, c = small_cases["ct_3d_ragged"]
+    e = engine_for(prob, f, m)
+    D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+    g_ref = g.cpu().numpy().ravel()
+    tol = 1e-7 * float(np.abs(g_ref).max())
+    cp = torch.from_numpy(np.ascontiguousarray(c.ravel())).pin_memory()
+    g_pageable = np.zeros(c.size, np.float32)
+    assert e.value_and_grad_host(cp.numpy(), g_pageable) == D
+    assert np.allclose(g_pageable, g_ref, rtol=1e-5, atol=tol)
+    gp = torch.zeros_like(cp).pin_memory()
+    c_pageable = np.ascontiguousarray(c.ravel()).copy()
+    assert e.value_and_grad_host(c_pageable, gp.numpy()) == D
+    assert np.allclose(gp.numpy(), g_ref, rtol=1e-5, atol=tol)
+    bad = cp.clone().pin_memory()
+    bad[5] = float("inf")
+    with pytest.raises(eng.SrwcrError, match="ENUMERIC"):
+        e.value_and_grad_host(bad.numpy(), g_pageable)
+    assert e.value_and_grad_host(cp.numpy(), g_pageable) == D
+
+
 def test_exact_functional_dependence_gives_zero_on_gpu():
     prob = synth.problem(3, (40, 36, 20), (5, 5, 5), (3, 3, 2), 16)
     rng = np.random.default_rng(3)
