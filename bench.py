@@ -729,8 +729,10 @@ def main():
     c_host, g_host = c_pin.numpy(), g_pin.numpy()
     for _ in range(2):
         e.value_and_grad_host(c_host, g_host)
+    # 200 synchronising calls (about 50 ms at the 256x256x96 workload): with a
+    # few milliseconds of timed work a single host stall would dominate.
+    n_e2e = max(200, args.steps)
     te = time.perf_counter()
-    n_e2e = max(3, min(args.steps, 20))
     for _ in range(n_e2e):
         e.value_and_grad_host(c_host, g_host)
     te = max_over_ranks(time.perf_counter() - te, dist, dev)
