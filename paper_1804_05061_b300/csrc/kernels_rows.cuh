@@ -1255,18 +1255,57 @@ __device__ __forceinline__ void zcontract_item(const Geo& g, long long i, const 
   out[o] = s;
 }
 
+// Block (x, z) takes a share of image plane z's entries; the plane's z cell
+// and weights are formed once per block (an item of zcontract_item forms
+// them itself), with the same terms in the same order.  The blocks also
+// clear the nzero floats at `zero` (the gradient the adjoint that follows
+// accumulates into), which saves the step a memset.
 template <int DIM>
 __global__ void __launch_bounds__(256)
 k_zcontract(const Geo g, const int* __restrict__ ubins, int nu, const float* __restrict__ U,
             const float* __restrict__ V, const float* __restrict__ X, float* __restrict__ out,
             float* __restrict__ zero, long long nzero) {
-  // Also clears the nzero floats at `zero` (the gradient the adjoint that
-  // follows accumulates into), which saves the step a memset.
-  const long long n = zcontract_items(g, nu);
-  const long long m = n > nzero ? n : nzero;
-  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < m; i += (long long)gridDim.x * 256) {
-    if (i < n) zcontract_item<DIM>(g, i, ubins, nu, U, V, X, out);
-    if (i < nzero) zero[i] = 0.f;
+  __shared__ AxisEntry ze;
+  const int z = blockIdx.y;
+  if (threadIdx.x == 0) {
+    if (DIM == 3) axis_entry(g, 2, z, 0, 0, &ze);
+    else axis_unit(&ze);
+  }
+  const long long nthr = (long long)gridDim.x * gridDim.y * 256;
+  for (long long i = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 256 + threadIdx.x; i < nzero;
+       i += nthr)
+    zero[i] = 0.f;
+  __syncthreads();
+  const AxisEntry e = ze;
+  const int nb = g.nbins;
+  const long long P1 = (long long)g.nsb[1] * g.nsb[0];
+  const long long nzp = (long long)g.n[2] * P1;
+  const long long per = (2 + nu) * P1;           // entries of one plane
+  const int NZ = DIM == 3 ? 4 : 1;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < per; i += (long long)gridDim.x * 256) {
+    int col;
+    long long rr, o;
+    if (i < 2 * P1) {
+      col = (int)(i / P1);
+      rr = i - col * P1;
+      o = col * nzp + (long long)z * P1 + rr;
+    } else {
+      const long long r = i - 2 * P1;
+      rr = r / nu;
+      const int a = __ldg(ubins + (r - rr * nu));
+      col = 2 + a;
+      o = 2 * nzp + ((long long)z * P1 + rr) * nb + a;
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < NZ; ++q) {
+      const int r2 = e.srel + q;
+      if (r2 >= g.nsb[2]) continue;
+      const long long r = r2 * P1 + rr;
+      const float tv = col == 0 ? __ldg(U + r) : (col == 1 ? __ldg(V + r) : __ldg(X + r * nb + (col - 2)));
+      s += e.bs[q] * tv;
+    }
+    out[o] = s;
   }
 }
 

@@ -441,16 +441,19 @@ srwcr_status launch_adjoint(srwcr_ctx* ctx, Level& lv, const float* c, const flo
   }
   if (lv.rows) {
     // Per-plane z-contraction of the region tables, then the adjoint.
-    // The contraction also clears g (see run_grad).
+    // The contraction also clears g (see run_grad).  Blocks of 256 threads,
+    // about 2 entries per thread (each entry waits on L2 loads), per image
+    // plane.
     const long long ng = lv.g.ncoef * ctx->cfg.ndim;
-    const long long nz = std::max(zcontract_items(lv.g, lv.nu), ng);
-    const int zb = (int)std::min<long long>(148 * 16, (nz + 255) / 256);
+    const long long per = (2LL + lv.nu) * lv.g.nsb[1] * lv.g.nsb[0];
+    const dim3 zgrid((unsigned)std::max<long long>(1, std::min<long long>(128, (per + 511) / 512)),
+                     (unsigned)lv.g.n[2]);
     if (ctx->cfg.ndim == 3)
-      k_zcontract<3><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.ubins, lv.nu, lv.U, lv.V, lv.X, lv.uvxz,
-                                                  g, ng);
+      k_zcontract<3><<<zgrid, 256, 0, ctx->stream>>>(lv.g, lv.ubins, lv.nu, lv.U, lv.V, lv.X, lv.uvxz,
+                                                     g, ng);
     else
-      k_zcontract<2><<<zb, 256, 0, ctx->stream>>>(lv.g, lv.ubins, lv.nu, lv.U, lv.V, lv.X, lv.uvxz,
-                                                  g, ng);
+      k_zcontract<2><<<zgrid, 256, 0, ctx->stream>>>(lv.g, lv.ubins, lv.nu, lv.U, lv.V, lv.X, lv.uvxz,
+                                                     g, ng);
     CKL();
     ctx->launches += 1;
     if (ctx->cfg.ndim == 3) launch_rows_adj<3, T>(ctx, lv, c, gD, g, nblk, kept_warp);
