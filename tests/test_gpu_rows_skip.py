@@ -81,3 +81,30 @@ def test_kept_and_recomputed_warp_agree(storage):
     torch.cuda.synchronize()
     assert float(D_dev) == Dk
     assert float((gb - gk).abs().max()) <= 1e-5 * scale
+
+
+def test_row_records_follow_the_coefficients_across_evaluations():
+    # One engine evaluated at small, large, spatially mixed (large
+    # displacements on half of the control grid only, so some tiles' bounds
+    # skip most rows and others none) and again small coefficients: the rows
+    # skipped before any load, the rows skipped by their own bound and the
+    # adjoint's per-row records are all re-derived at every evaluation, and
+    # each result matches the oracle at its coefficients.
+    prob = synth.problem(3, (96, 80, 40), (6, 6, 5), (3, 3, 2), 32)
+    f, m = synth.small_pair("ct", prob.dims, prob.ffd_spacing, 2.0, 71)
+    small = synth.coefficients(prob, 75, 0.5)
+    large = synth.coefficients(prob, 76, 6.0)
+    mixed = small.copy()
+    half = prob.coef_shape[-1] // 2
+    mixed[..., :half] = large[..., :half]
+    e = engine(prob, f, m)
+    geo = oracle.Geometry.from_problem(prob)
+    A, M = oracle.prepare(f, m, prob.n_bins)
+    for c in (small, large, mixed, small):
+        D, g = e.value_and_grad(torch.from_numpy(c).cuda())
+        st = oracle.value(geo, A, M, c)
+        go = oracle.gradient(geo, A, M, c, st)
+        assert abs(D - st.D) <= D_RTOL * st.D, (D, st.D)
+        g = g.cpu().numpy().astype(np.float64)
+        assert abs(np.linalg.norm(g) - np.linalg.norm(go)) <= GNORM_RTOL * np.linalg.norm(go)
+        assert np.abs(g - go).max() <= G_ELEM * np.abs(go).max()
