@@ -640,12 +640,18 @@ int finalize_lanes_auto(const std::vector<const std::vector<int>*>& lists, int d
     default: CALL(32); break;           \
   }
 
+// Two warps per block: the kernel's groups of G lanes are independent (no
+// shared memory, no block barrier), and small blocks spread its few warps
+// over every SM's FP64 unit (256-thread blocks left most SMs idle: 53 blocks
+// for 847 regions at 16 lanes).
+constexpr int kFinBlock = 64;
+
 void launch_finalize_sparse(srwcr_ctx* ctx, const Level& lv) {
   const long long threads = ((lv.g.R * lv.fin_lanes + 31) / 32) * 32;
-  const int blocks = (int)((threads + kBlock - 1) / kBlock);
+  const int blocks = (int)((threads + kFinBlock - 1) / kFinBlock);
   const RegionStatic rs = region_static(lv);
 #define SRWCR_FIN_CALL(G)                                                                 \
-  k_finalize_sparse<G><<<blocks, kBlock, 0, ctx->stream>>>(lv.g.R, lv.g.nbins, rs, lv.S,  \
+  k_finalize_sparse<G><<<blocks, kFinBlock, 0, ctx->stream>>>(lv.g.R, lv.g.nbins, rs, lv.S,  \
                                                            1.0 / lv.s1, 1.0 / lv.s2,       \
                                                            1.0 / lv.Z, lv.U, lv.V, lv.X, \
                                                            lv.Dr, lv.stats)
