@@ -640,10 +640,10 @@ int finalize_lanes_auto(const std::vector<const std::vector<int>*>& lists, int d
     default: CALL(32); break;           \
   }
 
-// Two warps per block: the kernel's groups of G lanes are independent (no
-// shared memory, no block barrier), and small blocks spread its few warps
-// over every SM's FP64 unit (256-thread blocks left most SMs idle: 53 blocks
-// for 847 regions at 16 lanes).
+// Two warps per block for the finalisations: their lane groups are
+// independent (no shared memory, no block barrier), and small blocks spread
+// their few warps over every SM's FP64 unit (256-thread blocks left most SMs
+// idle: 53 blocks for 847 regions at 16 lanes).
 constexpr int kFinBlock = 64;
 
 void launch_finalize_sparse(srwcr_ctx* ctx, const Level& lv) {
@@ -672,10 +672,10 @@ srwcr_status run_value(srwcr_ctx* ctx, Level& lv, const float* c, bool keep_warp
                    : launch_accumulate<float>(ctx, lv, c, false, lv.s1, lv.s2, keep_warp);
   if (st != SRWCR_OK) return st;
   prof_end(ctx, kProfAccumulate, ev);
-  const int fblk = (int)((lv.g.R * 32 + kBlock - 1) / kBlock);
+  const int fblk = (int)((lv.g.R * 32 + kFinBlock - 1) / kFinBlock);
   ev = prof_begin(ctx);
   if (mas_a)
-    k_finalize_mas_a<<<fblk, kBlock, 0, ctx->stream>>>(lv.g, lv.S, 1.0 / lv.s0, 1.0 / lv.s1,
+    k_finalize_mas_a<<<fblk, kFinBlock, 0, ctx->stream>>>(lv.g, lv.S, 1.0 / lv.s0, 1.0 / lv.s1,
                                                        1.0 / lv.s2, 1.0 / lv.Z, lv.X, lv.Y2, lv.DY, lv.Dr,
                                                        lv.stats);
   else
