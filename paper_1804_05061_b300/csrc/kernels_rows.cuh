@@ -1205,43 +1205,36 @@ k_adjoint_rows(const Geo g, const AdjArgs args) {
 // [U | V | X], U and V as [z][r1][r0] (P = nz * nsb1 * nsb0 plane-columns),
 // X as [z][r1][r0][a]; each entry is sum_q beta_q(z) T[(cell(z) + q, r1, r0)]
 // (Eq. 7 weights along z; the same terms and order as a per-tile
-// contraction).  Item i enumerates the U and V entries and the X entries of
-// the nu fixed-image bins that occur anywhere in the image (ubins); the
-// adjoint reads no other X entry.
+// contraction).  Only the X entries of the nu fixed-image bins that occur
+// anywhere in the image (ubins) are formed; the adjoint reads no other.
 __host__ __device__ inline long long zcontract_len(const Geo& g) {
   return (long long)g.n[2] * g.nsb[1] * g.nsb[0] * (2 + g.nbins);
 }
 
-__host__ __device__ inline long long zcontract_items(const Geo& g, int nu) {
-  return (long long)g.n[2] * g.nsb[1] * g.nsb[0] * (2 + nu);
-}
-
+// Entry i of image plane z (weights e of that plane): i < 2 P enumerates U
+// and V over the plane's P = nsb1 * nsb0 spatial-bin columns, then X for the
+// nu bins of ubins per column.
 template <int DIM>
-__device__ __forceinline__ void zcontract_item(const Geo& g, long long i, const int* __restrict__ ubins,
-                                               int nu, const float* __restrict__ U,
-                                               const float* __restrict__ V,
-                                               const float* __restrict__ X, float* __restrict__ out) {
+__device__ __forceinline__ void zcontract_entry(const Geo& g, const AxisEntry& e, int z, long long i,
+                                                const int* __restrict__ ubins, int nu,
+                                                const float* __restrict__ U, const float* __restrict__ V,
+                                                const float* __restrict__ X, float* __restrict__ out) {
   const int nb = g.nbins;
   const long long P1 = (long long)g.nsb[1] * g.nsb[0];
   const long long nzp = (long long)g.n[2] * P1;
-  long long zr, o;
   int col;
-  if (i < 2 * nzp) {
-    col = (int)(i / nzp);
-    zr = i - col * nzp;
-    o = i;
+  long long rr, o;
+  if (i < 2 * P1) {
+    col = (int)(i / P1);
+    rr = i - col * P1;
+    o = col * nzp + (long long)z * P1 + rr;
   } else {
-    const long long r = i - 2 * nzp;
-    zr = r / nu;
-    const int a = __ldg(ubins + (r - zr * nu));
+    const long long r = i - 2 * P1;
+    rr = r / nu;
+    const int a = __ldg(ubins + (r - rr * nu));
     col = 2 + a;
-    o = 2 * nzp + zr * nb + a;
+    o = 2 * nzp + ((long long)z * P1 + rr) * nb + a;
   }
-  const int z = (int)(zr / P1);
-  const long long rr = zr - (long long)z * P1;
-  AxisEntry e;
-  if (DIM == 3) axis_entry(g, 2, z, 0, 0, &e);
-  else axis_unit(&e);
   const int NZ = DIM == 3 ? 4 : 1;
   float s = 0.f;
 #pragma unroll
@@ -1255,11 +1248,24 @@ __device__ __forceinline__ void zcontract_item(const Geo& g, long long i, const 
   out[o] = s;
 }
 
+// The plane's z cell and weights (Eq. 7 weights along z), formed by thread 0
+// into shared memory; every thread of the block must call it.
+template <int DIM>
+__device__ __forceinline__ AxisEntry zcontract_plane(const Geo& g, int z, AxisEntry* ze) {
+  __syncthreads();                              // earlier readers of *ze are done
+  if (threadIdx.x == 0) {
+    if (DIM == 3) axis_entry(g, 2, z, 0, 0, ze);
+    else axis_unit(ze);
+  }
+  __syncthreads();
+  return *ze;
+}
+
 // Block (x, z) takes a share of image plane z's entries; the plane's z cell
-// and weights are formed once per block (an item of zcontract_item forms
-// them itself), with the same terms in the same order.  The blocks also
-// clear the nzero floats at `zero` (the gradient the adjoint that follows
-// accumulates into), which saves the step a memset.
+// and weights are formed once per block, the entries summed with the same
+// terms in the same order as before.  The blocks also clear the nzero floats
+// at `zero` (the gradient the adjoint that follows accumulates into), which
+// saves the step a memset.
 template <int DIM>
 __global__ void __launch_bounds__(256)
 k_zcontract(const Geo g, const int* __restrict__ ubins, int nu, const float* __restrict__ U,
@@ -1267,46 +1273,14 @@ k_zcontract(const Geo g, const int* __restrict__ ubins, int nu, const float* __r
             float* __restrict__ zero, long long nzero) {
   __shared__ AxisEntry ze;
   const int z = blockIdx.y;
-  if (threadIdx.x == 0) {
-    if (DIM == 3) axis_entry(g, 2, z, 0, 0, &ze);
-    else axis_unit(&ze);
-  }
   const long long nthr = (long long)gridDim.x * gridDim.y * 256;
   for (long long i = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * 256 + threadIdx.x; i < nzero;
        i += nthr)
     zero[i] = 0.f;
-  __syncthreads();
-  const AxisEntry e = ze;
-  const int nb = g.nbins;
-  const long long P1 = (long long)g.nsb[1] * g.nsb[0];
-  const long long nzp = (long long)g.n[2] * P1;
-  const long long per = (2 + nu) * P1;           // entries of one plane
-  const int NZ = DIM == 3 ? 4 : 1;
-  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < per; i += (long long)gridDim.x * 256) {
-    int col;
-    long long rr, o;
-    if (i < 2 * P1) {
-      col = (int)(i / P1);
-      rr = i - col * P1;
-      o = col * nzp + (long long)z * P1 + rr;
-    } else {
-      const long long r = i - 2 * P1;
-      rr = r / nu;
-      const int a = __ldg(ubins + (r - rr * nu));
-      col = 2 + a;
-      o = 2 * nzp + ((long long)z * P1 + rr) * nb + a;
-    }
-    float s = 0.f;
-#pragma unroll
-    for (int q = 0; q < NZ; ++q) {
-      const int r2 = e.srel + q;
-      if (r2 >= g.nsb[2]) continue;
-      const long long r = r2 * P1 + rr;
-      const float tv = col == 0 ? __ldg(U + r) : (col == 1 ? __ldg(V + r) : __ldg(X + r * nb + (col - 2)));
-      s += e.bs[q] * tv;
-    }
-    out[o] = s;
-  }
+  const AxisEntry e = zcontract_plane<DIM>(g, z, &ze);
+  const long long per = (2 + nu) * (long long)g.nsb[1] * g.nsb[0];   // entries of one plane
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < per; i += (long long)gridDim.x * 256)
+    zcontract_entry<DIM>(g, e, z, i, ubins, nu, U, V, X, out);
 }
 
 // Static L-infinity distance (voxels, capped at kRowDistCap) from each voxel
