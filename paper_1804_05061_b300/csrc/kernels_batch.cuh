@@ -138,17 +138,11 @@ k_finalize_batch(const BatchPair* __restrict__ pairs, int n, long long total,
 template <int DIM>
 __global__ void __launch_bounds__(256)
 k_zcontract_batch(const BatchPair* __restrict__ pairs, const int* __restrict__ active) {
-  // The pair's blocks take its image planes in turn; a plane's z weights
-  // are formed once per block and plane.
   const BatchPair& bp = pairs[blockIdx.y];
-  if (!batch_active(active, bp.id)) return;   // block-uniform
-  __shared__ AxisEntry ze;
-  const long long per = (2 + bp.nu) * (long long)bp.g.nsb[1] * bp.g.nsb[0];
-  for (int z = blockIdx.x; z < bp.g.n[2]; z += gridDim.x) {
-    const AxisEntry e = zcontract_plane<DIM>(bp.g, z, &ze);
-    for (long long i = threadIdx.x; i < per; i += 256)
-      zcontract_entry<DIM>(bp.g, e, z, i, bp.ubins, bp.nu, bp.U, bp.V, bp.X, bp.uvxz);
-  }
+  if (!batch_active(active, bp.id)) return;
+  const long long n = zcontract_items(bp.g, bp.nu);
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+    zcontract_item<DIM>(bp.g, i, bp.ubins, bp.nu, bp.U, bp.V, bp.X, bp.uvxz);
 }
 
 // One block per table slot: D = sum of the region shares in a fixed order.

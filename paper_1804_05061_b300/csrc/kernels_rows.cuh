@@ -1211,6 +1211,53 @@ __host__ __device__ inline long long zcontract_len(const Geo& g) {
   return (long long)g.n[2] * g.nsb[1] * g.nsb[0] * (2 + g.nbins);
 }
 
+// The batched contraction enumerates entries over all planes at once (item
+// i), each item forming its plane's weights: with many pairs of uneven
+// plane counts in one launch, that keeps every block's threads on
+// independent entries.
+__host__ __device__ inline long long zcontract_items(const Geo& g, int nu) {
+  return (long long)g.n[2] * g.nsb[1] * g.nsb[0] * (2 + nu);
+}
+
+template <int DIM>
+__device__ __forceinline__ void zcontract_item(const Geo& g, long long i, const int* __restrict__ ubins,
+                                               int nu, const float* __restrict__ U,
+                                               const float* __restrict__ V,
+                                               const float* __restrict__ X, float* __restrict__ out) {
+  const int nb = g.nbins;
+  const long long P1 = (long long)g.nsb[1] * g.nsb[0];
+  const long long nzp = (long long)g.n[2] * P1;
+  long long zr, o;
+  int col;
+  if (i < 2 * nzp) {
+    col = (int)(i / nzp);
+    zr = i - col * nzp;
+    o = i;
+  } else {
+    const long long r = i - 2 * nzp;
+    zr = r / nu;
+    const int a = __ldg(ubins + (r - zr * nu));
+    col = 2 + a;
+    o = 2 * nzp + zr * nb + a;
+  }
+  const int z = (int)(zr / P1);
+  const long long rr = zr - (long long)z * P1;
+  AxisEntry e;
+  if (DIM == 3) axis_entry(g, 2, z, 0, 0, &e);
+  else axis_unit(&e);
+  const int NZ = DIM == 3 ? 4 : 1;
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < NZ; ++q) {
+    const int r2 = e.srel + q;
+    if (r2 >= g.nsb[2]) continue;
+    const long long r = r2 * P1 + rr;
+    const float tv = col == 0 ? __ldg(U + r) : (col == 1 ? __ldg(V + r) : __ldg(X + r * nb + (col - 2)));
+    s += e.bs[q] * tv;
+  }
+  out[o] = s;
+}
+
 // Entry i of image plane z (weights e of that plane): i < 2 P enumerates U
 // and V over the plane's P = nsb1 * nsb0 spatial-bin columns, then X for the
 // nu bins of ubins per column.
