@@ -155,11 +155,17 @@ srwcr_status srwcr_value_and_grad_async(srwcr_ctx* ctx, int level, const float* 
                                         double* D_dev, float* g_dev);
 
 /* End-to-end form with host buffers: copies c_host (n_params floats) to the
- * device, evaluates, copies g back to g_host and D to D_host.  Uses
- * context-owned staging buffers; host buffers may be pageable or pinned.
- * With page-locked buffers the whole call is captured as a CUDA graph on
- * first use for this (level, c_host, g_host) and replayed afterwards; the
- * graph is dropped when srwcr_autotune re-selects a level's kernels. */
+ * device, evaluates, copies g back to g_host (n_params floats) and D to
+ * D_host (may be NULL).  Uses context-owned staging buffers; host buffers
+ * may be pageable or pinned; the call synchronises.  A buffer counts as
+ * page-locked only if its first and last byte lie in page-locked memory
+ * mapped at one contiguous device range: then c is read by a kernel through
+ * that mapping, and with both buffers page-locked the whole call is captured
+ * as a CUDA graph on first use for this (level, c_host, g_host) and replayed
+ * afterwards (the graph is dropped when srwcr_autotune re-selects a level's
+ * kernels).  Buffers shorter than n_params floats are undefined behaviour.
+ * Errors: SRWCR_EINVAL for a bad level or a NULL buffer, SRWCR_ENUMERIC for a
+ * non-finite coefficient or value (g_host then holds no meaningful values). */
 srwcr_status srwcr_value_and_grad_host(srwcr_ctx* ctx, int level, const float* c_host,
                                        double* D_host, float* g_host);
 

@@ -267,14 +267,39 @@ class SRWCR:
         return self._torch.zeros(self.coef_shape(level), dtype=self._torch.float32,
                                  device=self.device)
 
-    def _c(self, c, level):
-        t = self._torch
-        if not (isinstance(c, t.Tensor) and c.is_cuda and c.dtype == t.float32):
-            raise TypeError("c must be a float32 CUDA tensor")
-        if c.numel() != self.levels[level].n_params:
-            raise ValueError(f"c has {c.numel()} entries, level {level} needs "
-                             f"{self.levels[level].n_params}")
-        return c.contiguous()
+    def _dev(self, t, n, dtype, name, inplace=False):
+        """t checked as a CUDA tensor of this engine's device holding n values
+        of dtype.  The library takes plain pointers and reads or writes
+        exactly n values: a buffer it writes (inplace) must be contiguous
+        itself; an input is passed as a contiguous copy if it is not."""
+        torch = self._torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype):
+            raise TypeError(f"{name} must be a {dtype} CUDA tensor")
+        if t.device != self.device:
+            raise ValueError(f"{name} is on {t.device}, the engine on {self.device}")
+        if t.numel() != n:
+            raise ValueError(f"{name} has {t.numel()} entries, needs {n}")
+        if inplace and not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous (the library writes it in place)")
+        return t if inplace else t.contiguous()
+
+    def _c(self, c, level, inplace=False):
+        return self._dev(c, self.levels[level].n_params, self._torch.float32,
+                         f"c (level {level})", inplace)
+
+    def _host(self, a, level, name, writes=False):
+        """a checked as a C-contiguous float32 NumPy array of the level's
+        coefficient count (the library copies exactly that many values)."""
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float32):
+            raise TypeError(f"{name} must be a float32 NumPy array")
+        n = self.levels[level].n_params
+        if a.size != n:
+            raise ValueError(f"{name} has {a.size} entries, level {level} needs {n}")
+        if not a.flags.c_contiguous:
+            raise ValueError(f"{name} must be C-contiguous")
+        if writes and not a.flags.writeable:
+            raise ValueError(f"{name} is read-only")
+        return a
 
     # -- evaluation --------------------------------------------------------
     def value(self, c, level: int = 0) -> float:
@@ -286,21 +311,31 @@ class SRWCR:
 
     def value_and_grad(self, c, level: int = 0, out=None):
         c = self._c(c, level)
-        g = self._torch.empty_like(c) if out is None else out
+        if out is None:
+            g = self._torch.empty_like(c)
+        else:
+            g = self._dev(out, c.numel(), self._torch.float32, "out", inplace=True)
         D = ctypes.c_double()
         _check(load().srwcr_value_and_grad(self._h, level, _ptr(c), ctypes.byref(D), _ptr(g)))
         self._gen[level] += 1
         return D.value, g
 
     def value_and_grad_async(self, c, D_out, g_out, level: int = 0):
-        """Queue value+gradient on the stream; D_out is a float64 CUDA scalar."""
+        """Queue value+gradient on the stream; D_out is a float64 CUDA scalar.
+        Every buffer is used in place (the call may be captured in a graph),
+        so c must be contiguous too."""
+        t = self._torch
+        c = self._c(c, level, inplace=True)
+        D_out = self._dev(D_out, 1, t.float64, "D_out", inplace=True)
+        g_out = self._dev(g_out, c.numel(), t.float32, "g_out", inplace=True)
         _check(load().srwcr_value_and_grad_async(self._h, level, _ptr(c), _ptr(D_out),
                                                  _ptr(g_out)))
         self._gen[level] += 1
 
     def value_and_grad_host(self, c_host: np.ndarray, g_host: np.ndarray, level: int = 0) -> float:
         """End-to-end call with host buffers (copies inside the library)."""
-        assert c_host.dtype == np.float32 and g_host.dtype == np.float32
+        c_host = self._host(c_host, level, "c_host")
+        g_host = self._host(g_host, level, "g_host", writes=True)
         D = ctypes.c_double()
         _check(load().srwcr_value_and_grad_host(
             self._h, level, c_host.ctypes.data_as(ctypes.c_void_p), ctypes.byref(D),
@@ -309,11 +344,18 @@ class SRWCR:
         return D.value
 
     def forward(self, c, D_out, level: int = 0) -> int:
+        c = self._c(c, level)
+        D_out = self._dev(D_out, 1, self._torch.float64, "D_out", inplace=True)
         _check(load().srwcr_forward(self._h, level, _ptr(c), _ptr(D_out)))
         self._gen[level] += 1
         return self._gen[level]
 
     def backward(self, c, gD, g_out, level: int = 0):
+        t = self._torch
+        c = self._c(c, level)
+        if gD is not None:
+            gD = self._dev(gD, 1, t.float32, "gD")
+        g_out = self._dev(g_out, c.numel(), t.float32, "g_out", inplace=True)
         _check(load().srwcr_backward(self._h, level, _ptr(c),
                                      _ptr(gD) if gD is not None else None, _ptr(g_out)))
 
@@ -373,11 +415,17 @@ class SRWCR:
         """d = -H g from the library's two-loop recursion; S, Y: (k, n)
         float32 CUDA tensors of (s, y) pairs, oldest first."""
         t = self._torch
-        g = g.contiguous().view(-1)
+        if not isinstance(g, t.Tensor):
+            raise TypeError("g must be a float32 CUDA tensor")
+        n = g.numel()
+        g = self._dev(g, n, t.float32, "g").view(-1)
         k = 0 if S is None else int(S.shape[0])
         d = t.empty_like(g)
-        S = S.contiguous() if k else None
-        Y = Y.contiguous() if k else None
+        if k:
+            if Y is None or tuple(S.shape) != (k, n) or tuple(Y.shape) != (k, n):
+                raise ValueError(f"S and Y must both be ({k}, {n})")
+            S = self._dev(S, k * n, t.float32, "S")
+            Y = self._dev(Y, k * n, t.float32, "Y")
         t.cuda.current_stream(self.device).synchronize()
         _check(load().srwcr_lbfgs_direction(self._h, g.numel(), k, _ptr(S) if k else None,
                                             _ptr(Y) if k else None, _ptr(g), _ptr(d)))
@@ -412,6 +460,9 @@ class SRWCR:
         """C_p of Eq. (1) at c (synchronises); if grad_into is given, adds
         weight * dC_p/dc to it."""
         c = self._c(c, level)
+        if grad_into is not None:
+            grad_into = self._dev(grad_into, c.numel(), self._torch.float32, "grad_into",
+                                  inplace=True)
         E = self._torch.zeros((), dtype=self._torch.float64, device=self.device)
         _check(load().srwcr_bending_energy(self._h, level, _ptr(c), _ptr(E),
                                            _ptr(grad_into) if grad_into is not None else None,
@@ -427,7 +478,7 @@ class SRWCR:
 
     def register(self, c, n_levels: int = 1, opts: Optional[LbfgsOpts] = None,
                  check: bool = True) -> Report:
-        c = self._c(c, 0)
+        c = self._c(c, 0, inplace=True)   # the result is written into c
         rep = Report()
         st = load().srwcr_register(self._h, _ptr(c), int(n_levels),
                                    ctypes.byref(opts) if opts is not None else None,

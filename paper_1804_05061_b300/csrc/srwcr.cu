@@ -1458,17 +1458,9 @@ srwcr_status srwcr_value_and_grad_async(srwcr_ctx* ctx, int level, const float* 
 
 namespace {
 
-bool host_page_locked(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeHost;
-}
-
-// The device address of page-locked host memory (null if it has none).
-void* host_device_alias(const void* p) {
+// The device address through which the page-locked host byte at p is
+// reached (null if p is not page-locked).
+void* host_byte_alias(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -1476,6 +1468,20 @@ void* host_device_alias(const void* p) {
   }
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
+
+// The device address of the n bytes at p (n > 0), or null unless both ends
+// lie in page-locked memory mapped at one contiguous device range: a buffer
+// that ends in pageable memory (shorter than the caller claims, or running
+// past its registration) is never read or written through the mapping or by
+// a direct copy, but takes the copy path through pageable memory.
+void* host_device_alias(const void* p, size_t n) {
+  char* a0 = static_cast<char*>(host_byte_alias(p));
+  if (!a0) return nullptr;
+  const char* a1 = static_cast<const char*>(host_byte_alias(static_cast<const char*>(p) + (n - 1)));
+  return a1 == a0 + (n - 1) ? a0 : nullptr;
+}
+
+bool host_page_locked(const void* p, size_t n) { return host_device_alias(p, n) != nullptr; }
 
 // One host-buffer call on ctx->stream: copy c in, check it, value and
 // gradient, copy g and D out (the caller synchronises).
@@ -1485,9 +1491,9 @@ void* host_device_alias(const void* p) {
 // copies and a memset; the host clears the flag before each launch.
 srwcr_status queue_host_call(srwcr_ctx* ctx, Level& lv, int64_t np, const float* c_host,
                              float* g_host) {
-  const float* c_map = static_cast<const float*>(host_device_alias(c_host));
-  int* flag_map = static_cast<int*>(host_device_alias(ctx->flag_host));
-  double* D_map = static_cast<double*>(host_device_alias(ctx->D_host));
+  const float* c_map = static_cast<const float*>(host_device_alias(c_host, sizeof(float) * np));
+  int* flag_map = static_cast<int*>(host_device_alias(ctx->flag_host, sizeof(int)));
+  double* D_map = static_cast<double*>(host_device_alias(ctx->D_host, sizeof(double)));
   if (c_map && flag_map && D_map) {
     const int blocks = (int)std::min<int64_t>(4 * 148, (np + 255) / 256);
     k_stage_checked<<<blocks, 256, 0, ctx->stream>>>(c_map, ctx->c_stage, np, flag_map);
@@ -1556,7 +1562,9 @@ srwcr_status srwcr_value_and_grad_host(srwcr_ctx* ctx, int level, const float* c
   }
   // Page-locked host buffers: replay the call from a CUDA graph (captured on
   // first use for this level and these buffers); otherwise queue it.
-  const bool graph_ok = !ctx->profiling && host_page_locked(c_host) && host_page_locked(g_host);
+  const size_t bytes = sizeof(float) * (size_t)np;
+  const bool graph_ok = !ctx->profiling && host_page_locked(c_host, bytes) &&
+                        host_page_locked(g_host, bytes);
   if (graph_ok && !(ctx->host_graph && ctx->host_graph_level == level &&
                     ctx->host_graph_c == c_host && ctx->host_graph_g == g_host))
     capture_host_call(ctx, level, np, c_host, g_host);

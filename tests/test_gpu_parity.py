@@ -330,6 +330,66 @@ def test_errors_are_reported_not_raised_as_crashes(small_cases):
     assert np.isfinite(D)
 
 
+def test_caller_buffers_are_checked_before_the_library_sees_them(small_cases):
+    # The C ABI takes plain pointers and reads or writes exactly the level's
+    # coefficient count: the binding rejects a buffer of the wrong size,
+    # dtype, device or layout (a buffer the library writes must be contiguous
+    # itself) before any call, and the context stays usable.
+    prob, f, m, c = small_cases["ct_3d_ragged"]
+    e = engine_for(prob, f, m)
+    ct = torch.from_numpy(c).cuda()
+    n = ct.numel()
+    D_ref, g_ref = e.value_and_grad(ct)
+    f32, f64 = torch.float32, torch.float64
+    short = torch.zeros(n - 1, device="cuda")
+    strided = torch.zeros(2 * n, device="cuda")[::2]
+    D_dev = torch.zeros((), dtype=f64, device="cuda")
+    g_dev = torch.zeros(n, device="cuda")
+    cases = [
+        (TypeError, lambda: e.value(ct.cpu())),
+        (TypeError, lambda: e.value(ct.double())),
+        (ValueError, lambda: e.value(short)),
+        (ValueError, lambda: e.value_and_grad(ct, out=short)),
+        (TypeError, lambda: e.value_and_grad(ct, out=torch.zeros(n, dtype=f64, device="cuda"))),
+        (ValueError, lambda: e.value_and_grad(ct, out=strided)),
+        (ValueError, lambda: e.value_and_grad_async(strided, D_dev, g_dev)),
+        (TypeError, lambda: e.value_and_grad_async(ct, torch.zeros((), dtype=f32, device="cuda"),
+                                                   g_dev)),
+        (ValueError, lambda: e.value_and_grad_async(ct, D_dev, short)),
+        (ValueError, lambda: e.value_and_grad_host(np.zeros(n - 1, np.float32),
+                                                   np.zeros(n, np.float32))),
+        (TypeError, lambda: e.value_and_grad_host(c.ravel().astype(np.float32),
+                                                  np.zeros(n, np.float64))),
+        (ValueError, lambda: e.value_and_grad_host(c.ravel().astype(np.float32),
+                                                   np.zeros(2 * n, np.float32)[::2])),
+        (ValueError, lambda: e.value_and_grad_host(c.ravel().astype(np.float32),
+                                                   _read_only(n))),
+        (TypeError, lambda: e.forward(ct, torch.zeros((), dtype=f32, device="cuda"))),
+        (TypeError, lambda: e.backward(ct, torch.ones(1, dtype=f64, device="cuda"), g_dev)),
+        (ValueError, lambda: e.backward(ct, None, short)),
+        (ValueError, lambda: e.bending_energy(ct, grad_into=short)),
+        (ValueError, lambda: e.lbfgs_direction(g_dev, torch.zeros(2, n, device="cuda"),
+                                               torch.zeros(2, n + 1, device="cuda"))),
+        (ValueError, lambda: e.register(strided, 1)),
+    ]
+    for exc, call in cases:
+        with pytest.raises(exc):
+            call()
+        torch.cuda.synchronize()
+    D, g = e.value_and_grad(ct)
+    assert D == D_ref
+    assert float((g - g_ref).abs().max()) <= 1e-5 * float(g_ref.abs().max())
+    # A non-contiguous input is passed as a contiguous copy where the library
+    # only reads it.
+    assert e.value(strided.copy_(ct.view(-1))) == D_ref
+
+
+def _read_only(n):
+    a = np.zeros(n, np.float32)
+    a.setflags(write=False)
+    return a
+
+
 # ---------------------------------------------------------------------------
 # Full-size workloads
 # ---------------------------------------------------------------------------
