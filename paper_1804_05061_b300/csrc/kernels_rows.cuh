@@ -1186,19 +1186,24 @@ __device__ __forceinline__ void adj_rows_body(const Geo& g, const AdjArgs& args,
   }
 }
 
-// One problem: one CTA per tile.
+// One problem: one CTA per tile.  order[b] (NULL: b) is the tile of CTA b:
+// blocks start roughly in index order, so listing the costly tiles first
+// leaves the cheap ones for the end of the launch, where they fill the SMs
+// that the last costly tiles leave idle.
 template <int DIM, typename T, int NXB, bool SKIP>
 __global__ void __launch_bounds__(kAccWarps * 32, 2)
-k_accumulate_rows(const Geo g, const AccArgs args) {
+k_accumulate_rows(const Geo g, const AccArgs args, const int* __restrict__ order) {
   extern __shared__ __align__(16) unsigned long long smem_acc[];
-  acc_rows_body<DIM, T, NXB, SKIP>(g, args, blockIdx.x, smem_acc);
+  const int tile = order ? __ldg(order + blockIdx.x) : (int)blockIdx.x;
+  acc_rows_body<DIM, T, NXB, SKIP>(g, args, tile, smem_acc);
 }
 
 template <int DIM, typename T, int NXB>
 __global__ void __launch_bounds__(kAdjWarps * 32, 4)
-k_adjoint_rows(const Geo g, const AdjArgs args) {
+k_adjoint_rows(const Geo g, const AdjArgs args, const int* __restrict__ order) {
   extern __shared__ __align__(16) float smem_adj[];
-  adj_rows_body<DIM, T, NXB>(g, args, blockIdx.x, smem_adj);
+  const int tile = order ? __ldg(order + blockIdx.x) : (int)blockIdx.x;
+  adj_rows_body<DIM, T, NXB>(g, args, tile, smem_adj);
 }
 
 // Region tables contracted over z for every image plane z.  Output layout:

@@ -106,6 +106,8 @@ struct Level {
   float4* bg = nullptr;               // per voxel (B, dM/dy) of the last kept warp
   unsigned char* rowdist = nullptr;   // per 32-voxel row: static distance to nonzero M (capped)
   unsigned char* rowlive = nullptr;   // per row: nonzero dM/dy at the last kept warp
+  std::vector<unsigned char> rowdist_host;   // host copy of rowdist (tile order)
+  int* order = nullptr;               // row kernels: tile of each CTA, costly first (or NULL)
   float* uvxz = nullptr;              // U, V, X contracted over z per image plane
   float2* dyz = nullptr;              // M as A: table differences contracted over z per plane
   int* ubins = nullptr;               // fixed-image bins present in the image (any tile)
@@ -322,11 +324,11 @@ AdjArgs adj_args(const Level& lv, const float* c, const float* gD, float* g, boo
 template <int DIM, typename T, bool SKIP>
 void launch_rows_acc_s(srwcr_ctx* ctx, Level& lv, const AccArgs& a, int nblk) {
   if (lv.nxb_rows == 4)
-    k_accumulate_rows<DIM, T, 4, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
+    k_accumulate_rows<DIM, T, 4, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a, lv.order);
   else if (lv.nxb_rows == 8)
-    k_accumulate_rows<DIM, T, 8, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
+    k_accumulate_rows<DIM, T, 8, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a, lv.order);
   else
-    k_accumulate_rows<DIM, T, 12, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a);
+    k_accumulate_rows<DIM, T, 12, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a, lv.order);
 }
 
 // Levels without the per-row records run the kernel with the per-row tests
@@ -343,11 +345,11 @@ void launch_rows_adj(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD,
                      int nblk, bool kept) {
   const AdjArgs a = adj_args(lv, c, gD, g, kept);
   if (lv.nxb_rows == 4)
-    k_adjoint_rows<DIM, T, 4><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a);
+    k_adjoint_rows<DIM, T, 4><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a, lv.order);
   else if (lv.nxb_rows == 8)
-    k_adjoint_rows<DIM, T, 8><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a);
+    k_adjoint_rows<DIM, T, 8><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a, lv.order);
   else
-    k_adjoint_rows<DIM, T, 12><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a);
+    k_adjoint_rows<DIM, T, 12><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a, lv.order);
 }
 
 AccArgsA acc_args_a(const Level& lv, const float* c, bool keep_warp) {
@@ -867,7 +869,7 @@ srwcr_status finish_sync(srwcr_ctx* ctx, Level& lv, double* D_host) {
 void free_level(Level& lv) {
   void* ptrs[] = {lv.A, lv.M, lv.S, lv.P, lv.U, lv.V, lv.X, lv.Dr, lv.stats, lv.D, lv.ndeg, lv.perm,
                   lv.binmask, lv.Wr, lv.nz_ptr, lv.nz_bin, lv.nz_inv_p, lv.bg, lv.uvxz,
-                  lv.ubins, lv.Y2, lv.DY, lv.rowdist, lv.rowlive, lv.dyz};
+                  lv.ubins, lv.Y2, lv.DY, lv.rowdist, lv.rowlive, lv.dyz, lv.order};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   lv = Level();
@@ -941,6 +943,48 @@ srwcr_status select_rows_path_mas_a(srwcr_ctx* ctx, Level& lv, const int* force_
     if (!lv.dyz) CK(cudaMalloc((void**)&lv.dyz, sizeof(float2) * zcontract_dy_len(g)));
     return SRWCR_OK;
   }
+  return SRWCR_OK;
+}
+
+// Rows within this L-infinity distance of a nonzero moving-image voxel count
+// toward a tile's cost in the launch order below.
+constexpr unsigned char kOrderDist = 8;
+
+// Launch order of the row kernels' tiles (moving image as B, levels with the
+// per-row distances): a tile's cost is its number of rows within kOrderDist
+// of a nonzero moving-image voxel (the rows the value pass visits at
+// moderate displacements; the adjoint visits the subset with a nonzero
+// moving-image gradient), the tiles go out costly first (longest-first
+// scheduling, so the launch ends on cheap tiles) in 16 cost classes, and
+// tiles of one class keep their index order (neighbouring tiles, which read
+// nearby moving-image voxels, still run close together in time).
+srwcr_status build_tile_order(srwcr_ctx* ctx, Level& lv) {
+  if (lv.order) cudaFree(lv.order);
+  lv.order = nullptr;
+  if (!lv.rows || !lv.rowdist || lv.rowdist_host.empty() || ctx->cfg.role != SRWCR_ROLE_M_AS_B)
+    return SRWCR_OK;
+  const Geo& g = lv.g;
+  const int nt0 = g.ntile[0], nt1 = g.ntile[1], nt2 = g.ntile[2];
+  const int ntiles = nt0 * nt1 * nt2;
+  const int nxb = (g.n[0] + 31) / 32;           // tile[0] == 32: tile column tx is row block tx
+  std::vector<int> cost(ntiles, 0);
+  for (int t = 0; t < ntiles; ++t) {
+    const int tx = t % nt0, ty = (t / nt0) % nt1, tz = t / (nt0 * nt1);
+    const int y1 = std::min(g.n[1], (ty + 1) * g.tile[1]), z1 = std::min(g.n[2], (tz + 1) * g.tile[2]);
+    int c = 0;
+    for (int z = tz * g.tile[2]; z < z1; ++z)
+      for (int y = ty * g.tile[1]; y < y1; ++y)
+        c += lv.rowdist_host[((size_t)z * g.n[1] + y) * nxb + tx] <= kOrderDist;
+    cost[t] = c;
+  }
+  const long long cmax = *std::max_element(cost.begin(), cost.end());
+  std::vector<int> order(ntiles);
+  for (int t = 0; t < ntiles; ++t) order[t] = t;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return cost[a] * 16LL / (cmax + 1) > cost[b] * 16LL / (cmax + 1);
+  });
+  CK(cudaMalloc((void**)&lv.order, sizeof(int) * ntiles));
+  CK(cudaMemcpy(lv.order, order.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice));
   return SRWCR_OK;
 }
 
@@ -1025,7 +1069,7 @@ srwcr_status select_rows_path(srwcr_ctx* ctx, Level& lv, const int* force_tile =
     if (is_bf16(ctx)) k_row_perm<__nv_bfloat16><<<1024, 256, 0, ctx->stream>>>(g, (const __nv_bfloat16*)lv.A, lv.perm);
     else k_row_perm<float><<<1024, 256, 0, ctx->stream>>>(g, (const float*)lv.A, lv.perm);
     CKL();
-    return SRWCR_OK;
+    return build_tile_order(ctx, lv);   // a no-op before the row distances exist
   }
   return SRWCR_OK;
 }
@@ -1069,8 +1113,10 @@ srwcr_status build_row_dist(srwcr_ctx* ctx, Level& lv) {
     cudaFree(lv.rowlive);
     lv.rowdist = nullptr;
     lv.rowlive = nullptr;
+    return SRWCR_OK;
   }
-  return SRWCR_OK;
+  lv.rowdist_host = std::move(hd);
+  return build_tile_order(ctx, lv);
 }
 
 void free_bend(srwcr_ctx* ctx);  // bending.cuh
@@ -1934,8 +1980,10 @@ void tune_store(const std::string& key, const std::array<int, 3>& t) {
 void release_rows(Level& lv) {
   if (lv.perm) cudaFree(lv.perm);
   if (lv.binmask) cudaFree(lv.binmask);
+  if (lv.order) cudaFree(lv.order);
   lv.perm = nullptr;
   lv.binmask = nullptr;
+  lv.order = nullptr;
   lv.rows = false;
   lv.g = lv.gv;
 }
