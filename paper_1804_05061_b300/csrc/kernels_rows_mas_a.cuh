@@ -573,16 +573,18 @@ __device__ __forceinline__ void adj_rows_mas_a_body(const Geo& g, const AdjArgsA
 
 template <int DIM, typename T, int NXB>
 __global__ void __launch_bounds__(kAccWarps * 32, 2)
-k_accumulate_rows_mas_a(const Geo g, const AccArgsA args) {
+k_accumulate_rows_mas_a(const Geo g, const AccArgsA args, const int* __restrict__ order) {
   extern __shared__ __align__(16) unsigned long long smem_acc_a[];
-  acc_rows_mas_a_body<DIM, T, NXB>(g, args, blockIdx.x, smem_acc_a);
+  const int tile = order ? __ldg(order + blockIdx.x) : (int)blockIdx.x;   // as k_accumulate_rows
+  acc_rows_mas_a_body<DIM, T, NXB>(g, args, tile, smem_acc_a);
 }
 
 template <int DIM, typename T, int NXB>
 __global__ void __launch_bounds__(kAdjWarps * 32, 4)
-k_adjoint_rows_mas_a(const Geo g, const AdjArgsA args) {
+k_adjoint_rows_mas_a(const Geo g, const AdjArgsA args, const int* __restrict__ order) {
   extern __shared__ __align__(16) float smem_adj_a[];
-  adj_rows_mas_a_body<DIM, T, NXB>(g, args, blockIdx.x, smem_adj_a);
+  const int tile = order ? __ldg(order + blockIdx.x) : (int)blockIdx.x;
+  adj_rows_mas_a_body<DIM, T, NXB>(g, args, tile, smem_adj_a);
 }
 
 }  // namespace srwcr

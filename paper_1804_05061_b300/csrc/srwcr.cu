@@ -364,9 +364,9 @@ template <int DIM, typename T>
 void launch_rows_acc_mas_a(srwcr_ctx* ctx, Level& lv, const float* c, int nblk, bool keep) {
   const AccArgsA a = acc_args_a(lv, c, keep);
   const size_t sm = lv.smem_acc_rows;
-  if (lv.nxb_rows == 4) k_accumulate_rows_mas_a<DIM, T, 4><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a);
-  else if (lv.nxb_rows == 8) k_accumulate_rows_mas_a<DIM, T, 8><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a);
-  else k_accumulate_rows_mas_a<DIM, T, 12><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a);
+  if (lv.nxb_rows == 4) k_accumulate_rows_mas_a<DIM, T, 4><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
+  else if (lv.nxb_rows == 8) k_accumulate_rows_mas_a<DIM, T, 8><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
+  else k_accumulate_rows_mas_a<DIM, T, 12><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
 }
 
 template <int DIM, typename T>
@@ -377,9 +377,9 @@ void launch_rows_adj_mas_a(srwcr_ctx* ctx, Level& lv, const float* c, const floa
   a.bg = kept ? lv.bg : nullptr; a.rowlive = kept ? lv.rowlive : nullptr;
   a.invZ = (float)(1.0 / lv.Z); a.grad = g;
   const size_t sm = lv.smem_adj_rows;
-  if (lv.nxb_rows == 4) k_adjoint_rows_mas_a<DIM, T, 4><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a);
-  else if (lv.nxb_rows == 8) k_adjoint_rows_mas_a<DIM, T, 8><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a);
-  else k_adjoint_rows_mas_a<DIM, T, 12><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a);
+  if (lv.nxb_rows == 4) k_adjoint_rows_mas_a<DIM, T, 4><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
+  else if (lv.nxb_rows == 8) k_adjoint_rows_mas_a<DIM, T, 8><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
+  else k_adjoint_rows_mas_a<DIM, T, 12><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
 }
 
 template <typename T>
@@ -912,6 +912,8 @@ bool rows_allowed(const srwcr_config& cfg) {
 // Moving image as A: the largest listed tile whose histogram (every bin)
 // and tables fit in shared memory, with at most 128 rows per plane (an entry
 // takes up to two updates per row, each < 2^48 in two 24-bit words).
+srwcr_status build_tile_order(srwcr_ctx* ctx, Level& lv);
+
 srwcr_status select_rows_path_mas_a(srwcr_ctx* ctx, Level& lv, const int* force_tile) {
   const srwcr_config& cfg = ctx->cfg;
   const int nd = cfg.ndim;
@@ -941,7 +943,7 @@ srwcr_status select_rows_path_mas_a(srwcr_ctx* ctx, Level& lv, const int* force_
     lv.smem_acc_rows = sa;
     lv.smem_adj_rows = sj;
     if (!lv.dyz) CK(cudaMalloc((void**)&lv.dyz, sizeof(float2) * zcontract_dy_len(g)));
-    return SRWCR_OK;
+    return build_tile_order(ctx, lv);   // a no-op before the row distances exist
   }
   return SRWCR_OK;
 }
@@ -950,10 +952,10 @@ srwcr_status select_rows_path_mas_a(srwcr_ctx* ctx, Level& lv, const int* force_
 // toward a tile's cost in the launch order below.
 constexpr unsigned char kOrderDist = 8;
 
-// Launch order of the row kernels' tiles (moving image as B, levels with the
-// per-row distances): a tile's cost is its number of rows within kOrderDist
-// of a nonzero moving-image voxel (the rows the value pass visits at
-// moderate displacements; the adjoint visits the subset with a nonzero
+// Launch order of the row kernels' tiles (levels with the per-row
+// distances): a tile's cost is its number of rows within kOrderDist of a
+// nonzero moving-image voxel (the rows whose warp the value pass computes
+// at moderate displacements; the adjoint visits the subset with a nonzero
 // moving-image gradient), the tiles go out costly first (longest-first
 // scheduling, so the launch ends on cheap tiles) in 16 cost classes, and
 // tiles of one class keep their index order (neighbouring tiles, which read
@@ -961,8 +963,7 @@ constexpr unsigned char kOrderDist = 8;
 srwcr_status build_tile_order(srwcr_ctx* ctx, Level& lv) {
   if (lv.order) cudaFree(lv.order);
   lv.order = nullptr;
-  if (!lv.rows || !lv.rowdist || lv.rowdist_host.empty() || ctx->cfg.role != SRWCR_ROLE_M_AS_B)
-    return SRWCR_OK;
+  if (!lv.rows || !lv.rowdist || lv.rowdist_host.empty()) return SRWCR_OK;
   const Geo& g = lv.g;
   const int nt0 = g.ntile[0], nt1 = g.ntile[1], nt2 = g.ntile[2];
   const int ntiles = nt0 * nt1 * nt2;
