@@ -108,6 +108,7 @@ struct Level {
   unsigned char* rowlive = nullptr;   // per row: nonzero dM/dy at the last kept warp
   std::vector<unsigned char> rowdist_host;   // host copy of rowdist (tile order)
   int* order = nullptr;               // row kernels: tile of each CTA, costly first (or NULL)
+  int order_len = 0;                  // tiles in order (a launch of another size ignores it)
   float* uvxz = nullptr;              // U, V, X contracted over z per image plane
   float2* dyz = nullptr;              // M as A: table differences contracted over z per plane
   int* ubins = nullptr;               // fixed-image bins present in the image (any tile)
@@ -321,14 +322,21 @@ AdjArgs adj_args(const Level& lv, const float* c, const float* gD, float* g, boo
   return a;
 }
 
+// The level's tile order if it was built for a launch of nblk tiles (the
+// kernels read order[blockIdx.x]), else NULL: index order.
+const int* tile_order(const Level& lv, int nblk) {
+  return lv.order && lv.order_len == nblk ? lv.order : nullptr;
+}
+
 template <int DIM, typename T, bool SKIP>
 void launch_rows_acc_s(srwcr_ctx* ctx, Level& lv, const AccArgs& a, int nblk) {
+  const int* ord = tile_order(lv, nblk);
   if (lv.nxb_rows == 4)
-    k_accumulate_rows<DIM, T, 4, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a, lv.order);
+    k_accumulate_rows<DIM, T, 4, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a, ord);
   else if (lv.nxb_rows == 8)
-    k_accumulate_rows<DIM, T, 8, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a, lv.order);
+    k_accumulate_rows<DIM, T, 8, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a, ord);
   else
-    k_accumulate_rows<DIM, T, 12, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a, lv.order);
+    k_accumulate_rows<DIM, T, 12, SKIP><<<nblk, kAccWarps * 32, lv.smem_acc_rows, ctx->stream>>>(lv.g, a, ord);
 }
 
 // Levels without the per-row records run the kernel with the per-row tests
@@ -344,12 +352,13 @@ template <int DIM, typename T>
 void launch_rows_adj(srwcr_ctx* ctx, Level& lv, const float* c, const float* gD, float* g,
                      int nblk, bool kept) {
   const AdjArgs a = adj_args(lv, c, gD, g, kept);
+  const int* ord = tile_order(lv, nblk);
   if (lv.nxb_rows == 4)
-    k_adjoint_rows<DIM, T, 4><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a, lv.order);
+    k_adjoint_rows<DIM, T, 4><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a, ord);
   else if (lv.nxb_rows == 8)
-    k_adjoint_rows<DIM, T, 8><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a, lv.order);
+    k_adjoint_rows<DIM, T, 8><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a, ord);
   else
-    k_adjoint_rows<DIM, T, 12><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a, lv.order);
+    k_adjoint_rows<DIM, T, 12><<<nblk, kAdjWarps * 32, lv.smem_adj_rows, ctx->stream>>>(lv.g, a, ord);
 }
 
 AccArgsA acc_args_a(const Level& lv, const float* c, bool keep_warp) {
@@ -363,10 +372,11 @@ AccArgsA acc_args_a(const Level& lv, const float* c, bool keep_warp) {
 template <int DIM, typename T>
 void launch_rows_acc_mas_a(srwcr_ctx* ctx, Level& lv, const float* c, int nblk, bool keep) {
   const AccArgsA a = acc_args_a(lv, c, keep);
+  const int* ord = tile_order(lv, nblk);
   const size_t sm = lv.smem_acc_rows;
-  if (lv.nxb_rows == 4) k_accumulate_rows_mas_a<DIM, T, 4><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
-  else if (lv.nxb_rows == 8) k_accumulate_rows_mas_a<DIM, T, 8><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
-  else k_accumulate_rows_mas_a<DIM, T, 12><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
+  if (lv.nxb_rows == 4) k_accumulate_rows_mas_a<DIM, T, 4><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a, ord);
+  else if (lv.nxb_rows == 8) k_accumulate_rows_mas_a<DIM, T, 8><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a, ord);
+  else k_accumulate_rows_mas_a<DIM, T, 12><<<nblk, kAccWarps * 32, sm, ctx->stream>>>(lv.g, a, ord);
 }
 
 template <int DIM, typename T>
@@ -376,10 +386,11 @@ void launch_rows_adj_mas_a(srwcr_ctx* ctx, Level& lv, const float* c, const floa
   a.F = lv.A; a.M = lv.M; a.c = c; a.dyz = lv.dyz; a.gscale = gD;
   a.bg = kept ? lv.bg : nullptr; a.rowlive = kept ? lv.rowlive : nullptr;
   a.invZ = (float)(1.0 / lv.Z); a.grad = g;
+  const int* ord = tile_order(lv, nblk);
   const size_t sm = lv.smem_adj_rows;
-  if (lv.nxb_rows == 4) k_adjoint_rows_mas_a<DIM, T, 4><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
-  else if (lv.nxb_rows == 8) k_adjoint_rows_mas_a<DIM, T, 8><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
-  else k_adjoint_rows_mas_a<DIM, T, 12><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a, lv.order);
+  if (lv.nxb_rows == 4) k_adjoint_rows_mas_a<DIM, T, 4><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a, ord);
+  else if (lv.nxb_rows == 8) k_adjoint_rows_mas_a<DIM, T, 8><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a, ord);
+  else k_adjoint_rows_mas_a<DIM, T, 12><<<nblk, kAdjWarps * 32, sm, ctx->stream>>>(lv.g, a, ord);
 }
 
 template <typename T>
@@ -963,6 +974,7 @@ constexpr unsigned char kOrderDist = 8;
 srwcr_status build_tile_order(srwcr_ctx* ctx, Level& lv) {
   if (lv.order) cudaFree(lv.order);
   lv.order = nullptr;
+  lv.order_len = 0;
   if (!lv.rows || !lv.rowdist || lv.rowdist_host.empty()) return SRWCR_OK;
   const Geo& g = lv.g;
   const int nt0 = g.ntile[0], nt1 = g.ntile[1], nt2 = g.ntile[2];
@@ -986,6 +998,7 @@ srwcr_status build_tile_order(srwcr_ctx* ctx, Level& lv) {
   });
   CK(cudaMalloc((void**)&lv.order, sizeof(int) * ntiles));
   CK(cudaMemcpy(lv.order, order.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice));
+  lv.order_len = ntiles;
   return SRWCR_OK;
 }
 
@@ -1985,6 +1998,7 @@ void release_rows(Level& lv) {
   lv.perm = nullptr;
   lv.binmask = nullptr;
   lv.order = nullptr;
+  lv.order_len = 0;
   lv.rows = false;
   lv.g = lv.gv;
 }
