@@ -54,8 +54,9 @@ enum { SRWCR_STORAGE_F32 = 0, SRWCR_STORAGE_BF16 = 1 };
 /* Which image is binned (Sec. II-E).  M as B (default): the fixed image F is
  * the model image A and the warped moving image the estimated image B
  * (gradient Eq. 19).  M as A: the warped moving image is A, binned by
- * Eq. (5), and F is B (gradient Eq. 21); runs on the general per-voxel
- * kernels. */
+ * Eq. (5), and F is B (gradient Eq. 21).  Either role runs on the
+ * row-parallel kernels where the level's geometry allows them, else on the
+ * general per-voxel kernels (srwcr_level_desc.kernel_path). */
 enum { SRWCR_ROLE_M_AS_B = 0, SRWCR_ROLE_M_AS_A = 1 };
 
 /* Spatial distribution w(r, x) of Eq. (3).  B-spline (default): the cubic
@@ -227,6 +228,26 @@ srwcr_status srwcr_level_images(srwcr_ctx* ctx, int level, float* fixed_dev, flo
 srwcr_status srwcr_debug_fixed_point(const float* v_dev, int64_t n, const uint32_t* hi_dev,
                                      const uint32_t* lo_dev, int64_t m, uint64_t* fixed_dev,
                                      float* float_dev, int reference);
+
+/* Launch order of the row kernels' tiles, computed on the host (no device
+ * work; the library builds it once per tile choice for every level that
+ * keeps the static row distances).  A launch ends on its cheap tiles when
+ * the costly ones go first (longest-first scheduling).
+ * rowdist_host: one byte per 32-voxel x-row segment, laid out [z][y][x block]
+ * with ceil(dims[0] / 32) blocks per row: the L-infinity distance from the
+ * segment to the nearest nonzero moving-image voxel, capped at 255.
+ * dims: voxels per axis (x, y, z; 1 for the z axis of a 2-D image).  tile:
+ * 32 x tile[1] x tile[2] voxels.  Tiles are numbered x block fastest, then
+ * y, then z, as the row kernels number their CTAs; there are
+ * ntiles = ceil(dims[0] / 32) * ceil(dims[1] / tile[1]) * ceil(dims[2] / tile[2]).
+ * order_out (ntiles ints) receives the tiles in launch order, cost_out (may
+ * be NULL, ntiles ints) each tile's cost.  A tile's cost is its number of
+ * segments at distance <= 8.  Tiles are ordered by cost class
+ * (cost * 16 / (max cost + 1)), classes in decreasing order, tiles of one
+ * class in increasing index.  Errors: SRWCR_EINVAL for a NULL array, a size
+ * out of range or tile[0] != 32. */
+srwcr_status srwcr_tile_order(const unsigned char* rowdist_host, const int* dims, const int* tile,
+                              int* order_out, int* cost_out);
 
 /* Benchmark hooks.  With profiling enabled the library brackets each of its
  * kernels with CUDA events on the context's stream.  srwcr_profile_read

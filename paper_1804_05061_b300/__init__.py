@@ -38,7 +38,7 @@ EXPORTS = ("srwcr_create", "srwcr_destroy", "srwcr_last_error", "srwcr_level_inf
            "srwcr_batch_sync", "srwcr_batch_register", "srwcr_bending_energy",
            "srwcr_rigid_value_and_grad", "srwcr_rigid_to_ffd", "srwcr_rigid_register",
            "srwcr_debug_warp_grad", "srwcr_level_images", "srwcr_refine",
-           "srwcr_lbfgs_direction", "srwcr_debug_fixed_point")
+           "srwcr_lbfgs_direction", "srwcr_debug_fixed_point", "srwcr_tile_order")
 
 
 class SrwcrError(RuntimeError):
@@ -126,6 +126,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "srwcr_lbfgs_direction": (st, [vp, ctypes.c_int64, ctypes.c_int, vp, vp, vp, vp]),
         "srwcr_debug_fixed_point": (st, [vp, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, vp,
                                          ctypes.c_int]),
+        "srwcr_tile_order": (st, [vp, vp, vp, vp, vp]),
         "srwcr_lbfgs_default_opts": (None, [ctypes.POINTER(LbfgsOpts)]),
         "srwcr_set_profiling": (st, [vp, ctypes.c_int]),
         "srwcr_profile_read": (st, [vp, vp, vp, i64p, ctypes.c_int]),
@@ -683,3 +684,25 @@ def debug_fixed_point(v, hi, lo, reference: bool = False):
     _check(load().srwcr_debug_fixed_point(_ptr(v), v.numel(), _ptr(hi), _ptr(lo), hi.numel(),
                                           _ptr(fixed), _ptr(flt), int(bool(reference))))
     return fixed, flt
+
+
+def tile_order(rowdist, dims, tile):
+    """The row kernels' tile launch order, computed on the host
+    (srwcr_tile_order): rowdist holds one byte per 32-voxel x-row segment,
+    [z][y][x block]; dims = (nx, ny[, nz]), tile = (32, ty[, tz]).  Returns
+    (order, cost) as int32 arrays over the tiles."""
+    rowdist = np.ascontiguousarray(rowdist, dtype=np.uint8)
+    d = [int(v) for v in dims] + [1] * (3 - len(dims))
+    t = [int(v) for v in tile] + [1] * (3 - len(tile))
+    if min(d) < 1 or min(t) < 1:
+        raise ValueError("dims and tile must be positive")
+    nxb = (d[0] + 31) // 32
+    if rowdist.size != nxb * d[1] * d[2]:
+        raise ValueError(f"rowdist has {rowdist.size} entries, dims need {nxb * d[1] * d[2]}")
+    nt = nxb * (-(-d[1] // t[1])) * (-(-d[2] // t[2]))
+    order = np.empty(nt, np.int32)
+    cost = np.empty(nt, np.int32)
+    _check(load().srwcr_tile_order(rowdist.ctypes.data_as(ctypes.c_void_p), (ctypes.c_int * 3)(*d),
+                                   (ctypes.c_int * 3)(*t), order.ctypes.data_as(ctypes.c_void_p),
+                                   cost.ctypes.data_as(ctypes.c_void_p)))
+    return order, cost

@@ -963,39 +963,55 @@ srwcr_status select_rows_path_mas_a(srwcr_ctx* ctx, Level& lv, const int* force_
 // toward a tile's cost in the launch order below.
 constexpr unsigned char kOrderDist = 8;
 
-// Launch order of the row kernels' tiles (levels with the per-row
-// distances): a tile's cost is its number of rows within kOrderDist of a
-// nonzero moving-image voxel (the rows whose warp the value pass computes
-// at moderate displacements; the adjoint visits the subset with a nonzero
+// Launch order of the row kernels' tiles, on the host (see srwcr_tile_order):
+// a tile's cost is its number of rows within kOrderDist of a nonzero
+// moving-image voxel (the rows whose warp the value pass computes at
+// moderate displacements; the adjoint visits the subset with a nonzero
 // moving-image gradient), the tiles go out costly first (longest-first
 // scheduling, so the launch ends on cheap tiles) in 16 cost classes, and
 // tiles of one class keep their index order (neighbouring tiles, which read
-// nearby moving-image voxels, still run close together in time).
+// nearby moving-image voxels, still run close together in time).  n: voxels
+// per axis (1 for an absent axis); tile: 32 x tile[1] x tile[2]; rowdist:
+// [z][y][x block] with ceil(n[0] / 32) blocks per row; tiles numbered x
+// block fastest, then y, then z, as the kernels number their CTAs.
+void tile_order_host(const unsigned char* rowdist, const int n[3], const int tile[3],
+                     std::vector<int>* order, std::vector<int>* cost) {
+  const int nt0 = (n[0] + 31) / 32, nt1 = (n[1] + tile[1] - 1) / tile[1];
+  const int nt2 = (n[2] + tile[2] - 1) / tile[2];
+  const int ntiles = nt0 * nt1 * nt2;
+  cost->assign(ntiles, 0);
+  for (int t = 0; t < ntiles; ++t) {
+    const int tx = t % nt0, ty = (t / nt0) % nt1, tz = t / (nt0 * nt1);
+    const int y1 = std::min(n[1], (ty + 1) * tile[1]), z1 = std::min(n[2], (tz + 1) * tile[2]);
+    int c = 0;
+    for (int z = tz * tile[2]; z < z1; ++z)
+      for (int y = ty * tile[1]; y < y1; ++y)
+        c += rowdist[((size_t)z * n[1] + y) * nt0 + tx] <= kOrderDist;
+    (*cost)[t] = c;
+  }
+  const long long cmax = *std::max_element(cost->begin(), cost->end());
+  const std::vector<int>& cs = *cost;
+  order->resize(ntiles);
+  for (int t = 0; t < ntiles; ++t) (*order)[t] = t;
+  std::stable_sort(order->begin(), order->end(), [&](int a, int b) {
+    return cs[a] * 16LL / (cmax + 1) > cs[b] * 16LL / (cmax + 1);
+  });
+}
+
+// The level's tile order on the device (levels with the per-row distances;
+// others launch in index order).
 srwcr_status build_tile_order(srwcr_ctx* ctx, Level& lv) {
+  (void)ctx;
   if (lv.order) cudaFree(lv.order);
   lv.order = nullptr;
   lv.order_len = 0;
   if (!lv.rows || !lv.rowdist || lv.rowdist_host.empty()) return SRWCR_OK;
-  const Geo& g = lv.g;
-  const int nt0 = g.ntile[0], nt1 = g.ntile[1], nt2 = g.ntile[2];
-  const int ntiles = nt0 * nt1 * nt2;
-  const int nxb = (g.n[0] + 31) / 32;           // tile[0] == 32: tile column tx is row block tx
-  std::vector<int> cost(ntiles, 0);
-  for (int t = 0; t < ntiles; ++t) {
-    const int tx = t % nt0, ty = (t / nt0) % nt1, tz = t / (nt0 * nt1);
-    const int y1 = std::min(g.n[1], (ty + 1) * g.tile[1]), z1 = std::min(g.n[2], (tz + 1) * g.tile[2]);
-    int c = 0;
-    for (int z = tz * g.tile[2]; z < z1; ++z)
-      for (int y = ty * g.tile[1]; y < y1; ++y)
-        c += lv.rowdist_host[((size_t)z * g.n[1] + y) * nxb + tx] <= kOrderDist;
-    cost[t] = c;
-  }
-  const long long cmax = *std::max_element(cost.begin(), cost.end());
-  std::vector<int> order(ntiles);
-  for (int t = 0; t < ntiles; ++t) order[t] = t;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return cost[a] * 16LL / (cmax + 1) > cost[b] * 16LL / (cmax + 1);
-  });
+  std::vector<int> order, cost;
+  tile_order_host(lv.rowdist_host.data(), lv.g.n, lv.g.tile, &order, &cost);
+  const int ntiles = (int)order.size();
+  if (ntiles != lv.g.ntile[0] * lv.g.ntile[1] * lv.g.ntile[2])
+    return fail(SRWCR_EINVAL, "tile order: %d tiles against %d (internal)", ntiles,
+                lv.g.ntile[0] * lv.g.ntile[1] * lv.g.ntile[2]);
   CK(cudaMalloc((void**)&lv.order, sizeof(int) * ntiles));
   CK(cudaMemcpy(lv.order, order.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice));
   lv.order_len = ntiles;
@@ -1754,6 +1770,19 @@ srwcr_status srwcr_debug_fixed_point(const float* v_dev, int64_t n, const uint32
                               reinterpret_cast<unsigned long long*>(fixed_dev), float_dev, reference);
   CKL();
   CK(cudaDeviceSynchronize());
+  return SRWCR_OK;
+}
+
+srwcr_status srwcr_tile_order(const unsigned char* rowdist_host, const int* dims, const int* tile,
+                              int* order_out, int* cost_out) {
+  if (!rowdist_host || !dims || !tile || !order_out) return fail(SRWCR_EINVAL, "null host pointer");
+  for (int d = 0; d < 3; ++d)
+    if (dims[d] < 1 || dims[d] > 65535 || tile[d] < 1) return fail(SRWCR_EINVAL, "dims or tile out of range");
+  if (tile[0] != 32) return fail(SRWCR_EINVAL, "tile[0] must be 32");
+  std::vector<int> order, cost;
+  tile_order_host(rowdist_host, dims, tile, &order, &cost);
+  std::copy(order.begin(), order.end(), order_out);
+  if (cost_out) std::copy(cost.begin(), cost.end(), cost_out);
   return SRWCR_OK;
 }
 
