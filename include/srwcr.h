@@ -245,7 +245,7 @@ srwcr_status srwcr_debug_fixed_point(const float* v_dev, int64_t n, const uint32
  * segments at distance <= 8.  Tiles are ordered by cost class
  * (cost * 16 / (max cost + 1)), classes in decreasing order, tiles of one
  * class in increasing index.  Errors: SRWCR_EINVAL for a NULL array, a size
- * out of range or tile[0] != 32. */
+ * out of range (more than 2^31 - 1 row segments included) or tile[0] != 32. */
 srwcr_status srwcr_tile_order(const unsigned char* rowdist_host, const int* dims, const int* tile,
                               int* order_out, int* cost_out);
 

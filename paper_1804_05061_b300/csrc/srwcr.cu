@@ -1779,6 +1779,8 @@ srwcr_status srwcr_tile_order(const unsigned char* rowdist_host, const int* dims
   for (int d = 0; d < 3; ++d)
     if (dims[d] < 1 || dims[d] > 65535 || tile[d] < 1) return fail(SRWCR_EINVAL, "dims or tile out of range");
   if (tile[0] != 32) return fail(SRWCR_EINVAL, "tile[0] must be 32");
+  if ((long long)((dims[0] + 31) / 32) * dims[1] * dims[2] > INT32_MAX)
+    return fail(SRWCR_EINVAL, "more than 2^31 - 1 row segments");
   std::vector<int> order, cost;
   tile_order_host(rowdist_host, dims, tile, &order, &cost);
   std::copy(order.begin(), order.end(), order_out);
