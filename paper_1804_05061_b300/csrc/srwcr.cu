@@ -860,6 +860,15 @@ __global__ void k_stage_checked(const float* src, float* __restrict__ dst, long 
   if (bad) *reinterpret_cast<volatile int*>(flag) = 1;
 }
 
+// Copies n floats from device memory into page-locked host memory through
+// its device mapping (coalesced stores over the bus): the gradient of a
+// host-buffer call, without a copy-engine transfer.
+__global__ void k_copy_to_mapped(const float* __restrict__ src, float* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
 srwcr_status check_finite_async(srwcr_ctx* ctx, const float* c, long long n) {
   CK(cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int), ctx->stream));
   k_check_finite<<<(int)std::min<long long>(1024, (n + 255) / 256), 256, 0, ctx->stream>>>(c, n, ctx->flag_dev);
@@ -1563,8 +1572,9 @@ bool host_page_locked(const void* p, size_t n) { return host_device_alias(p, n) 
 // gradient, copy g and D out (the caller synchronises).
 // With c_host and the context's flag and D words device-mapped (page-locked
 // buffers), one kernel uploads and checks c and the value's sum stores D
-// into host memory itself, so the call holds one copy (g) instead of four
-// copies and a memset; the host clears the flag before each launch.
+// into host memory itself, and with g_host page-locked too a kernel writes g
+// through its mapping: no copy-engine transfer and no memset instead of
+// four copies and a memset; the host clears the flag before each launch.
 srwcr_status queue_host_call(srwcr_ctx* ctx, Level& lv, int64_t np, const float* c_host,
                              float* g_host) {
   const float* c_map = static_cast<const float*>(host_device_alias(c_host, sizeof(float) * np));
@@ -1574,8 +1584,18 @@ srwcr_status queue_host_call(srwcr_ctx* ctx, Level& lv, int64_t np, const float*
     const int blocks = (int)std::min<int64_t>(4 * 148, (np + 255) / 256);
     k_stage_checked<<<blocks, 256, 0, ctx->stream>>>(c_map, ctx->c_stage, np, flag_map);
     CKL();
+    ctx->launches += 1;
     RET_IF(run_value_and_grad(ctx, lv, ctx->c_stage, ctx->g_stage, D_map));
-    CK(cudaMemcpyAsync(g_host, ctx->g_stage, sizeof(float) * np, cudaMemcpyDeviceToHost, ctx->stream));
+    // A page-locked g_host is written by a kernel through its mapping too
+    // (about 2.5 us per call less than a copy-engine transfer of 220 KB).
+    float* g_map = static_cast<float*>(host_device_alias(g_host, sizeof(float) * np));
+    if (g_map) {
+      k_copy_to_mapped<<<blocks, 256, 0, ctx->stream>>>(ctx->g_stage, g_map, np);
+      CKL();
+      ctx->launches += 1;
+    } else {
+      CK(cudaMemcpyAsync(g_host, ctx->g_stage, sizeof(float) * np, cudaMemcpyDeviceToHost, ctx->stream));
+    }
     return SRWCR_OK;
   }
   CK(cudaMemcpyAsync(ctx->c_stage, c_host, sizeof(float) * np, cudaMemcpyHostToDevice, ctx->stream));
