@@ -235,7 +235,8 @@ srwcr_status srwcr_debug_fixed_point(const float* v_dev, int64_t n, const uint32
  * the costly ones go first (longest-first scheduling).
  * rowdist_host: one byte per 32-voxel x-row segment, laid out [z][y][x block]
  * with ceil(dims[0] / 32) blocks per row: the L-infinity distance from the
- * segment to the nearest nonzero moving-image voxel, capped at 255.
+ * segment to the nearest nonzero moving-image voxel (the library's own maps
+ * cap it at 64; any byte value is accepted).
  * dims: voxels per axis (x, y, z; 1 for the z axis of a 2-D image).  tile:
  * 32 x tile[1] x tile[2] voxels.  Tiles are numbered x block fastest, then
  * y, then z, as the row kernels number their CTAs; there are
